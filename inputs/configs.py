@@ -1,0 +1,167 @@
+"""Workload descriptions: the synthetic stand-ins for the paper's cases.
+
+Each `Case` is plain data: grid, box boundary kinds, geometry kind and
+parameters, physical constants, time step and step count.  The integer codes
+below are the ones the C-ABI header declares (ibm_bc, ibm_geom_kind,
+ibm_bmode, ibm_flow_mode); they are data-format constants, not arithmetic.
+
+Cases (the paper's own runs need data that is not available, so these stand in):
+  * channel_c1  - 2D laminar plane channel, 64x32, walls off-grid at
+                  y=0.137 and y=0.861 imposed by the IBM (Sec. 2.2 / Eq. 3-6 style
+                  steady Laplacian test generalised to Navier-Stokes).
+  * cylinder_c2 - 2D cylinder, D=1, seeded sub-cell centre offset (Sec. 4.1 shape).
+  * wavy_c3     - 3D channel over a sinusoidal lower wall, 384x256x256,
+                  constant flow rate, Re_b=5600 (Sec. 4.2 shape).
+  * small_case  - the same physics at sizes the oracle finishes in seconds,
+                  with ragged tails against 32-wide warps.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+import math
+
+BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW, BC_OUTFLOW = 0, 1, 2, 3, 4
+GEOM_NONE, GEOM_PLANES, GEOM_CYLINDER, GEOM_SPHERE, GEOM_SINE_WALL, GEOM_TUBES, GEOM_SAMPLED = range(7)
+B_EXACT, B_EULER, B_TAYLOR2 = 0, 1, 2
+FLOW_FORCED, FLOW_CONST_FLUX = 0, 1
+
+
+@dataclass
+class Case:
+    name: str
+    ndim: int
+    n: tuple            # (nx, ny, nz); nz == 1 in 2D
+    L: tuple            # box lengths
+    origin: tuple       # box lower corner
+    bc_lo: tuple        # per direction, BC_* codes
+    bc_hi: tuple
+    geom_kind: int
+    geom_params: tuple  # kind-specific, see include/ibm.h
+    nu: float
+    dt: float
+    g: tuple = (0.0, 0.0, 0.0)
+    bmode: int = B_EXACT
+    flow_mode: int = FLOW_FORCED
+    target_flux: float = 0.0   # volume integral of u over the fluid (FLOW_CONST_FLUX)
+    wall_u: tuple = (0.0, 0.0, 0.0)
+    precision: str = "fp64"    # "fp64" or "fp32" (FP32 momentum, FP64 tridiagonal/reductions)
+    steps: int = 1
+    init: dict = field(default_factory=lambda: {"kind": "zero"})
+    seed: int = 0
+
+    @property
+    def ncells(self) -> int:
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def with_(self, **kw) -> "Case":
+        return replace(self, **kw)
+
+
+def channel_c1(precision: str = "fp64", steps: int = 2000) -> Case:
+    """2D plane channel: 64x32 on [0,2]x[0,1], periodic x, IBM walls at y=0.137/0.861.
+
+    Re = 10 on the centreline velocity U_c = 1 and the half height h = 0.362,
+    so nu = 0.0362; the body force g_x = 2 nu / h^2 makes the exact profile
+    u = 1 - ((y - y_c)/h)^2 with y_c = 0.499.
+    """
+    h = 0.362
+    nu = 1.0 * h / 10.0
+    return Case(name="c1_channel_64x32", ndim=2, n=(64, 32, 1), L=(2.0, 1.0, 1.0),
+                origin=(0.0, 0.0, 0.0), bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
+                bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), geom_kind=GEOM_PLANES,
+                geom_params=(0.137, 0.861), nu=nu, dt=0.008, g=(2.0 * nu / h ** 2, 0.0, 0.0),
+                precision=precision, steps=steps, init={"kind": "zero"})
+
+
+def couette_case(nx: int = 16, ny: int = 24, a: float = 0.113, b: float = 0.871,
+                 U: float = 1.0, nu: float = 0.05) -> Case:
+    """Plane Couette flow between an IBM wall at rest (y=a) and one moving at U (y=b)."""
+    return Case(name=f"couette_{nx}x{ny}", ndim=2, n=(nx, ny, 1), L=(1.0, 1.0, 1.0),
+                origin=(0.0, 0.0, 0.0), bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
+                bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), geom_kind=GEOM_PLANES,
+                geom_params=(a, b), nu=nu, dt=0.2 * (1.0 / ny) ** 2 / nu,
+                wall_u=(U, 0.0, 0.0), init={"kind": "couette", "a": a, "b": b, "U": U})
+
+
+def cylinder_c2(re: float = 40.0, precision: str = "fp64", steps: int = 10, seed: int = 0,
+                n=(1536, 768)) -> Case:
+    """2D cylinder D=1 in a 30D x 15D box; centre offset by a seeded fraction of a cell.
+
+    Stand-in reading: x is periodic (the box is long enough for the wake to
+    decay) and the lateral faces are free-slip walls; the stream is driven at
+    a constant flow rate U = 1 by a uniform forcing adjusted every substage.
+    This keeps the Poisson operator separable with the tridiagonal direction
+    along y.  Uniform inflow with convective outflow is not built.
+    """
+    from .generators import cell_offset
+    nx, ny = n
+    Lx, Ly = 30.0, 15.0
+    dx = Lx / nx
+    ox, oy = cell_offset(seed, dx)
+    return Case(name=f"c2_cylinder_{nx}x{ny}_re{int(re)}", ndim=2, n=(nx, ny, 1), L=(Lx, Ly, 1.0),
+                origin=(-10.0, -7.5, 0.0), bc_lo=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC),
+                bc_hi=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC), geom_kind=GEOM_CYLINDER,
+                geom_params=(ox, oy, 0.5, -1.0), nu=1.0 / re, dt=0.004 if re <= 40 else 0.008,
+                flow_mode=FLOW_CONST_FLUX, target_flux=1.0 * (Lx * Ly - math.pi * 0.25),
+                precision=precision, steps=steps, init={"kind": "uniform", "U": 1.0}, seed=seed)
+
+
+def wavy_c3(precision: str = "fp32", steps: int = 10, n=(384, 256, 256), seed: int = 0) -> Case:
+    """3D channel over y_w(x) = 0.1 sin(2 pi x) (A = 0.1h, lambda = h, h = 1).
+
+    Box x in [0,4], y in [-0.125, 1.875], z in [0,2]; periodic x and z; the top
+    box face y = 1.875 is an on-grid no-slip wall.  Constant flow rate with
+    bulk velocity U_b = 1 and Re_b = U_b 2h / nu = 5600.
+    """
+    nx, ny, nz = n
+    nu = 2.0 / 5600.0
+    ylo, ytop = 0.0, 1.875
+    # target volume flux: U_b times the mean fluid cross-section times the box length
+    target = 1.0 * (ytop - ylo) * 4.0 * 2.0
+    return Case(name=f"c3_wavy_{nx}x{ny}x{nz}", ndim=3, n=(nx, ny, nz), L=(4.0, 2.0, 2.0),
+                origin=(0.0, -0.125, 0.0), bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
+                bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), geom_kind=GEOM_SINE_WALL,
+                geom_params=(0.0, 0.1, 1.0, 1.0e30), nu=nu, dt=0.002,
+                flow_mode=FLOW_CONST_FLUX, target_flux=target, precision=precision, steps=steps,
+                init={"kind": "channel_noise", "ylo": ylo, "yhi": ytop, "Ub": 1.0, "noise": 0.05},
+                seed=seed)
+
+
+def pipe_case(N: int = 40, R: float = 1.0, nu: float = 1.0, nz: int = 1) -> Case:
+    """Straight circular pipe along z on a 2.5R square of N x N cells (Sec. 2.3 example)."""
+    L = 2.5 * R
+    return Case(name=f"pipe_{N}", ndim=3, n=(N, N, nz), L=(L, L, 1.0),
+                origin=(-L / 2, -L / 2, 0.0), bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
+                bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), geom_kind=GEOM_CYLINDER,
+                geom_params=(0.0, 0.0, R, 1.0), nu=nu, dt=0.1 * (L / N) ** 2 / nu)
+
+
+def small_case(kind: str, precision: str = "fp64", seed: int = 0) -> Case:
+    """Oracle-sized cases spanning several 32-wide tiles with ragged tails."""
+    if kind == "channel2d":
+        c = channel_c1(precision=precision, steps=3)
+        return c.with_(name="channel2d_70x37", n=(70, 37, 1), dt=0.004, seed=seed,
+                       init={"kind": "channel_noise", "ylo": 0.137, "yhi": 0.861, "Ub": 0.6667,
+                             "noise": 0.05})
+    if kind == "cylinder2d":
+        c = cylinder_c2(re=100.0, precision=precision, steps=2, seed=seed, n=(96, 50))
+        return c.with_(name="cylinder2d_96x50", dt=0.01)
+    if kind == "wavy3d":
+        c = wavy_c3(precision=precision, steps=2, n=(70, 36, 20), seed=seed)
+        return c.with_(name="wavy3d_70x36x20", dt=0.002)
+    if kind == "sphere3d":
+        return Case(name="sphere3d_48x30x26", ndim=3, n=(48, 30, 26), L=(1.6, 1.0, 1.0),
+                    origin=(0.0, 0.0, 0.0), bc_lo=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC),
+                    bc_hi=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC), geom_kind=GEOM_SPHERE,
+                    geom_params=(0.61, 0.47, 0.52, 0.23, -1.0), nu=0.01, dt=0.004,
+                    g=(1.0, 0.0, 0.0), precision=precision, steps=2, seed=seed,
+                    init={"kind": "uniform_noise", "U": 0.5, "noise": 0.1})
+    raise ValueError(kind)
+
+
+def describe(case: Case) -> dict:
+    """A JSON-friendly summary used by the bench line's `config`."""
+    return {"workload": case.name, "cells": case.ncells, "grid": list(case.n[:case.ndim]),
+            "precision": case.precision, "geometry": case.geom_kind, "nu": case.nu,
+            "dt": case.dt, "flow_mode": case.flow_mode}
+

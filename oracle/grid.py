@@ -1,0 +1,82 @@
+"""Staggered Cartesian grid (paper Sec. 2.1, figure `staggered-grid`).
+
+Pressure lives at cell centres and each velocity component on the cell face
+normal to it.  Arrays have shape (nz, ny, nx), x fastest.  Direction d
+(0=x, 1=y, 2=z) maps to numpy axis AX[d].  Cell (i,j,k) has centre
+origin + ((i+1/2)dx, (j+1/2)dy, (k+1/2)dz); component c of index (i,j,k)
+sits on the cell's +c face, i.e. its coordinate along c is origin_c+(idx_c+1)d_c.
+
+Box boundaries: a periodic direction wraps.  In a non-periodic direction d
+the +d box face carries the stored value of index n_d-1 of component d (a
+prescribed "boundary" point, never solved); the -d box face value is implied
+by the boundary condition (zero for the walls supported here).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+AX = {0: 2, 1: 1, 2: 0}
+BC_PERIODIC, BC_NOSLIP, BC_FREESLIP = 0, 1, 2
+
+
+class Grid:
+    def __init__(self, case):
+        self.ndim = int(case.ndim)
+        self.n = tuple(int(v) for v in case.n)
+        self.L = tuple(float(v) for v in case.L)
+        self.origin = tuple(float(v) for v in case.origin)
+        self.bc_lo = tuple(int(v) for v in case.bc_lo)
+        self.bc_hi = tuple(int(v) for v in case.bc_hi)
+        # grid spacing: Delta_d = L_d / n_d
+        self.d = tuple(self.L[i] / self.n[i] for i in range(3))
+        self.shape = (self.n[2], self.n[1], self.n[0])
+        self.ncomp = 3 if self.ndim == 3 else 2
+        if self.ndim == 2 and self.n[2] != 1:
+            raise ValueError("2D grids have nz == 1")
+        for dd in (0, 2):
+            if self.bc_lo[dd] != BC_PERIODIC or self.bc_hi[dd] != BC_PERIODIC:
+                raise NotImplementedError("x and z must be periodic (y carries the walls)")
+        if self.bc_lo[1] not in (BC_NOSLIP, BC_FREESLIP) or self.bc_hi[1] not in (BC_NOSLIP, BC_FREESLIP):
+            raise NotImplementedError("y box faces must be no-slip or free-slip walls")
+        if self.n[1] < 2:
+            raise ValueError("ny >= 2")
+
+    def periodic(self, d: int) -> bool:
+        return self.bc_lo[d] == BC_PERIODIC
+
+    def axis_coords(self, d: int, offset: float) -> np.ndarray:
+        """origin_d + (index + offset) * Delta_d for every index along d."""
+        return self.origin[d] + (np.arange(self.n[d]) + offset) * self.d[d]
+
+    def coords(self, c: int):
+        """Broadcastable (x, y, z) coordinates of the points of component c.
+
+        c = 0,1,2 for u,v,w; c = 3 for cell centres (pressure)."""
+        out = []
+        for d in range(3):
+            off = 1.0 if d == c else 0.5
+            a = self.axis_coords(d, off)
+            shp = [1, 1, 1]
+            shp[AX[d]] = self.n[d]
+            out.append(a.reshape(shp))
+        return out
+
+    def boundary_points(self, c: int) -> np.ndarray:
+        """Mask of prescribed box-face points of component c (normal component on a wall)."""
+        m = np.zeros(self.shape, dtype=bool)
+        if c < 3 and not self.periodic(c):
+            idx = [slice(None)] * 3
+            idx[AX[c]] = self.n[c] - 1
+            m[tuple(idx)] = True
+        return m
+
+    def cell_volume(self) -> float:
+        v = self.d[0] * self.d[1]
+        if self.ndim == 3:
+            v *= self.d[2]
+        return v
+
+    def wall_sign(self, side: str) -> float:
+        """Ghost factor for tangential velocity beyond a y wall: -1 no-slip, +1 free-slip."""
+        bc = self.bc_lo[1] if side == "lo" else self.bc_hi[1]
+        return -1.0 if bc == BC_NOSLIP else 1.0

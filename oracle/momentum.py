@@ -1,0 +1,165 @@
+"""Explicit right-hand side and the implicit-IBM RK3 stage (paper Sec. 2.1, 2.4).
+
+Right-hand side at internal points (Eq. ns, Eq. semidisc-mom):
+    N_c = -C_c(u) + nu L_c(u) + g_c + s_c
+  * L is the 3-point-per-direction Laplacian (Eq. disclapl) with d(+-1) =
+    1/Delta^2, d(0) = -2/Delta^2, read with every external velocity equal to
+    zero.  With the explicit right-hand side the ghost term then vanishes on
+    its own and the IBM reduces to -lambda w (Eq. semidisc-mom-comp).
+  * C is not written out in the paper.  Reading taken: the divergence
+    (flux) form on the staggered grid with two-point arithmetic averages
+    (Harlow-Welch):  C_u = d(uu)/dx + d(vu)/dy + d(wu)/dz with uu at cell
+    centres, vu / wu at cell edges; no IBM correction of convection (Sec. 2).
+  * s_c is the wall-velocity source (zero for walls at rest).
+Box walls in y: tangential velocity ghosts mirror the adjacent value (sign -1
+no-slip, +1 free-slip); the wall-normal velocity on the wall face is zero.
+
+Stage k (Eq. rk3-rai), with the pressure of the incremental projection
+(Sec. 2.1) carried with weight c_k (reading taken):
+    R   = Delta t (a_k N^{k-1} + b_k N^{k-2}) - c_k Delta t G p^{k-1}
+    x   = lambda c_k Delta t
+    u*  = (B(x) u^{k-1} + R) / (B(x) + x)     at internal points
+    u*  = 0                                   at external points
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .grid import AX
+
+
+def masked(grid, cls, fields):
+    """Velocity with every non-internal point read as zero (external and wall faces)."""
+    return [np.where(cls.internal[c], fields[c], 0.0) if c < grid.ncomp else np.zeros(grid.shape)
+            for c in range(3)]
+
+
+def nb(q, grid, c: int, d: int, s: int):
+    """Values of component-c field q at P + s e_d, with the box rules of y walls."""
+    if grid.periodic(d):
+        return np.roll(q, -s, axis=AX[d])
+    n = grid.n[d]
+    ax = AX[d]
+    out = np.empty_like(q)
+    src = [slice(None)] * 3
+    dst = [slice(None)] * 3
+    edge_dst = [slice(None)] * 3
+    edge_src = [slice(None)] * 3
+    if s > 0:
+        src[ax] = slice(1, n)
+        dst[ax] = slice(0, n - 1)
+        edge_dst[ax] = slice(n - 1, n)
+        edge_src[ax] = slice(n - 1, n)
+        sign = grid.wall_sign("hi")
+    else:
+        src[ax] = slice(0, n - 1)
+        dst[ax] = slice(1, n)
+        edge_dst[ax] = slice(0, 1)
+        edge_src[ax] = slice(0, 1)
+        sign = grid.wall_sign("lo")
+    out[tuple(dst)] = q[tuple(src)]
+    if c == d:
+        # wall-normal component: the value beyond is the wall face (zero)
+        out[tuple(edge_dst)] = 0.0
+    else:
+        out[tuple(edge_dst)] = sign * q[tuple(edge_src)]
+    return out
+
+
+def rhs(grid, cls, fields, nu: float, g, src):
+    """N_c at every point (meaningful at internal points), FP64."""
+    U, V, W = masked(grid, cls, fields)
+    dx, dy, dz = grid.d
+    three = grid.ndim == 3
+    out = []
+
+    # ---- u ----
+    uE, uW = nb(U, grid, 0, 0, +1), nb(U, grid, 0, 0, -1)
+    uN, uS = nb(U, grid, 0, 1, +1), nb(U, grid, 0, 1, -1)
+    cx = (((U + uE) / 2) ** 2 - ((uW + U) / 2) ** 2) / dx
+    vN = (V + nb(V, grid, 1, 0, +1)) / 2                       # v(i,j) + v(i+1,j)
+    vS = (nb(V, grid, 1, 1, -1) + nb(nb(V, grid, 1, 0, +1), grid, 1, 1, -1)) / 2
+    cy = (vN * ((U + uN) / 2) - vS * ((uS + U) / 2)) / dy
+    lap = (uE - 2 * U + uW) / dx ** 2 + (uN - 2 * U + uS) / dy ** 2
+    cz = 0.0
+    if three:
+        uT, uB = nb(U, grid, 0, 2, +1), nb(U, grid, 0, 2, -1)
+        wT = (W + nb(W, grid, 2, 0, +1)) / 2                   # w(i,j,k) + w(i+1,j,k)
+        wB = (nb(W, grid, 2, 2, -1) + nb(nb(W, grid, 2, 0, +1), grid, 2, 2, -1)) / 2
+        cz = (wT * ((U + uT) / 2) - wB * ((uB + U) / 2)) / dz
+        lap = lap + (uT - 2 * U + uB) / dz ** 2
+    out.append(-(cx + cy + cz) + nu * lap + g[0] + src[0])
+
+    # ---- v ----
+    vE, vW = nb(V, grid, 1, 0, +1), nb(V, grid, 1, 0, -1)
+    vNn, vSs = nb(V, grid, 1, 1, +1), nb(V, grid, 1, 1, -1)
+    uEe = (U + nb(U, grid, 0, 1, +1)) / 2                      # u(i,j) + u(i,j+1)
+    uWe = (nb(U, grid, 0, 0, -1) + nb(nb(U, grid, 0, 0, -1), grid, 0, 1, +1)) / 2
+    cx = (uEe * ((V + vE) / 2) - uWe * ((vW + V) / 2)) / dx
+    cy = (((V + vNn) / 2) ** 2 - ((vSs + V) / 2) ** 2) / dy
+    lap = (vE - 2 * V + vW) / dx ** 2 + (vNn - 2 * V + vSs) / dy ** 2
+    cz = 0.0
+    if three:
+        vT, vB = nb(V, grid, 1, 2, +1), nb(V, grid, 1, 2, -1)
+        wTe = (W + nb(W, grid, 2, 1, +1)) / 2                  # w(i,j,k) + w(i,j+1,k)
+        wBe = (nb(W, grid, 2, 2, -1) + nb(nb(W, grid, 2, 2, -1), grid, 2, 1, +1)) / 2
+        cz = (wTe * ((V + vT) / 2) - wBe * ((vB + V) / 2)) / dz
+        lap = lap + (vT - 2 * V + vB) / dz ** 2
+    out.append(-(cx + cy + cz) + nu * lap + g[1] + src[1])
+
+    # ---- w ----
+    if three:
+        wE, wW = nb(W, grid, 2, 0, +1), nb(W, grid, 2, 0, -1)
+        wN, wS = nb(W, grid, 2, 1, +1), nb(W, grid, 2, 1, -1)
+        wT, wB = nb(W, grid, 2, 2, +1), nb(W, grid, 2, 2, -1)
+        uEe = (U + nb(U, grid, 0, 2, +1)) / 2                  # u(i,j,k) + u(i,j,k+1)
+        uWe = (nb(U, grid, 0, 0, -1) + nb(nb(U, grid, 0, 0, -1), grid, 0, 2, +1)) / 2
+        cx = (uEe * ((W + wE) / 2) - uWe * ((wW + W) / 2)) / dx
+        vNe = (V + nb(V, grid, 1, 2, +1)) / 2                  # v(i,j,k) + v(i,j,k+1)
+        vSe = (nb(V, grid, 1, 1, -1) + nb(nb(V, grid, 1, 1, -1), grid, 1, 2, +1)) / 2
+        cy = (vNe * ((W + wN) / 2) - vSe * ((wS + W) / 2)) / dy
+        cz = (((W + wT) / 2) ** 2 - ((wB + W) / 2) ** 2) / dz
+        lap = (wE - 2 * W + wW) / dx ** 2 + (wN - 2 * W + wS) / dy ** 2 + (wT - 2 * W + wB) / dz ** 2
+        out.append(-(cx + cy + cz) + nu * lap + g[2] + src[2])
+    else:
+        out.append(np.zeros(grid.shape))
+    return out
+
+
+def pressure_gradient(grid, p):
+    """(G p)_c on the faces; zero on wall faces (Gp is not used there)."""
+    out = []
+    for c in range(3):
+        if c >= grid.ncomp:
+            out.append(np.zeros(grid.shape))
+            continue
+        if grid.periodic(c):
+            out.append((np.roll(p, -1, axis=AX[c]) - p) / grid.d[c])
+        else:
+            gph = np.zeros(grid.shape)
+            n = grid.n[c]
+            a = [slice(None)] * 3
+            b = [slice(None)] * 3
+            o = [slice(None)] * 3
+            a[AX[c]] = slice(1, n)
+            b[AX[c]] = slice(0, n - 1)
+            o[AX[c]] = slice(0, n - 1)
+            gph[tuple(o)] = (p[tuple(a)] - p[tuple(b)]) / grid.d[c]
+            out.append(gph)
+    return out
+
+
+def stage_update(grid, cls, u_prev, N_cur, N_prev, gradp, lam, k: int, dt: float,
+                 bmode: int, a, b, cc, B_of_x):
+    """u* of Eq. (rk3-rai) at internal points, zero elsewhere (k = 0, 1, 2)."""
+    out = []
+    for c in range(3):
+        if c >= grid.ncomp:
+            out.append(np.zeros(grid.shape))
+            continue
+        R = dt * (a[k] * N_cur[c] + b[k] * N_prev[c]) - cc[k] * dt * gradp[c]
+        x = lam[c] * cc[k] * dt
+        B = B_of_x(x, bmode)
+        ustar = (B * u_prev[c] + R) / (B + x)
+        out.append(np.where(cls.internal[c], ustar, 0.0))
+    return out

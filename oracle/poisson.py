@@ -1,0 +1,184 @@
+"""Projection pieces: divergence, gradient and the pressure-correction Poisson solve.
+
+Paper Sec. 2.1: after the momentum predictor the velocity is projected onto a
+solenoidal field; the pressure increment solves a Poisson equation.  Sec. 3.3:
+no pressure boundary condition at the body, and the continuity equation is
+solved everywhere "as though there was no boundary".  Reading taken (the
+"unmodified projection"): the Poisson operator is the plain D G of the full
+box, with the box boundary conditions only:
+  * periodic directions wrap;
+  * wall directions: the wall-normal velocity is prescribed, so G phi is not
+    applied on wall faces (homogeneous Neumann for phi).
+The correction u = u* - c_k Delta t G phi is applied on every non-wall face
+and p += phi in every cell.  The operator is singular (constants); the gauge
+is: mean of phi over the box = 0.
+
+Two solvers, which must agree:
+  * solve_direct: the definition written out, a sparse LU of D G augmented
+    with the zero-mean constraint (small grids, used as a pin);
+  * solve_spectral: FFT (numpy, a library primitive) in the periodic
+    directions x and z and a Thomas solve along y for every wavenumber pair,
+    with the modified wavenumbers 4 sin^2(pi k/n)/Delta^2 of the 3-point
+    second difference.  The (0,0) mode fixes phi_0 = 0, solves the rest and
+    then removes the mean over y.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .grid import AX
+
+
+def divergence(grid, vel):
+    """(D u) at every cell: sum_d (u_d(idx) - u_d(idx - e_d)) / Delta_d; the -y wall face is 0."""
+    out = np.zeros(grid.shape)
+    for d in range(grid.ncomp):
+        q = vel[d]
+        if grid.periodic(d):
+            qm = np.roll(q, 1, axis=AX[d])
+        else:
+            qm = np.zeros_like(q)
+            n = grid.n[d]
+            a = [slice(None)] * 3
+            b = [slice(None)] * 3
+            a[AX[d]] = slice(1, n)
+            b[AX[d]] = slice(0, n - 1)
+            qm[tuple(a)] = q[tuple(b)]
+        out = out + (q - qm) / grid.d[d]
+    return out
+
+
+def gradient(grid, phi):
+    """(G phi) on every non-wall face; zero on wall faces."""
+    out = []
+    for c in range(3):
+        if c >= grid.ncomp:
+            out.append(np.zeros(grid.shape))
+            continue
+        if grid.periodic(c):
+            out.append((np.roll(phi, -1, axis=AX[c]) - phi) / grid.d[c])
+        else:
+            g = np.zeros(grid.shape)
+            n = grid.n[c]
+            a = [slice(None)] * 3
+            b = [slice(None)] * 3
+            a[AX[c]] = slice(1, n)
+            b[AX[c]] = slice(0, n - 1)
+            g[tuple(b)] = (phi[tuple(a)] - phi[tuple(b)]) / grid.d[c]
+            out.append(g)
+    return out
+
+
+def thomas(a, b, c, d):
+    """Plain Thomas algorithm along axis 0 for many systems at once.
+
+    a: sub-diagonal (a[0] unused), b: diagonal, c: super-diagonal (c[-1] unused),
+    d: right-hand sides; a, b, c broadcast against d."""
+    n = d.shape[0]
+    cp = np.zeros(np.broadcast(b[0], d[0]).shape, dtype=np.float64)
+    cps = []
+    dps = []
+    bet = b[0] * np.ones_like(cp)
+    dp = d[0] / bet
+    cp = c[0] / bet
+    cps.append(cp)
+    dps.append(dp)
+    for j in range(1, n):
+        bet = b[j] - a[j] * cps[-1]
+        dp = (d[j] - a[j] * dps[-1]) / bet
+        cp = (c[j] / bet) if j < n - 1 else np.zeros_like(bet)
+        cps.append(cp)
+        dps.append(dp)
+    x = [None] * n
+    x[n - 1] = dps[n - 1]
+    for j in range(n - 2, -1, -1):
+        x[j] = dps[j] - cps[j] * x[j + 1]
+    return np.stack(x, axis=0)
+
+
+def modified_wavenumbers(n: int, Delta: float) -> np.ndarray:
+    k = np.arange(n)
+    return 4.0 * np.sin(np.pi * k / n) ** 2 / Delta ** 2
+
+
+def solve_spectral(grid, rhs):
+    nx, ny, nz = grid.n
+    dy = grid.d[1]
+    rh = np.fft.fft2(rhs, axes=(0, 2))                 # (kz, y, kx)
+    K = modified_wavenumbers(nx, grid.d[0])[None, :]
+    if grid.ndim == 3:
+        K = K + modified_wavenumbers(nz, grid.d[2])[:, None]
+    else:
+        K = K + np.zeros((nz, 1))
+    # y-systems: (phi_{j-1} - 2 phi_j + phi_{j+1})/dy^2 - K phi_j = r_j, Neumann ends
+    d = np.moveaxis(rh, 1, 0)                          # (y, kz, kx)
+    inv = 1.0 / dy ** 2
+    a = np.full(ny, inv)
+    c = np.full(ny, inv)
+    a[0] = 0.0
+    c[-1] = 0.0
+    diag = np.full(ny, -2.0 * inv)
+    diag[0] = -inv
+    diag[-1] = -inv
+    b = diag[:, None, None] - K[None, :, :]
+    zero = (K == 0.0)
+    b_safe = np.where(zero[None], -1.0, b)            # placeholder; the zero mode is solved below
+    sol = thomas(a[:, None, None], b_safe, c[:, None, None], d)
+    # zero mode (kx = kz = 0): phi_0 = 0, rows 1..ny-1, then zero mean along y
+    zk = np.argwhere(zero)
+    for (kz, kx) in zk:
+        dz = d[:, kz, kx]
+        a1 = a[1:].copy()
+        a1[0] = 0.0
+        b1 = diag[1:].copy()
+        c1 = c[1:].copy()
+        x = np.zeros(ny, dtype=complex)
+        x[1:] = thomas(a1, b1, c1, dz[1:])
+        x -= x.mean()
+        sol[:, kz, kx] = x
+    ph = np.moveaxis(sol, 0, 1)
+    return np.real(np.fft.ifft2(ph, axes=(0, 2)))
+
+
+def operator_matrix(grid):
+    """Sparse D G on the full box (periodic x,z; Neumann y)."""
+    nx, ny, nz = grid.n
+    N = nx * ny * nz
+    idx = np.arange(N).reshape(grid.shape)
+    rows, cols, vals = [], [], []
+    for d in range(grid.ncomp):
+        inv = 1.0 / grid.d[d] ** 2
+        ax = AX[d]
+        n = grid.n[d]
+        for s in (+1, -1):
+            nbr = np.roll(idx, -s, axis=ax)
+            valid = np.ones(grid.shape, dtype=bool)
+            if not grid.periodic(d):
+                pos = np.arange(n)
+                shp = [1, 1, 1]
+                shp[ax] = n
+                pos = pos.reshape(shp)
+                valid = np.broadcast_to((pos + s >= 0) & (pos + s <= n - 1), grid.shape)
+            if n == 1 and grid.periodic(d):
+                continue
+            r = idx[valid]
+            q = nbr[valid]
+            rows += [r, r]
+            cols += [q, r]
+            vals += [np.full(r.size, inv), np.full(r.size, -inv)]
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+
+
+def solve_direct(grid, rhs):
+    A = operator_matrix(grid)
+    N = A.shape[0]
+    e = np.ones((N, 1))
+    M = sp.bmat([[A, sp.csr_matrix(e)], [sp.csr_matrix(e.T), None]], format="csc")
+    b = np.concatenate([rhs.ravel(), [0.0]])
+    x = spla.spsolve(M, b)
+    return x[:N].reshape(grid.shape)

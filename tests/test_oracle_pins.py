@@ -1,0 +1,455 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a value
+printed in the paper (tests/golden/paper_values.json), a closed form, an
+invariant, a brute-force restatement on a tiny grid, or a direct sparse solve.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from inputs import (Case, channel_c1, couette_case, pipe_case, small_case, initial_field,
+                    BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, GEOM_NONE, GEOM_PLANES, GEOM_CYLINDER,
+                    B_EXACT, B_EULER, B_TAYLOR2)
+from oracle import (Grid, LevelSet, classify, build_weights, B_of_x, RK3_A, RK3_B, RK3_C,
+                    OracleSolver, solve_direct, solve_spectral, divergence, gradient, steady)
+from oracle.momentum import rhs, stage_update
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def _setup(case):
+    g = Grid(case)
+    ls = LevelSet(case.geom_kind, case.geom_params)
+    cls = classify(g, ls)
+    w = build_weights(g, ls, cls, case.nu, case.wall_u)
+    return g, ls, cls, w
+
+
+def _channel(ny, a, b, nx=8, bc=BC_NOSLIP, nu=1.0):
+    return Case(name="ch", ndim=2, n=(nx, ny, 1), L=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
+                bc_lo=(BC_PERIODIC, bc, BC_PERIODIC), bc_hi=(BC_PERIODIC, bc, BC_PERIODIC),
+                geom_kind=GEOM_PLANES, geom_params=(a, b), nu=nu, dt=1e-3)
+
+
+# ------------------------------------------------------------------ time integration
+def test_rk3_coefficients_match_paper():
+    gold = GOLDEN["rai_moin_rk3"]
+    assert np.allclose(RK3_A, np.array(gold["a_over_120"]) / 120.0, rtol=0, atol=1e-16)
+    assert np.allclose(RK3_B, np.array(gold["b_over_120"]) / 120.0, rtol=0, atol=1e-16)
+    # the three substages advance time by exactly one step
+    assert abs(sum(RK3_C) - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("mode", [B_EXACT, B_EULER, B_TAYLOR2])
+def test_B_bounds(mode):
+    """Sec. 2.4: 1 >= B >= 0 for every Delta t, and B(0) = 1 (plain scheme recovered)."""
+    x = np.concatenate([[0.0], np.logspace(-12, 4, 200)])
+    B = B_of_x(x, mode)
+    assert np.all(B <= 1.0) and np.all(B >= 0.0)
+    assert B[0] == 1.0
+
+
+class _Pt:
+    """A one-point grid for the scalar ODE dw/dt = -lambda w + f."""
+    ncomp = 1
+    shape = (1, 1, 1)
+
+
+class _PtCls:
+    internal = [np.ones((1, 1, 1), dtype=bool)]
+
+
+def _ode_step(w0, lam, f, dt, mode):
+    w = np.array([[[w0]]])
+    Nprev = [np.zeros((1, 1, 1))]
+    for k in range(3):
+        N = [np.array([[[f]]])]
+        w = stage_update(_Pt, _PtCls, [w], N, Nprev, [np.zeros((1, 1, 1))], [np.array([[[lam]]])],
+                         k, dt, mode, RK3_A, RK3_B, RK3_C, B_of_x)[0]
+        Nprev = N
+    return float(w[0, 0, 0])
+
+
+@pytest.mark.parametrize("lam", [0.5, 7.0, 300.0, 1e6])
+def test_exponential_B_integrates_ibm_term_exactly(lam):
+    """Eq. (Bexpr)/(expint): with constant f the update is exact: w_inf + (w0 - w_inf) e^{-lambda dt}."""
+    w0, f, dt = 0.8, 3.0, 0.01
+    winf = f / lam
+    exact = winf + (w0 - winf) * math.exp(-lam * dt)
+    got = _ode_step(w0, lam, f, dt, B_EXACT)
+    assert abs(got - exact) <= 1e-14 * max(1.0, abs(exact))
+    # implicit Euler B = 1 is not exact for finite lambda dt (first order)
+    if 0.01 < lam * dt < 50:
+        assert abs(_ode_step(w0, lam, f, dt, B_EULER) - exact) > 1e-6
+
+
+def test_lambda_infinite_enforces_zero():
+    """Sec. 2.4: lambda -> infinity gives w* = 0 (the exact boundary condition)."""
+    for mode in (B_EXACT, B_EULER, B_TAYLOR2):
+        assert abs(_ode_step(0.9, 1e300, 5.0, 0.01, mode)) < 1e-250
+
+
+def test_plain_rk3_third_order_without_ibm():
+    """lambda = 0: the scheme is the Rai-Moin RK3 on dw/dt = f(w); check on dw/dt = -w."""
+    def run(dt, T=1.0):
+        w = np.array([[[1.0]]])
+        Nprev = [np.zeros((1, 1, 1))]
+        for _ in range(int(round(T / dt))):
+            for k in range(3):
+                N = [-w]
+                w = stage_update(_Pt, _PtCls, [w], N, Nprev, [np.zeros((1, 1, 1))],
+                                 [np.zeros((1, 1, 1))], k, dt, B_EXACT, RK3_A, RK3_B, RK3_C, B_of_x)[0]
+                Nprev = N
+        return abs(float(w[0, 0, 0]) - math.exp(-1.0))
+    e1, e2 = run(0.1), run(0.05)
+    assert 2.7 < math.log2(e1 / e2) < 3.3
+
+
+# ------------------------------------------------------------------ classification
+def _brute_classify(g, ls):
+    """Per-point restatement of the staircase rules on a tiny grid (pure Python loops)."""
+    nx, ny, nz = g.n
+    nc = g.ncomp
+    def phi_at(c, i, j, k):
+        idx = (i, j, k)
+        P = [g.origin[d] + (idx[d] + (1.0 if d == c else 0.5)) * g.d[d] for d in range(3)]
+        return float(ls.phi(P[0], P[1], P[2]))
+    def state(c, i, j, k):
+        """'int', 'ext', 'bnd' or None (outside the box)."""
+        for d, v in zip(range(3), (i, j, k)):
+            if not (0 <= v < g.n[d]):
+                if g.periodic(d):
+                    continue
+                return None
+        i %= nx; j %= ny; k %= nz
+        if c == 1 and not g.periodic(1) and j == ny - 1:
+            return "bnd"
+        return "int" if phi_at(c, i, j, k) < 0.0 else "ext"
+    mask = np.zeros(g.shape, dtype=np.uint8)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                m = 0
+                for c in range(nc):
+                    if state(c, i, j, k) == "int":
+                        m |= 1 << c
+                        for d in range(g.ndim):
+                            for s in (1, -1):
+                                q = [i, j, k]
+                                q[d] += s
+                                if state(c, *q) == "ext":
+                                    m |= 1 << (4 + c)
+                pint = False
+                for c in range(nc):
+                    q = [i, j, k]
+                    if state(c, *q) == "int":
+                        pint = True
+                    q[c] -= 1
+                    if state(c, *q) == "int":
+                        pint = True
+                if pint:
+                    m |= 8
+                mask[k, j, i] = m
+    return mask
+
+
+@pytest.mark.parametrize("case", [
+    _channel(9, 0.137, 0.861, nx=5),
+    Case(name="cyl", ndim=2, n=(11, 9, 1), L=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
+         bc_lo=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC),
+         geom_kind=GEOM_CYLINDER, geom_params=(0.47, 0.52, 0.31, -1.0), nu=0.1, dt=1e-3),
+    small_case("sphere3d").with_(n=(9, 7, 6)),
+    small_case("wavy3d").with_(n=(10, 8, 3)),
+])
+def test_classification_brute_force(case):
+    g = Grid(case)
+    ls = LevelSet(case.geom_kind, case.geom_params)
+    cls = classify(g, ls)
+    assert np.array_equal(cls.mask, _brute_classify(g, ls))
+
+
+def test_internal_velocity_reads_only_internal_pressure():
+    """Sec. 3.3: internal p cells are the only ones the momentum equations read."""
+    for case in (small_case("sphere3d"), small_case("wavy3d"), small_case("channel2d")):
+        g = Grid(case)
+        cls = classify(g, LevelSet(case.geom_kind, case.geom_params))
+        for c in range(g.ncomp):
+            P = cls.internal[c]
+            ax = {0: 2, 1: 1, 2: 0}[c]
+            assert np.all(cls.p_internal[P])
+            assert np.all(np.roll(cls.p_internal, -1, axis=ax)[P])
+
+
+def test_classification_mirror_symmetry():
+    """A body centred in a power-of-two box classifies mirror-symmetrically (exact positions)."""
+    case = Case(name="sym", ndim=2, n=(32, 32, 1), L=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
+                bc_lo=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC),
+                geom_kind=GEOM_CYLINDER, geom_params=(0.5, 0.5, 0.3, -1.0), nu=0.1, dt=1e-3)
+    g = Grid(case)
+    cls = classify(g, LevelSet(case.geom_kind, case.geom_params))
+    n = 32
+    # v: y-mirror maps face j to n-2-j (wall face n-1 excluded), x-mirror maps cell i to n-1-i
+    v = cls.internal[1][0]
+    assert np.array_equal(v[:n - 1, :], v[:n - 1, ::-1])
+    assert np.array_equal(v[:n - 1, :], v[n - 2::-1, :])
+    u = cls.internal[0][0]
+    iu = np.array([(n - 2 - i) % n for i in range(n)])
+    assert np.array_equal(u, u[:, iu])
+    assert np.array_equal(u, u[::-1, :])
+    # u and v see the same body rotated by 90 degrees
+    assert np.array_equal(u[:, :n - 1], v[:n - 1, :].T)
+
+
+def test_circle_area_from_counts():
+    """External u points of a circle of radius R cover pi R^2 up to a perimeter-sized error."""
+    R, n = 0.3, 64
+    case = Case(name="area", ndim=2, n=(n, n, 1), L=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
+                bc_lo=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC),
+                geom_kind=GEOM_CYLINDER, geom_params=(0.5013, 0.4987, R, -1.0), nu=0.1, dt=1e-3)
+    g = Grid(case)
+    cls = classify(g, LevelSet(case.geom_kind, case.geom_params))
+    area = cls.external[0].sum() / n ** 2
+    assert abs(area - math.pi * R * R) < 2 * math.pi * R / n
+
+
+# ------------------------------------------------------------------ weights
+def test_interface_on_grid_line_gives_standard_stencil():
+    """delta = Delta (wall through the u-grid line) gives lambda = 0: IBM == staircase, bit for bit."""
+    ny = 32
+    dy = 1.0 / ny
+    a = (3 + 0.5) * dy          # passes through the u points of row 3
+    b = (27 + 0.5) * dy
+    case = _channel(ny, a, b, nu=0.05).with_(g=(1.0, 0.0, 0.0), dt=2e-4)
+    g, ls, cls, w = _setup(case)
+    assert len(cls.lists[0]) > 0 and np.all(w.lam_list[0] == 0.0)
+    s1 = OracleSolver(case)
+    s2 = OracleSolver(case, no_ibm=True)
+    s1.step(5)
+    s2.step(5)
+    assert np.array_equal(s1.u[0], s2.u[0])
+
+
+def test_flat_wall_lambda_and_monotonicity():
+    """Eq. (lambda): lambda = nu d(-1) (Delta - delta)/delta for a single crossed arm, growing as delta -> 0."""
+    ny = 32
+    dy = 1.0 / ny
+    nu = 0.07
+    lams = []
+    for frac in (0.9, 0.6, 0.3, 0.1, 0.01):
+        # wall between u rows 3 and 4 at distance frac*dy below row 4
+        a = (4 + 0.5) * dy - frac * dy
+        g, ls, cls, w = _setup(_channel(ny, a, 0.9, nu=nu))
+        row = w.lam[0][0, 4, :]
+        expect = nu * (1.0 / dy ** 2) * (dy - frac * dy) / (frac * dy)
+        assert np.allclose(row, expect, rtol=1e-9, atol=0)
+        lams.append(row[0])
+    assert all(l2 > l1 for l1, l2 in zip(lams, lams[1:]))
+
+
+def test_corrections_are_additive_over_arms():
+    """End of Sec. 2.2: a point whose two arms cross the boundary carries the sum of both corrections."""
+    ny = 16
+    dy = 1.0 / ny
+    # a one-cell channel: the single internal u row has both y arms external
+    a = (7 + 0.5) * dy - 0.25 * dy
+    b = (7 + 0.5) * dy + 0.4 * dy
+    g, ls, cls, w = _setup(_channel(ny, a, b, nu=1.0))
+    lam = w.lam[0][0, 7, 0]
+    e1 = (dy - 0.25 * dy) / (0.25 * dy) / dy ** 2
+    e2 = (dy - 0.4 * dy) / (0.4 * dy) / dy ** 2
+    assert abs(lam - (e1 + e2)) < 1e-9 * lam
+
+
+def test_circle_closed_form_delta_matches_bisection():
+    ls = LevelSet(GEOM_CYLINDER, (0.43, 0.51, 0.27, -1.0))
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        P = [0.43 + 0.27 + 0.01 * rng.random(), 0.51 + 0.1 * (rng.random() - 0.5), 0.0]
+        phiP = float(ls.phi(*P))
+        Q = [P[0] - 0.05, P[1], 0.0]
+        phiQ = float(ls.phi(*Q))
+        if not (phiP < 0 <= phiQ):
+            continue
+        d1 = ls._closed_form(P, 0, -1, 0.05)
+        d2 = ls._bisect(P, 0, -1, 0.05)
+        assert abs(d1 - d2) < 1e-15
+
+
+# ------------------------------------------------------------------ steady examples of the paper
+def test_hagen_poiseuille_fRe_matches_paper():
+    """Sec. 2.3: f Re_b -> 64; at N = 104 the paper prints 3% (staircase) and 0.01% (IBM).
+
+    The paper does not give its grid arrangement, so the check is on the
+    order of magnitude: IBM error below 0.05%, staircase error above 1%."""
+    gold = GOLDEN["hagen_poiseuille"]
+    N = gold["N"]
+    case = pipe_case(N=N)
+    g, ls, cls, w = _setup(case)
+    res = {}
+    for ibm in (True, False):
+        q = steady.solve_component(g, cls, w, 2, 1.0, 1.0, use_ibm=ibm)
+        Ub = q.sum() * g.d[0] * g.d[1] / math.pi
+        res[ibm] = 100.0 * abs(8.0 / Ub - gold["fRe_exact"]) / gold["fRe_exact"]
+    assert res[True] < 5 * gold["err_pct_ibm"]
+    assert res[False] > gold["err_pct_staircase"] / 3
+
+
+def _poiseuille_error(ny, use_ibm):
+    """Plane Poiseuille error with the walls at a fixed fraction of a cell from the u grid.
+
+    Keeping the sub-cell wall position the same at every resolution removes
+    the scatter that a fixed wall position causes, so the slope is clean."""
+    dy = 1.0 / ny
+    a = (math.floor(0.137 * ny) + 0.5 + 0.37) * dy
+    b = (math.floor(0.861 * ny) + 0.5 + 0.61) * dy
+    case = _channel(ny, a, b, nx=4, nu=1.0)
+    g, ls, cls, w = _setup(case)
+    q = steady.solve_component(g, cls, w, 0, 1.0, 1.0, use_ibm=use_ibm)
+    y = g.coords(0)[1]
+    exact = np.broadcast_to(0.5 * (y - a) * (b - y), g.shape)
+    return np.abs(q - exact)[cls.internal[0]].max()
+
+
+def test_channel_refinement_slopes():
+    """Second order for the IBM, first order for the staircase (Sec. 2.3, figure space-convergence)."""
+    ns = [32, 64, 128, 256, 512]
+    e_ibm = [_poiseuille_error(n, True) for n in ns]
+    e_st = [_poiseuille_error(n, False) for n in ns]
+    p_ibm = -np.polyfit(np.log(ns), np.log(e_ibm), 1)[0]
+    p_st = -np.polyfit(np.log(ns), np.log(e_st), 1)[0]
+    assert p_ibm > 1.9
+    assert 0.8 < p_st < 1.2
+
+
+def test_couette_linear_profile_is_a_fixed_point():
+    """Linear extrapolation is exact for a linear profile: one full step leaves it unchanged."""
+    case = couette_case()
+    s = OracleSolver(case)
+    f = initial_field(case)
+    s.set_state(f["u"], f["v"], f["w"], f["p"])
+    u0 = np.where(s.cls.internal[0], s.u[0], 0.0)
+    s.step(3)
+    u1 = np.where(s.cls.internal[0], s.u[0], 0.0)
+    assert np.abs(u1 - u0).max() < 1e-13 * case.wall_u[0]
+    assert np.abs(s.u[1]).max() < 1e-13
+
+
+def test_channel_c1_reaches_its_discrete_steady_state_and_the_parabola():
+    case = channel_c1(steps=2000)
+    s = OracleSolver(case)
+    s.step(case.steps)
+    g, cls = s.grid, s.cls
+    ss = steady.solve_component(g, cls, s.w, 0, case.nu, case.g[0])
+    interior = cls.internal[0]
+    rel = np.abs(s.u[0] - ss)[interior].max() / np.abs(ss).max()
+    assert rel < 1e-4
+    y = g.coords(0)[1]
+    exact = np.broadcast_to(1.0 - ((y - 0.499) / 0.362) ** 2, g.shape)
+    assert np.abs(ss - exact)[interior].max() < 5e-3
+
+
+# ------------------------------------------------------------------ projection
+@pytest.mark.parametrize("case", [_channel(10, 0.1, 0.9, nx=12), small_case("sphere3d").with_(n=(8, 10, 6)),
+                                  small_case("wavy3d").with_(n=(8, 6, 1))])
+def test_spectral_poisson_equals_direct_solve(case):
+    g = Grid(case)
+    r = np.random.default_rng(5).standard_normal(g.shape)
+    r -= r.mean()
+    a = solve_spectral(g, r)
+    b = solve_direct(g, r)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+    assert abs(a.mean()) < 1e-14 * np.abs(a).max()
+
+
+def test_projection_is_divergence_free_and_idempotent():
+    case = small_case("sphere3d")
+    s = OracleSolver(case)
+    f = initial_field(case)
+    s.set_state(f["u"], f["v"], f["w"], f["p"])
+    s.project()
+    g = s.grid
+    div = divergence(g, s.u)
+    umax = max(np.abs(a).max() for a in s.u)
+    assert np.abs(div).max() < 1e-13 * umax / min(g.d)
+    u1 = [a.copy() for a in s.u]
+    s._project(u1, 1.0, update_p=False)
+    assert max(np.abs(s.u[c] - u1[c]).max() for c in range(3)) < 1e-13 * umax
+
+
+def test_projection_removes_gradients_and_keeps_solenoidal_fields():
+    case = small_case("wavy3d").with_(n=(16, 12, 8))
+    g = Grid(case)
+    psi = np.random.default_rng(2).standard_normal(g.shape)
+    Gpsi = gradient(g, psi)
+    s = OracleSolver(case.with_(geom_kind=GEOM_NONE, geom_params=()))
+    s._project([a.copy() for a in Gpsi], 1.0, update_p=False)
+    assert max(np.abs(a).max() for a in s.u) < 1e-12 * max(np.abs(a).max() for a in Gpsi)
+    # u = u(y) only (v = w = 0) is solenoidal in a box periodic in x and z
+    y = g.coords(0)[1]
+    u = np.broadcast_to(np.sin(3.0 * y) + y ** 2, g.shape).copy()
+    s._project([u, np.zeros(g.shape), np.zeros(g.shape)], 1.0, update_p=False)
+    assert np.abs(s.u[0] - u).max() < 1e-13
+
+
+# ------------------------------------------------------------------ momentum operator
+def test_momentum_conservation_free_slip_box():
+    """Flux-form convection, Laplacian with free-slip mirrors and periodic pressure gradient conserve x and z momentum."""
+    case = small_case("sphere3d").with_(geom_kind=GEOM_NONE, geom_params=(), g=(0.0, 0.0, 0.0), dt=0.002)
+    s = OracleSolver(case)
+    f = initial_field(case)
+    s.set_state(f["u"], f["v"], f["w"], f["p"])
+    s.project()
+    m0 = [s.u[0].sum(), s.u[2].sum()]
+    s.step(3)
+    m1 = [s.u[0].sum(), s.u[2].sum()]
+    assert abs(m1[0] - m0[0]) < 1e-11 * abs(m0[0])
+    assert abs(m1[1] - m0[1]) < 1e-11 * max(1.0, abs(m0[1]))
+
+
+def test_convection_of_a_sine_mode_by_uniform_stream():
+    """u = U, v = eps sin(kx): the RHS of v is the centred difference of a sine in closed form."""
+    nx, ny = 32, 8
+    case = Case(name="adv", ndim=2, n=(nx, ny, 1), L=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
+                bc_lo=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC),
+                geom_kind=GEOM_NONE, geom_params=(), nu=0.3, dt=1e-3)
+    g = Grid(case)
+    cls = classify(g, LevelSet(GEOM_NONE))
+    U, eps, k = 1.7, 0.01, 2 * math.pi * 3
+    x = g.coords(1)[0]
+    u = np.full(g.shape, U)
+    v = np.broadcast_to(eps * np.sin(k * x), g.shape).copy()
+    v[:, ny - 1, :] = 0.0
+    N = rhs(g, cls, [u, v, np.zeros(g.shape)], case.nu, (0, 0, 0), [np.zeros(g.shape)] * 3)
+    dx = g.d[0]
+    xx = np.broadcast_to(x, g.shape)
+    conv = U * eps * np.cos(k * xx) * math.sin(k * dx) / dx
+    visc = -case.nu * eps * np.sin(k * xx) * 4 * math.sin(k * dx / 2) ** 2 / dx ** 2
+    inner = np.s_[:, 1:ny - 2, :]          # away from the walls, where v's y-neighbours are interior
+    assert np.abs(N[1][inner] - (-conv + visc)[inner]).max() < 1e-12
+    # the u equation sees d(uv)/dy = U dv/dy = 0 there and no x variation
+    assert np.abs(N[0][inner]).max() < 1e-12
+
+
+def _startup_flux(dt, mode, T=0.05):
+    case = _channel(24, 0.137, 0.861, nx=4, nu=1.0).with_(g=(1.0, 0.0, 0.0), dt=dt, bmode=mode)
+    s = OracleSolver(case)
+    s.step(int(round(T / dt)))
+    return s.diagnostics()["flux"][0]
+
+
+def test_temporal_order_exact_B_vs_euler():
+    """Sec. 2.5: second order in time with the exponential B, first order with B = 1.
+
+    Errors are taken against a run with the exponential B at dt/16 of the
+    coarsest step; the slope is read from the two finest pairs."""
+    T = 0.0496
+    ref = _startup_flux(1.25e-5, B_EXACT, T=T)
+    dts = [2e-4, 1e-4, 5e-5]
+    for mode, lo, hi in ((B_EXACT, 1.8, 2.6), (B_EULER, 0.85, 1.15)):
+        e = [abs(_startup_flux(dt, mode, T=T) - ref) for dt in dts]
+        p = math.log2(e[1] / e[2])
+        assert lo < p < hi, (mode, p)
