@@ -1,0 +1,219 @@
+/*
+ * ibm.h -- C ABI of libibm.so: the per-time-step hot path of the implicit,
+ * second-order sharp-interface immersed-boundary method of Luchini, Gatti,
+ * Chiarini, Gattere, Atzori and Quadrio ("A simple and efficient second-order
+ * immersed-boundary method for the incompressible Navier-Stokes equations"),
+ * on one GB300 GPU (sm_103a).
+ *
+ * Problem (paper Sec. 2.1, Eq. ns): du/dt + (u.grad)u - nu lap u + grad p = g,
+ * div u = 0, on a staggered Cartesian grid with 3-point central differences.
+ * The body enters only as a per-point increase lambda of the Laplacian's
+ * centre weight (Sec. 2.2, Eq. disclapl-extr / lambda), applied implicitly
+ * (Sec. 2.4, Eq. Bexpr / expint) inside the Rai-Moin RK3 (Eq. rk3-rai); each
+ * substage ends with the unmodified pressure projection (Sec. 2.1, Sec. 3.3).
+ *
+ * Conventions
+ *   - Every array is (nz, ny, nx) with x fastest; linear index i + nx*(j + ny*k).
+ *     Cell (i,j,k) has its centre at origin + ((i+1/2)dx, (j+1/2)dy, (k+1/2)dz),
+ *     dx = L[0]/n[0] etc.; u(i,j,k) sits on the cell's +x face, v on its +y
+ *     face, w on its +z face.  In 2D, nz = 1 and w is absent.
+ *   - x and z must be periodic; y is bounded by box walls (no-slip or
+ *     free-slip).  v(i, ny-1, k) lies on the +y wall and is held at zero.
+ *     Other combinations return IBM_E_UNSUPPORTED.
+ *   - Memory: the caller allocates every device buffer (fields, workspace,
+ *     weights) and keeps it alive until ibm_destroy.  The library never
+ *     allocates or frees device memory except inside cuFFT plans (twiddle
+ *     tables); cuFFT's work area comes from the caller's workspace.
+ *   - Streams: all device work is enqueued on the stream given at setup.
+ *     Calls are asynchronous except where stated ("blocking").
+ *   - Errors: every call returns an ibm_status; nothing throws across the
+ *     ABI.  ibm_last_error() gives a thread-local message.  After a CUDA
+ *     error the handle is failed and later calls return IBM_E_STATE.
+ *   - Precision: IBM_FP64 runs every step in FP64.  IBM_FP32 stores fields in
+ *     FP32 and runs the momentum stencil, the IBM division, the divergence
+ *     and the FFTs in FP32; the tridiagonal sweeps, all reductions and the
+ *     IBM weights are FP64.
+ */
+#ifndef IBM_H
+#define IBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IBM_OK = 0,
+    IBM_E_INVALID = -1,      /* bad argument, size or pointer */
+    IBM_E_CUDA = -2,         /* a CUDA or cuFFT call failed */
+    IBM_E_NOMEM = -3,        /* a caller buffer is smaller than required */
+    IBM_E_UNSUPPORTED = -4,  /* valid request outside what this build implements */
+    IBM_E_DIVERGED = -5,     /* non-finite field found by ibm_diagnostics */
+    IBM_E_TIMEOUT = -6,      /* a bounded device wait gave up */
+    IBM_E_STATE = -7         /* handle failed earlier, or call out of order */
+} ibm_status;
+
+/* box boundary condition per face */
+enum { IBM_BC_PERIODIC = 0, IBM_BC_NOSLIP = 1, IBM_BC_FREESLIP = 2, IBM_BC_INFLOW = 3, IBM_BC_OUTFLOW = 4 };
+/* field precision */
+enum { IBM_FP64 = 0, IBM_FP32 = 1 };
+/* geometry kinds: level set phi < 0 is fluid, phi >= 0 is solid (Sec. 3.3) */
+enum {
+    IBM_GEOM_NONE = 0,      /* no body                                                      */
+    IBM_GEOM_PLANES = 1,    /* param = {a, b}: fluid for a < y < b; the plane y=b moves       */
+    IBM_GEOM_CYLINDER = 2,  /* param = {xc, yc, R, s}: axis along z; s=+1 fluid inside,
+                               s=-1 fluid outside; phi = s((x-xc)^2+(y-yc)^2-R^2)            */
+    IBM_GEOM_SPHERE = 3,    /* param = {xc, yc, zc, R, s}                                    */
+    IBM_GEOM_SINE_WALL = 4, /* param = {y0, A, lam, ytop}: fluid for
+                               y0 + A sin(2 pi x/lam) < y < ytop; the wavy wall moves         */
+    IBM_GEOM_TUBES = 5,     /* reserved (IBM_E_UNSUPPORTED)                                   */
+    IBM_GEOM_SAMPLED = 6    /* reserved (IBM_E_UNSUPPORTED)                                   */
+};
+/* B(x) of Eq. (Bexpr), x = lambda c_k dt */
+enum { IBM_B_EXACT = 0, IBM_B_EULER = 1, IBM_B_TAYLOR2 = 2 };
+/* forcing */
+enum { IBM_FLOW_FORCED = 0, IBM_FLOW_CONST_FLUX = 1 };
+/* ibm_step flags */
+enum {
+    IBM_STEP_PREDICTOR_ONLY = 1u, /* run only the stage-1 predictor: fields <- u*, no projection */
+    IBM_STEP_GRAPH = 2u           /* replay the step from a CUDA graph captured on first use   */
+};
+/* packed mask bits returned by ibm_get_classification */
+enum { IBM_MASK_U = 1, IBM_MASK_V = 2, IBM_MASK_W = 4, IBM_MASK_P = 8,
+       IBM_MASK_IBM_U = 16, IBM_MASK_IBM_V = 32, IBM_MASK_IBM_W = 64 };
+
+typedef struct {
+    int ndim;           /* 2 or 3 */
+    int n[3];           /* cells nx, ny, nz; nz = 1 when ndim = 2; ny >= 2 */
+    double L[3];        /* box lengths */
+    double origin[3];   /* box lower corner */
+    int bc_lo[3];       /* IBM_BC_* per direction, low face */
+    int bc_hi[3];       /* IBM_BC_* per direction, high face */
+    int precision;      /* IBM_FP64 or IBM_FP32 */
+} ibm_grid_desc;
+
+typedef struct {
+    int kind;           /* IBM_GEOM_* */
+    int nparam;         /* number of valid entries in param */
+    double param[32];   /* kind-specific parameters (see the enum) */
+} ibm_geom_desc;
+
+typedef struct {
+    void* u[3];         /* device: u, v, w fields, N elements of the grid precision each;
+                           u[2] unused in 2D.  Hold the current velocity between calls. */
+    void* p;            /* device: pressure, N elements */
+    void* work;         /* device workspace, 256-byte aligned, ibm_workspace_bytes() bytes */
+    size_t work_bytes;
+} ibm_buffers;
+
+typedef struct {
+    double nu;          /* kinematic viscosity (1/Re) */
+    double dt;          /* time step */
+    double g[3];        /* uniform body force */
+    int bmode;          /* IBM_B_* */
+    int flow_mode;      /* IBM_FLOW_* */
+    double target_flux; /* IBM_FLOW_CONST_FLUX: target volume integral of u over internal u points */
+    double wall_u[3];   /* velocity of the moving surface (see the geometry kinds) */
+    int no_ibm;         /* 1: lambda := 0, no wall source (the staircase baseline) */
+} ibm_physics;
+
+typedef struct {
+    double div_l2;      /* sqrt(mean over cells of (D u)^2) */
+    double div_linf;    /* max over cells |D u| */
+    double cfl;         /* dt * sum_c max_internal |u_c| / d_c */
+    double flux[3];     /* sum over internal points of u_c * cell volume */
+    double ke;          /* 1/2 sum over internal points of u_c^2 * cell volume */
+    double pi;          /* forcing of the last constant-flow-rate substage */
+    long long step;     /* completed full steps */
+    int status;         /* IBM_OK or IBM_E_DIVERGED */
+} ibm_diag;
+
+typedef struct {
+    const char* name;   /* kernel name */
+    int launches;       /* timed launches since the last reset */
+    double total_ms;    /* summed CUDA-event duration */
+} ibm_kernel_time;
+
+typedef struct ibm_solver ibm_solver;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int ibm_version(void);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* ibm_last_error(void);
+
+/* Bytes of device workspace a grid needs (mask, RK history, predictor,
+ * Poisson spectrum and pivots, cuFFT work area, reduction scratch).
+ * Creates and destroys a temporary cuFFT plan to size its work area, so a
+ * CUDA device must be present.  Blocking. */
+ibm_status ibm_workspace_bytes(const ibm_grid_desc* grid, size_t* bytes);
+
+/* Classify the staggered grids against the geometry (Sec. 3.3) and prepare
+ * the Poisson solver.  `stream` is a cudaStream_t (NULL = legacy default).
+ * On success *out holds a new handle.  Copies grid and geometry; keeps the
+ * buffer pointers.  Blocking: the IBM-point counts are read back. */
+ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* geom,
+                              const ibm_buffers* buffers, void* stream, ibm_solver** out);
+
+/* Device bytes the weights need (IBM-point lists, lambda, wall source and
+ * per-stage coefficients), known after ibm_setup_geometry. */
+ibm_status ibm_weights_bytes(const ibm_solver* h, size_t* bytes);
+
+/* Compute delta per crossed stencil arm, lambda (Sec. 2.2, Eq. lambda) and
+ * the per-stage implicit coefficients (Eq. Bexpr, rk3-rai) into the caller's
+ * device buffer `weights` (256-byte aligned).  May be called again with new
+ * physics.  Blocking (reads back the flux-control sums). */
+ibm_status ibm_build_weights(ibm_solver* h, const ibm_physics* phys, void* weights,
+                             size_t weights_bytes);
+
+/* Advance nsteps full RK3 steps (3 substages, each: predictor with the
+ * implicit IBM division, then projection).  Asynchronous on the stream. */
+ibm_status ibm_step(ibm_solver* h, int nsteps, unsigned flags);
+
+/* Zero the velocity outside the fluid and project it onto divergence-free
+ * fields (initial conditions); the pressure is unchanged.  Asynchronous. */
+ibm_status ibm_project(ibm_solver* h);
+
+/* Solve D G phi = rhs on the full box (x, z periodic, homogeneous Neumann in
+ * y), zero box mean; `rhs_inout` is a device array of N grid-precision values
+ * overwritten by phi.  The rhs must sum to zero.  Asynchronous. */
+ibm_status ibm_poisson(ibm_solver* h, void* rhs_inout);
+
+/* Norms, CFL, flux, kinetic energy of the current fields.  Blocking; returns
+ * IBM_E_DIVERGED (and fills out->status) if a field is not finite. */
+ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out);
+
+/* Blocking copies of the classification: host_mask (N bytes, or NULL), the
+ * IBM-point lists (ascending linear index; host_idx[c] may be NULL) and
+ * their lengths counts[3] (always written). */
+ibm_status ibm_get_classification(ibm_solver* h, unsigned char* host_mask, int* host_idx[3],
+                                  int counts[3]);
+
+/* Blocking copies of lambda and the wall source per IBM point, in list order
+ * (either array pointer may be NULL).  Needs ibm_build_weights first. */
+ibm_status ibm_get_weights(ibm_solver* h, double* host_lambda[3], double* host_src[3]);
+
+/* Bytes of a state snapshot (u, v, w, p, RK history, step counter). */
+ibm_status ibm_state_bytes(const ibm_solver* h, size_t* bytes);
+/* Blocking copy of the state to / from a host buffer of ibm_state_bytes(). */
+ibm_status ibm_export_state(ibm_solver* h, void* host, size_t bytes);
+ibm_status ibm_import_state(ibm_solver* h, const void* host, size_t bytes);
+
+/* Kernel timing with CUDA events on the solver's stream: enable (1) or
+ * disable (0); enabling resets the counters.  Not available in graph mode. */
+ibm_status ibm_timing(ibm_solver* h, int enable);
+/* Blocking: per-kernel launches and summed durations since the last reset. */
+ibm_status ibm_get_timing(ibm_solver* h, ibm_kernel_time* out, int max, int* count);
+/* Kernels this library has launched through this handle (a running count). */
+ibm_status ibm_launch_count(const ibm_solver* h, long long* count);
+
+/* Release host metadata, events, graphs and cuFFT plans; never frees the
+ * caller's device buffers.  Safe on NULL. */
+void ibm_destroy(ibm_solver* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBM_H */

@@ -1,0 +1,565 @@
+// C ABI of libibm (declared in include/ibm.h): argument checking, workspace
+// carve-out, cuFFT plans, stream capture, event timing and state export.
+#include "common.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr size_t ALIGN = 256;
+constexpr int MOM_BY2 = 8, MOM_BY3 = 4, MOM_BZ3 = 2;   // momentum block shape (x is always 32)
+constexpr int DIAG_PART = 304 * 12;
+constexpr int SCAN_CH = 512 * 8;
+constexpr uint64_t STATE_MAGIC = 0x31534d4249ull;     // "IBMS1"
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+ibm_status check_grid(const ibm_grid_desc* d) {
+    if (!d) return ibm_set_error(IBM_E_INVALID, "grid descriptor is NULL");
+    if (d->ndim != 2 && d->ndim != 3) return ibm_set_error(IBM_E_INVALID, "ndim must be 2 or 3");
+    for (int i = 0; i < 3; ++i) {
+        if (d->n[i] < 1) return ibm_set_error(IBM_E_INVALID, "n[d] must be >= 1");
+        if (!(d->L[i] > 0.0) || !std::isfinite(d->L[i])) return ibm_set_error(IBM_E_INVALID, "L[d] must be > 0");
+        if (!std::isfinite(d->origin[i])) return ibm_set_error(IBM_E_INVALID, "origin must be finite");
+    }
+    if (d->ndim == 2 && d->n[2] != 1) return ibm_set_error(IBM_E_INVALID, "2D grids have n[2] == 1");
+    if (d->n[1] < 2) return ibm_set_error(IBM_E_INVALID, "ny must be >= 2");
+    long long N = (long long)d->n[0] * d->n[1] * d->n[2];
+    if (N >= (1ll << 31)) return ibm_set_error(IBM_E_INVALID, "more than 2^31-1 cells");
+    if (d->precision != IBM_FP64 && d->precision != IBM_FP32) return ibm_set_error(IBM_E_INVALID, "bad precision");
+    for (int dd : {0, 2})
+        if (d->bc_lo[dd] != IBM_BC_PERIODIC || d->bc_hi[dd] != IBM_BC_PERIODIC)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "x and z must be periodic in this build");
+    for (int b : {d->bc_lo[1], d->bc_hi[1]})
+        if (b != IBM_BC_NOSLIP && b != IBM_BC_FREESLIP)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "y faces must be no-slip or free-slip walls in this build");
+    return IBM_OK;
+}
+
+GridP make_gridp(const ibm_grid_desc* d) {
+    GridP g;
+    g.nx = d->n[0];
+    g.ny = d->n[1];
+    g.nz = d->n[2];
+    g.ndim = d->ndim;
+    g.ncomp = d->ndim == 3 ? 3 : 2;
+    g.nsegx = (g.nx + IBM_WARP - 1) / IBM_WARP;
+    g.nxh = g.nx / 2 + 1;
+    g.N = (long long)g.nx * g.ny * g.nz;
+    g.dx = d->L[0] / d->n[0];
+    g.dy = d->L[1] / d->n[1];
+    g.dz = d->L[2] / d->n[2];
+    g.ox = d->origin[0];
+    g.oy = d->origin[1];
+    g.oz = d->origin[2];
+    g.sig_lo = d->bc_lo[1] == IBM_BC_NOSLIP ? -1.0 : 1.0;
+    g.sig_hi = d->bc_hi[1] == IBM_BC_NOSLIP ? -1.0 : 1.0;
+    return g;
+}
+
+int momentum_blocks(const GridP& g) {
+    if (g.ndim == 3) return g.nsegx * ((g.ny + MOM_BY3 - 1) / MOM_BY3) * ((g.nz + MOM_BZ3 - 1) / MOM_BZ3);
+    return g.nsegx * ((g.ny + MOM_BY2 - 1) / MOM_BY2) * g.nz;
+}
+
+// Creates forward/inverse plans with auto-allocation off; returns the larger work size.
+ibm_status make_plans(const GridP& g, int prec, cufftHandle* pf, cufftHandle* pi, size_t* work) {
+    cufftType tf = prec == IBM_FP64 ? CUFFT_D2Z : CUFFT_R2C;
+    cufftType ti = prec == IBM_FP64 ? CUFFT_Z2D : CUFFT_C2R;
+    long long nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
+    size_t wf = 0, wi = 0;
+    if (cufftCreate(pf) != CUFFT_SUCCESS || cufftCreate(pi) != CUFFT_SUCCESS)
+        return ibm_set_error(IBM_E_CUDA, "cufftCreate failed");
+    cufftSetAutoAllocation(*pf, 0);
+    cufftSetAutoAllocation(*pi, 0);
+    cufftResult r1, r2;
+    if (g.nz > 1) {
+        long long n[2] = {nz, nx};
+        long long ie[2] = {nz, ny * nx};
+        long long oe[2] = {nz, ny * nxh};
+        r1 = cufftMakePlanMany64(*pf, 2, n, ie, 1, nx, oe, 1, nxh, tf, ny, &wf);
+        r2 = cufftMakePlanMany64(*pi, 2, n, oe, 1, nxh, ie, 1, nx, ti, ny, &wi);
+    } else {
+        long long n[1] = {nx};
+        long long ie[1] = {nx};
+        long long oe[1] = {nxh};
+        r1 = cufftMakePlanMany64(*pf, 1, n, ie, 1, nx, oe, 1, nxh, tf, ny * nz, &wf);
+        r2 = cufftMakePlanMany64(*pi, 1, n, oe, 1, nxh, ie, 1, nx, ti, ny * nz, &wi);
+    }
+    if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS) {
+        cufftDestroy(*pf);
+        cufftDestroy(*pi);
+        return ibm_set_error(IBM_E_CUDA, "cufftMakePlanMany64 failed (code " + std::to_string((int)r1) + "/" +
+                                             std::to_string((int)r2) + ")");
+    }
+    *work = wf > wi ? wf : wi;
+    return IBM_OK;
+}
+
+// Carve the workspace; with base == nullptr only the size is computed.
+size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* base) {
+    size_t off = 0;
+    size_t esz = prec == IBM_FP64 ? 8 : 4;
+    long long nseg = (long long)g.nsegx * g.ny * g.nz;
+    long long nspec = (long long)g.nz * g.ny * g.nxh;
+    int nscanb = (int)((nseg + SCAN_CH - 1) / SCAN_CH);
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += align_up(bytes > 0 ? bytes : 1);
+        return p;
+    };
+    char* mask = take(g.N);
+    char* velbits = take(g.N);
+    char* segcnt[3];
+    char* segoff[3];
+    for (int c = 0; c < 3; ++c) segcnt[c] = take(nseg * sizeof(int));
+    for (int c = 0; c < 3; ++c) segoff[c] = take(nseg * sizeof(int));
+    char* scan_tmp = take(3 * (size_t)nscanb * sizeof(int));
+    char* counts = take(4 * sizeof(int));
+    char* ustar[3] = {nullptr, nullptr, nullptr};
+    char* Nh[3] = {nullptr, nullptr, nullptr};
+    for (int c = 0; c < g.ncomp; ++c) ustar[c] = take(g.N * esz);
+    for (int c = 0; c < g.ncomp; ++c) Nh[c] = take(g.N * esz);
+    char* rhs = take(g.N * esz);
+    char* spec = take(nspec * 2 * esz);
+    char* piv = take(nspec * sizeof(double));
+    char* dtemp = prec == IBM_FP32 ? take(nspec * 2 * sizeof(double)) : nullptr;
+    char* fftw = take(fft_work);
+    int npart = momentum_blocks(g);
+    if (npart < DIAG_PART) npart = DIAG_PART;
+    if (npart < 120 * 4) npart = 120 * 4;
+    char* partials = take((size_t)npart * sizeof(double));
+    char* scal = take(16 * sizeof(double));
+    if (h && base) {
+        h->mask = (uint8_t*)mask;
+        h->velbits = (uint8_t*)velbits;
+        for (int c = 0; c < 3; ++c) {
+            h->segcnt[c] = (int*)segcnt[c];
+            h->segoff[c] = (int*)segoff[c];
+            h->ustar[c] = ustar[c];
+            h->Nh[c] = Nh[c];
+        }
+        h->scan_tmp = (int*)scan_tmp;
+        h->d_counts = (int*)counts;
+        h->rhs = rhs;
+        h->spec = spec;
+        h->pivots = (double*)piv;
+        h->dtemp = dtemp;
+        h->fft_work = fftw;
+        h->partials = (double*)partials;
+        h->npartials = npart;
+        h->scal = (double*)scal;
+    }
+    return off;
+}
+
+size_t weights_layout(ibm_solver* h, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += align_up(bytes > 0 ? bytes : 1);
+        return p;
+    };
+    for (int c = 0; c < 3; ++c) {
+        size_t n = (size_t)h->counts[c];
+        char* idx = take(n * sizeof(int));
+        char* lam = take(n * sizeof(double));
+        char* src = take(n * sizeof(double));
+        char* coef = take(3 * n * 4 * h->esz);
+        if (base) {
+            h->idx[c] = (int*)idx;
+            h->lam[c] = (double*)lam;
+            h->src[c] = (double*)src;
+            h->coef[c] = coef;
+        }
+    }
+    return off;
+}
+
+ibm_status check_handle(const ibm_solver* h) {
+    if (!h) return ibm_set_error(IBM_E_INVALID, "handle is NULL");
+    if (h->failed) return ibm_set_error(IBM_E_STATE, "handle failed after an earlier CUDA error");
+    return IBM_OK;
+}
+
+void drop_graph(ibm_solver* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_ready = false;
+}
+
+}  // namespace
+
+ibm_status ibm_set_error(ibm_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+void timer_begin(ibm_solver* h, const char* name, cudaEvent_t* ev) {
+    (void)name;
+    *ev = nullptr;
+    if (!h->timing) return;
+    if (cudaEventCreate(ev) != cudaSuccess) { *ev = nullptr; return; }
+    cudaEventRecord(*ev, h->stream);
+}
+
+void timer_end(ibm_solver* h, cudaEvent_t a, const char* name) {
+    if (!h->timing || !a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEventRecord(b, h->stream);
+    h->timers.push_back(KernelTimer{name, a, b});
+}
+
+extern "C" {
+
+int ibm_version(void) { return 10000; }
+
+const char* ibm_last_error(void) { return g_last_error.c_str(); }
+
+ibm_status ibm_workspace_bytes(const ibm_grid_desc* grid, size_t* bytes) {
+    ibm_status st = check_grid(grid);
+    if (st != IBM_OK) return st;
+    if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");
+    GridP g = make_gridp(grid);
+    cufftHandle pf, pi;
+    size_t work = 0;
+    st = make_plans(g, grid->precision, &pf, &pi, &work);
+    if (st != IBM_OK) return st;
+    cufftDestroy(pf);
+    cufftDestroy(pi);
+    *bytes = carve(nullptr, g, grid->precision, work, nullptr);
+    return IBM_OK;
+}
+
+ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* geom, const ibm_buffers* buffers,
+                              void* stream, ibm_solver** out) {
+    ibm_status st = check_grid(grid);
+    if (st != IBM_OK) return st;
+    if (!geom || !buffers || !out) return ibm_set_error(IBM_E_INVALID, "NULL argument");
+    *out = nullptr;
+    int kind = geom->kind;
+    int need = kind == IBM_GEOM_PLANES ? 2 : kind == IBM_GEOM_CYLINDER ? 4 : kind == IBM_GEOM_SPHERE ? 5
+             : kind == IBM_GEOM_SINE_WALL ? 4 : 0;
+    if (kind == IBM_GEOM_TUBES || kind == IBM_GEOM_SAMPLED)
+        return ibm_set_error(IBM_E_UNSUPPORTED, "geometry kind not built");
+    if (kind < IBM_GEOM_NONE || kind > IBM_GEOM_SAMPLED) return ibm_set_error(IBM_E_INVALID, "bad geometry kind");
+    if (geom->nparam < need) return ibm_set_error(IBM_E_INVALID, "too few geometry parameters");
+    if (kind == IBM_GEOM_SINE_WALL && !(geom->param[2] != 0.0))
+        return ibm_set_error(IBM_E_INVALID, "sine wall wavelength must be nonzero");
+    if ((kind == IBM_GEOM_CYLINDER && std::fabs(geom->param[3]) != 1.0) ||
+        (kind == IBM_GEOM_SPHERE && std::fabs(geom->param[4]) != 1.0))
+        return ibm_set_error(IBM_E_INVALID, "body sign s must be +1 or -1");
+    GridP g = make_gridp(grid);
+    for (int c = 0; c < g.ncomp; ++c)
+        if (!buffers->u[c]) return ibm_set_error(IBM_E_INVALID, "velocity buffer is NULL");
+    if (!buffers->p || !buffers->work) return ibm_set_error(IBM_E_INVALID, "pressure or workspace buffer is NULL");
+    if ((uintptr_t)buffers->work % ALIGN) return ibm_set_error(IBM_E_INVALID, "workspace must be 256-byte aligned");
+
+    ibm_solver* h = new (std::nothrow) ibm_solver();
+    if (!h) return ibm_set_error(IBM_E_INVALID, "host allocation failed");
+    h->grid = *grid;
+    h->geom = *geom;
+    h->buf = *buffers;
+    h->stream = (cudaStream_t)stream;
+    h->gp = g;
+    h->geo.kind = kind;
+    for (int q = 0; q < 8; ++q) h->geo.p[q] = q < geom->nparam ? geom->param[q] : 0.0;
+    h->prec = grid->precision;
+    h->esz = grid->precision == IBM_FP64 ? 8 : 4;
+    h->N = g.N;
+    h->nspec = (long long)g.nz * g.ny * g.nxh;
+    h->nseg = (long long)g.nsegx * g.ny * g.nz;
+
+    size_t work = 0;
+    st = make_plans(g, h->prec, &h->plan_f, &h->plan_i, &work);
+    if (st != IBM_OK) { delete h; return st; }
+    h->plans = true;
+    size_t need_bytes = carve(nullptr, g, h->prec, work, nullptr);
+    if (buffers->work_bytes < need_bytes) {
+        ibm_destroy(h);
+        return ibm_set_error(IBM_E_NOMEM, "workspace too small: need " + std::to_string(need_bytes) + " bytes");
+    }
+    carve(h, g, h->prec, work, (char*)buffers->work);
+    h->fft_work_bytes = work;
+    if (cufftSetWorkArea(h->plan_f, h->fft_work) != CUFFT_SUCCESS ||
+        cufftSetWorkArea(h->plan_i, h->fft_work) != CUFFT_SUCCESS ||
+        cufftSetStream(h->plan_f, h->stream) != CUFFT_SUCCESS || cufftSetStream(h->plan_i, h->stream) != CUFFT_SUCCESS) {
+        ibm_destroy(h);
+        return ibm_set_error(IBM_E_CUDA, "cufft work area / stream setup failed");
+    }
+    st = geom_classify(h);
+    if (st == IBM_OK) st = geom_pivots(h);
+    if (st == IBM_OK) {
+        cudaError_t e = cudaMemsetAsync(h->scal, 0, 16 * sizeof(double), h->stream);
+        if (e != cudaSuccess) st = ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e));
+    }
+    if (st != IBM_OK) {
+        ibm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return IBM_OK;
+}
+
+ibm_status ibm_weights_bytes(const ibm_solver* h, size_t* bytes) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");
+    *bytes = weights_layout(const_cast<ibm_solver*>(h), nullptr);
+    return IBM_OK;
+}
+
+ibm_status ibm_build_weights(ibm_solver* h, const ibm_physics* phys, void* weights, size_t weights_bytes) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!phys || !weights) return ibm_set_error(IBM_E_INVALID, "NULL argument");
+    if (!(phys->dt > 0.0) || !(phys->nu >= 0.0) || !std::isfinite(phys->dt) || !std::isfinite(phys->nu))
+        return ibm_set_error(IBM_E_INVALID, "need dt > 0 and nu >= 0");
+    if (phys->bmode < IBM_B_EXACT || phys->bmode > IBM_B_TAYLOR2) return ibm_set_error(IBM_E_INVALID, "bad bmode");
+    if (phys->flow_mode != IBM_FLOW_FORCED && phys->flow_mode != IBM_FLOW_CONST_FLUX)
+        return ibm_set_error(IBM_E_INVALID, "bad flow_mode");
+    if ((uintptr_t)weights % ALIGN) return ibm_set_error(IBM_E_INVALID, "weights must be 256-byte aligned");
+    size_t need = weights_layout(h, nullptr);
+    if (weights_bytes < need) return ibm_set_error(IBM_E_NOMEM, "weights buffer too small: need " + std::to_string(need));
+    drop_graph(h);
+    h->phys = *phys;
+    weights_layout(h, (char*)weights);
+    st = geom_build_lists_and_weights(h);
+    if (st == IBM_OK) st = geom_stage_coefficients(h);
+    if (st != IBM_OK) return st;
+    if (phys->flow_mode == IBM_FLOW_CONST_FLUX)
+        for (int k = 0; k < 3; ++k)
+            if (!(h->S[k] > 0.0)) return ibm_set_error(IBM_E_INVALID, "constant flow rate needs internal u points");
+    h->weights_ready = true;
+    return IBM_OK;
+}
+
+ibm_status ibm_step(ibm_solver* h, int nsteps, unsigned flags) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!h->weights_ready) return ibm_set_error(IBM_E_STATE, "ibm_build_weights has not run");
+    if (nsteps < 0) return ibm_set_error(IBM_E_INVALID, "nsteps < 0");
+    if (flags & IBM_STEP_PREDICTOR_ONLY) {
+        drop_graph(h);
+        return run_substage(h, 0, true);
+    }
+    if (flags & IBM_STEP_GRAPH) {
+        if (h->timing) return ibm_set_error(IBM_E_STATE, "timing is not available in graph mode");
+        if (!h->graph_ready) {
+            cudaGraph_t graph;
+            IBM_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            long long before = h->launches;
+            for (int k = 0; k < 3 && st == IBM_OK; ++k) st = run_substage(h, k, false);
+            cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+            if (st != IBM_OK) return st;
+            if (e != cudaSuccess) { h->failed = true; return ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e)); }
+            e = cudaGraphInstantiate(&h->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { h->failed = true; return ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e)); }
+            h->graph_launches = h->launches - before;
+            h->launches = before;
+            h->graph_ready = true;
+        }
+        for (int n = 0; n < nsteps; ++n) {
+            IBM_CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
+            h->launches += h->graph_launches;
+            h->steps++;
+        }
+        return IBM_OK;
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        for (int k = 0; k < 3; ++k) {
+            st = run_substage(h, k, false);
+            if (st != IBM_OK) return st;
+        }
+        h->steps++;
+    }
+    return IBM_OK;
+}
+
+ibm_status ibm_project(ibm_solver* h) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    return run_project(h);
+}
+
+ibm_status ibm_poisson(ibm_solver* h, void* rhs_inout) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!rhs_inout) return ibm_set_error(IBM_E_INVALID, "rhs is NULL");
+    return run_poisson(h, rhs_inout);
+}
+
+ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!out) return ibm_set_error(IBM_E_INVALID, "out is NULL");
+    double r[16];
+    st = run_diagnostics(h, r);
+    if (st != IBM_OK) return st;
+    const GridP& g = h->gp;
+    double dV = g.dx * g.dy * (g.ndim == 3 ? g.dz : 1.0);
+    const double* s = r + 4;
+    std::memset(out, 0, sizeof(*out));
+    out->div_l2 = std::sqrt(s[0] / (double)g.N);
+    out->div_linf = s[1];
+    double d[3] = {g.dx, g.dy, g.dz};
+    double cfl = 0.0;
+    for (int c = 0; c < g.ncomp; ++c) {
+        cfl += s[2 + c] / d[c];
+        out->flux[c] = s[5 + c] * dV;
+        out->ke += 0.5 * s[8 + c] * dV;
+    }
+    out->cfl = cfl * h->phys.dt;
+    out->pi = r[0];
+    out->step = h->steps;
+    bool finite = s[11] == 0.0 && std::isfinite(out->div_l2) && std::isfinite(out->ke);
+    out->status = finite ? IBM_OK : IBM_E_DIVERGED;
+    if (!finite) return ibm_set_error(IBM_E_DIVERGED, "non-finite values in the fields");
+    return IBM_OK;
+}
+
+ibm_status ibm_get_classification(ibm_solver* h, unsigned char* host_mask, int* host_idx[3], int counts[3]) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!counts) return ibm_set_error(IBM_E_INVALID, "counts is NULL");
+    for (int c = 0; c < 3; ++c) counts[c] = h->counts[c];
+    if (host_mask)
+        IBM_CUDA_TRY(cudaMemcpyAsync(host_mask, h->mask, h->N, cudaMemcpyDeviceToHost, h->stream));
+    if (host_idx) {
+        for (int c = 0; c < 3; ++c) {
+            if (!host_idx[c] || h->counts[c] == 0) continue;
+            if (!h->weights_ready) return ibm_set_error(IBM_E_STATE, "lists are built by ibm_build_weights");
+            IBM_CUDA_TRY(cudaMemcpyAsync(host_idx[c], h->idx[c], h->counts[c] * sizeof(int), cudaMemcpyDeviceToHost,
+                                         h->stream));
+        }
+    }
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return IBM_OK;
+}
+
+ibm_status ibm_get_weights(ibm_solver* h, double* host_lambda[3], double* host_src[3]) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!h->weights_ready) return ibm_set_error(IBM_E_STATE, "ibm_build_weights has not run");
+    for (int c = 0; c < 3; ++c) {
+        if (h->counts[c] == 0) continue;
+        if (host_lambda && host_lambda[c])
+            IBM_CUDA_TRY(cudaMemcpyAsync(host_lambda[c], h->lam[c], h->counts[c] * sizeof(double),
+                                         cudaMemcpyDeviceToHost, h->stream));
+        if (host_src && host_src[c])
+            IBM_CUDA_TRY(cudaMemcpyAsync(host_src[c], h->src[c], h->counts[c] * sizeof(double), cudaMemcpyDeviceToHost,
+                                         h->stream));
+    }
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return IBM_OK;
+}
+
+ibm_status ibm_state_bytes(const ibm_solver* h, size_t* bytes) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");
+    *bytes = 64 + (size_t)(h->gp.ncomp + 1) * h->N * h->esz;
+    return IBM_OK;
+}
+
+ibm_status ibm_export_state(ibm_solver* h, void* host, size_t bytes) {
+    size_t need = 0;
+    ibm_status st = ibm_state_bytes(h, &need);
+    if (st != IBM_OK) return st;
+    if (!host || bytes < need) return ibm_set_error(IBM_E_INVALID, "host buffer NULL or too small");
+    uint64_t hdr[8] = {STATE_MAGIC, (uint64_t)h->prec, (uint64_t)h->N, (uint64_t)h->gp.ncomp, (uint64_t)h->steps, 0, 0, 0};
+    std::memcpy(host, hdr, sizeof(hdr));
+    char* p = (char*)host + 64;
+    size_t fb = h->N * h->esz;
+    for (int c = 0; c < h->gp.ncomp; ++c, p += fb)
+        IBM_CUDA_TRY(cudaMemcpyAsync(p, h->buf.u[c], fb, cudaMemcpyDeviceToHost, h->stream));
+    IBM_CUDA_TRY(cudaMemcpyAsync(p, h->buf.p, fb, cudaMemcpyDeviceToHost, h->stream));
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return IBM_OK;
+}
+
+ibm_status ibm_import_state(ibm_solver* h, const void* host, size_t bytes) {
+    size_t need = 0;
+    ibm_status st = ibm_state_bytes(h, &need);
+    if (st != IBM_OK) return st;
+    if (!host || bytes < need) return ibm_set_error(IBM_E_INVALID, "host buffer NULL or too small");
+    uint64_t hdr[8];
+    std::memcpy(hdr, host, sizeof(hdr));
+    if (hdr[0] != STATE_MAGIC || hdr[1] != (uint64_t)h->prec || hdr[2] != (uint64_t)h->N ||
+        hdr[3] != (uint64_t)h->gp.ncomp)
+        return ibm_set_error(IBM_E_INVALID, "state snapshot does not match this solver");
+    const char* p = (const char*)host + 64;
+    size_t fb = h->N * h->esz;
+    for (int c = 0; c < h->gp.ncomp; ++c, p += fb)
+        IBM_CUDA_TRY(cudaMemcpyAsync(h->buf.u[c], p, fb, cudaMemcpyHostToDevice, h->stream));
+    IBM_CUDA_TRY(cudaMemcpyAsync(h->buf.p, p, fb, cudaMemcpyHostToDevice, h->stream));
+    h->steps = (long long)hdr[4];
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return IBM_OK;
+}
+
+ibm_status ibm_timing(ibm_solver* h, int enable) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    for (auto& t : h->timers) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    h->timers.clear();
+    h->timing = enable != 0;
+    return IBM_OK;
+}
+
+ibm_status ibm_get_timing(ibm_solver* h, ibm_kernel_time* out, int max, int* count) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!count) return ibm_set_error(IBM_E_INVALID, "count is NULL");
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    std::vector<ibm_kernel_time> agg;
+    for (auto& t : h->timers) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        bool found = false;
+        for (auto& a : agg)
+            if (std::strcmp(a.name, t.name) == 0) {
+                a.launches++;
+                a.total_ms += ms;
+                found = true;
+            }
+        if (!found) agg.push_back(ibm_kernel_time{t.name, 1, (double)ms});
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    h->timers.clear();
+    *count = (int)agg.size();
+    for (int q = 0; q < (int)agg.size() && q < max && out; ++q) out[q] = agg[q];
+    return IBM_OK;
+}
+
+ibm_status ibm_launch_count(const ibm_solver* h, long long* count) {
+    if (!h || !count) return ibm_set_error(IBM_E_INVALID, "NULL argument");
+    *count = h->launches;
+    return IBM_OK;
+}
+
+void ibm_destroy(ibm_solver* h) {
+    if (!h) return;
+    for (auto& t : h->timers) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    drop_graph(h);
+    if (h->plans) {
+        cufftDestroy(h->plan_f);
+        cufftDestroy(h->plan_i);
+    }
+    delete h;
+}
+
+}  // extern "C"

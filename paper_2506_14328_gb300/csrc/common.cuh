@@ -1,0 +1,185 @@
+// Shared declarations of libibm: kernel parameter blocks, small device helpers,
+// and the host-side solver handle.  Layout conventions are those of include/ibm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/ibm.h"
+
+#define IBM_WARP 32
+
+// ---------------------------------------------------------------------------
+// Kernel parameter blocks (passed by value)
+// ---------------------------------------------------------------------------
+struct GridP {
+    int nx, ny, nz;
+    int ndim, ncomp;
+    int nsegx;              // x segments of 32 points per row
+    int nxh;                // nx/2 + 1 (half spectrum)
+    long long N;            // cells
+    double dx, dy, dz;
+    double ox, oy, oz;
+    double sig_lo, sig_hi;  // tangential ghost factor at the y walls (-1 no-slip, +1 free-slip)
+};
+
+struct GeomP {
+    int kind;
+    double p[8];
+};
+
+// The IBM coefficients of one stage for one component: indexed by list
+// position; segoff gives the list position of the first IBM point of every
+// 32-point x segment (lists are sorted by linear index).
+template <typename T> struct Coef4 { T a, b, s, pad; };
+
+template <typename T> struct IbmStage {
+    const int* segoff[3];
+    const Coef4<T>* coef[3];   // already offset to the stage
+};
+
+template <typename T> struct StageP {
+    T dta, dtb;        // dt a_k, dt b_k
+    T ckdt;            // c_k dt
+    T nu;
+    T g[3];
+    T idx, idy, idz;   // 1/dx ...
+    T idx2, idy2, idz2;
+    int read_prev;     // stage k > 1: add b_k N^{k-2}
+    int write_n;       // stage k < 3: store N^{k-1}
+    int flux_sum;      // accumulate the predictor flux (constant flow rate)
+};
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side handle
+// ---------------------------------------------------------------------------
+struct KernelTimer {
+    const char* name;   // a string literal
+    cudaEvent_t a, b;
+};
+
+struct ibm_solver {
+    ibm_grid_desc grid;
+    ibm_geom_desc geom;
+    ibm_buffers buf;
+    cudaStream_t stream = nullptr;
+    GridP gp;
+    GeomP geo;
+    int prec = IBM_FP64;
+    size_t esz = 8;            // field element size
+    long long N = 0;
+    long long nspec = 0;       // nz * ny * nxh
+    long long nseg = 0;
+
+    // workspace carve-out
+    uint8_t* mask = nullptr;
+    uint8_t* velbits = nullptr;
+    int* segcnt[3] = {nullptr, nullptr, nullptr};
+    int* segoff[3] = {nullptr, nullptr, nullptr};
+    int* scan_tmp = nullptr;
+    int* d_counts = nullptr;
+    void* ustar[3] = {nullptr, nullptr, nullptr};
+    void* Nh[3] = {nullptr, nullptr, nullptr};
+    void* rhs = nullptr;
+    void* spec = nullptr;
+    double* pivots = nullptr;
+    void* dtemp = nullptr;
+    void* fft_work = nullptr;
+    double* partials = nullptr;
+    double* scal = nullptr;    // device scalars: [0] = Pi of the current substage
+    size_t fft_work_bytes = 0;
+    int npartials = 0;
+
+    int counts[3] = {0, 0, 0};
+
+    // weights
+    bool weights_ready = false;
+    ibm_physics phys;
+    int* idx[3] = {nullptr, nullptr, nullptr};
+    double* lam[3] = {nullptr, nullptr, nullptr};
+    double* src[3] = {nullptr, nullptr, nullptr};
+    void* coef[3] = {nullptr, nullptr, nullptr};
+    double S[3] = {0, 0, 0};   // flux-control response per stage
+    double last_pi = 0.0;
+
+    cufftHandle plan_f = 0, plan_i = 0;
+    bool plans = false;
+
+    bool failed = false;
+    long long steps = 0;
+    long long launches = 0;
+
+    bool timing = false;
+    std::vector<KernelTimer> timers;
+
+    cudaGraphExec_t graph = nullptr;
+    bool graph_ready = false;
+    long long graph_launches = 0;   // kernels of this library in one captured step
+};
+
+// ---------------------------------------------------------------------------
+// Host entry points between translation units
+// ---------------------------------------------------------------------------
+ibm_status ibm_set_error(ibm_status st, const std::string& msg);
+
+// geometry.cu
+ibm_status geom_classify(ibm_solver* h);
+ibm_status geom_build_lists_and_weights(ibm_solver* h);
+ibm_status geom_stage_coefficients(ibm_solver* h);
+ibm_status geom_pivots(ibm_solver* h);
+
+// step.cu
+ibm_status run_substage(ibm_solver* h, int k, bool predictor_only);
+ibm_status run_project(ibm_solver* h);
+ibm_status run_poisson(ibm_solver* h, void* rhs_inout);
+ibm_status run_diagnostics(ibm_solver* h, double* out11);
+
+// timing hooks used by both
+void timer_begin(ibm_solver* h, const char* name, cudaEvent_t* ev);
+void timer_end(ibm_solver* h, cudaEvent_t ev_begin, const char* name);
+
+#define IBM_CUDA_TRY(expr)                                                                  \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            h->failed = true;                                                               \
+            return ibm_set_error(IBM_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+        }                                                                                   \
+    } while (0)
+
+#define IBM_LAUNCH_CHECK()                                                                  \
+    do {                                                                                    \
+        cudaError_t _e = cudaGetLastError();                                                \
+        if (_e != cudaSuccess) {                                                            \
+            h->failed = true;                                                               \
+            return ibm_set_error(IBM_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(_e)); \
+        }                                                                                   \
+        h->launches++;                                                                      \
+    } while (0)

@@ -1,0 +1,556 @@
+// Setup kernels: staircase classification, IBM-point lists, weights (delta,
+// lambda, wall source), per-stage implicit coefficients and Poisson pivots.
+//
+// This translation unit is compiled with -fmad=false and writes its level-set
+// arithmetic with explicitly rounded operations, so the sign of phi at every
+// grid point is the same as an FP64 evaluation of the same formula in the
+// same order on any IEEE machine (classification is bit-exact).
+#include "common.cuh"
+
+#include <cmath>
+
+namespace {
+
+constexpr double TWO_PI = 6.283185307179586;
+
+// ---------------------------------------------------------------------------
+// Level set: phi < 0 fluid, phi >= 0 solid (Sec. 3.3, "true boundary")
+// ---------------------------------------------------------------------------
+__device__ double phi_at(const GeomP& g, double x, double y, double z) {
+    const double* p = g.p;
+    switch (g.kind) {
+        case IBM_GEOM_PLANES:
+            return fmax(__dsub_rn(p[0], y), __dsub_rn(y, p[1]));
+        case IBM_GEOM_CYLINDER: {
+            double dx = __dsub_rn(x, p[0]);
+            double dy = __dsub_rn(y, p[1]);
+            double q = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            return __dmul_rn(p[3], __dsub_rn(q, __dmul_rn(p[2], p[2])));
+        }
+        case IBM_GEOM_SPHERE: {
+            double dx = __dsub_rn(x, p[0]);
+            double dy = __dsub_rn(y, p[1]);
+            double dz = __dsub_rn(z, p[2]);
+            double q = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            return __dmul_rn(p[4], __dsub_rn(q, __dmul_rn(p[3], p[3])));
+        }
+        case IBM_GEOM_SINE_WALL: {
+            double yw = __dadd_rn(p[0], __dmul_rn(p[1], sin(__dmul_rn(TWO_PI, __ddiv_rn(x, p[2])))));
+            return fmax(__dsub_rn(yw, y), __dsub_rn(y, p[3]));
+        }
+        default:
+            return -1.0;
+    }
+}
+
+// coordinate of component c (0..2; 3 = cell centre) of index idx along direction d
+__device__ __forceinline__ double coord(const GridP& g, int d, int idx, int c) {
+    double off = (d == c) ? 1.0 : 0.5;
+    double o = d == 0 ? g.ox : (d == 1 ? g.oy : g.oz);
+    double D = d == 0 ? g.dx : (d == 1 ? g.dy : g.dz);
+    return __dadd_rn(o, __dmul_rn(__dadd_rn((double)idx, off), D));
+}
+
+// Is (i,j,k) of component c a prescribed wall-face point (v on the +y wall)?
+__device__ __forceinline__ bool wall_face(const GridP& g, int c, int j) { return c == 1 && j == g.ny - 1; }
+
+// ---------------------------------------------------------------------------
+// Classification
+// ---------------------------------------------------------------------------
+__global__ void k_classify_vel(GridP g, GeomP geo, uint8_t* __restrict__ velbits) {
+    long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    int i = (int)(id % g.nx);
+    int j = (int)((id / g.nx) % g.ny);
+    int k = (int)(id / ((long long)g.nx * g.ny));
+    uint8_t b = 0;
+    for (int c = 0; c < g.ncomp; ++c) {
+        if (wall_face(g, c, j)) continue;
+        double x = coord(g, 0, i, c), y = coord(g, 1, j, c), z = coord(g, 2, k, c);
+        if (phi_at(geo, x, y, z) < 0.0) b |= (uint8_t)(1u << c);
+    }
+    velbits[id] = b;
+}
+
+__device__ __forceinline__ bool vel_internal(const GridP& g, const uint8_t* vb, int c, int i, int j, int k) {
+    return (vb[i + (long long)g.nx * (j + (long long)g.ny * k)] >> c) & 1u;
+}
+
+// external = a stored, non-wall-face point that is not internal
+__device__ __forceinline__ bool vel_external(const GridP& g, const uint8_t* vb, int c, int i, int j, int k) {
+    if (wall_face(g, c, j)) return false;
+    return !vel_internal(g, vb, c, i, j, k);
+}
+
+// Neighbour of (i,j,k) along d by s on component c's grid; false if beyond a wall face.
+__device__ __forceinline__ bool neighbour(const GridP& g, int d, int s, int& i, int& j, int& k) {
+    if (d == 0) { i = wrapi(i + s, g.nx); return true; }
+    if (d == 2) { k = wrapi(k + s, g.nz); return true; }
+    j += s;
+    return j >= 0 && j < g.ny;
+}
+
+__global__ void k_classify_final(GridP g, const uint8_t* __restrict__ vb, uint8_t* __restrict__ mask) {
+    long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    int i = (int)(id % g.nx);
+    int j = (int)((id / g.nx) % g.ny);
+    int k = (int)(id / ((long long)g.nx * g.ny));
+    uint8_t own = vb[id];
+    uint8_t m = own;
+    // internal pressure: any of the cell's face velocities internal
+    bool pint = own != 0;
+    for (int c = 0; c < g.ncomp && !pint; ++c) {
+        int ii = i, jj = j, kk = k;
+        if (c == 0) ii = wrapi(i - 1, g.nx);
+        else if (c == 2) kk = wrapi(k - 1, g.nz);
+        else { jj = j - 1; if (jj < 0) continue; }
+        if (vel_internal(g, vb, c, ii, jj, kk)) pint = true;
+    }
+    if (pint) m |= IBM_MASK_P;
+    // IBM point: internal with an external same-component neighbour along an arm
+    for (int c = 0; c < g.ncomp; ++c) {
+        if (!((own >> c) & 1u)) continue;
+        bool ext = false;
+        for (int d = 0; d < g.ndim && !ext; ++d)
+            for (int s = 1; s >= -1 && !ext; s -= 2) {
+                int ii = i, jj = j, kk = k;
+                if (!neighbour(g, d, s, ii, jj, kk)) continue;
+                if (vel_external(g, vb, c, ii, jj, kk)) ext = true;
+            }
+        if (ext) m |= (uint8_t)(IBM_MASK_IBM_U << c);
+    }
+    mask[id] = m;
+}
+
+// One warp per 32-point x segment: IBM points per component
+__global__ void k_segcount(GridP g, long long nseg, const uint8_t* __restrict__ mask, int* cnt0, int* cnt1, int* cnt2) {
+    long long seg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / IBM_WARP;
+    int lane = threadIdx.x & 31;
+    if (seg >= nseg) return;
+    int sx = (int)(seg % g.nsegx);
+    long long row = seg / g.nsegx;
+    int i = sx * IBM_WARP + lane;
+    uint8_t m = i < g.nx ? mask[row * g.nx + i] : 0;
+    int* cnt[3] = {cnt0, cnt1, cnt2};
+    for (int c = 0; c < 3; ++c) {
+        unsigned b = __ballot_sync(0xffffffffu, (m >> (4 + c)) & 1u);
+        if (lane == 0) cnt[c][seg] = __popc(b);
+    }
+}
+
+__global__ void k_compact(GridP g, long long nseg, const uint8_t* __restrict__ mask, const int* off0,
+                          const int* off1, const int* off2, int* idx0, int* idx1, int* idx2) {
+    long long seg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / IBM_WARP;
+    int lane = threadIdx.x & 31;
+    if (seg >= nseg) return;
+    int sx = (int)(seg % g.nsegx);
+    long long row = seg / g.nsegx;
+    int i = sx * IBM_WARP + lane;
+    long long lin = row * g.nx + i;
+    uint8_t m = i < g.nx ? mask[lin] : 0;
+    const int* off[3] = {off0, off1, off2};
+    int* idx[3] = {idx0, idx1, idx2};
+    for (int c = 0; c < 3; ++c) {
+        bool bit = (m >> (4 + c)) & 1u;
+        unsigned b = __ballot_sync(0xffffffffu, bit);
+        if (bit) idx[c][off[c][seg] + __popc(b & lanemask_lt())] = (int)lin;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int counts (three arrays, blockIdx.y = component)
+// ---------------------------------------------------------------------------
+constexpr int SCAN_T = 512;      // threads per block
+constexpr int SCAN_E = 8;        // elements per thread
+constexpr int SCAN_CH = SCAN_T * SCAN_E;
+
+__device__ int block_exclusive_scan(int v, int* sh, int& total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int y = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        if (lane < nw) sh[lane] = y;
+    }
+    __syncthreads();
+    int warp_off = wid > 0 ? sh[wid - 1] : 0;
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+struct ScanArgs {
+    const int* in[3];
+    int* out[3];
+};
+
+__global__ void k_scan_partials(ScanArgs a, long long n, int* bsum, int nblocks) {
+    __shared__ int sh[32];
+    int c = blockIdx.y;
+    long long base = (long long)blockIdx.x * SCAN_CH + (long long)threadIdx.x * SCAN_E;
+    int s = 0;
+    for (int e = 0; e < SCAN_E; ++e)
+        if (base + e < n) s += a.in[c][base + e];
+    int total;
+    block_exclusive_scan(s, sh, total);
+    if (threadIdx.x == 0) bsum[c * nblocks + blockIdx.x] = total;
+}
+
+__global__ void k_scan_top(int* bsum, int nblocks, int* totals) {
+    __shared__ int sh[32];
+    int c = blockIdx.x;
+    int run = 0;
+    for (int base = 0; base < nblocks; base += blockDim.x) {
+        int t = base + threadIdx.x;
+        int v = t < nblocks ? bsum[c * nblocks + t] : 0;
+        int total;
+        int ex = block_exclusive_scan(v, sh, total);
+        if (t < nblocks) bsum[c * nblocks + t] = run + ex;
+        run += total;
+    }
+    if (threadIdx.x == 0) totals[c] = run;
+}
+
+__global__ void k_scan_apply(ScanArgs a, long long n, const int* boff, int nblocks) {
+    __shared__ int sh[32];
+    int c = blockIdx.y;
+    long long base = (long long)blockIdx.x * SCAN_CH + (long long)threadIdx.x * SCAN_E;
+    int v[SCAN_E];
+    int s = 0;
+    for (int e = 0; e < SCAN_E; ++e) {
+        v[e] = (base + e < n) ? a.in[c][base + e] : 0;
+        s += v[e];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, sh, total) + boff[c * nblocks + blockIdx.x];
+    for (int e = 0; e < SCAN_E; ++e) {
+        if (base + e < n) a.out[c][base + e] = ex;
+        ex += v[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weights: delta per crossed arm, lambda and the wall source (Sec. 2.2)
+// ---------------------------------------------------------------------------
+__device__ double delta_bisect(const GeomP& geo, const double P[3], int d, int s, double D) {
+    double lo = 0.0, hi = D;
+    for (int it = 0; it < 200; ++it) {
+        double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+        if (mid <= lo || mid >= hi) break;
+        double Q[3] = {P[0], P[1], P[2]};
+        Q[d] = __dadd_rn(P[d], __dmul_rn((double)s, mid));
+        if (phi_at(geo, Q[0], Q[1], Q[2]) < 0.0) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+// closed-form distance, or a negative value when none applies
+__device__ double delta_closed(const GeomP& geo, const double P[3], int d, int s, double D) {
+    const double* p = geo.p;
+    if (geo.kind == IBM_GEOM_PLANES && d == 1) return s < 0 ? __dsub_rn(P[1], p[0]) : __dsub_rn(p[1], P[1]);
+    if (geo.kind == IBM_GEOM_SINE_WALL && d == 1) {
+        if (s < 0) {
+            double yw = __dadd_rn(p[0], __dmul_rn(p[1], sin(__dmul_rn(TWO_PI, __ddiv_rn(P[0], p[2])))));
+            return __dsub_rn(P[1], yw);
+        }
+        return __dsub_rn(p[3], P[1]);
+    }
+    if (geo.kind == IBM_GEOM_CYLINDER || geo.kind == IBM_GEOM_SPHERE) {
+        bool sph = geo.kind == IBM_GEOM_SPHERE;
+        double ctr[3] = {p[0], p[1], sph ? p[2] : 0.0};
+        double R = sph ? p[3] : p[2];
+        int nd = sph ? 3 : 2;
+        if (d >= nd) return -1.0;
+        double rho2 = 0.0;
+        for (int e = 0; e < nd; ++e) {
+            if (e == d) continue;
+            double t = __dsub_rn(P[e], ctr[e]);
+            rho2 = __dadd_rn(rho2, __dmul_rn(t, t));
+        }
+        double h2 = __dsub_rn(__dmul_rn(R, R), rho2);
+        if (h2 < 0.0) return -1.0;
+        double hh = __dsqrt_rn(h2);
+        double xp = P[d];
+        double xq = __dadd_rn(xp, __dmul_rn((double)s, D));
+        double lo = fmin(xp, xq), hi = fmax(xp, xq);
+        double r1 = __dsub_rn(ctr[d], hh), r2 = __dadd_rn(ctr[d], hh);
+        bool in1 = lo <= r1 && r1 <= hi, in2 = lo <= r2 && r2 <= hi;
+        if (in1 == in2) return -1.0;
+        return fabs(__dsub_rn(in1 ? r1 : r2, xp));
+    }
+    return -1.0;
+}
+
+__device__ double wall_factor(int kind, int d, int s) {
+    if (kind == IBM_GEOM_PLANES) return (d == 1 && s > 0) ? 1.0 : 0.0;
+    if (kind == IBM_GEOM_SINE_WALL) return (d == 1 && s > 0) ? 0.0 : 1.0;
+    return 1.0;
+}
+
+struct WeightArgs {
+    const int* idx[3];
+    double* lam[3];
+    double* src[3];
+    int count[3];
+    double nu;
+    double wall_u[3];
+    int no_ibm;
+};
+
+__global__ void k_weights(GridP g, GeomP geo, WeightArgs a, const uint8_t* __restrict__ mask) {
+    int c = blockIdx.y;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.ncomp || m >= a.count[c]) return;
+    int lin = a.idx[c][m];
+    int i = lin % g.nx;
+    int j = (lin / g.nx) % g.ny;
+    int k = lin / (g.nx * g.ny);
+    double lam = 0.0, src = 0.0;
+    if (!a.no_ibm) {
+        double P[3] = {coord(g, 0, i, c), coord(g, 1, j, c), coord(g, 2, k, c)};
+        double phiP = phi_at(geo, P[0], P[1], P[2]);
+        for (int d = 0; d < g.ndim; ++d) {
+            double D = d == 0 ? g.dx : (d == 1 ? g.dy : g.dz);
+            for (int s = 1; s >= -1; s -= 2) {
+                int ii = i, jj = j, kk = k;
+                if (!neighbour(g, d, s, ii, jj, kk)) continue;
+                if (wall_face(g, c, jj)) continue;
+                long long q = ii + (long long)g.nx * (jj + (long long)g.ny * kk);
+                if ((mask[q] >> c) & 1u) continue;       // internal neighbour
+                double phiQ = phi_at(geo, coord(g, 0, ii, c), coord(g, 1, jj, c), coord(g, 2, kk, c));
+                double dl;
+                if (phiQ == 0.0) {
+                    dl = D;
+                } else {
+                    dl = delta_closed(geo, P, d, s, D);
+                    if (dl < 0.0) dl = delta_bisect(geo, P, d, s, D);
+                }
+                dl = fmin(fmax(dl, 1e-12 * D), D);
+                (void)phiP;
+                lam = lam + a.nu * (D - dl) / (dl * D * D);
+                src = src + a.nu * (a.wall_u[c] * wall_factor(geo.kind, d, s)) / (dl * D);
+            }
+        }
+    }
+    a.lam[c][m] = lam;
+    a.src[c][m] = src;
+}
+
+// ---------------------------------------------------------------------------
+// Per-stage implicit coefficients (Eq. Bexpr / expint / rk3-rai)
+// ---------------------------------------------------------------------------
+__device__ double B_of_x(double x, int mode) {
+    if (mode == IBM_B_EULER) return 1.0;
+    if (mode == IBM_B_TAYLOR2) return 1.0 / (1.0 + x / 2.0);
+    if (!(x > 0.0)) return 1.0;
+    return x / expm1(x);
+}
+
+template <typename T>
+struct CoefArgs {
+    const double* lam[3];
+    const double* src[3];
+    Coef4<T>* coef[3];   // [3 stages][count]
+    int count[3];
+    double ckdt[3];
+    int bmode;
+};
+
+template <typename T>
+__global__ void k_coefs(CoefArgs<T> a) {
+    int c = blockIdx.y;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.count[c]) return;
+    double lam = a.lam[c][m];
+    double s = a.src[c][m];
+    for (int st = 0; st < 3; ++st) {
+        double x = lam * a.ckdt[st];
+        double B = B_of_x(x, a.bmode);
+        Coef4<T> q;
+        q.a = (T)(B / (B + x));
+        q.b = (T)(1.0 / (B + x));
+        q.s = (T)s;
+        q.pad = (T)0;
+        a.coef[c][(long long)st * a.count[c] + m] = q;
+    }
+}
+
+// Flux control response: sum over the u IBM points of (1 - beta_k) and the
+// number of internal u points (the exact beta of non-IBM points is 1).
+__global__ void k_flux_response(GridP g, const uint8_t* __restrict__ mask, const double* __restrict__ lam_u,
+                                int count_u, double ck0, double ck1, double ck2, int bmode, double* out) {
+    __shared__ double sh[4][32];
+    double acc[4] = {0, 0, 0, 0};
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += stride)
+        acc[0] += (mask[id] & IBM_MASK_U) ? 1.0 : 0.0;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < count_u; m += stride) {
+        double l = lam_u[m];
+        double ck[3] = {ck0, ck1, ck2};
+        for (int st = 0; st < 3; ++st) {
+            double x = l * ck[st];
+            double B = B_of_x(x, bmode);
+            acc[1 + st] += 1.0 - 1.0 / (B + x);
+        }
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < 4; ++q) {
+        double v = warp_sum(acc[q]);
+        if (lane == 0) sh[q][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[threadIdx.x][w];
+        out[blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Thomas pivots of the y systems, one thread per (kz, kx)
+// ---------------------------------------------------------------------------
+__global__ void k_pivots(GridP g, double* __restrict__ piv) {
+    long long sys = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long nsys = (long long)g.nz * g.nxh;
+    if (sys >= nsys) return;
+    int kx = (int)(sys % g.nxh);
+    int kz = (int)(sys / g.nxh);
+    const double PI = 3.141592653589793;
+    double sx = sin(PI * kx / g.nx);
+    double K = 4.0 * sx * sx / (g.dx * g.dx);
+    if (g.ndim == 3 && g.nz > 1) {
+        double sz = sin(PI * kz / g.nz);
+        K += 4.0 * sz * sz / (g.dz * g.dz);
+    }
+    double Kd = K * g.dy * g.dy;
+    bool zero = (kx == 0 && kz == 0);
+    double wprev = 0.0;
+    for (int j = 0; j < g.ny; ++j) {
+        bool end = (j == 0 || j == g.ny - 1);
+        double b = (end ? -1.0 : -2.0) - Kd;
+        double w;
+        if (j == 0) w = zero ? 0.0 : 1.0 / b;
+        else w = 1.0 / (b - wprev);
+        piv[((long long)kz * g.ny + j) * g.nxh + kx] = w;
+        wprev = w;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+ibm_status geom_classify(ibm_solver* h) {
+    const GridP& g = h->gp;
+    int nb = (int)((g.N + 255) / 256);
+    cudaEvent_t t;
+    timer_begin(h, "classify", &t);
+    k_classify_vel<<<nb, 256, 0, h->stream>>>(g, h->geo, h->velbits);
+    IBM_LAUNCH_CHECK();
+    k_classify_final<<<nb, 256, 0, h->stream>>>(g, h->velbits, h->mask);
+    IBM_LAUNCH_CHECK();
+    timer_end(h, t, "classify");
+    long long nthreads = h->nseg * IBM_WARP;
+    int nbs = (int)((nthreads + 255) / 256);
+    k_segcount<<<nbs, 256, 0, h->stream>>>(g, h->nseg, h->mask, h->segcnt[0], h->segcnt[1], h->segcnt[2]);
+    IBM_LAUNCH_CHECK();
+    int nblocks = (int)((h->nseg + SCAN_CH - 1) / SCAN_CH);
+    ScanArgs sa;
+    for (int c = 0; c < 3; ++c) { sa.in[c] = h->segcnt[c]; sa.out[c] = h->segoff[c]; }
+    k_scan_partials<<<dim3(nblocks, 3), SCAN_T, 0, h->stream>>>(sa, h->nseg, h->scan_tmp, nblocks);
+    IBM_LAUNCH_CHECK();
+    k_scan_top<<<3, 1024, 0, h->stream>>>(h->scan_tmp, nblocks, h->d_counts);
+    IBM_LAUNCH_CHECK();
+    k_scan_apply<<<dim3(nblocks, 3), SCAN_T, 0, h->stream>>>(sa, h->nseg, h->scan_tmp, nblocks);
+    IBM_LAUNCH_CHECK();
+    IBM_CUDA_TRY(cudaMemcpyAsync(h->counts, h->d_counts, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return IBM_OK;
+}
+
+ibm_status geom_build_lists_and_weights(ibm_solver* h) {
+    const GridP& g = h->gp;
+    long long nthreads = h->nseg * IBM_WARP;
+    int nbs = (int)((nthreads + 255) / 256);
+    k_compact<<<nbs, 256, 0, h->stream>>>(g, h->nseg, h->mask, h->segoff[0], h->segoff[1], h->segoff[2],
+                                          h->idx[0], h->idx[1], h->idx[2]);
+    IBM_LAUNCH_CHECK();
+    WeightArgs a;
+    int maxc = 1;
+    for (int c = 0; c < 3; ++c) {
+        a.idx[c] = h->idx[c];
+        a.lam[c] = h->lam[c];
+        a.src[c] = h->src[c];
+        a.count[c] = h->counts[c];
+        a.wall_u[c] = h->phys.wall_u[c];
+        if (h->counts[c] > maxc) maxc = h->counts[c];
+    }
+    a.nu = h->phys.nu;
+    a.no_ibm = h->phys.no_ibm;
+    k_weights<<<dim3((maxc + 127) / 128, 3), 128, 0, h->stream>>>(g, h->geo, a, h->mask);
+    IBM_LAUNCH_CHECK();
+    return IBM_OK;
+}
+
+ibm_status geom_stage_coefficients(ibm_solver* h) {
+    const double rkc[3] = {64.0 / 120.0, 16.0 / 120.0, 40.0 / 120.0};
+    int maxc = 1;
+    for (int c = 0; c < 3; ++c) maxc = h->counts[c] > maxc ? h->counts[c] : maxc;
+    dim3 grid((maxc + 127) / 128, 3);
+    if (h->prec == IBM_FP64) {
+        CoefArgs<double> a;
+        for (int c = 0; c < 3; ++c) {
+            a.lam[c] = h->lam[c]; a.src[c] = h->src[c]; a.count[c] = h->counts[c];
+            a.coef[c] = (Coef4<double>*)h->coef[c]; a.ckdt[c] = rkc[c] * h->phys.dt;
+        }
+        a.bmode = h->phys.bmode;
+        k_coefs<double><<<grid, 128, 0, h->stream>>>(a);
+    } else {
+        CoefArgs<float> a;
+        for (int c = 0; c < 3; ++c) {
+            a.lam[c] = h->lam[c]; a.src[c] = h->src[c]; a.count[c] = h->counts[c];
+            a.coef[c] = (Coef4<float>*)h->coef[c]; a.ckdt[c] = rkc[c] * h->phys.dt;
+        }
+        a.bmode = h->phys.bmode;
+        k_coefs<float><<<grid, 128, 0, h->stream>>>(a);
+    }
+    IBM_LAUNCH_CHECK();
+    // flux-control response S_k = c_k dt dV sum_internal beta_k
+    const GridP& g = h->gp;
+    int nb = 120;
+    k_flux_response<<<nb, 256, 0, h->stream>>>(g, h->mask, h->lam[0], h->counts[0], rkc[0] * h->phys.dt,
+                                               rkc[1] * h->phys.dt, rkc[2] * h->phys.dt, h->phys.bmode, h->partials);
+    IBM_LAUNCH_CHECK();
+    std::vector<double> part(nb * 4);
+    IBM_CUDA_TRY(cudaMemcpyAsync(part.data(), h->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int q = 0; q < 4; ++q) acc[q] += part[b * 4 + q];
+    double dV = g.dx * g.dy * (g.ndim == 3 ? g.dz : 1.0);
+    for (int st = 0; st < 3; ++st) h->S[st] = rkc[st] * h->phys.dt * dV * (acc[0] - acc[1 + st]);
+    return IBM_OK;
+}
+
+ibm_status geom_pivots(ibm_solver* h) {
+    long long nsys = (long long)h->gp.nz * h->gp.nxh;
+    k_pivots<<<(int)((nsys + 127) / 128), 128, 0, h->stream>>>(h->gp, h->pivots);
+    IBM_LAUNCH_CHECK();
+    return IBM_OK;
+}

@@ -1,0 +1,180 @@
+"""A solver object over the C ABI, with device memory from PyTorch.
+
+PyTorch provides the device buffers (fields, workspace, weights) and the
+stream; every computation is a call into libibm.so.  Host copies of the
+fields are plain numpy arrays of shape (nz, ny, nx).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import (ibm_grid_desc, ibm_geom_desc, ibm_buffers, ibm_physics, IBM_FP64, IBM_FP32,
+               ibm_workspace_bytes, ibm_setup_geometry, ibm_weights_bytes, ibm_build_weights, ibm_step,
+               ibm_project, ibm_poisson, ibm_diagnostics, ibm_get_classification, ibm_get_weights,
+               ibm_state_bytes, ibm_export_state, ibm_import_state, ibm_timing, ibm_get_timing,
+               ibm_launch_count, ibm_destroy)
+
+
+class Solver:
+    """One IBM solve resident on a CUDA device.
+
+    Parameters mirror the C structs: ndim, n=(nx,ny,nz), L, origin, bc_lo,
+    bc_hi, precision ('fp64'|'fp32'), geom_kind, geom_params, and physics
+    nu, dt, g, bmode, flow_mode, target_flux, wall_u, no_ibm."""
+
+    def __init__(self, *, ndim, n, L, origin, bc_lo, bc_hi, precision, geom_kind, geom_params, nu, dt,
+                 g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0, wall_u=(0.0, 0.0, 0.0), no_ibm=False,
+                 device="cuda", stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the IBM solver needs a CUDA device")
+        self.device = torch.device(device)
+        # a stream of its own: graph capture is not allowed on the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.ndim = int(ndim)
+        self.n = tuple(int(v) for v in n)
+        self.shape = (self.n[2], self.n[1], self.n[0])
+        self.N = self.n[0] * self.n[1] * self.n[2]
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.np_dtype = np.float64 if precision == "fp64" else np.float32
+        gd = ibm_grid_desc()
+        gd.ndim = self.ndim
+        for d in range(3):
+            gd.n[d] = self.n[d]
+            gd.L[d] = float(L[d])
+            gd.origin[d] = float(origin[d])
+            gd.bc_lo[d] = int(bc_lo[d])
+            gd.bc_hi[d] = int(bc_hi[d])
+        gd.precision = IBM_FP64 if precision == "fp64" else IBM_FP32
+        self.grid = gd
+        geo = ibm_geom_desc()
+        geo.kind = int(geom_kind)
+        geo.nparam = len(geom_params)
+        for q, v in enumerate(geom_params):
+            geo.param[q] = float(v)
+        self.geom = geo
+        with torch.cuda.device(self.device):
+            kw = dict(dtype=self.dtype, device=self.device)
+            self.u = [torch.zeros(self.shape, **kw) for _ in range(3)]
+            self.p = torch.zeros(self.shape, **kw)
+            wb = ibm_workspace_bytes(gd)
+            self.work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+            bufs = ibm_buffers()
+            for c in range(3):
+                bufs.u[c] = self.u[c].data_ptr()
+            bufs.p = self.p.data_ptr()
+            bufs.work = self.work.data_ptr()
+            bufs.work_bytes = wb
+            self.buffers = bufs
+            torch.cuda.synchronize(self.device)
+            self.h = ibm_setup_geometry(gd, geo, bufs, self.stream.cuda_stream)
+            self.weights = None
+            self.set_physics(nu=nu, dt=dt, g=g, bmode=bmode, flow_mode=flow_mode, target_flux=target_flux,
+                             wall_u=wall_u, no_ibm=no_ibm)
+
+    @classmethod
+    def from_case(cls, case, precision=None, no_ibm=False, **kw):
+        """Build from any object with the attributes of a workload description."""
+        return cls(ndim=case.ndim, n=case.n, L=case.L, origin=case.origin, bc_lo=case.bc_lo, bc_hi=case.bc_hi,
+                   precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,
+                   nu=case.nu, dt=case.dt, g=case.g, bmode=case.bmode, flow_mode=case.flow_mode,
+                   target_flux=case.target_flux, wall_u=case.wall_u, no_ibm=no_ibm, **kw)
+
+    def set_physics(self, *, nu, dt, g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0,
+                    wall_u=(0.0, 0.0, 0.0), no_ibm=False):
+        ph = ibm_physics()
+        ph.nu = float(nu)
+        ph.dt = float(dt)
+        for c in range(3):
+            ph.g[c] = float(g[c])
+            ph.wall_u[c] = float(wall_u[c])
+        ph.bmode = int(bmode)
+        ph.flow_mode = int(flow_mode)
+        ph.target_flux = float(target_flux)
+        ph.no_ibm = 1 if no_ibm else 0
+        self.phys = ph
+        wb = ibm_weights_bytes(self.h)
+        if self.weights is None or self.weights.numel() < wb:
+            self.weights = torch.empty(max(wb, 256), dtype=torch.uint8, device=self.device)
+            torch.cuda.synchronize(self.device)
+        ibm_build_weights(self.h, ph, self.weights.data_ptr(), self.weights.numel())
+
+    # ---- calls -------------------------------------------------------------
+    def step(self, nsteps=1, flags=0):
+        ibm_step(self.h, nsteps, flags)
+
+    def project(self):
+        ibm_project(self.h)
+
+    def poisson(self, rhs: torch.Tensor):
+        assert rhs.dtype == self.dtype and rhs.is_contiguous() and rhs.numel() == self.N
+        torch.cuda.synchronize(self.device)
+        ibm_poisson(self.h, rhs.data_ptr())
+        self.stream.synchronize()
+
+    def diagnostics(self, raise_on_diverged=True) -> dict:
+        d = ibm_diagnostics(self.h, raise_on_diverged)
+        return {"div_l2": d.div_l2, "div_linf": d.div_linf, "cfl": d.cfl, "flux": list(d.flux), "ke": d.ke,
+                "pi": d.pi, "step": d.step, "status": d.status}
+
+    def classification(self):
+        counts = ibm_get_classification(self.h, None, None)
+        mask = np.empty(self.shape, dtype=np.uint8)
+        lists = [np.empty(max(c, 1), dtype=np.int32) for c in counts]
+        ibm_get_classification(self.h, mask.ctypes.data, [l.ctypes.data for l in lists])
+        return mask, [lists[c][:counts[c]].astype(np.int64) for c in range(3)]
+
+    def weights_lists(self):
+        counts = ibm_get_classification(self.h, None, None)
+        lam = [np.empty(max(c, 1)) for c in counts]
+        src = [np.empty(max(c, 1)) for c in counts]
+        ibm_get_weights(self.h, [a.ctypes.data for a in lam], [a.ctypes.data for a in src])
+        return [lam[c][:counts[c]] for c in range(3)], [src[c][:counts[c]] for c in range(3)]
+
+    def set_state(self, u, v, w, p):
+        torch.cuda.synchronize(self.device)
+        for t, a in zip(self.u + [self.p], (u, v, w, p)):
+            t.copy_(torch.as_tensor(np.ascontiguousarray(a, dtype=self.np_dtype)).reshape(self.shape))
+        torch.cuda.synchronize(self.device)
+
+    def sync(self):
+        self.stream.synchronize()
+
+    def state(self):
+        torch.cuda.synchronize(self.device)
+        out = [t.detach().cpu().numpy().astype(np.float64) for t in self.u + [self.p]]
+        return out[:3], out[3]
+
+    def state_bytes(self) -> int:
+        return ibm_state_bytes(self.h)
+
+    def export_state(self, host: np.ndarray):
+        ibm_export_state(self.h, host.ctypes.data, host.nbytes)
+
+    def import_state(self, host: np.ndarray):
+        ibm_import_state(self.h, host.ctypes.data, host.nbytes)
+
+    def import_state_ptr(self, ptr: int, nbytes: int):
+        ibm_import_state(self.h, ptr, nbytes)
+
+    def timing(self, enable=True):
+        ibm_timing(self.h, enable)
+
+    def get_timing(self) -> dict:
+        return ibm_get_timing(self.h)
+
+    def launch_count(self) -> int:
+        return ibm_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ibm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

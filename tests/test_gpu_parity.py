@@ -1,0 +1,298 @@
+"""GPU path (libibm.so through the C ABI) against the FP64 oracle.
+
+Tolerances:
+  * integer/byte work (mask, IBM-point lists): bit-exact;
+  * FP64 fields: 1e-12 relative per step (max abs difference over the
+    component's internal points divided by the oracle's max magnitude);
+  * FP32 fields: the error against FP64 is stated as a number in the test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+from inputs import (small_case, channel_c1, couette_case, wavy_c3, pipe_case, initial_field,  # noqa: E402
+                    B_EULER, B_TAYLOR2, GEOM_NONE)
+from oracle import OracleSolver, solve_spectral  # noqa: E402
+
+CASES = ["channel2d", "wavy3d", "sphere3d", "cylinder2d"]
+TOL64 = 1e-12
+
+
+def _gpu(case, **kw):
+    from paper_2506_14328_gb300.solver import Solver
+    return Solver.from_case(case, **kw)
+
+
+def _pair(case, no_ibm=False, precision=None):
+    f = initial_field(case)
+    g = _gpu(case, no_ibm=no_ibm, precision=precision)
+    g.set_state(f["u"], f["v"], f["w"], f["p"])
+    o = OracleSolver(case, no_ibm=no_ibm)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    return g, o
+
+
+def _rel(o, got, ref, c):
+    m = o.cls.internal[c]
+    if not m.any():
+        return 0.0
+    scale = max(np.abs(ref[m]).max(), 1e-300)
+    return float(np.abs(got[m] - ref[m]).max() / scale)
+
+
+def _rel_p(o, got, ref):
+    m = o.cls.p_internal
+    return float(np.abs(got[m] - ref[m]).max() / max(np.abs(ref[m]).max(), 1e-300))
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_classification_bit_exact(name):
+    case = small_case(name)
+    g = _gpu(case)
+    mask, lists = g.classification()
+    o = OracleSolver(case)
+    assert np.array_equal(mask, o.cls.mask)
+    for c in range(3):
+        assert np.array_equal(lists[c], o.cls.lists[c])
+
+
+def test_classification_pipe_3d_single_layer():
+    case = pipe_case(N=41, nz=1)
+    g = _gpu(case)
+    mask, lists = g.classification()
+    o = OracleSolver(case)
+    assert np.array_equal(mask, o.cls.mask)
+    assert all(np.array_equal(lists[c], o.cls.lists[c]) for c in range(3))
+
+
+@pytest.mark.parametrize("name", CASES + ["couette"])
+def test_weights_match_oracle(name):
+    case = couette_case() if name == "couette" else small_case(name)
+    g = _gpu(case)
+    lam, src = g.weights_lists()
+    o = OracleSolver(case)
+    for c in range(3):
+        ref = o.w.lam_list[c]
+        assert lam[c].shape == ref.shape
+        if ref.size:
+            assert np.abs(lam[c] - ref).max() <= TOL64 * max(np.abs(ref).max(), 1.0)
+            rs = o.w.src_list[c]
+            assert np.abs(src[c] - rs).max() <= TOL64 * max(np.abs(rs).max(), 1.0)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_predictor_matches_oracle(name):
+    case = small_case(name)
+    g, o = _pair(case)
+    g.step(1, flags=1)           # IBM_STEP_PREDICTOR_ONLY
+    o.substage(0, predictor_only=True)
+    ug, _ = g.state()
+    for c in range(o.grid.ncomp):
+        assert _rel(o, ug[c], o.u[c], c) < TOL64, c
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_poisson_matches_oracle(name):
+    case = small_case(name)
+    g = _gpu(case)
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal(g.shape)
+    r -= r.mean()
+    t = torch.tensor(r, dtype=torch.float64, device="cuda").contiguous()
+    g.poisson(t)
+    torch.cuda.synchronize()
+    ref = solve_spectral(OracleSolver(case).grid, r)
+    assert np.abs(t.cpu().numpy() - ref).max() < TOL64 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_full_steps_match_oracle(name):
+    case = small_case(name)
+    g, o = _pair(case)
+    for s in range(case.steps):
+        g.step(1)
+        o.step(1)
+        ug, pg = g.state()
+        for c in range(o.grid.ncomp):
+            assert _rel(o, ug[c], o.u[c], c) < TOL64, (s, c)
+        assert _rel_p(o, pg, o.p) < 1e-11, s
+
+
+def test_project_matches_oracle():
+    case = small_case("sphere3d")
+    g, o = _pair(case)
+    g.project()
+    o.project()
+    ug, _ = g.state()
+    for c in range(3):
+        assert _rel(o, ug[c], o.u[c], c) < TOL64
+    d = g.diagnostics()
+    assert d["div_linf"] < 1e-12 * max(np.abs(u).max() for u in ug) / min(o.grid.d)
+
+
+@pytest.mark.parametrize("mode", [B_EULER, B_TAYLOR2])
+def test_other_B_modes_match_oracle(mode):
+    case = small_case("channel2d").with_(bmode=mode)
+    g, o = _pair(case)
+    g.step(2)
+    o.step(2)
+    ug, _ = g.state()
+    for c in range(2):
+        assert _rel(o, ug[c], o.u[c], c) < TOL64
+
+
+def test_staircase_flag_matches_oracle():
+    case = small_case("sphere3d")
+    g, o = _pair(case, no_ibm=True)
+    g.step(1)
+    o.step(1)
+    ug, _ = g.state()
+    for c in range(3):
+        assert _rel(o, ug[c], o.u[c], c) < TOL64
+
+
+def test_diagnostics_match_oracle():
+    case = small_case("wavy3d")
+    g, o = _pair(case)
+    g.step(1)
+    o.step(1)
+    dg = g.diagnostics()
+    do = o.diagnostics()
+    for k in ("cfl", "ke"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * abs(do[k])
+    for c in range(3):
+        assert abs(dg["flux"][c] - do["flux"][c]) <= 1e-12 * max(abs(do["flux"][0]), 1.0)
+    assert abs(dg["div_linf"]) < 1e-9 and abs(do["div_linf"]) < 1e-9
+    assert abs(dg["pi"] - o.last_pi) <= 1e-10 * max(1.0, abs(o.last_pi))
+
+
+def test_couette_fixed_point_on_gpu():
+    case = couette_case()
+    f = initial_field(case)
+    g = _gpu(case)
+    g.set_state(f["u"], f["v"], f["w"], f["p"])
+    o = OracleSolver(case)
+    u0 = np.where(o.cls.internal[0], f["u"], 0.0)
+    g.step(5)
+    ug, _ = g.state()
+    u1 = np.where(o.cls.internal[0], ug[0], 0.0)
+    assert np.abs(u1 - u0).max() < 1e-13
+
+
+def test_channel_c1_2000_steps_matches_oracle_and_parabola():
+    case = channel_c1(steps=2000)
+    g, o = _pair(case)
+    g.step(case.steps, flags=2)   # graph replay
+    o.step(case.steps)
+    ug, _ = g.state()
+    assert _rel(o, ug[0], o.u[0], 0) < TOL64
+    y = o.grid.coords(0)[1]
+    exact = np.broadcast_to(1.0 - ((y - 0.499) / 0.362) ** 2, o.grid.shape)
+    m = o.cls.internal[0]
+    assert np.abs(ug[0] - exact)[m].max() < 5e-3
+
+
+def test_graph_replay_equals_stream_launches():
+    case = small_case("wavy3d")
+    g1, _ = _pair(case)
+    g2, _ = _pair(case)
+    g1.step(3)
+    g2.step(3, flags=2)
+    a, pa = g1.state()
+    b, pb = g2.state()
+    for c in range(3):
+        assert np.array_equal(a[c], b[c])
+    assert np.array_equal(pa, pb)
+
+
+def test_checkpoint_resume_is_bitwise():
+    case = small_case("sphere3d")
+    g1, _ = _pair(case)
+    g1.step(2)
+    snap = np.empty(g1.state_bytes(), dtype=np.uint8)
+    g1.export_state(snap)
+    g1.step(2)
+    a, pa = g1.state()
+    g2 = _gpu(case)
+    g2.import_state(snap)
+    g2.step(2)
+    b, pb = g2.state()
+    for c in range(3):
+        assert np.array_equal(a[c], b[c])
+    assert np.array_equal(pa, pb)
+    assert g2.diagnostics()["step"] == 4
+
+
+@pytest.mark.parametrize("name", ["channel2d", "wavy3d", "sphere3d"])
+def test_fp32_error_against_fp64(name):
+    """FP32 momentum / FP32 FFT / FP64 tridiagonal against the FP64 path after the case's steps."""
+    case = small_case(name)
+    g64, _ = _pair(case, precision="fp64")
+    g32, o = _pair(case, precision="fp32")
+    g64.step(case.steps)
+    g32.step(case.steps)
+    a, _ = g64.state()
+    b, _ = g32.state()
+    err = max(_rel(o, b[c], a[c], c) for c in range(o.grid.ncomp))
+    assert err < 2e-5, err
+
+
+def test_fp32_laminar_steady_state_within_1e5():
+    """FP32 steady laminar channel against FP64: <= 1e-5 relative (C1 physics, 2000 steps)."""
+    case = channel_c1(steps=2000)
+    g64, o = _pair(case, precision="fp64")
+    g32, _ = _pair(case, precision="fp32")
+    g64.step(case.steps, flags=2)
+    g32.step(case.steps, flags=2)
+    a, _ = g64.state()
+    b, _ = g32.state()
+    assert _rel(o, b[0], a[0], 0) <= 1e-5
+
+
+def test_diverged_status_on_nonfinite_field():
+    from paper_2506_14328_gb300 import IBM_E_DIVERGED
+    case = small_case("channel2d")
+    g, _ = _pair(case)
+    g.u[0][0, 5, 7] = float("nan")
+    torch.cuda.synchronize()
+    d = g.diagnostics(raise_on_diverged=False)
+    assert d["status"] == IBM_E_DIVERGED
+    g.u[0][0, 5, 7] = 0.0
+    torch.cuda.synchronize()
+    assert g.diagnostics()["status"] == 0
+
+
+def test_no_body_box_projection_divergence_free():
+    case = small_case("wavy3d").with_(geom_kind=GEOM_NONE, geom_params=(), flow_mode=0)
+    g, o = _pair(case)
+    g.project()
+    assert g.diagnostics()["div_linf"] < 1e-12 * 2.0 / min(o.grid.d)
+
+
+def test_full_size_wavy_channel_launch_configuration():
+    """384x256x256 in the bench's launch configuration: bit-exact classification against the
+    oracle at full size, and the properties every step must keep (flux at target, divergence
+    at FP32 round-off, finite fields)."""
+    case = wavy_c3(precision="fp32", steps=2)
+    f = initial_field(case)
+    g = _gpu(case)
+    mask, lists = g.classification()
+    from oracle import Grid, LevelSet, classify
+    cls = classify(Grid(case), LevelSet(case.geom_kind, case.geom_params))
+    mism = int((mask != cls.mask).sum())
+    assert mism == 0, mism
+    for c in range(3):
+        assert np.array_equal(lists[c], cls.lists[c])
+    g.set_state(f["u"], f["v"], f["w"], f["p"])
+    g.project()
+    g.step(2)
+    d = g.diagnostics()
+    assert d["status"] == 0
+    umax = 3.0
+    assert d["div_linf"] < 1e-4 * umax / (2.0 / 256)
+    assert abs(g.diagnostics()["pi"]) < 1e3
