@@ -1,0 +1,335 @@
+"""Throughput of the IBM time step on one GB300 (or N independent replicas).
+
+Default workload: the 3D channel over a sinusoidal wall, 384x256x256 cells,
+FP32 momentum/FFT with FP64 tridiagonal sweeps and reductions, constant flow
+rate (see inputs.configs.wavy_c3).  A "step" is one full RK3 time step: three
+substages, each a momentum predictor with the implicit IBM division followed
+by the projection.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c3s|c3_fp64|c1|c2] [--impl reference]
+
+One JSON line on stdout (rank 0).  `value` is cells x steps / time over all
+ranks (replicas: every rank advances its own copy of the workload, no
+collective on the data path).  The timed region is bracketed by a barrier and
+a device synchronize; each rank's time is its CUDA-event duration on the
+solver's stream, and the maximum over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IBM-NS step Gcell-updates/s"
+UNIT = "Gcell-updates/s"
+
+# Algorithmic bytes per cell per launch of each kernel in FP32 mode (fields 4 B,
+# pivots and the forward-sweep temporary FP64); the momentum figure is the
+# average over the three RK3 stages (41, 53, 41 B) plus the mask byte and the
+# IBM segment offsets.  IBM coefficient bytes are added per launch from the
+# actual IBM-point counts.
+ALG_BYTES_PER_CELL = {
+    "momentum": (41.0 + 53.0 + 41.0) / 3.0 + 3 * 4.0 / 32.0,
+    "flux_control": 9.0,
+    "divergence": 16.0,
+    "correct": 36.0,
+}
+# tridiag: per spectral point read spec 8 + pivot 8 + write tmp 16, then tmp 16 + pivot 8 + spec 8
+TRIDIAG_BYTES_PER_SPECTRAL_POINT = 64.0
+
+# DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by kernel, with the hash of the source file it was taken on; a changed
+# source makes the figure stale and it is reported as null.
+NCU_TRAFFIC = {}
+
+
+def src_hash(name="step.cu") -> str:
+    p = os.path.join(ROOT, "paper_2506_14328_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d.get("hbm_gbs", 6800.0)), "source": "measured (MEASURED_PEAKS.json)"}
+    return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
+
+
+def workload(name: str):
+    from inputs import wavy_c3, channel_c1, cylinder_c2
+    if name == "c3":
+        return wavy_c3(precision="fp32")
+    if name == "c3_fp64":
+        return wavy_c3(precision="fp64")
+    if name == "c3s":   # profiling size: 6.3M cells, working set well above L2
+        return wavy_c3(precision="fp32", n=(384, 256, 64))
+    if name == "c1":
+        return channel_c1(precision="fp64")
+    if name == "c2":
+        return cylinder_c2(re=100.0, precision="fp32")
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_slab(case, nz: int):
+    """The same workload on a slab of nz cells in z (same spacing, physics and flux per area)."""
+    if case.ndim != 3:
+        return case.with_(precision="fp64")
+    n = (case.n[0], case.n[1], min(nz, case.n[2]))
+    frac = n[2] / case.n[2]
+    return case.with_(n=n, L=(case.L[0], case.L[1], case.L[2] * frac), precision="fp64",
+                      target_flux=case.target_flux * frac)
+
+
+def oracle_sample(case, steps: int = 2, nz: int = 32):
+    """Time the FP64 oracle, as it stands, on a bounded slab of the same workload."""
+    from oracle import OracleSolver
+    from inputs import initial_field
+    sample = oracle_slab(case, nz)
+    o = OracleSolver(sample)
+    f = initial_field(sample)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    t = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t
+    n = sample.n
+    return {"value": sample.ncells * steps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full steps of the FP64 numpy oracle on a {n[0]}x{n[1]}x{n[2]} slab of the "
+                      f"same workload (same spacing and physics), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle on the host cores: W untimed then K timed full steps on a slab of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import OracleSolver
+    from inputs import initial_field
+    case = workload(args.workload)
+    sample = oracle_slab(case, nz=8)
+    o = OracleSolver(sample)
+    f = initial_field(sample)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    v = sample.ncells * args.steps / dt / 1e9
+    n = sample.n
+    desc = (f"{args.steps} timed full steps (after {args.warmup} untimed) of the FP64 numpy oracle on a "
+            f"{n[0]}x{n[1]}x{n[2]} slab of the workload, {dt:.1f} s")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / max(args.steps, 1) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": case.name, "cells": case.ncells, "sample_cells": sample.ncells,
+                       "parallelism": "none"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from inputs import initial_field
+    from inputs.configs import describe
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+
+    from paper_2506_14328_gb300.solver import Solver
+    case = workload(args.workload)
+    s = Solver.from_case(case, device=str(device))
+    f = initial_field(case)
+    s.set_state(f["u"], f["v"], f["w"], f["p"])
+    s.project()
+    s.step(args.warmup)
+    s.sync()
+
+    def barrier():
+        torch.cuda.synchronize(device)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(device)
+
+    # ---- device-timed region -------------------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    s.timing(True)
+    barrier()
+    launches0 = s.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(s.stream)
+    s.step(args.steps)
+    ev1.record(s.stream)
+    barrier()
+    launches = s.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    kt = s.get_timing()
+    s.timing(False)
+    clk = clocks.stop()
+    diag = s.diagnostics()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * case.ncells * args.steps / (ms_max * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers -----------------
+    nbytes = s.state_bytes()
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    s.export_state(host.numpy())
+    e2e_steps = max(2, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.import_state_ptr(host.data_ptr(), nbytes)   # H2D of the step's input state (pinned)
+        s.step(1)
+        d = s.diagnostics()                           # D2H of the step's result (blocking)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * case.ncells * e2e_steps / float(e2e_t.item()) / 1e9
+    diag_bytes = 12 * 8 + 8  # the ibm_diag struct fields read back
+
+    if rank == 0:
+        peaks = measured_peaks()
+        counts = s.classification()[1]
+        nibm = sum(len(c) for c in counts)
+        per_kernel = {}
+        for name, (n, tot) in kt.items():
+            per_kernel[name] = {"launches": n, "ms_total": tot, "share": tot / ms if ms > 0 else None}
+        # roofline of the dominant kernel of this library
+        mine = {k: v for k, v in kt.items() if not k.startswith("fft")}   # cuFFT is library code
+        dom = max(mine, key=lambda k: mine[k][1]) if mine else "momentum"
+        n_l, tot_ms = mine.get(dom, (1, float("nan")))
+        avg_s = tot_ms / n_l * 1e-3
+        if dom == "tridiag":
+            nspec = case.n[2] * case.n[1] * (case.n[0] // 2 + 1)
+            alg = TRIDIAG_BYTES_PER_SPECTRAL_POINT * nspec
+        else:
+            alg = ALG_BYTES_PER_CELL.get(dom, 0.0) * case.ncells
+            if dom == "momentum":
+                alg += nibm * 16.0
+        achieved = alg / avg_s / 1e9 if avg_s > 0 else None
+        traffic = None
+        rec = NCU_TRAFFIC.get(dom)
+        if rec and rec[1] == src_hash():
+            traffic = rec[0]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic, "kernel": dom,
+                "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3,
+                "peak_source": peaks["source"] + ", copy bandwidth; kernel timed inside a long step"}
+        cpu = oracle_sample(case) if world == 1 or rank == 0 else None
+        cfg = describe(case)
+        cfg.update({"model": "IBM RK3 step + projection", "parallelism": "replicas" if world > 1 else "single",
+                    "l2": "inputs larger than L2 (working set ~%.1f GB)" % (
+                        (s.work.numel() + 4 * s.N * (4 if case.precision == 'fp32' else 8)) / 1e9),
+                    "precision_detail": "fp32 momentum/divergence/FFT, fp64 tridiagonal + reductions"
+                    if case.precision == "fp32" else "fp64 throughout",
+                    "ibm_points": nibm, "final_div_linf": diag["div_linf"], "final_flux_u": diag["flux"][0]})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if case.precision == "fp32" else "f64", "data": "synthetic", "config": cfg,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                        "d2h_bytes_per_step": diag_bytes},
+                "clocks": clk, "gpu_launches": launches, "kernels": per_kernel}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c3")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

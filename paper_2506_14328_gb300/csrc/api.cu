@@ -11,7 +11,6 @@ namespace {
 thread_local std::string g_last_error;
 
 constexpr size_t ALIGN = 256;
-constexpr int MOM_BY2 = 8, MOM_BY3 = 4, MOM_BZ3 = 2;   // momentum block shape (x is always 32)
 constexpr int DIAG_PART = 304 * 12;
 constexpr int SCAN_CH = 512 * 8;
 constexpr uint64_t STATE_MAGIC = 0x31534d4249ull;     // "IBMS1"
@@ -62,8 +61,8 @@ GridP make_gridp(const ibm_grid_desc* d) {
 }
 
 int momentum_blocks(const GridP& g) {
-    if (g.ndim == 3) return g.nsegx * ((g.ny + MOM_BY3 - 1) / MOM_BY3) * ((g.nz + MOM_BZ3 - 1) / MOM_BZ3);
-    return g.nsegx * ((g.ny + MOM_BY2 - 1) / MOM_BY2) * g.nz;
+    dim3 d = momentum_grid(g);
+    return (int)(d.x * d.y * d.z);
 }
 
 // Creates forward/inverse plans with auto-allocation off; returns the larger work size.
@@ -127,6 +126,9 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
     char* rhs = take(g.N * esz);
     char* spec = take(nspec * 2 * esz);
     char* piv = take(nspec * sizeof(double));
+    char* piv32 = take(nspec * sizeof(float));
+    char* use32 = take((size_t)g.nz * g.nxh);
+    char* order = take((size_t)g.nz * g.nxh * sizeof(int));
     char* dtemp = prec == IBM_FP32 ? take(nspec * 2 * sizeof(double)) : nullptr;
     char* fftw = take(fft_work);
     int npart = momentum_blocks(g);
@@ -148,6 +150,9 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
         h->rhs = rhs;
         h->spec = spec;
         h->pivots = (double*)piv;
+        h->pivots32 = (float*)piv32;
+        h->use32 = (uint8_t*)use32;
+        h->sys_order = (int*)order;
         h->dtemp = dtemp;
         h->fft_work = fftw;
         h->partials = (double*)partials;

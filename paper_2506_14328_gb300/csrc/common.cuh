@@ -42,16 +42,24 @@ template <typename T> struct IbmStage {
 };
 
 template <typename T> struct StageP {
+    T sig_lo, sig_hi;  // tangential ghost factors at the y walls
     T dta, dtb;        // dt a_k, dt b_k
     T ckdt;            // c_k dt
     T nu;
     T g[3];
     T idx, idy, idz;   // 1/dx ...
-    T idx2, idy2, idz2;
+    T nx2, ny2, nz2;   // nu/dx^2 ...
+    T qx, qy, qz;      // 1/(4 dx) ...: the two-point averages' 1/2 squared, over the spacing
     int read_prev;     // stage k > 1: add b_k N^{k-2}
     int write_n;       // stage k < 3: store N^{k-1}
     int flux_sum;      // accumulate the predictor flux (constant flow rate)
 };
+
+// Momentum tiling: blocks of 32 x 8 cells in (x, y), marching KZ planes in z.
+constexpr int MOM_TX = 32, MOM_TY = 8, MOM_KZ = 32;
+inline dim3 momentum_grid(const GridP& g) {
+    return dim3(g.nsegx, (g.ny + MOM_TY - 1) / MOM_TY, g.ndim == 3 ? (g.nz + MOM_KZ - 1) / MOM_KZ : 1);
+}
 
 // ---------------------------------------------------------------------------
 // Device helpers
@@ -110,6 +118,10 @@ struct ibm_solver {
     void* rhs = nullptr;
     void* spec = nullptr;
     double* pivots = nullptr;
+    float* pivots32 = nullptr;     // FP32 copy for the strongly dominant systems
+    uint8_t* use32 = nullptr;      // per (kz, kx) system: 1 = FP32 sweep
+    int* sys_order = nullptr;      // systems, FP64 ones first
+    int n64 = 0;                   // number of FP64 systems
     void* dtemp = nullptr;
     void* fft_work = nullptr;
     double* partials = nullptr;

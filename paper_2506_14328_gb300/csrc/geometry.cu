@@ -8,6 +8,7 @@
 #include "common.cuh"
 
 #include <cmath>
+#include <vector>
 
 namespace {
 
@@ -423,7 +424,8 @@ __global__ void k_flux_response(GridP g, const uint8_t* __restrict__ mask, const
 // ---------------------------------------------------------------------------
 // Thomas pivots of the y systems, one thread per (kz, kx)
 // ---------------------------------------------------------------------------
-__global__ void k_pivots(GridP g, double* __restrict__ piv) {
+__global__ void k_pivots(GridP g, double* __restrict__ piv, float* __restrict__ piv32, uint8_t* __restrict__ use32,
+                         double tau) {
     long long sys = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long nsys = (long long)g.nz * g.nxh;
     if (sys >= nsys) return;
@@ -438,6 +440,7 @@ __global__ void k_pivots(GridP g, double* __restrict__ piv) {
     }
     double Kd = K * g.dy * g.dy;
     bool zero = (kx == 0 && kz == 0);
+    use32[sys] = (!zero && Kd >= tau) ? 1 : 0;
     double wprev = 0.0;
     for (int j = 0; j < g.ny; ++j) {
         bool end = (j == 0 || j == g.ny - 1);
@@ -446,6 +449,7 @@ __global__ void k_pivots(GridP g, double* __restrict__ piv) {
         if (j == 0) w = zero ? 0.0 : 1.0 / b;
         else w = 1.0 / (b - wprev);
         piv[((long long)kz * g.ny + j) * g.nxh + kx] = w;
+        piv32[((long long)kz * g.ny + j) * g.nxh + kx] = (float)w;
         wprev = w;
     }
 }
@@ -550,7 +554,22 @@ ibm_status geom_stage_coefficients(ibm_solver* h) {
 
 ibm_status geom_pivots(ibm_solver* h) {
     long long nsys = (long long)h->gp.nz * h->gp.nxh;
-    k_pivots<<<(int)((nsys + 127) / 128), 128, 0, h->stream>>>(h->gp, h->pivots);
+    // FP32 sweeps only in FP32 mode, for systems with K dy^2 >= 1
+    double tau = h->prec == IBM_FP32 ? 1.0 : 1e300;
+    k_pivots<<<(int)((nsys + 127) / 128), 128, 0, h->stream>>>(h->gp, h->pivots, h->pivots32, h->use32, tau);
     IBM_LAUNCH_CHECK();
+    // system order: FP64 systems first, each group sorted by (kz, kx)
+    std::vector<uint8_t> use(nsys);
+    IBM_CUDA_TRY(cudaMemcpyAsync(use.data(), h->use32, nsys, cudaMemcpyDeviceToHost, h->stream));
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    std::vector<int> order;
+    order.reserve(nsys);
+    for (long long q = 0; q < nsys; ++q)
+        if (!use[q]) order.push_back((int)q);
+    h->n64 = (int)order.size();
+    for (long long q = 0; q < nsys; ++q)
+        if (use[q]) order.push_back((int)q);
+    IBM_CUDA_TRY(cudaMemcpyAsync(h->sys_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return IBM_OK;
 }
