@@ -209,6 +209,31 @@ ibm_status ibm_get_timing(ibm_solver* h, ibm_kernel_time* out, int max, int* cou
 /* Kernels this library has launched through this handle (a running count). */
 ibm_status ibm_launch_count(const ibm_solver* h, long long* count);
 
+/* Diagnostics without a handle and without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not allocate device memory themselves or through this library --
+ * for instance code whose device memory is owned entirely by another
+ * allocator (a framework's caching pool), or a latency-critical loop that
+ * cannot afford cudaMalloc's implicit synchronisation.  It computes what
+ * ibm_diagnostics computes (pi = 0, step = -1) from device pointers to the
+ * fields u, v, w (w unused in 2D), p and the packed mask of
+ * ibm_get_classification (N bytes each in the grid precision, mask 1 byte),
+ * on `stream` (a cudaStream_t, NULL = legacy default).  Blocking.
+ *   - Scratch: the per-block partial sums live in a fixed array of this
+ *     library's own device memory (196,736 bytes, present on every GPU that
+ *     loads the library until the process exits); nothing is allocated.
+ *   - Limit: grids of at most 134,217,728 cells; larger ones return
+ *     IBM_E_INVALID with a message.  x and z must be periodic.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - All calls share the array: calls that overlap on the GPU (unordered
+ *     streams) race on it and must be serialised by the caller.
+ * Returns IBM_E_DIVERGED (and fills out->status) on non-finite values. */
+ibm_status ibm_diagnostics_noalloc(const ibm_grid_desc* grid, const void* u, const void* v, const void* w,
+                                   const void* p, const unsigned char* mask, double dt, void* stream,
+                                   ibm_diag* out);
+
 /* Release host metadata, events, graphs and cuFFT plans; never frees the
  * caller's device buffers.  Safe on NULL. */
 void ibm_destroy(ibm_solver* h);

@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "IBM_OK", -1: "IBM_E_INVALID", -2: "IBM_E_CUDA", -3: "IBM_E_N
 EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_geometry", "ibm_weights_bytes",
             "ibm_build_weights", "ibm_step", "ibm_project", "ibm_poisson", "ibm_diagnostics",
             "ibm_get_classification", "ibm_get_weights", "ibm_state_bytes", "ibm_export_state",
-            "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_destroy")
+            "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_diagnostics_noalloc",
+            "ibm_destroy")
 
 
 class ibm_grid_desc(C.Structure):
@@ -89,6 +90,8 @@ def _load() -> C.CDLL:
         "ibm_timing": ([C.c_void_p, C.c_int], C.c_int),
         "ibm_get_timing": ([C.c_void_p, P(ibm_kernel_time), C.c_int, P(C.c_int)], C.c_int),
         "ibm_launch_count": ([C.c_void_p, P(C.c_longlong)], C.c_int),
+        "ibm_diagnostics_noalloc": ([P(ibm_grid_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_double, C.c_void_p, P(ibm_diag)], C.c_int),
         "ibm_destroy": ([C.c_void_p], None),
     }
     for name, (args, res) in sig.items():
@@ -202,6 +205,17 @@ def ibm_launch_count(h: int) -> int:
     n = C.c_longlong(0)
     _check(lib.ibm_launch_count(C.c_void_p(h), C.byref(n)), "ibm_launch_count")
     return n.value
+
+
+def ibm_diagnostics_noalloc(grid: ibm_grid_desc, u: int, v: int, w: int, p: int, mask: int, dt: float,
+                            stream: int, raise_on_diverged: bool = True) -> ibm_diag:
+    """Diagnostics from device pointers alone, for callers that must not allocate device memory."""
+    d = ibm_diag()
+    st = lib.ibm_diagnostics_noalloc(C.byref(grid), C.c_void_p(u), C.c_void_p(v), C.c_void_p(w or None),
+                                     C.c_void_p(p), C.c_void_p(mask), float(dt), C.c_void_p(stream), C.byref(d))
+    if st != IBM_E_DIVERGED or raise_on_diverged:
+        _check(st, "ibm_diagnostics_noalloc")
+    return d
 
 
 def ibm_destroy(h: int):
