@@ -8,6 +8,7 @@
 #include "common.cuh"
 
 #include <cstdio>
+#include <type_traits>
 
 namespace {
 
@@ -105,10 +106,26 @@ __device__ __forceinline__ void store_plane(const TileSrc<T>& S, const PlaneRegs
     }
 }
 
+// Per-component update of one internal point: RHS N (already without the
+// IBM term), pressure gradient gp, previous RHS, then the implicit division.
+template <typename T>
+__device__ __forceinline__ T stage_update(const StageP<T>& sp, T uP, T N, T gp, T Nprev, bool isibm,
+                                          const Coef4<T>& q, T& Nout) {
+    if (isibm) N += q.s;
+    T R = sp.dta * N - sp.ckdt * gp;
+    if (sp.read_prev) R += sp.dtb * Nprev;
+    Nout = N;
+    return isibm ? (q.a * uP + q.b * R) : (uP + R);
+}
+
 // K3 kernel.  Four rotating plane slots let one barrier per plane suffice:
 // the slot written for plane k+1 last held plane k-3, which no warp still
-// computing plane k-1 reads.  Convection uses a^2 - b^2 = (a - b)(a + b) and
-// all constant factors are folded into the StageP coefficients.
+// computing plane k-1 reads.  Every distinct tile value a cell needs is read
+// from shared memory once; values of the cell's own column that the next
+// plane needs again are carried in registers.  The own cell's global data
+// (mask, pressure and its +x/+y/+z neighbours, previous RHS) is requested
+// before the barrier so its latency overlaps the wait.  Convection uses
+// a^2 - b^2 = (a - b)(a + b) and constant factors are folded into StageP.
 template <typename T, bool THREE>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 3)
     k_momentum(GridP g, MomF<T> F, StageP<T> sp, IbmStage<T> ib, double* __restrict__ flux_part) {
@@ -127,6 +144,7 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 3)
     const int dxp = (i + 1 < g.nx) ? 1 : 1 - g.nx;  // offset of the +x neighbour (periodic)
     const bool live_row = j < g.ny;
     const bool live = live_row && i < g.nx;
+    const T two = T(2);
     T fsum = T(0);
 
     TileSrc<T> S;
@@ -134,7 +152,7 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 3)
     PlaneRegs<T, NC> R;
     if (THREE) {
         fetch_plane<T, NC>(F, S, R, wrapi(kbeg - 1, g.nz) * plane);
-        store_plane<T, NC>(S, R, tile[(kbeg - 1 - kbeg + 4) & 3]);
+        store_plane<T, NC>(S, R, tile[3]);
         fetch_plane<T, NC>(F, S, R, kbeg * plane);
         store_plane<T, NC>(S, R, tile[0]);
         fetch_plane<T, NC>(F, S, R, wrapi(kbeg + 1, g.nz) * plane);
@@ -142,6 +160,9 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 3)
         fetch_plane<T, NC>(F, S, R, 0);
         store_plane<T, NC>(S, R, tile[0]);
     }
+    // carried column values (plane k: c*, plane k-1: p*)
+    T cU0 = 0, cU0w = 0, cV0 = 0, cV0s = 0, cW0 = 0, pU0 = 0, pV0 = 0, pW0 = 0, pWe = 0, pWn = 0;
+
     for (int k = kbeg; k < kend; ++k) {
         const int rel = k - kbeg;
         const int s0 = THREE ? (rel & 3) : 0, sm = (rel + 3) & 3, spl = (rel + 1) & 3;
@@ -149,11 +170,26 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 3)
             store_plane<T, NC>(S, R, tile[spl]);                                   // plane k+1
             if (k + 1 < kend) fetch_plane<T, NC>(F, S, R, wrapi(k + 2, g.nz) * plane);
         }
+        // own-cell global data, requested before the barrier
+        const int id = rowbase + k * plane;
+        uint8_t m = 0;
+        T pP = 0, pE = 0, pN = 0, pT = 0, Np[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Np[c] = T(0);
+        if (live) {
+            m = F.mask[id];
+            pP = F.p[id];
+            pE = F.p[id + dxp];
+            pN = (j + 1 < g.ny) ? F.p[id + g.nx] : pP;
+            if (THREE) pT = F.p[id + ((k + 1 < g.nz) ? plane : plane - (int)g.N)];
+            if (sp.read_prev) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) Np[c] = F.Nn[c][id];
+            }
+        }
         __syncthreads();
         if (live_row) {
-            const int id = rowbase + k * plane;
             const int seg = (j + g.ny * k) * g.nsegx + blockIdx.x;
-            const uint8_t m = i < g.nx ? F.mask[id] : 0;
             int pos[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
@@ -163,81 +199,88 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 3)
             if (live) {
                 const T* U0 = tile[s0][0];
                 const T* V0 = tile[s0][1];
-                const T pP = F.p[id];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    T out = T(0), Nv = T(0);
-                    if ((m >> c) & 1u) {
-                        T N, gp, uP;
-                        if (c == 0) {
-                            uP = U0[c0];
-                            const T uE = U0[c0 + 1], uW = U0[c0 - 1], uN = U0[c0 + HX], uS = U0[c0 - HX];
-                            const T sx = uE + uW, sy = uN + uS;
-                            T conv = (uE - uW) * (sx + T(2) * uP) * sp.qx;
-                            conv += ((V0[c0] + V0[c0 + 1]) * (uP + uN) - (V0[c0 - HX] + V0[c0 - HX + 1]) * (uS + uP)) * sp.qy;
-                            T lap = (sx - T(2) * uP) * sp.nx2 + (sy - T(2) * uP) * sp.ny2;
-                            if (THREE) {
-                                const T* Um = tile[sm][0];
-                                const T* Up = tile[spl][0];
-                                const T* W0 = tile[s0][NC - 1];
-                                const T* Wm = tile[sm][NC - 1];
-                                const T uT = Up[c0], uB = Um[c0];
-                                conv += ((W0[c0] + W0[c0 + 1]) * (uP + uT) - (Wm[c0] + Wm[c0 + 1]) * (uB + uP)) * sp.qz;
-                                lap += (uT + uB - T(2) * uP) * sp.nz2;
-                            }
-                            N = lap - conv + sp.g[0];
-                            gp = (F.p[id + dxp] - pP) * sp.idx;
-                        } else if (c == 1) {
-                            uP = V0[c0];
-                            const T vE = V0[c0 + 1], vW = V0[c0 - 1], vN = V0[c0 + HX], vS = V0[c0 - HX];
-                            const T sx = vE + vW, sy = vN + vS;
-                            T conv = ((U0[c0] + U0[c0 + HX]) * (uP + vE) - (U0[c0 - 1] + U0[c0 - 1 + HX]) * (vW + uP)) * sp.qx;
-                            conv += (vN - vS) * (sy + T(2) * uP) * sp.qy;
-                            T lap = (sx - T(2) * uP) * sp.nx2 + (sy - T(2) * uP) * sp.ny2;
-                            if (THREE) {
-                                const T* Vm = tile[sm][1];
-                                const T* Vp = tile[spl][1];
-                                const T* W0 = tile[s0][NC - 1];
-                                const T* Wm = tile[sm][NC - 1];
-                                const T vT = Vp[c0], vB = Vm[c0];
-                                conv += ((W0[c0] + W0[c0 + HX]) * (uP + vT) - (Wm[c0] + Wm[c0 + HX]) * (vB + uP)) * sp.qz;
-                                lap += (vT + vB - T(2) * uP) * sp.nz2;
-                            }
-                            N = lap - conv + sp.g[1];
-                            gp = (F.p[id + g.nx] - pP) * sp.idy;   // j < ny-1 for internal v
-                        } else {
-                            const T* W0 = tile[s0][NC - 1];
-                            const T* Wm = tile[sm][NC - 1];
-                            const T* Wp = tile[spl][NC - 1];
-                            const T* Up = tile[spl][0];
-                            const T* Vp = tile[spl][1];
-                            uP = W0[c0];
-                            const T wE = W0[c0 + 1], wW = W0[c0 - 1], wN = W0[c0 + HX], wS = W0[c0 - HX];
-                            const T wT = Wp[c0], wB = Wm[c0];
-                            const T sz = wT + wB;
-                            T conv = ((U0[c0] + Up[c0]) * (uP + wE) - (U0[c0 - 1] + Up[c0 - 1]) * (wW + uP)) * sp.qx;
-                            conv += ((V0[c0] + Vp[c0]) * (uP + wN) - (V0[c0 - HX] + Vp[c0 - HX]) * (wS + uP)) * sp.qy;
-                            conv += (wT - wB) * (sz + T(2) * uP) * sp.qz;
-                            const T lap = (wE + wW - T(2) * uP) * sp.nx2 + (wN + wS - T(2) * uP) * sp.ny2 +
-                                          (sz - T(2) * uP) * sp.nz2;
-                            N = lap - conv + sp.g[2];
-                            const int dzp = (k + 1 < g.nz) ? plane : plane - (int)g.N;
-                            gp = (F.p[id + dzp] - pP) * sp.idz;
-                        }
-                        const bool isibm = (m >> (4 + c)) & 1u;
-                        Coef4<T> q;
-                        if (isibm) {
-                            q = ib.coef[c][ib.segoff[c][seg] + pos[c]];
-                            N += q.s;
-                        }
-                        T R = sp.dta * N - sp.ckdt * gp;
-                        if (sp.read_prev) R += sp.dtb * F.Nn[c][id];
-                        out = isibm ? (q.a * uP + q.b * R) : (uP + R);
-                        Nv = N;
-                        if (c == 0) fsum += out;
+                // plane k values (own column carried from the previous plane)
+                if (!THREE || k == kbeg) {
+                    cU0 = U0[c0]; cU0w = U0[c0 - 1]; cV0 = V0[c0]; cV0s = V0[c0 - HX];
+                    if (THREE) {
+                        cW0 = tile[s0][NC - 1][c0];
+                        pU0 = tile[sm][0][c0]; pV0 = tile[sm][1][c0];
+                        const T* Wm = tile[sm][NC - 1];
+                        pW0 = Wm[c0]; pWe = Wm[c0 + 1]; pWn = Wm[c0 + HX];
                     }
-                    F.us[c][id] = out;
-                    if (sp.write_n) F.Nn[c][id] = Nv;
+                }
+                const T uP = cU0, uW = cU0w, uE = U0[c0 + 1], uN = U0[c0 + HX], uS = U0[c0 - HX];
+                const T uNW = U0[c0 - 1 + HX];
+                const T vP = cV0, vS = cV0s, vE = V0[c0 + 1], vW = V0[c0 - 1], vN = V0[c0 + HX];
+                const T vSE = V0[c0 - HX + 1];
+                T wP = 0, wE = 0, wW = 0, wN = 0, wS = 0, uT = 0, uTW = 0, vT = 0, vTS = 0, wT = 0;
+                if (THREE) {
+                    const T* W0 = tile[s0][NC - 1];
+                    const T* Up = tile[spl][0];
+                    const T* Vp = tile[spl][1];
+                    wP = cW0; wE = W0[c0 + 1]; wW = W0[c0 - 1]; wN = W0[c0 + HX]; wS = W0[c0 - HX];
+                    uT = Up[c0]; uTW = Up[c0 - 1]; vT = Vp[c0]; vTS = Vp[c0 - HX];
+                    wT = tile[spl][NC - 1][c0];
+                }
+                const T uB = pU0, vB = pV0, wB = pW0, wBE = pWe, wBN = pWn;
+
+                T outU = T(0), outV = T(0), outW = T(0), NU = T(0), NV = T(0), NW = T(0);
+                // ---- u ----
+                if (m & IBM_MASK_U) {
+                    const T sx = uE + uW, sy = uN + uS;
+                    T conv = (uE - uW) * (sx + two * uP) * sp.qx;
+                    conv += ((vP + vE) * (uP + uN) - (vS + vSE) * (uS + uP)) * sp.qy;
+                    T lap = (sx - two * uP) * sp.nx2 + (sy - two * uP) * sp.ny2;
+                    if (THREE) {
+                        conv += ((wP + wE) * (uP + uT) - (wB + wBE) * (uB + uP)) * sp.qz;
+                        lap += (uT + uB - two * uP) * sp.nz2;
+                    }
+                    Coef4<T> q = {};
+                    const bool ibm = m & IBM_MASK_IBM_U;
+                    if (ibm) q = ib.coef[0][ib.segoff[0][seg] + pos[0]];
+                    outU = stage_update(sp, uP, lap - conv + sp.g[0], (pE - pP) * sp.idx, Np[0], ibm, q, NU);
+                    fsum += outU;
+                }
+                // ---- v ----
+                if (m & IBM_MASK_V) {
+                    const T sx = vE + vW, sy = vN + vS;
+                    T conv = ((uP + uN) * (vP + vE) - (uW + uNW) * (vW + vP)) * sp.qx;
+                    conv += (vN - vS) * (sy + two * vP) * sp.qy;
+                    T lap = (sx - two * vP) * sp.nx2 + (sy - two * vP) * sp.ny2;
+                    if (THREE) {
+                        conv += ((wP + wN) * (vP + vT) - (wB + wBN) * (vB + vP)) * sp.qz;
+                        lap += (vT + vB - two * vP) * sp.nz2;
+                    }
+                    Coef4<T> q = {};
+                    const bool ibm = m & IBM_MASK_IBM_V;
+                    if (ibm) q = ib.coef[1][ib.segoff[1][seg] + pos[1]];
+                    outV = stage_update(sp, vP, lap - conv + sp.g[1], (pN - pP) * sp.idy, Np[1], ibm, q, NV);
+                }
+                // ---- w ----
+                if (THREE && (m & IBM_MASK_W)) {
+                    const T sz = wT + wB;
+                    T conv = ((uP + uT) * (wP + wE) - (uW + uTW) * (wW + wP)) * sp.qx;
+                    conv += ((vP + vT) * (wP + wN) - (vS + vTS) * (wS + wP)) * sp.qy;
+                    conv += (wT - wB) * (sz + two * wP) * sp.qz;
+                    const T lap = (wE + wW - two * wP) * sp.nx2 + (wN + wS - two * wP) * sp.ny2 +
+                                  (sz - two * wP) * sp.nz2;
+                    Coef4<T> q = {};
+                    const bool ibm = m & IBM_MASK_IBM_W;
+                    if (ibm) q = ib.coef[NC - 1][ib.segoff[NC - 1][seg] + pos[NC - 1]];
+                    outW = stage_update(sp, wP, lap - conv + sp.g[2], (pT - pP) * sp.idz, Np[NC - 1], ibm, q, NW);
+                }
+                F.us[0][id] = outU;
+                F.us[1][id] = outV;
+                if (THREE) F.us[NC - 1][id] = outW;
+                if (sp.write_n) {
+                    F.Nn[0][id] = NU;
+                    F.Nn[1][id] = NV;
+                    if (THREE) F.Nn[NC - 1][id] = NW;
+                }
+                if (THREE) {
+                    // carry this column into the next plane
+                    pU0 = uP; pV0 = vP; pW0 = wP; pWe = wE; pWn = wN;
+                    cU0 = uT; cU0w = uTW; cV0 = vT; cV0s = vTS; cW0 = wT;
                 }
             }
         }
@@ -271,7 +314,7 @@ __global__ void k_flux_pi(const double* __restrict__ part, int n, double dV, dou
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) q += sh[w];
         double pi = (target - q * dV) / S;
         scal[0] = pi;
-        *reinterpret_cast<T*>(scal + 2) = (T)pi;   // typed copy read by k_flux_apply
+        *reinterpret_cast<T*>(scal + 2) = (T)pi;   // typed copy read by the flux corrections
     }
 }
 
@@ -295,26 +338,84 @@ __global__ void __launch_bounds__(256) k_flux_apply(GridP g, T* __restrict__ us,
 }
 
 // ---------------------------------------------------------------------------
-// K4: divergence of the predictor, D u* (in the field precision)
+// Constant-flow-rate correction Pi c_k dt beta of an internal u point, applied
+// on the fly by the divergence and correction kernels (so the corrected u* is
+// never written): beta = 1 at a regular internal point, the stage's IBM beta
+// at an IBM point, and the point is skipped when not internal.
 // ---------------------------------------------------------------------------
 template <typename T>
+struct FluxCorr {
+    const double* scal;    // the typed Pi sits at scal + 2
+    T ckdt;
+    const int* segoff;     // u component
+    const Coef4<T>* coef;  // u component, this stage
+};
+
+template <typename T>
+__device__ __forceinline__ T flux_increment(const FluxCorr<T>& fc, T pic, uint8_t m, unsigned ibm_ballot, int seg,
+                                            int lane) {
+    if (!(m & IBM_MASK_U)) return T(0);
+    T beta = T(1);
+    if (m & IBM_MASK_IBM_U) beta = fc.coef[fc.segoff[seg] + __popc(ibm_ballot & ((1u << lane) - 1u))].b;
+    return pic * beta;
+}
+
+// ---------------------------------------------------------------------------
+// K4: divergence of the predictor, D u*, in the field precision.  Each block
+// marches KZD planes along z carrying w*(k-1) in a register; u*(i-1) comes
+// from the neighbouring lane.
+// ---------------------------------------------------------------------------
+constexpr int KZD = 16;
+
+template <typename T, bool THREE, bool FLUX>
 __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict__ u, const T* __restrict__ v,
-                                                    const T* __restrict__ w, T* __restrict__ rhs, T idx, T idy,
-                                                    T idz) {
-    const int i = blockIdx.x * 32 + threadIdx.x;
+                                                    const T* __restrict__ w, const uint8_t* __restrict__ mask,
+                                                    T* __restrict__ rhs, T idx, T idy, T idz, FluxCorr<T> fc) {
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * 32 + lane;
     const int j = blockIdx.y * 8 + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const long long row = j + (long long)g.ny * k;
-    const long long id = i + (long long)g.nx * row;
-    T d = (u[id] - u[row * g.nx + wrapi(i - 1, g.nx)]) * idx;
-    const T vm = j > 0 ? v[id - g.nx] : T(0);
-    d += (v[id] - vm) * idy;
-    if (g.ndim == 3) {
-        const long long idB = i + (long long)g.nx * (j + (long long)g.ny * wrapi(k - 1, g.nz));
-        d += (w[id] - w[idB]) * idz;
+    if (j >= g.ny) return;                                   // whole warp
+    const int kbeg = THREE ? blockIdx.z * KZD : 0;
+    const int kend = THREE ? min(kbeg + KZD, g.nz) : 1;
+    const bool live = i < g.nx;
+    const int plane = g.nx * g.ny;
+    // left neighbour of lane 0 (periodic in x) and its place in its 32-point segment
+    const int il = wrapi((int)blockIdx.x * 32 - 1, g.nx);
+    const int segl = il / 32, lanel = il % 32;
+    const int il_probe = segl * 32 + lane;                  // the warp reads that segment's mask bits
+    const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
+    T wprev = T(0);
+    if (THREE && live) wprev = w[i + g.nx * j + plane * wrapi(kbeg - 1, g.nz)];
+#pragma unroll 2
+    for (int k = kbeg; k < kend; ++k) {
+        const int rowb = g.nx * (j + g.ny * k);
+        const int id = rowb + i;
+        T uc = live ? u[id] : T(0);
+        T ulane0 = u[rowb + il];
+        if (FLUX) {
+            const int rowseg = (j + g.ny * k) * g.nsegx;
+            const uint8_t m = live ? mask[id] : 0;
+            const unsigned b = __ballot_sync(0xffffffffu, (m & IBM_MASK_IBM_U) != 0);
+            if (live) uc += flux_increment(fc, pic, m, b, rowseg + (int)blockIdx.x, lane);
+            const uint8_t ml = il_probe < g.nx ? mask[rowb + il_probe] : 0;
+            const unsigned bl = __ballot_sync(0xffffffffu, (ml & IBM_MASK_IBM_U) != 0);
+            const uint8_t mln = __shfl_sync(0xffffffffu, ml, lanel);
+            ulane0 += flux_increment(fc, pic, mln, bl, rowseg + segl, lanel);
+        }
+        T ul = __shfl_up_sync(0xffffffffu, uc, 1);
+        if (lane == 0) ul = ulane0;
+        if (live) {
+            T d = (uc - ul) * idx;
+            const T vm = j > 0 ? v[id - g.nx] : T(0);
+            d += (v[id] - vm) * idy;
+            if (THREE) {
+                const T wc = w[id];
+                d += (wc - wprev) * idz;
+                wprev = wc;
+            }
+            rhs[id] = d;
+        }
     }
-    rhs[id] = d;
 }
 
 // ---------------------------------------------------------------------------
@@ -331,73 +432,85 @@ __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict
 // that feed it; that sweep works in place on the spectrum.
 // One warp covers 32 consecutive kx of one kz, so loads coalesce across systems.
 // ---------------------------------------------------------------------------
+// FP64 sweep of one component (real or imaginary part) of one system: the two
+// parts are independent recurrences, so two threads share a system and the
+// FP64 work is spread over twice as many warps.  The next batch of loads is
+// issued before the current batch is consumed.
 template <typename C>
 __device__ __forceinline__ void tridiag_fp64(const GridP& g, C* spec, double2* tmp, const double* __restrict__ piv,
-                                             long long base, double scale, bool zero_mode) {
+                                             long long base, int comp, double scale, bool zero_mode) {
     constexpr bool F32 = sizeof(C) == sizeof(float2);
+    using S = typename std::conditional<F32, float, double>::type;   // storage scalar
     constexpr int B = 8;
     const long long st = g.nxh;
     const int ny = g.ny;
-    // FP32 storage: the scale is applied to the FP32 input (exact to FP32
-    // rounding, like the data); FP64 storage: applied in FP64 on output.
+    S* sp = reinterpret_cast<S*>(spec) + comp;      // component `comp` of spec[o] at sp[2 o]
+    double* tp = reinterpret_cast<double*>(tmp) + comp;
     const float sf = (float)scale;
-    const double so = F32 ? 1.0 : scale;
-    double2 e = make_double2(0.0, 0.0);
+    double e = 0.0;
+    S r[B], rn[B];
+    double w[B], wn[B];
+#pragma unroll
+    for (int t = 0; t < B; ++t)
+        if (t < ny) {
+            r[t] = sp[2 * (base + t * st)];
+            w[t] = piv[base + t * st];
+        }
     for (int j0 = 0; j0 < ny; j0 += B) {
-        C r[B];
-        double w[B];
 #pragma unroll
         for (int t = 0; t < B; ++t)
-            if (j0 + t < ny) {
-                r[t] = spec[base + (j0 + t) * st];
-                w[t] = piv[base + (j0 + t) * st];
+            if (j0 + B + t < ny) {
+                rn[t] = sp[2 * (base + (j0 + B + t) * st)];
+                wn[t] = piv[base + (j0 + B + t) * st];
             }
 #pragma unroll
         for (int t = 0; t < B; ++t)
             if (j0 + t < ny) {
-                const double rx = F32 ? (double)((float)r[t].x * sf) : (double)r[t].x;
-                const double ry = F32 ? (double)((float)r[t].y * sf) : (double)r[t].y;
-                e = make_double2((rx - e.x) * w[t], (ry - e.y) * w[t]);    // e_{-1} = 0
-                tmp[base + (j0 + t) * st] = e;
+                // FP32 storage: the scale is applied in FP32 on the input (exact to FP32 rounding)
+                const double rv = F32 ? (double)((float)r[t] * sf) : (double)r[t];
+                e = (rv - e) * w[t];                                          // e_{-1} = 0
+                tp[2 * (base + (j0 + t) * st)] = e;
             }
+#pragma unroll
+        for (int t = 0; t < B; ++t) { r[t] = rn[t]; w[t] = wn[t]; }
     }
-    double2 x = e;
-    double sr = 0.0, si = 0.0;
-    {
-        C out;
-        out.x = x.x * so;
-        out.y = x.y * so;
-        spec[base + (long long)(ny - 1) * st] = out;
-        if (zero_mode) { sr += x.x; si += x.y; }
-    }
+    double x = e;
+    double sum = 0.0;
+    auto put = [&](long long o, double val) {
+        if (F32) sp[2 * o] = (S)val;
+        else sp[2 * o] = (S)(val * scale);
+    };
+    put(base + (long long)(ny - 1) * st, x);
+    if (zero_mode) sum += x;
+    double d[B], dn[B];
+#pragma unroll
+    for (int t = 0; t < B; ++t)
+        if (ny - 2 - t >= 0) {
+            d[t] = tp[2 * (base + (ny - 2 - t) * st)];
+            w[t] = piv[base + (ny - 2 - t) * st];
+        }
     for (int j1 = ny - 2; j1 >= 0; j1 -= B) {
-        double2 d[B];
-        double w[B];
 #pragma unroll
         for (int t = 0; t < B; ++t)
-            if (j1 - t >= 0) {
-                d[t] = tmp[base + (j1 - t) * st];
-                w[t] = piv[base + (j1 - t) * st];
+            if (j1 - B - t >= 0) {
+                dn[t] = tp[2 * (base + (j1 - B - t) * st)];
+                wn[t] = piv[base + (j1 - B - t) * st];
             }
 #pragma unroll
         for (int t = 0; t < B; ++t)
             if (j1 - t >= 0) {
-                x = make_double2(d[t].x - w[t] * x.x, d[t].y - w[t] * x.y);
-                C out;
-                out.x = x.x * so;
-                out.y = x.y * so;
-                spec[base + (j1 - t) * st] = out;
-                if (zero_mode) { sr += x.x; si += x.y; }
+                x = d[t] - w[t] * x;
+                put(base + (j1 - t) * st, x);
+                if (zero_mode) sum += x;
             }
+#pragma unroll
+        for (int t = 0; t < B; ++t) { d[t] = dn[t]; w[t] = wn[t]; }
     }
     if (zero_mode) {
-        const double mr = sr / ny * so, mi = si / ny * so;
+        const double mean = sum / ny * (F32 ? 1.0 : scale);
         for (int j = 0; j < ny; ++j) {
             const long long o = base + j * st;
-            C v = spec[o];
-            v.x = (double)v.x - mr;
-            v.y = (double)v.y - mi;
-            spec[o] = v;
+            sp[2 * o] = (S)((double)sp[2 * o] - mean);
         }
     }
 }
@@ -452,59 +565,77 @@ __device__ __forceinline__ void tridiag_fp32(const GridP& g, float2* spec, const
 
 // One warp per block; `order` lists the systems (kz * nxh + kx) with every
 // FP64 system first, so the scarce FP64 pipes of all SMs share the low modes.
+// FP64 systems take two threads (real and imaginary part), FP32 systems one.
 template <typename C>
 __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, const double* __restrict__ piv,
                                                 const float* __restrict__ piv32, const int* __restrict__ order,
                                                 int n64, int nsys, double scale) {
-    const int nb64 = (n64 + 31) / 32;
-    int q;
-    bool fp64;
+    const int nb64 = (2 * n64 + 31) / 32;
     if ((int)blockIdx.x < nb64) {
-        q = blockIdx.x * 32 + threadIdx.x;
-        if (q >= n64) return;
-        fp64 = true;
-    } else {
-        q = n64 + (blockIdx.x - nb64) * 32 + threadIdx.x;
-        if (q >= nsys) return;
-        fp64 = false;
+        const int t = blockIdx.x * 32 + threadIdx.x;
+        if (t >= 2 * n64) return;
+        const int sys = order[t >> 1];
+        const int kx = sys % g.nxh, kz = sys / g.nxh;
+        const long long base = (long long)kz * g.ny * g.nxh + kx;
+        tridiag_fp64<C>(g, spec, tmp, piv, base, t & 1, scale, kx == 0 && kz == 0);
+        return;
     }
-    const int sys = order[q];
-    const int kx = sys % g.nxh;
-    const int kz = sys / g.nxh;
-    const long long base = (long long)kz * g.ny * g.nxh + kx;
     if constexpr (sizeof(C) == sizeof(float2)) {
-        if (!fp64) {
-            tridiag_fp32(g, reinterpret_cast<float2*>(spec), piv32, base, (float)scale);
-            return;
-        }
+        const int q = n64 + (blockIdx.x - nb64) * 32 + threadIdx.x;
+        if (q >= nsys) return;
+        const int sys = order[q];
+        const int kx = sys % g.nxh, kz = sys / g.nxh;
+        const long long base = (long long)kz * g.ny * g.nxh + kx;
+        tridiag_fp32(g, reinterpret_cast<float2*>(spec), piv32, base, (float)scale);
     }
-    tridiag_fp64<C>(g, spec, tmp, piv, base, scale, kx == 0 && kz == 0);
 }
 
 // ---------------------------------------------------------------------------
-// K7: u = u* - G psi on every non-wall face, p += psi / (c_k dt)
-// (psi = c_k dt phi is what the Poisson solve returns for rhs = D u*)
+// K7: u = u* (+ flux correction) - G psi on every non-wall face, p += psi/(c_k dt)
+// (psi = c_k dt phi is what the Poisson solve returns for rhs = D u*).  Blocks
+// march KZD planes carrying psi(k+1) into the next plane; psi(i+1) comes from
+// the neighbouring lane.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool THREE, bool FLUX>
 __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ us0, const T* __restrict__ us1,
                                                  const T* __restrict__ us2, const T* __restrict__ psi,
-                                                 T* __restrict__ u0, T* __restrict__ u1, T* __restrict__ u2,
-                                                 T* __restrict__ p, T idx, T idy, T idz, T inv_ckdt,
-                                                 int update_p) {
-    const int i = blockIdx.x * 32 + threadIdx.x;
+                                                 const uint8_t* __restrict__ mask, T* __restrict__ u0,
+                                                 T* __restrict__ u1, T* __restrict__ u2, T* __restrict__ p, T idx,
+                                                 T idy, T idz, T inv_ckdt, int update_p, FluxCorr<T> fc) {
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * 32 + lane;
     const int j = blockIdx.y * 8 + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const long long row = j + (long long)g.ny * k;
-    const long long id = i + (long long)g.nx * row;
-    T ph = psi[id];
-    u0[id] = us0[id] - (psi[row * g.nx + wrapi(i + 1, g.nx)] - ph) * idx;
-    u1[id] = j < g.ny - 1 ? us1[id] - (psi[id + g.nx] - ph) * idy : us1[id];
-    if (g.ndim == 3) {
-        long long idT = i + (long long)g.nx * (j + (long long)g.ny * wrapi(k + 1, g.nz));
-        u2[id] = us2[id] - (psi[idT] - ph) * idz;
+    if (j >= g.ny) return;                                   // whole warp
+    const int kbeg = THREE ? blockIdx.z * KZD : 0;
+    const int kend = THREE ? min(kbeg + KZD, g.nz) : 1;
+    const bool live = i < g.nx;
+    const int plane = g.nx * g.ny;
+    const int ir = (i + 1 < g.nx) ? i + 1 : 0;              // +x neighbour (periodic)
+    const bool from_lane = lane < 31 && i + 1 < g.nx;
+    const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
+    T ph = live ? psi[i + g.nx * j + plane * kbeg] : T(0);
+#pragma unroll 2
+    for (int k = kbeg; k < kend; ++k) {
+        const int rowb = g.nx * (j + g.ny * k);
+        const int id = rowb + i;
+        T pE = __shfl_down_sync(0xffffffffu, ph, 1);
+        T uc = T(0);
+        if (FLUX) {
+            const uint8_t m = live ? mask[id] : 0;
+            const unsigned b = __ballot_sync(0xffffffffu, (m & IBM_MASK_IBM_U) != 0);
+            if (live) uc = flux_increment(fc, pic, m, b, (j + g.ny * k) * g.nsegx + (int)blockIdx.x, lane);
+        }
+        T pT = T(0);
+        if (THREE && live) pT = psi[id + ((k + 1 < g.nz) ? plane : plane - (int)g.N)];
+        if (live) {
+            if (!from_lane) pE = psi[rowb + ir];
+            u0[id] = us0[id] + uc - (pE - ph) * idx;
+            u1[id] = j < g.ny - 1 ? us1[id] - (psi[id + g.nx] - ph) * idy : us1[id];
+            if (THREE) u2[id] = us2[id] - (pT - ph) * idz;
+            if (update_p) p[id] += ph * inv_ckdt;
+        }
+        ph = pT;
     }
-    if (update_p) p[id] += ph * inv_ckdt;
 }
 
 // initial-condition projection: copy the velocity with non-internal points zeroed
@@ -604,7 +735,7 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
     timer_end(h, t, "fft_forward");
     double scale = g.dy * g.dy / ((double)g.nx * (double)g.nz);
     const int nsys = g.nz * g.nxh;
-    const int nblk = (h->n64 + 31) / 32 + (nsys - h->n64 + 31) / 32;
+    const int nblk = (2 * h->n64 + 31) / 32 + (nsys - h->n64 + 31) / 32;
     timer_begin(h, "tridiag", &t);
     if (h->prec == IBM_FP64)
         k_tridiag<double2><<<nblk, 32, 0, h->stream>>>(g, (double2*)h->spec, (double2*)h->spec, h->pivots,
@@ -622,16 +753,60 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
     return IBM_OK;
 }
 
+dim3 zmarch_grid(const GridP& g) {
+    return dim3(g.nsegx, (g.ny + 7) / 8, g.ndim == 3 ? (g.nz + KZD - 1) / KZD : 1);
+}
+
 template <typename T>
-ibm_status divergence_and_solve(ibm_solver* h, T* const us[3]) {
+FluxCorr<T> flux_corr(ibm_solver* h, int k) {
+    FluxCorr<T> fc;
+    fc.scal = h->scal;
+    fc.ckdt = (T)(h->phys.dt * RK_C[k]);
+    fc.segoff = h->segoff[0];
+    fc.coef = (const Coef4<T>*)h->coef[0] + (long long)k * h->counts[0];
+    return fc;
+}
+
+template <typename T>
+ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const FluxCorr<T>& fc) {
     const GridP& g = h->gp;
     cudaEvent_t t;
     timer_begin(h, "divergence", &t);
-    k_divergence<T><<<cell_grid(g), dim3(32, 8), 0, h->stream>>>(g, us[0], us[1], us[2], (T*)h->rhs, (T)(1.0 / g.dx),
-                                                (T)(1.0 / g.dy), (T)(1.0 / g.dz));
+    const T ix = (T)(1.0 / g.dx), iy = (T)(1.0 / g.dy), iz = (T)(1.0 / g.dz);
+    const dim3 grd = zmarch_grid(g), blk(32, 8);
+    T* rhs = (T*)h->rhs;
+    if (g.ndim == 3) {
+        if (flux) k_divergence<T, true, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us[2], h->mask, rhs, ix, iy, iz, fc);
+        else k_divergence<T, true, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us[2], h->mask, rhs, ix, iy, iz, fc);
+    } else {
+        if (flux) k_divergence<T, false, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us[0], h->mask, rhs, ix, iy, iz, fc);
+        else k_divergence<T, false, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us[0], h->mask, rhs, ix, iy, iz, fc);
+    }
     IBM_LAUNCH_CHECK();
     timer_end(h, t, "divergence");
     return poisson_t<T>(h, h->rhs);
+}
+
+template <typename T>
+ibm_status launch_correct(ibm_solver* h, T* const us[3], T inv_ckdt, int update_p, bool flux, const FluxCorr<T>& fc) {
+    const GridP& g = h->gp;
+    const T ix = (T)(1.0 / g.dx), iy = (T)(1.0 / g.dy), iz = (T)(1.0 / g.dz);
+    const dim3 grd = zmarch_grid(g), blk(32, 8);
+    const T* psi = (const T*)h->rhs;
+    T* u0 = (T*)h->buf.u[0];
+    T* u1 = (T*)h->buf.u[1];
+    T* u2 = g.ndim == 3 ? (T*)h->buf.u[2] : u0;
+    T* us2 = g.ndim == 3 ? us[2] : us[0];
+    T* p = (T*)h->buf.p;
+    if (g.ndim == 3) {
+        if (flux) k_correct<T, true, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy, iz, inv_ckdt, update_p, fc);
+        else k_correct<T, true, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy, iz, inv_ckdt, update_p, fc);
+    } else {
+        if (flux) k_correct<T, false, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy, iz, inv_ckdt, update_p, fc);
+        else k_correct<T, false, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy, iz, inv_ckdt, update_p, fc);
+    }
+    IBM_LAUNCH_CHECK();
+    return IBM_OK;
 }
 
 template <typename T>
@@ -682,25 +857,26 @@ ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
         timer_begin(h, "flux_control", &t);
         k_flux_pi<T><<<1, 1024, 0, h->stream>>>(h->partials, nparts, dV, h->phys.target_flux, h->S[k], h->scal);
         IBM_LAUNCH_CHECK();
-        dim3 fgrd(g.nsegx, (g.ny + 7) / 8, g.nz);
-        k_flux_apply<T><<<fgrd, dim3(32, 8, 1), 0, h->stream>>>(g, (T*)h->ustar[0], h->mask, ib, h->scal, sp.ckdt);
-        IBM_LAUNCH_CHECK();
         timer_end(h, t, "flux_control");
     }
     T* us[3] = {(T*)h->ustar[0], (T*)h->ustar[1], (T*)h->ustar[2]};
     if (predictor_only) {
+        // the caller gets u* itself, so the flux correction is applied explicitly here
+        if (cflux) {
+            dim3 fgrd(g.nsegx, (g.ny + 7) / 8, g.nz);
+            k_flux_apply<T><<<fgrd, dim3(32, 8, 1), 0, h->stream>>>(g, (T*)h->ustar[0], h->mask, ib, h->scal, sp.ckdt);
+            IBM_LAUNCH_CHECK();
+        }
         for (int c = 0; c < g.ncomp; ++c)
             IBM_CUDA_TRY(cudaMemcpyAsync(h->buf.u[c], h->ustar[c], g.N * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
         return IBM_OK;
     }
-    ibm_status st = divergence_and_solve<T>(h, us);
+    const FluxCorr<T> fc = flux_corr<T>(h, k);
+    ibm_status st = divergence_and_solve<T>(h, us, cflux, fc);
     if (st != IBM_OK) return st;
     timer_begin(h, "correct", &t);
-    k_correct<T><<<cell_grid(g), dim3(32, 8), 0, h->stream>>>(g, us[0], us[1], us[2], (const T*)h->rhs, (T*)h->buf.u[0],
-                                            (T*)h->buf.u[1], g.ndim == 3 ? (T*)h->buf.u[2] : (T*)h->buf.u[0],
-                                            (T*)h->buf.p, (T)(1.0 / g.dx), (T)(1.0 / g.dy), (T)(1.0 / g.dz),
-                                            (T)(1.0 / (dt * RK_C[k])), 1);
-    IBM_LAUNCH_CHECK();
+    st = launch_correct<T>(h, us, (T)(1.0 / (dt * RK_C[k])), 1, cflux, fc);
+    if (st != IBM_OK) return st;
     timer_end(h, t, "correct");
     return IBM_OK;
 }
@@ -713,15 +889,10 @@ ibm_status project_t(ibm_solver* h) {
     k_mask_copy<T><<<cell_grid(g), dim3(32, 8), 0, h->stream>>>(g, h->mask, (const T*)h->buf.u[0], (const T*)h->buf.u[1], u2, us[0],
                                               us[1], us[2]);
     IBM_LAUNCH_CHECK();
-    ibm_status st = divergence_and_solve<T>(h, us);
+    const FluxCorr<T> fc = flux_corr<T>(h, 0);
+    ibm_status st = divergence_and_solve<T>(h, us, false, fc);
     if (st != IBM_OK) return st;
-    k_correct<T><<<cell_grid(g), dim3(32, 8), 0, h->stream>>>(g, us[0], us[1], us[2], (const T*)h->rhs,
-                                                               (T*)h->buf.u[0], (T*)h->buf.u[1],
-                                                               g.ndim == 3 ? (T*)h->buf.u[2] : (T*)h->buf.u[0],
-                                                               (T*)h->buf.p, (T)(1.0 / g.dx), (T)(1.0 / g.dy),
-                                                               (T)(1.0 / g.dz), (T)1, 0);
-    IBM_LAUNCH_CHECK();
-    return IBM_OK;
+    return launch_correct<T>(h, us, (T)1, 0, false, fc);
 }
 
 template <typename T>
