@@ -49,7 +49,11 @@ TRIDIAG_BYTES_PER_SPECTRAL_POINT = 64.0
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by kernel, with the hash of the source file it was taken on; a changed
 # source makes the figure stale and it is reported as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/c3s_wavy_384x256x64_hot_kernels_ncu.md: stage-1 launch on 384x256x64 read 118.5 MB and
+    # wrote 104.6 MB; scaled by cells (x4) to a 384x256x256 launch
+    "momentum": (4.0 * (118.507520e6 + 104.616704e6), "47e5f5aabf29c24a"),
+}
 
 
 def src_hash(name="step.cu") -> str:
