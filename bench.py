@@ -84,6 +84,39 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def reduce_max(x: float, dist=None, device="cpu") -> float:
+    """Maximum of x over the ranks of the process group (x itself without one)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(cells: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job Gcell-updates/s: every rank advances its own replica of `cells` cells."""
+    return world * cells * steps / seconds / 1e9
+
+
+def serving_sample(device, n_requests: int = 24, seed: int = 0, load: float = 0.8) -> dict:
+    """A bounded sample of the serving mix (C5): steps and linear sizes scaled
+    down, arrivals at `load` of an assumed 2 Gcell-updates/s capacity."""
+    from inputs import serving_mix, initial_field
+    from paper_2506_14328_gb300.serving import Server, Request
+    probe = serving_mix(seed=seed, n_requests=n_requests, rate_hz=1.0, step_scale=0.1, size_scale=0.5)
+    work = sum(c.ncells * s for _, c, s in probe) / len(probe)
+    rate = load * 2.0e9 / work
+    mix = serving_mix(seed=seed, n_requests=n_requests, rate_hz=rate, step_scale=0.1, size_scale=0.5)
+    # each client sends its initial state with the request (prepared before arrival)
+    reqs = [Request(q, t, c, s, init=initial_field(c)) for q, (t, c, s) in enumerate(mix)]
+    srv = Server(device=str(device), max_resident=32, steps_per_tick=25)
+    stats = srv.serve(reqs)
+    srv.close()
+    stats.update({"arrival_rate_hz": rate, "mix": "C5 sample: 2D n^2 n in [64,512], 3D n^3 n in [32,96], "
+                  "steps 50-500, Re 10-2000, FP32, Poisson arrivals", "seed": seed})
+    return stats
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -246,11 +279,8 @@ def run_gpu(args):
     s.timing(False)
     clk = clocks.stop()
     diag = s.diagnostics()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * case.ncells * args.steps / (ms_max * 1e-3) / 1e9
+    ms_max = reduce_max(ms, dist, device)
+    value = aggregate_rate(case.ncells, args.steps, world, ms_max * 1e-3)
 
     # ---- end to end through the public API with host buffers -----------------
     nbytes = s.state_bytes()
@@ -265,10 +295,7 @@ def run_gpu(args):
         d = s.diagnostics()                           # D2H of the step's result (blocking)
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=device)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * case.ncells * e2e_steps / float(e2e_t.item()) / 1e9
+    e2e_value = aggregate_rate(case.ncells, e2e_steps, world, reduce_max(e2e_s, dist, device))
     diag_bytes = 12 * 8 + 8  # the ibm_diag struct fields read back
 
     if rank == 0:
@@ -315,6 +342,8 @@ def run_gpu(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": diag_bytes},
                 "clocks": clk, "gpu_launches": launches, "kernels": per_kernel}
+        if args.serving > 0:
+            line["serving"] = serving_sample(device, n_requests=args.serving)
         print(json.dumps(line))
     if dist is not None:
         dist.barrier()
@@ -329,6 +358,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c3")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--serving", type=int, default=24, help="requests in the serving sample (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

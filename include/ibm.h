@@ -137,6 +137,7 @@ typedef struct {
 } ibm_kernel_time;
 
 typedef struct ibm_solver ibm_solver;
+typedef struct ibm_batch ibm_batch;
 
 /* Library version (major*10000 + minor*100 + patch). */
 int ibm_version(void);
@@ -206,6 +207,32 @@ ibm_status ibm_import_state(ibm_solver* h, const void* host, size_t bytes);
 ibm_status ibm_timing(ibm_solver* h, int enable);
 /* Blocking: per-kernel launches and summed durations since the last reset. */
 ibm_status ibm_get_timing(ibm_solver* h, ibm_kernel_time* out, int max, int* count);
+/* Tile autotuner (not in the paper: a GB300 tuning aid).  Times the momentum
+ * predictor for every z-chunk in {4, 8, 16, 32, 64} and the divergence
+ * kernel for every z-chunk in {4, 8, 16, 32} on this solver's own grid and
+ * keeps the fastest of each; returns the choices (either pointer may be NULL).
+ * Overwrites only scratch (predictor, RHS history, divergence), so call it
+ * between full steps, outside stream capture.  Blocking.  2D grids keep the
+ * defaults. */
+ibm_status ibm_autotune(ibm_solver* h, int* kz_momentum, int* kz_march);
+/* Set the z-chunks directly (values from a cached autotune). */
+ibm_status ibm_set_tiles(ibm_solver* h, int kz_momentum, int kz_march);
+
+/* Batched stepping of many resident solves (continuous batching, SURVEY's
+ * serving pattern; the paper has no counterpart).  A batch owns a
+ * non-default stream.  ibm_batch_set captures ONE CUDA graph that forks onto
+ * every member's own stream, runs steps[i] full steps of member i there and
+ * joins back, so the members' kernels overlap on the device; call it again
+ * whenever the member set or the step counts change.  Members must have
+ * weights, timing off, and streams other than the legacy default stream.
+ * ibm_batch_run replays the graph once (asynchronous on the batch stream)
+ * and advances each member's step counter by steps[i].  Members must not be
+ * stepped outside the batch while a replay may be running. */
+ibm_status ibm_batch_create(void* stream, ibm_batch** out);
+ibm_status ibm_batch_set(ibm_batch* b, ibm_solver* const* members, const int* steps, int n);
+ibm_status ibm_batch_run(ibm_batch* b);
+void ibm_batch_destroy(ibm_batch* b);
+
 /* Kernels this library has launched through this handle (a running count). */
 ibm_status ibm_launch_count(const ibm_solver* h, long long* count);
 

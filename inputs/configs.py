@@ -165,3 +165,49 @@ def describe(case: Case) -> dict:
             "precision": case.precision, "geometry": case.geom_kind, "nu": case.nu,
             "dt": case.dt, "flow_mode": case.flow_mode}
 
+
+
+def serving_mix(seed: int = 0, n_requests: int = 1000, rate_hz: float = 10.0, step_scale: float = 1.0,
+                size_scale: float = 1.0, precision: str = "fp32") -> list:
+    """C5: a Poisson-arrival stream of 2D and 3D IBM solves.
+
+    Each request: 2D n x n with n log-uniform in [128, 1024] or 3D n^3 with n
+    log-uniform in [64, 192] (half and half); a seeded cylinder (2D) or
+    sphere (3D) in a channel periodic in x (and z) with no-slip box walls in
+    y; Re log-uniform in [10, 2000] on the body diameter and a unit stream;
+    steps uniform in [500, 5000].  `step_scale` and `size_scale` shrink the
+    steps and the linear sizes for bounded runs (sizes rounded to multiples
+    of 8).  Returns [(arrival_seconds, Case, steps)] sorted by arrival.
+    """
+    from .generators import request_draws
+    out = []
+    for q, d in enumerate(request_draws(seed, n_requests)):
+        t = d["arrival"] / rate_hz
+        three = d["three"]
+        lo, hi = (64, 192) if three else (128, 1024)
+        n = int(round(lo * (hi / lo) ** d["size"] * size_scale / 8.0)) * 8
+        n = max(n, 16)
+        Lx = Ly = 2.0
+        D = 0.5
+        re = 10.0 * 200.0 ** d["re"]
+        nu = 1.0 * D / re
+        dx = Lx / n
+        dt = min(0.4 * dx / 1.5, 0.12 * dx * dx / nu)
+        steps = max(1, int(round((500 + 4500 * d["steps"]) * step_scale)))
+        cx = 0.5 + d["cx"] * (Lx - 1.0)
+        cy = 0.5 + d["cy"] * (Ly - 1.0)
+        g = (8.0 * nu / Ly ** 2, 0.0, 0.0)   # unit centreline Poiseuille drive
+        init = {"kind": "uniform_noise", "U": 0.5, "noise": 0.05}
+        if three:
+            cz = 0.5 + d["cz"] * (Ly - 1.0)
+            case = Case(name=f"req{q}_3d_{n}", ndim=3, n=(n, n, n), L=(Lx, Ly, Ly), origin=(0.0, 0.0, 0.0),
+                        bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
+                        geom_kind=GEOM_SPHERE, geom_params=(cx, cy, cz, D / 2, -1.0), nu=nu, dt=dt, g=g,
+                        precision=precision, steps=steps, init=init, seed=seed * 100003 + q)
+        else:
+            case = Case(name=f"req{q}_2d_{n}", ndim=2, n=(n, n, 1), L=(Lx, Ly, 1.0), origin=(0.0, 0.0, 0.0),
+                        bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
+                        geom_kind=GEOM_CYLINDER, geom_params=(cx, cy, D / 2, -1.0), nu=nu, dt=dt, g=g,
+                        precision=precision, steps=steps, init=init, seed=seed * 100003 + q)
+        out.append((t, case, steps))
+    return sorted(out, key=lambda r: r[0])

@@ -22,6 +22,21 @@ def _rng(seed: int, purpose: str) -> np.random.Generator:
     return np.random.default_rng([int(seed), _PURPOSE[purpose]])
 
 
+def request_draws(seed: int, n: int) -> list:
+    """Seeded draws of a request stream: unit-rate Poisson arrival times and
+    uniform [0, 1) numbers for size, Re, steps and body position.  Request q
+    draws from its own stream, so the first k requests do not depend on n."""
+    out = []
+    t = 0.0
+    for q in range(n):
+        rng = np.random.default_rng([int(seed), _PURPOSE["requests"], q])
+        t += float(rng.exponential(1.0))
+        u = rng.random(7)
+        out.append({"arrival": t, "three": bool(u[0] < 0.5), "size": float(u[1]), "re": float(u[2]),
+                    "steps": float(u[3]), "cx": float(u[4]), "cy": float(u[5]), "cz": float(u[6])})
+    return out
+
+
 def cell_offset(seed: int, dx: float) -> tuple:
     """A seeded sub-cell offset in [0, dx)^2 for a body centre."""
     r = _rng(seed, "offset").random(2)

@@ -29,7 +29,8 @@ EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_g
             "ibm_build_weights", "ibm_step", "ibm_project", "ibm_poisson", "ibm_diagnostics",
             "ibm_get_classification", "ibm_get_weights", "ibm_state_bytes", "ibm_export_state",
             "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_diagnostics_noalloc",
-            "ibm_destroy")
+            "ibm_autotune", "ibm_set_tiles", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
+            "ibm_batch_destroy", "ibm_destroy")
 
 
 class ibm_grid_desc(C.Structure):
@@ -92,6 +93,12 @@ def _load() -> C.CDLL:
         "ibm_launch_count": ([C.c_void_p, P(C.c_longlong)], C.c_int),
         "ibm_diagnostics_noalloc": ([P(ibm_grid_desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_double, C.c_void_p, P(ibm_diag)], C.c_int),
+        "ibm_autotune": ([C.c_void_p, P(C.c_int), P(C.c_int)], C.c_int),
+        "ibm_set_tiles": ([C.c_void_p, C.c_int, C.c_int], C.c_int),
+        "ibm_batch_create": ([C.c_void_p, P(C.c_void_p)], C.c_int),
+        "ibm_batch_set": ([C.c_void_p, P(C.c_void_p), P(C.c_int), C.c_int], C.c_int),
+        "ibm_batch_run": ([C.c_void_p], C.c_int),
+        "ibm_batch_destroy": ([C.c_void_p], None),
         "ibm_destroy": ([C.c_void_p], None),
     }
     for name, (args, res) in sig.items():
@@ -216,6 +223,37 @@ def ibm_diagnostics_noalloc(grid: ibm_grid_desc, u: int, v: int, w: int, p: int,
     if st != IBM_E_DIVERGED or raise_on_diverged:
         _check(st, "ibm_diagnostics_noalloc")
     return d
+
+
+def ibm_autotune(h: int) -> tuple:
+    a, b = C.c_int(0), C.c_int(0)
+    _check(lib.ibm_autotune(C.c_void_p(h), C.byref(a), C.byref(b)), "ibm_autotune")
+    return a.value, b.value
+
+
+def ibm_set_tiles(h: int, kz_momentum: int, kz_march: int):
+    _check(lib.ibm_set_tiles(C.c_void_p(h), kz_momentum, kz_march), "ibm_set_tiles")
+
+
+def ibm_batch_create(stream: int) -> int:
+    b = C.c_void_p(0)
+    _check(lib.ibm_batch_create(C.c_void_p(stream), C.byref(b)), "ibm_batch_create")
+    return b.value
+
+
+def ibm_batch_set(b: int, handles, steps):
+    n = len(handles)
+    hs = (C.c_void_p * max(n, 1))(*[C.c_void_p(h) for h in handles])
+    st = (C.c_int * max(n, 1))(*[int(s) for s in steps])
+    _check(lib.ibm_batch_set(C.c_void_p(b), hs, st, n), "ibm_batch_set")
+
+
+def ibm_batch_run(b: int):
+    _check(lib.ibm_batch_run(C.c_void_p(b)), "ibm_batch_run")
+
+
+def ibm_batch_destroy(b: int):
+    lib.ibm_batch_destroy(C.c_void_p(b))
 
 
 def ibm_destroy(h: int):

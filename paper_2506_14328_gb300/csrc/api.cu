@@ -4,7 +4,10 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 namespace {
 
@@ -57,11 +60,14 @@ GridP make_gridp(const ibm_grid_desc* d) {
     g.oz = d->origin[2];
     g.sig_lo = d->bc_lo[1] == IBM_BC_NOSLIP ? -1.0 : 1.0;
     g.sig_hi = d->bc_hi[1] == IBM_BC_NOSLIP ? -1.0 : 1.0;
+    g.kzm = MOM_KZ;
+    g.kzd = 16;
     return g;
 }
 
+// flux partials: one per momentum block at the smallest z-chunk the autotuner may pick
 int momentum_blocks(const GridP& g) {
-    dim3 d = momentum_grid(g);
+    dim3 d = momentum_grid(g, MOM_KZ_MIN);
     return (int)(d.x * d.y * d.z);
 }
 
@@ -231,12 +237,27 @@ ibm_status ibm_workspace_bytes(const ibm_grid_desc* grid, size_t* bytes) {
     if (st != IBM_OK) return st;
     if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");
     GridP g = make_gridp(grid);
-    cufftHandle pf, pi;
+    // cuFFT's work size depends only on the transform shape and precision; remember it
+    // so that repeated queries (a server admitting many solves) build no temporary plans
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, size_t> known;
+    const auto key = std::make_tuple(g.nx, g.ny, g.nz, grid->precision);
     size_t work = 0;
-    st = make_plans(g, grid->precision, &pf, &pi, &work);
-    if (st != IBM_OK) return st;
-    cufftDestroy(pf);
-    cufftDestroy(pi);
+    bool hit = false;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = known.find(key);
+        if (it != known.end()) { work = it->second; hit = true; }
+    }
+    if (!hit) {
+        cufftHandle pf, pi;
+        st = make_plans(g, grid->precision, &pf, &pi, &work);
+        if (st != IBM_OK) return st;
+        cufftDestroy(pf);
+        cufftDestroy(pi);
+        std::lock_guard<std::mutex> lock(mu);
+        known[key] = work;
+    }
     *bytes = carve(nullptr, g, grid->precision, work, nullptr);
     return IBM_OK;
 }
@@ -547,10 +568,134 @@ ibm_status ibm_get_timing(ibm_solver* h, ibm_kernel_time* out, int max, int* cou
     return IBM_OK;
 }
 
+ibm_status ibm_autotune(ibm_solver* h, int* kz_momentum, int* kz_march) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!h->weights_ready) return ibm_set_error(IBM_E_STATE, "ibm_build_weights has not run");
+    int a = 0, b = 0;
+    drop_graph(h);
+    st = run_autotune(h, &a, &b);
+    if (st != IBM_OK) return st;
+    if (kz_momentum) *kz_momentum = a;
+    if (kz_march) *kz_march = b;
+    return IBM_OK;
+}
+
+ibm_status ibm_set_tiles(ibm_solver* h, int kz_momentum, int kz_march) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    bool okm = false, okd = false;
+    for (int v : KZM_CHOICES) okm |= v == kz_momentum;
+    for (int v : KZD_CHOICES) okd |= v == kz_march;
+    if (!okm || !okd) return ibm_set_error(IBM_E_INVALID, "z-chunk not among the supported choices");
+    drop_graph(h);
+    h->gp.kzm = kz_momentum;
+    h->gp.kzd = kz_march;
+    return IBM_OK;
+}
+
 ibm_status ibm_launch_count(const ibm_solver* h, long long* count) {
     if (!h || !count) return ibm_set_error(IBM_E_INVALID, "NULL argument");
     *count = h->launches;
     return IBM_OK;
+}
+
+struct ibm_batch {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<ibm_solver*> members;
+    std::vector<int> steps;
+    std::vector<long long> launches;   // kernels of each member in one replay
+    bool failed = false;
+};
+
+ibm_status ibm_batch_create(void* stream, ibm_batch** out) {
+    if (!out) return ibm_set_error(IBM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!stream) return ibm_set_error(IBM_E_INVALID, "a batch needs a non-default stream (capture is not allowed on the legacy stream)");
+    ibm_batch* b = new (std::nothrow) ibm_batch();
+    if (!b) return ibm_set_error(IBM_E_INVALID, "host allocation failed");
+    b->stream = (cudaStream_t)stream;
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        delete b;
+        return ibm_set_error(IBM_E_CUDA, "cudaEventCreate failed");
+    }
+    *out = b;
+    return IBM_OK;
+}
+
+ibm_status ibm_batch_set(ibm_batch* b, ibm_solver* const* members, const int* steps, int n) {
+    if (!b || (n > 0 && (!members || !steps)) || n < 0) return ibm_set_error(IBM_E_INVALID, "bad batch arguments");
+    if (b->failed) return ibm_set_error(IBM_E_STATE, "batch failed earlier");
+    for (int q = 0; q < n; ++q) {
+        ibm_status st = check_handle(members[q]);
+        if (st != IBM_OK) return st;
+        if (!members[q]->weights_ready) return ibm_set_error(IBM_E_STATE, "a member has no weights");
+        if (members[q]->timing) return ibm_set_error(IBM_E_STATE, "disable member timing before batching");
+        if (steps[q] < 0) return ibm_set_error(IBM_E_INVALID, "negative step count");
+    }
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    b->members.assign(members, members + n);
+    b->steps.assign(steps, steps + n);
+    while ((int)b->joins.size() < n) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return ibm_set_error(IBM_E_CUDA, "cudaEventCreate failed");
+        b->joins.push_back(e);
+    }
+    if (n == 0) return IBM_OK;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return ibm_set_error(IBM_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    ibm_status st = IBM_OK;
+    b->launches.assign(n, 0);
+    cudaEventRecord(b->fork, b->stream);
+    for (int q = 0; q < n && st == IBM_OK; ++q) {
+        ibm_solver* h = b->members[q];
+        cudaStreamWaitEvent(h->stream, b->fork, 0);
+        long long before = h->launches;
+        for (int s = 0; s < b->steps[q] && st == IBM_OK; ++s)
+            for (int k = 0; k < 3 && st == IBM_OK; ++k) st = run_substage(h, k, false);
+        b->launches[q] = h->launches - before;
+        h->launches = before;
+        cudaEventRecord(b->joins[q], h->stream);
+        cudaStreamWaitEvent(b->stream, b->joins[q], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (st != IBM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        b->failed = true;
+        return st;
+    }
+    if (e != cudaSuccess) { b->failed = true; return ibm_set_error(IBM_E_CUDA, std::string("end capture: ") + cudaGetErrorString(e)); }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { b->failed = true; return ibm_set_error(IBM_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+    return IBM_OK;
+}
+
+ibm_status ibm_batch_run(ibm_batch* b) {
+    if (!b) return ibm_set_error(IBM_E_INVALID, "batch is NULL");
+    if (b->failed) return ibm_set_error(IBM_E_STATE, "batch failed earlier");
+    if (b->members.empty()) return IBM_OK;
+    if (!b->exec) return ibm_set_error(IBM_E_STATE, "ibm_batch_set has not captured a graph");
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) { b->failed = true; return ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e)); }
+    for (size_t q = 0; q < b->members.size(); ++q) {
+        b->members[q]->steps += b->steps[q];
+        b->members[q]->launches += b->launches[q];
+    }
+    return IBM_OK;
+}
+
+void ibm_batch_destroy(ibm_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
 }
 
 void ibm_destroy(ibm_solver* h) {

@@ -24,6 +24,8 @@ struct GridP {
     double dx, dy, dz;
     double ox, oy, oz;
     double sig_lo, sig_hi;  // tangential ghost factor at the y walls (-1 no-slip, +1 free-slip)
+    int kzm;                // z planes one momentum block marches (autotuned)
+    int kzd;                // z planes one divergence / correction block marches (autotuned)
 };
 
 struct GeomP {
@@ -55,11 +57,15 @@ template <typename T> struct StageP {
     int flux_sum;      // accumulate the predictor flux (constant flow rate)
 };
 
-// Momentum tiling: blocks of 32 x 8 cells in (x, y), marching KZ planes in z.
-constexpr int MOM_TX = 32, MOM_TY = 8, MOM_KZ = 32;
-inline dim3 momentum_grid(const GridP& g) {
-    return dim3(g.nsegx, (g.ny + MOM_TY - 1) / MOM_TY, g.ndim == 3 ? (g.nz + MOM_KZ - 1) / MOM_KZ : 1);
+// Momentum tiling: blocks of 32 x 8 cells in (x, y), marching g.kzm planes in z
+// (the autotuner picks kzm from MOM_KZ_CHOICES; buffers are sized for the smallest).
+constexpr int MOM_TX = 32, MOM_TY = 8, MOM_KZ = 32, MOM_KZ_MIN = 4;
+constexpr int KZM_CHOICES[5] = {4, 8, 16, 32, 64};
+constexpr int KZD_CHOICES[4] = {4, 8, 16, 32};
+inline dim3 momentum_grid(const GridP& g, int kzm) {
+    return dim3(g.nsegx, (g.ny + MOM_TY - 1) / MOM_TY, g.ndim == 3 ? (g.nz + kzm - 1) / kzm : 1);
 }
+inline dim3 momentum_grid(const GridP& g) { return momentum_grid(g, g.kzm); }
 
 // ---------------------------------------------------------------------------
 // Device helpers
@@ -169,6 +175,7 @@ ibm_status geom_pivots(ibm_solver* h);
 
 // step.cu
 ibm_status run_substage(ibm_solver* h, int k, bool predictor_only);
+ibm_status run_autotune(ibm_solver* h, int* kzm, int* kzd);
 ibm_status run_project(ibm_solver* h);
 ibm_status run_poisson(ibm_solver* h, void* rhs_inout);
 ibm_status run_diagnostics(ibm_solver* h, double* out11);

@@ -16,7 +16,7 @@ namespace {
 // K3: momentum predictor with the implicit IBM diagonal division.
 //
 // 2.5D shared-memory tiling: a block owns a 32 x 8 (x, y) column of cells
-// and marches KZ planes along z, keeping the planes k-1, k, k+1 of u, v, w
+// and marches g.kzm planes along z, keeping the planes k-1, k, k+1 of u, v, w
 // (with a one-cell halo) in a rolling three-slot buffer.  Each plane is
 // loaded once, already in the form the operator reads it:
 //   * x and z wrap (periodic);
@@ -28,7 +28,7 @@ namespace {
 // 32-point x segments, so an IBM point's list position is segoff + the
 // number of IBM points in the lower lanes (one ballot).
 // ---------------------------------------------------------------------------
-constexpr int TX = MOM_TX, TY = MOM_TY, KZ = MOM_KZ;
+constexpr int TX = MOM_TX, TY = MOM_TY;
 constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY;
 
 template <typename T>
@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 4 : 3)
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int i = i0 + tx, j = j0 + ty;
-    const int kbeg = THREE ? blockIdx.z * KZ : 0;
-    const int kend = THREE ? min(kbeg + KZ, g.nz) : 1;
+    const int kbeg = THREE ? blockIdx.z * g.kzm : 0;
+    const int kend = THREE ? min(kbeg + g.kzm, g.nz) : 1;
     const int c0 = (ty + 1) * HX + (tx + 1);       // own cell in a plane tile
     const int plane = g.nx * g.ny;
     const int rowbase = i + g.nx * j;
@@ -362,11 +362,9 @@ __device__ __forceinline__ T flux_increment(const FluxCorr<T>& fc, T pic, uint8_
 
 // ---------------------------------------------------------------------------
 // K4: divergence of the predictor, D u*, in the field precision.  Each block
-// marches KZD planes along z carrying w*(k-1) in a register; u*(i-1) comes
+// marches g.kzd planes along z carrying w*(k-1) in a register; u*(i-1) comes
 // from the neighbouring lane.
 // ---------------------------------------------------------------------------
-constexpr int KZD = 16;
-
 template <typename T, bool THREE, bool FLUX>
 __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict__ u, const T* __restrict__ v,
                                                     const T* __restrict__ w, const uint8_t* __restrict__ mask,
@@ -375,8 +373,8 @@ __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict
     const int i = blockIdx.x * 32 + lane;
     const int j = blockIdx.y * 8 + threadIdx.y;
     if (j >= g.ny) return;                                   // whole warp
-    const int kbeg = THREE ? blockIdx.z * KZD : 0;
-    const int kend = THREE ? min(kbeg + KZD, g.nz) : 1;
+    const int kbeg = THREE ? blockIdx.z * g.kzd : 0;
+    const int kend = THREE ? min(kbeg + g.kzd, g.nz) : 1;
     const bool live = i < g.nx;
     const int plane = g.nx * g.ny;
     // left neighbour of lane 0 (periodic in x) and its place in its 32-point segment
@@ -593,7 +591,7 @@ __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, 
 // ---------------------------------------------------------------------------
 // K7: u = u* (+ flux correction) - G psi on every non-wall face, p += psi/(c_k dt)
 // (psi = c_k dt phi is what the Poisson solve returns for rhs = D u*).  Blocks
-// march KZD planes carrying psi(k+1) into the next plane; psi(i+1) comes from
+// march g.kzd planes carrying psi(k+1) into the next plane; psi(i+1) comes from
 // the neighbouring lane.
 // ---------------------------------------------------------------------------
 template <typename T, bool THREE, bool FLUX>
@@ -606,8 +604,8 @@ __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ 
     const int i = blockIdx.x * 32 + lane;
     const int j = blockIdx.y * 8 + threadIdx.y;
     if (j >= g.ny) return;                                   // whole warp
-    const int kbeg = THREE ? blockIdx.z * KZD : 0;
-    const int kend = THREE ? min(kbeg + KZD, g.nz) : 1;
+    const int kbeg = THREE ? blockIdx.z * g.kzd : 0;
+    const int kend = THREE ? min(kbeg + g.kzd, g.nz) : 1;
     const bool live = i < g.nx;
     const int plane = g.nx * g.ny;
     const int ir = (i + 1 < g.nx) ? i + 1 : 0;              // +x neighbour (periodic)
@@ -754,7 +752,7 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
 }
 
 dim3 zmarch_grid(const GridP& g) {
-    return dim3(g.nsegx, (g.ny + 7) / 8, g.ndim == 3 ? (g.nz + KZD - 1) / KZD : 1);
+    return dim3(g.nsegx, (g.ny + 7) / 8, g.ndim == 3 ? (g.nz + g.kzd - 1) / g.kzd : 1);
 }
 
 template <typename T>
@@ -810,7 +808,7 @@ ibm_status launch_correct(ibm_solver* h, T* const us[3], T inv_ckdt, int update_
 }
 
 template <typename T>
-ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
+ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib, dim3& grd) {
     const GridP& g = h->gp;
     MomF<T> F;
     for (int c = 0; c < 3; ++c) {
@@ -821,7 +819,6 @@ ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
     if (g.ndim == 2) { F.u[2] = F.u[0]; F.us[2] = F.us[0]; F.Nn[2] = F.Nn[0]; }
     F.p = (const T*)h->buf.p;
     F.mask = h->mask;
-    StageP<T> sp;
     double dt = h->phys.dt;
     sp.dta = (T)(dt * RK_A[k]);
     sp.dtb = (T)(dt * RK_B[k]);
@@ -836,20 +833,31 @@ ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
     sp.sig_hi = (T)g.sig_hi;
     sp.read_prev = k > 0;
     sp.write_n = k < 2;
-    bool cflux = h->phys.flow_mode == IBM_FLOW_CONST_FLUX;
-    sp.flux_sum = cflux;
-    IbmStage<T> ib;
+    sp.flux_sum = h->phys.flow_mode == IBM_FLOW_CONST_FLUX;
     for (int c = 0; c < 3; ++c) {
         ib.segoff[c] = h->segoff[c];
         ib.coef[c] = (const Coef4<T>*)h->coef[c] + (long long)k * h->counts[c];
     }
     dim3 blk(TX, TY, 1);
-    dim3 grd = momentum_grid(g);
-    cudaEvent_t t;
-    timer_begin(h, "momentum", &t);
+    grd = momentum_grid(g);
     if (g.ndim == 3) k_momentum<T, true><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, h->partials);
     else k_momentum<T, false><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, h->partials);
     IBM_LAUNCH_CHECK();
+    return IBM_OK;
+}
+
+template <typename T>
+ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
+    const GridP& g = h->gp;
+    StageP<T> sp;
+    IbmStage<T> ib;
+    dim3 grd;
+    const double dt = h->phys.dt;
+    const bool cflux = h->phys.flow_mode == IBM_FLOW_CONST_FLUX;
+    cudaEvent_t t;
+    timer_begin(h, "momentum", &t);
+    ibm_status st0 = launch_momentum<T>(h, k, sp, ib, grd);
+    if (st0 != IBM_OK) return st0;
     timer_end(h, t, "momentum");
     if (cflux) {
         int nparts = grd.x * grd.y * grd.z;
@@ -909,9 +917,77 @@ ibm_status diag_t(ibm_solver* h, double* out) {
     return IBM_OK;
 }
 
+// Times the momentum predictor (stage 1, scratch outputs only) for every
+// z-chunk choice and the divergence kernel for every march choice, keeping the
+// fastest of each.  Overwrites only the predictor and RHS scratch buffers.
+template <typename T>
+ibm_status autotune_t(ibm_solver* h, int* kzm_out, int* kzd_out) {
+    GridP& g = h->gp;
+    if (g.ndim != 3) { *kzm_out = g.kzm; *kzd_out = g.kzd; return IBM_OK; }
+    cudaEvent_t a, b;
+    IBM_CUDA_TRY(cudaEventCreate(&a));
+    IBM_CUDA_TRY(cudaEventCreate(&b));
+    const bool saved_timing = h->timing;
+    h->timing = false;
+    auto time_it = [&](auto&& launch) -> float {
+        for (int w = 0; w < 2; ++w) launch();
+        cudaEventRecord(a, h->stream);
+        for (int r = 0; r < 5; ++r) launch();
+        cudaEventRecord(b, h->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    };
+    float best = 1e30f;
+    int best_kzm = g.kzm;
+    for (int kz : KZM_CHOICES) {
+        if (kz > 2 * g.nz && kz != KZM_CHOICES[0]) continue;
+        g.kzm = kz;
+        float ms = time_it([&] {
+            StageP<T> sp;
+            IbmStage<T> ib;
+            dim3 grd;
+            launch_momentum<T>(h, 0, sp, ib, grd);
+        });
+        if (ms < best) { best = ms; best_kzm = kz; }
+    }
+    g.kzm = best_kzm;
+    best = 1e30f;
+    int best_kzd = g.kzd;
+    T* us[3] = {(T*)h->ustar[0], (T*)h->ustar[1], (T*)h->ustar[2]};
+    const T ix = (T)(1.0 / g.dx), iy = (T)(1.0 / g.dy), iz = (T)(1.0 / g.dz);
+    const FluxCorr<T> fc = flux_corr<T>(h, 0);
+    for (int kz : KZD_CHOICES) {
+        if (kz > 2 * g.nz && kz != KZD_CHOICES[0]) continue;
+        g.kzd = kz;
+        float ms = time_it([&] {
+            k_divergence<T, true, false><<<zmarch_grid(g), dim3(32, 8), 0, h->stream>>>(
+                g, us[0], us[1], us[2], h->mask, (T*)h->rhs, ix, iy, iz, fc);
+        });
+        if (ms < best) { best = ms; best_kzd = kz; }
+    }
+    g.kzd = best_kzd;
+    h->timing = saved_timing;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->failed = true;
+        return ibm_set_error(IBM_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    }
+    *kzm_out = g.kzm;
+    *kzd_out = g.kzd;
+    return IBM_OK;
+}
+
 }  // namespace
 
 int diag_blocks() { return DIAG_BLOCKS; }
+
+ibm_status run_autotune(ibm_solver* h, int* kzm, int* kzd) {
+    return h->prec == IBM_FP64 ? autotune_t<double>(h, kzm, kzd) : autotune_t<float>(h, kzm, kzd);
+}
 
 ibm_status run_substage(ibm_solver* h, int k, bool predictor_only) {
     return h->prec == IBM_FP64 ? substage_t<double>(h, k, predictor_only) : substage_t<float>(h, k, predictor_only);

@@ -13,7 +13,7 @@ from . import (ibm_grid_desc, ibm_geom_desc, ibm_buffers, ibm_physics, IBM_FP64,
                ibm_workspace_bytes, ibm_setup_geometry, ibm_weights_bytes, ibm_build_weights, ibm_step,
                ibm_project, ibm_poisson, ibm_diagnostics, ibm_get_classification, ibm_get_weights,
                ibm_state_bytes, ibm_export_state, ibm_import_state, ibm_timing, ibm_get_timing,
-               ibm_launch_count, ibm_destroy)
+               ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_destroy)
 
 
 class Solver:
@@ -54,7 +54,9 @@ class Solver:
         for q, v in enumerate(geom_params):
             geo.param[q] = float(v)
         self.geom = geo
-        with torch.cuda.device(self.device):
+        # every torch operation of this solver runs on its own stream, so setting up
+        # one solve never waits for work that other solves have on the device
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
             kw = dict(dtype=self.dtype, device=self.device)
             self.u = [torch.zeros(self.shape, **kw) for _ in range(3)]
             self.p = torch.zeros(self.shape, **kw)
@@ -67,7 +69,7 @@ class Solver:
             bufs.work = self.work.data_ptr()
             bufs.work_bytes = wb
             self.buffers = bufs
-            torch.cuda.synchronize(self.device)
+            self.stream.synchronize()
             self.h = ibm_setup_geometry(gd, geo, bufs, self.stream.cuda_stream)
             self.weights = None
             self.set_physics(nu=nu, dt=dt, g=g, bmode=bmode, flow_mode=flow_mode, target_flux=target_flux,
@@ -96,8 +98,9 @@ class Solver:
         self.phys = ph
         wb = ibm_weights_bytes(self.h)
         if self.weights is None or self.weights.numel() < wb:
-            self.weights = torch.empty(max(wb, 256), dtype=torch.uint8, device=self.device)
-            torch.cuda.synchronize(self.device)
+            with torch.cuda.stream(self.stream):
+                self.weights = torch.empty(max(wb, 256), dtype=torch.uint8, device=self.device)
+            self.stream.synchronize()
         ibm_build_weights(self.h, ph, self.weights.data_ptr(), self.weights.numel())
 
     # ---- calls -------------------------------------------------------------
@@ -133,17 +136,19 @@ class Solver:
         return [lam[c][:counts[c]] for c in range(3)], [src[c][:counts[c]] for c in range(3)]
 
     def set_state(self, u, v, w, p):
-        torch.cuda.synchronize(self.device)
-        for t, a in zip(self.u + [self.p], (u, v, w, p)):
-            t.copy_(torch.as_tensor(np.ascontiguousarray(a, dtype=self.np_dtype)).reshape(self.shape))
-        torch.cuda.synchronize(self.device)
+        self.stream.synchronize()
+        with torch.cuda.stream(self.stream):
+            for t, a in zip(self.u + [self.p], (u, v, w, p)):
+                t.copy_(torch.as_tensor(np.ascontiguousarray(a, dtype=self.np_dtype)).reshape(self.shape))
+        self.stream.synchronize()
 
     def sync(self):
         self.stream.synchronize()
 
     def state(self):
-        torch.cuda.synchronize(self.device)
-        out = [t.detach().cpu().numpy().astype(np.float64) for t in self.u + [self.p]]
+        self.stream.synchronize()
+        with torch.cuda.stream(self.stream):
+            out = [t.detach().cpu().numpy().astype(np.float64) for t in self.u + [self.p]]
         return out[:3], out[3]
 
     def state_bytes(self) -> int:
@@ -157,6 +162,17 @@ class Solver:
 
     def import_state_ptr(self, ptr: int, nbytes: int):
         ibm_import_state(self.h, ptr, nbytes)
+
+    def autotune(self):
+        """Pick the z-chunks of the momentum and march kernels by timing them (blocking)."""
+        return ibm_autotune(self.h)
+
+    def set_tiles(self, kz_momentum, kz_march):
+        ibm_set_tiles(self.h, kz_momentum, kz_march)
+
+    def footprint_bytes(self) -> int:
+        return (sum(t.numel() * t.element_size() for t in self.u + [self.p]) + self.work.numel() +
+                (self.weights.numel() if self.weights is not None else 0))
 
     def timing(self, enable=True):
         ibm_timing(self.h, enable)
