@@ -208,7 +208,7 @@ ibm_status ibm_timing(ibm_solver* h, int enable);
 /* Blocking: per-kernel launches and summed durations since the last reset. */
 ibm_status ibm_get_timing(ibm_solver* h, ibm_kernel_time* out, int max, int* count);
 /* Tile autotuner (not in the paper: a GB300 tuning aid).  Times the momentum
- * predictor for every z-chunk in {4, 8, 16, 32, 64} and the divergence
+ * predictor for every z-chunk in {8, 12, 16, 24, 32, 48, 64, 86} and the divergence
  * kernel for every z-chunk in {4, 8, 16, 32} on this solver's own grid and
  * keeps the fastest of each; returns the choices (either pointer may be NULL).
  * Overwrites only scratch (predictor, RHS history, divergence), so call it

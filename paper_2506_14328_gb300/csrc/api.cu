@@ -60,7 +60,7 @@ GridP make_gridp(const ibm_grid_desc* d) {
     g.oz = d->origin[2];
     g.sig_lo = d->bc_lo[1] == IBM_BC_NOSLIP ? -1.0 : 1.0;
     g.sig_hi = d->bc_hi[1] == IBM_BC_NOSLIP ? -1.0 : 1.0;
-    g.kzm = MOM_KZ;
+    g.kzm = 32;             // replaced by momentum_default_kzm at setup
     g.kzd = 16;
     return g;
 }
@@ -300,6 +300,7 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     h->N = g.N;
     h->nspec = (long long)g.nz * g.ny * g.nxh;
     h->nseg = (long long)g.nsegx * g.ny * g.nz;
+    h->gp.kzm = momentum_default_kzm(h->gp, h->prec);
 
     size_t work = 0;
     st = make_plans(g, h->prec, &h->plan_f, &h->plan_i, &work);

@@ -57,10 +57,11 @@ template <typename T> struct StageP {
     int flux_sum;      // accumulate the predictor flux (constant flow rate)
 };
 
-// Momentum tiling: blocks of 32 x 8 cells in (x, y), marching g.kzm planes in z
-// (the autotuner picks kzm from MOM_KZ_CHOICES; buffers are sized for the smallest).
-constexpr int MOM_TX = 32, MOM_TY = 8, MOM_KZ = 32, MOM_KZ_MIN = 4;
-constexpr int KZM_CHOICES[5] = {4, 8, 16, 32, 64};
+// Momentum tiling: blocks of 32 x 8 threads own 32 x 16 cells in (x, y) and
+// march g.kzm planes in z.  The autotuner picks kzm from KZM_CHOICES; the flux
+// partials are sized for the smallest choice.
+constexpr int MOM_TX = 32, MOM_WARPS = 8, MOM_TY = 16, MOM_KZ_MIN = 8;
+constexpr int KZM_CHOICES[8] = {8, 12, 16, 24, 32, 48, 64, 86};
 constexpr int KZD_CHOICES[4] = {4, 8, 16, 32};
 inline dim3 momentum_grid(const GridP& g, int kzm) {
     return dim3(g.nsegx, (g.ny + MOM_TY - 1) / MOM_TY, g.ndim == 3 ? (g.nz + kzm - 1) / kzm : 1);
@@ -176,6 +177,7 @@ ibm_status geom_pivots(ibm_solver* h);
 // step.cu
 ibm_status run_substage(ibm_solver* h, int k, bool predictor_only);
 ibm_status run_autotune(ibm_solver* h, int* kzm, int* kzd);
+int momentum_default_kzm(const GridP& g, int prec);
 ibm_status run_project(ibm_solver* h);
 ibm_status run_poisson(ibm_solver* h, void* rhs_inout);
 ibm_status run_diagnostics(ibm_solver* h, double* out11);
