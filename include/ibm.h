@@ -217,6 +217,14 @@ ibm_status ibm_get_timing(ibm_solver* h, ibm_kernel_time* out, int max, int* cou
 ibm_status ibm_autotune(ibm_solver* h, int* kz_momentum, int* kz_march);
 /* Set the z-chunks directly (values from a cached autotune). */
 ibm_status ibm_set_tiles(ibm_solver* h, int kz_momentum, int kz_march);
+/* The z-chunks in use, and whether the momentum predictor runs its TMA form
+ * (*tma = 1: plane tiles arrive by tensor copies into a shared-memory ring;
+ * 0: loads through registers).  Any pointer may be NULL. */
+ibm_status ibm_get_tiles(ibm_solver* h, int* kz_momentum, int* kz_march, int* tma);
+/* Allow (1, the default) or forbid (0) the TMA form of the momentum
+ * predictor.  It is used only on 3D grids with nx a multiple of 16; both forms
+ * compute the same update (a tuning and testing aid, not in the paper). */
+ibm_status ibm_set_momentum_tma(ibm_solver* h, int enable);
 
 /* Batched stepping of many resident solves (continuous batching, SURVEY's
  * serving pattern; the paper has no counterpart).  A batch owns a

@@ -29,7 +29,7 @@ EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_g
             "ibm_build_weights", "ibm_step", "ibm_project", "ibm_poisson", "ibm_diagnostics",
             "ibm_get_classification", "ibm_get_weights", "ibm_state_bytes", "ibm_export_state",
             "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_diagnostics_noalloc",
-            "ibm_autotune", "ibm_set_tiles", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
+            "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
             "ibm_batch_destroy", "ibm_destroy")
 
 
@@ -95,6 +95,8 @@ def _load() -> C.CDLL:
                                      C.c_double, C.c_void_p, P(ibm_diag)], C.c_int),
         "ibm_autotune": ([C.c_void_p, P(C.c_int), P(C.c_int)], C.c_int),
         "ibm_set_tiles": ([C.c_void_p, C.c_int, C.c_int], C.c_int),
+        "ibm_get_tiles": ([C.c_void_p, P(C.c_int), P(C.c_int), P(C.c_int)], C.c_int),
+        "ibm_set_momentum_tma": ([C.c_void_p, C.c_int], C.c_int),
         "ibm_batch_create": ([C.c_void_p, P(C.c_void_p)], C.c_int),
         "ibm_batch_set": ([C.c_void_p, P(C.c_void_p), P(C.c_int), C.c_int], C.c_int),
         "ibm_batch_run": ([C.c_void_p], C.c_int),
@@ -233,6 +235,16 @@ def ibm_autotune(h: int) -> tuple:
 
 def ibm_set_tiles(h: int, kz_momentum: int, kz_march: int):
     _check(lib.ibm_set_tiles(C.c_void_p(h), kz_momentum, kz_march), "ibm_set_tiles")
+
+
+def ibm_get_tiles(h: int) -> tuple:
+    a, b, t = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(lib.ibm_get_tiles(C.c_void_p(h), C.byref(a), C.byref(b), C.byref(t)), "ibm_get_tiles")
+    return a.value, b.value, bool(t.value)
+
+
+def ibm_set_momentum_tma(h: int, enable: bool):
+    _check(lib.ibm_set_momentum_tma(C.c_void_p(h), 1 if enable else 0), "ibm_set_momentum_tma")
 
 
 def ibm_batch_create(stream: int) -> int:

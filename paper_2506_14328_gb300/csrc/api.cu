@@ -300,7 +300,6 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     h->N = g.N;
     h->nspec = (long long)g.nz * g.ny * g.nxh;
     h->nseg = (long long)g.nsegx * g.ny * g.nz;
-    h->gp.kzm = momentum_default_kzm(h->gp, h->prec);
 
     size_t work = 0;
     st = make_plans(g, h->prec, &h->plan_f, &h->plan_i, &work);
@@ -313,6 +312,8 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     }
     carve(h, g, h->prec, work, (char*)buffers->work);
     h->fft_work_bytes = work;
+    momentum_prepare(h);
+    h->gp.kzm = momentum_default_kzm(h->gp, h->prec, momentum_uses_tma(h));
     if (cufftSetWorkArea(h->plan_f, h->fft_work) != CUFFT_SUCCESS ||
         cufftSetWorkArea(h->plan_i, h->fft_work) != CUFFT_SUCCESS ||
         cufftSetStream(h->plan_f, h->stream) != CUFFT_SUCCESS || cufftSetStream(h->plan_i, h->stream) != CUFFT_SUCCESS) {
@@ -445,6 +446,12 @@ ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
     out->cfl = cfl * h->phys.dt;
     out->pi = r[0];
     out->step = h->steps;
+    if (r[3] != 0.0) {
+        // a TMA momentum block gave up waiting for its plane loads (a bounded wait ran out)
+        out->status = IBM_E_TIMEOUT;
+        h->failed = true;
+        return ibm_set_error(IBM_E_TIMEOUT, "momentum predictor: a plane load did not complete");
+    }
     bool finite = s[11] == 0.0 && std::isfinite(out->div_l2) && std::isfinite(out->ke);
     out->status = finite ? IBM_OK : IBM_E_DIVERGED;
     if (!finite) return ibm_set_error(IBM_E_DIVERGED, "non-finite values in the fields");
@@ -595,6 +602,23 @@ ibm_status ibm_set_tiles(ibm_solver* h, int kz_momentum, int kz_march) {
     return IBM_OK;
 }
 
+ibm_status ibm_get_tiles(ibm_solver* h, int* kz_momentum, int* kz_march, int* tma) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (kz_momentum) *kz_momentum = h->gp.kzm;
+    if (kz_march) *kz_march = h->gp.kzd;
+    if (tma) *tma = momentum_uses_tma(h) ? 1 : 0;
+    return IBM_OK;
+}
+
+ibm_status ibm_set_momentum_tma(ibm_solver* h, int enable) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    drop_graph(h);
+    h->mom_tma = enable != 0;
+    return IBM_OK;
+}
+
 ibm_status ibm_launch_count(const ibm_solver* h, long long* count) {
     if (!h || !count) return ibm_set_error(IBM_E_INVALID, "NULL argument");
     *count = h->launches;
@@ -710,6 +734,7 @@ void ibm_destroy(ibm_solver* h) {
         cufftDestroy(h->plan_f);
         cufftDestroy(h->plan_i);
     }
+    momentum_release(h);
     delete h;
 }
 

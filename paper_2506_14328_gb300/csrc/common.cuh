@@ -57,6 +57,11 @@ template <typename T> struct StageP {
     int flux_sum;      // accumulate the predictor flux (constant flow rate)
 };
 
+// Low-storage RK3 coefficients a_k, b_k and c_k = a_k + b_k (Sec. 2.4, Eq. rk3-rai)
+inline constexpr double RK_A[3] = {64.0 / 120.0, 50.0 / 120.0, 90.0 / 120.0};
+inline constexpr double RK_B[3] = {0.0, -34.0 / 120.0, -50.0 / 120.0};
+inline constexpr double RK_C[3] = {64.0 / 120.0, 16.0 / 120.0, 40.0 / 120.0};
+
 // Momentum tiling: blocks of 32 x 8 threads own 32 x 16 cells in (x, y) and
 // march g.kzm planes in z.  The autotuner picks kzm from KZM_CHOICES; the flux
 // partials are sized for the smallest choice.
@@ -158,10 +163,24 @@ struct ibm_solver {
     bool timing = false;
     std::vector<KernelTimer> timers;
 
+    void* mom_maps = nullptr;  // tensor maps of the TMA momentum kernel (momentum.cu), or NULL
+    bool mom_tma = true;       // use the TMA momentum kernel where the grid allows it
+
     cudaGraphExec_t graph = nullptr;
     bool graph_ready = false;
     long long graph_launches = 0;   // kernels of this library in one captured step
 };
+
+// The IBM coefficient lists of RK stage k (list position -> {alpha, beta, s}).
+template <typename T>
+inline IbmStage<T> stage_coefs(const ibm_solver* h, int k) {
+    IbmStage<T> ib;
+    for (int c = 0; c < 3; ++c) {
+        ib.segoff[c] = h->segoff[c];
+        ib.coef[c] = (const Coef4<T>*)h->coef[c] + (long long)k * h->counts[c];
+    }
+    return ib;
+}
 
 // ---------------------------------------------------------------------------
 // Host entry points between translation units
@@ -177,7 +196,16 @@ ibm_status geom_pivots(ibm_solver* h);
 // step.cu
 ibm_status run_substage(ibm_solver* h, int k, bool predictor_only);
 ibm_status run_autotune(ibm_solver* h, int* kzm, int* kzd);
-int momentum_default_kzm(const GridP& g, int prec);
+
+// momentum.cu
+// Launches the momentum predictor of RK stage k on the solver's stream;
+// *nparts receives the number of flux partials it wrote.
+ibm_status momentum_launch(ibm_solver* h, int k, int* nparts);
+int momentum_default_kzm(const GridP& g, int prec, bool tma);
+// Builds (or drops) the TMA kernel's tensor maps over the solver's buffers.
+void momentum_prepare(ibm_solver* h);
+void momentum_release(ibm_solver* h);
+bool momentum_uses_tma(const ibm_solver* h);
 ibm_status run_project(ibm_solver* h);
 ibm_status run_poisson(ibm_solver* h, void* rhs_inout);
 ibm_status run_diagnostics(ibm_solver* h, double* out11);

@@ -13,7 +13,8 @@ from . import (ibm_grid_desc, ibm_geom_desc, ibm_buffers, ibm_physics, IBM_FP64,
                ibm_workspace_bytes, ibm_setup_geometry, ibm_weights_bytes, ibm_build_weights, ibm_step,
                ibm_project, ibm_poisson, ibm_diagnostics, ibm_get_classification, ibm_get_weights,
                ibm_state_bytes, ibm_export_state, ibm_import_state, ibm_timing, ibm_get_timing,
-               ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_destroy)
+               ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_get_tiles, ibm_set_momentum_tma,
+               ibm_destroy)
 
 
 class Solver:
@@ -169,6 +170,13 @@ class Solver:
 
     def set_tiles(self, kz_momentum, kz_march):
         ibm_set_tiles(self.h, kz_momentum, kz_march)
+
+    def tiles(self):
+        """(kz_momentum, kz_march, momentum predictor runs its TMA form)"""
+        return ibm_get_tiles(self.h)
+
+    def use_tma(self, enable=True):
+        ibm_set_momentum_tma(self.h, enable)
 
     def footprint_bytes(self) -> int:
         return (sum(t.numel() * t.element_size() for t in self.u + [self.p]) + self.work.numel() +

@@ -298,14 +298,16 @@ def test_full_size_wavy_channel_launch_configuration():
     assert abs(g.diagnostics()["pi"]) < 1e3
 
 
+@pytest.mark.parametrize("nx", [70, 64])
 @pytest.mark.parametrize("flow", ["forced", "const_flux"])
-def test_predictor_every_z_chunk_matches_oracle(flow):
+def test_predictor_every_z_chunk_matches_oracle(flow, nx):
     """The momentum predictor at every z-chunk the autotuner may pick, on a grid whose
-    z extent (23) leaves odd and short chunks, against the oracle to 1e-12.  With a
-    forced flow u* is also the same bit for bit at every chunk; under the constant flow
-    rate the forcing sums per-block partials, whose grouping follows the chunking."""
+    z extent (23) leaves odd and short chunks, against the oracle to 1e-12.  nx = 64 runs
+    the TMA form (x a multiple of 16), nx = 70 the register form.  With a forced flow u*
+    is also the same bit for bit at every chunk; under the constant flow rate the forcing
+    sums per-block partials, whose grouping follows the chunking."""
     from inputs import FLOW_FORCED
-    case = small_case("wavy3d").with_(n=(70, 36, 23), name="wavy3d_70x36x23")
+    case = small_case("wavy3d").with_(n=(nx, 36, 23), name=f"wavy3d_{nx}x36x23")
     if flow == "forced":
         case = case.with_(flow_mode=FLOW_FORCED, g=(0.3, 0.0, 0.0))
     o = OracleSolver(case)
@@ -317,6 +319,7 @@ def test_predictor_every_z_chunk_matches_oracle(flow):
         g = _gpu(case)
         g.set_state(f["u"], f["v"], f["w"], f["p"])
         g.set_tiles(kz, 16)
+        assert g.tiles() == (kz, 16, nx % 16 == 0)
         g.step(1, flags=1)
         ug, _ = g.state()
         for c in range(3):
@@ -327,3 +330,25 @@ def test_predictor_every_z_chunk_matches_oracle(flow):
             for c in range(3):
                 assert np.array_equal(first[c], ug[c]), (kz, c, int((first[c] != ug[c]).sum()))
         g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tma_and_register_momentum_forms_agree(precision):
+    """Both forms of the momentum predictor on a ragged grid with x a multiple of 16
+    (48 x 30 x 26: a half-empty x tile, a partial y tile, free-slip ghosts), over full
+    steps: FP64 to 1e-12 of each other, FP32 to 1e-5."""
+    case = small_case("sphere3d", precision=precision)
+    f = initial_field(case)
+    runs = []
+    for tma in (True, False):
+        g = _gpu(case)
+        g.use_tma(tma)
+        assert g.tiles()[2] == tma
+        g.set_state(f["u"], f["v"], f["w"], f["p"])
+        g.step(case.steps)
+        runs.append(g.state())
+        g.close()
+    o = OracleSolver(case)
+    tol = TOL64 if precision == "fp64" else 1e-5
+    for c in range(3):
+        assert _rel(o, runs[0][0][c], runs[1][0][c], c) < tol, c
