@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
 //
 // Each block owns the same 32 x 16 column of cells as k_momentum.  One thread
 // issues, per plane, tensor copies of the boxes the stencil needs into one
-// stage of a TMA_D-deep ring in shared memory, completed on that stage's
+// stage of a ring of D stages in shared memory, completed on that stage's
 // mbarrier:
 //   u, v, w  40 x 18 at (i0-4, j0-1)   x start rounded down to 16 bytes
 //   mask     64 x 18 at (i0-16, j0-1)  (one byte per cell)
@@ -545,14 +545,14 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
 // computed its u, v, w tile is rewritten in place into the form the operator
 // reads (non-internal -> 0, ghost rows beyond a y wall, wrapped columns), and
 // the thread keeps its own two cells' values and masks in registers.  Plane
-// k+3 is requested while plane k is computed, so about three planes of every
-// block are in flight without any register cost.
+// k+D-1 is requested while plane k is computed (D = 3 for FP32, 4 for FP64),
+// so two or three planes of every block are in flight without register cost.
 // ---------------------------------------------------------------------------
-constexpr int TMA_D = 4;                // ring depth (planes)
-
 template <typename T>
 struct TmaLay {
     static constexpr int es = (int)sizeof(T);
+    // ring depth in planes: FP32 keeps three blocks of 256 threads per SM
+    static constexpr int D = sizeof(T) == 4 ? 3 : 4;
     static constexpr int RX = 40, RY = 18;      // u, v, w box
     static constexpr int MXB = 64;              // mask box width (bytes)
     static constexpr int PX = 40, PY = 17;      // pressure box
@@ -572,7 +572,7 @@ struct TmaLay {
     static constexpr int oWMR = oWML + a128(WMX * RY);
     static constexpr int oWPR = oWMR + a128(WMX * RY);
     static constexpr int SB = oWPR + a128(WX * PY * es);  // one stage
-    static constexpr int SMEM = TMA_D * SB + TMA_D * 8 + 128;   // + mbarriers + alignment slack
+    static constexpr int SMEM = D * SB + D * 8 + 128;   // + mbarriers + alignment slack
 };
 
 struct MomMaps {
@@ -739,14 +739,14 @@ __device__ __forceinline__ uint32_t tma_pass(unsigned char* st, const TmaPt<T>& 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
     k_momentum_tma(GridP g, MomF<T> F, StageP<T> sp, IbmStage<T> ib, double* __restrict__ flux_part,
                    double* __restrict__ status, const __grid_constant__ MomMaps maps) {
     using L = TmaLay<T>;
     extern __shared__ unsigned char dyn_smem[];
     __shared__ double shd[MW];
     unsigned char* ring = dyn_smem + ((128u - (smem_addr(dyn_smem) & 127u)) & 127u);
-    uint64_t* full = reinterpret_cast<uint64_t*>(ring + TMA_D * L::SB);
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring + L::D * L::SB);
     const int tx = threadIdx.x, w = threadIdx.y, tid = tx + MX * w;
     const int i0 = blockIdx.x * MX, j0 = blockIdx.y * MY;
     const int i = i0 + tx, jA = j0 + 2 * w;
@@ -785,24 +785,24 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
     const int ta = (2 * w + 1) * L::RX + tx + 4, tb = ta + L::RX;
 
     if (tid == 0) {
-        for (int s = 0; s < TMA_D; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < L::D; ++s) mbar_init(&full[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     int rel_issued = -1;                       // producer only
     auto issue = [&](int rel) {
         const int kk = kbeg - 1 + rel;
-        tma_issue<T>(maps, ring + (rel % TMA_D) * L::SB, &full[rel % TMA_D], kk, g, i0, j0, kk >= kbeg,
+        tma_issue<T>(maps, ring + (rel % L::D) * L::SB, &full[rel % L::D], kk, g, i0, j0, kk >= kbeg,
                      sp.read_prev && kk >= kbeg && kk < kend, xl, xr);
         rel_issued = rel;
     };
     if (tid == 0)
-        for (int rel = 0; rel < TMA_D && rel < nrel; ++rel) issue(rel);
-    auto stage = [&](int rel) { return ring + (rel % TMA_D) * L::SB; };
+        for (int rel = 0; rel < L::D && rel < nrel; ++rel) issue(rel);
+    auto stage = [&](int rel) { return ring + (rel % L::D) * L::SB; };
     auto abort_block = [&](int rel_from) {
         if (tid == 0) {
             status[3] = 1.0;                   // read back by ibm_diagnostics as a timeout
-            for (int r = rel_from; r <= rel_issued; ++r) mbar_wait_bounded(&full[r % TMA_D], (r / TMA_D) & 1);
+            for (int r = rel_from; r <= rel_issued; ++r) mbar_wait_bounded(&full[r % L::D], (r / L::D) & 1);
         }
     };
 
@@ -846,7 +846,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
     for (int k = kbeg; k < kend; ++k) {
         const int rel = k - kbeg + 1;
         // plane k+1 into operator form
-        ok = mbar_wait_bounded(&full[(rel + 1) % TMA_D], ((rel + 1) / TMA_D) & 1);
+        ok = mbar_wait_bounded(&full[(rel + 1) % L::D], ((rel + 1) / L::D) & 1);
         uint32_t mn = 0;
         if (ok) mn = tma_pass<T>(stage(rel + 1), qa, qb, qh, own_gen, has_h, pfix_row, pfix_col, ua, ub);
         fence_proxy_async();
@@ -854,8 +854,8 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
             abort_block(rel + 1);
             return;
         }
-        // the stage of plane k-1 is free: request plane k+3 into it
-        if (tid == 0 && rel + 3 < nrel) issue(rel + 3);
+        // the stage of plane k-1 is free: request plane k+D-1 into it
+        if (tid == 0 && rel + L::D - 1 < nrel) issue(rel + L::D - 1);
         const unsigned char* s0 = stage(rel);
         const unsigned char* s1 = stage(rel + 1);
         const T* Pk = reinterpret_cast<const T*>(s0 + L::oP);
