@@ -52,6 +52,8 @@ template <typename T> struct StageP {
     T idx, idy, idz;   // 1/dx ...
     T nx2, ny2, nz2;   // nu/dx^2 ...
     T qx, qy, qz;      // 1/(4 dx) ...: the two-point averages' 1/2 squared, over the spacing
+    T cgx, cgy, cgz;   // c_k dt / dx ...: pressure-gradient factors
+    T lc;              // 2 (nu/dx^2 + nu/dy^2 + nu/dz^2): the Laplacian's centre weight (3D)
     int read_prev;     // stage k > 1: add b_k N^{k-2}
     int write_n;       // stage k < 3: store N^{k-1}
     int flux_sum;      // accumulate the predictor flux (constant flow rate)

@@ -203,10 +203,11 @@ struct MomCarry {
 };
 
 // The stage update of one component of one cell before the IBM division:
-// out = uP + R with R = dt a_k N - c_k dt gp (+ dt b_k N^{k-2}).
+// out = uP + R with R = dt a_k N - (c_k dt / dx_c) dp (+ dt b_k N^{k-2}), dp the
+// pressure difference across the point.
 template <typename T>
-__device__ __forceinline__ void mom_update(const StageP<T>& sp, T uP, T N, T gp, T Nprev, T& out, T& R) {
-    R = sp.dta * N - sp.ckdt * gp;
+__device__ __forceinline__ void mom_update(const StageP<T>& sp, T uP, T N, T dp, T cg, T Nprev, T& out, T& R) {
+    R = sp.dta * N - cg * dp;
     if (sp.read_prev) R += sp.dtb * Nprev;
     out = uP + R;
 }
@@ -257,12 +258,12 @@ __device__ __forceinline__ void mom_write(const MomF<T>& F, const StageP<T>& sp,
 
 // One plane k of the 3D update.  t0 / t1: the tiles of planes k and k+1, with
 // rows RS apart and components CS apart; a, b: the tile positions of A and B.
-template <typename T, int RS, int CS>
+template <typename T, int RS, int CS, bool OWN>
 __device__ __forceinline__ void mom_plane3(const GridP& g, const MomF<T>& F, const StageP<T>& sp,
                                            const IbmStage<T>& ib, int a, int b, const T* __restrict__ t0,
                                            const T* __restrict__ t1, MomCarry<T>& C, const MomPre<T>& P,
-                                           uint32_t m, int k, int ida, int idb, bool liveA, bool liveB, int segA,
-                                           T& fsum) {
+                                           const T (&ownA)[3], const T (&ownB)[3], uint32_t m, int k, int ida,
+                                           int idb, bool liveA, bool liveB, int segA, T& fsum) {
     constexpr int HX = RS;
     const T* U0 = t0;
     const T* V0 = t0 + CS;
@@ -278,9 +279,11 @@ __device__ __forceinline__ void mom_plane3(const GridP& g, const MomF<T>& F, con
     const T wEA = W0[a + 1], wEB = W0[b + 1], wWA = W0[a - 1], wWB = W0[b - 1], wSA = W0[a - HX];
     const T wNB = W0[b + HX];
     // plane k+1
-    const T uTA = U1[a], uTB = U1[b], uTWA = U1[a - 1], uTWB = U1[b - 1];
-    const T vTA = V1[a], vTB = V1[b], vTSA = V1[a - HX];
-    const T wTA = W1[a], wTB = W1[b];
+    // plane k+1 at A and B: already in registers when OWN (ownA, ownB = u, v, w)
+    const T uTA = OWN ? ownA[0] : U1[a], uTB = OWN ? ownB[0] : U1[b];
+    const T vTA = OWN ? ownA[1] : V1[a], vTB = OWN ? ownB[1] : V1[b];
+    const T wTA = OWN ? ownA[2] : W1[a], wTB = OWN ? ownB[2] : W1[b];
+    const T uTWA = U1[a - 1], uTWB = U1[b - 1], vTSA = V1[a - HX];
     const T uA = C.uA, uB = C.uB, vA = C.vA, vB = C.vB, wA = C.wA, wB = C.wB;
     const T uWA = C.uWA, uWB = C.uWB, vSA = C.vSA;
 
@@ -304,49 +307,43 @@ __device__ __forceinline__ void mom_plane3(const GridP& g, const MomF<T>& F, con
         T conv = (uEA - uWA) * (uEA + uWA + two * uA) * sp.qx;
         conv += (xyA - xyAs) * sp.qy;
         conv += (xzA - C.fuA) * sp.qz;
-        T lap = (uEA + uWA - two * uA) * sp.nx2 + (uB + uSA - two * uA) * sp.ny2;
-        lap += (uTA + C.ubA - two * uA) * sp.nz2;
+        T lap = (uEA + uWA) * sp.nx2 + (uB + uSA) * sp.ny2 + (uTA + C.ubA) * sp.nz2 - sp.lc * uA;
         NA[0] = lap - conv + sp.g[0];
-        mom_update(sp, uA, NA[0], (P.eA - pA) * sp.idx, P.qA[0], oA[0], RA[0]);
+        mom_update(sp, uA, NA[0], P.eA - pA, sp.cgx, P.qA[0], oA[0], RA[0]);
         conv = (uEB - uWB) * (uEB + uWB + two * uB) * sp.qx;
         conv += (xyB - xyA) * sp.qy;
         conv += (xzB - C.fuB) * sp.qz;
-        lap = (uEB + uWB - two * uB) * sp.nx2 + (uNB + uA - two * uB) * sp.ny2;
-        lap += (uTB + C.ubB - two * uB) * sp.nz2;
+        lap = (uEB + uWB) * sp.nx2 + (uNB + uA) * sp.ny2 + (uTB + C.ubB) * sp.nz2 - sp.lc * uB;
         NB[0] = lap - conv + sp.g[0];
-        mom_update(sp, uB, NB[0], (P.eB - pB) * sp.idx, P.qB[0], oB[0], RB[0]);
+        mom_update(sp, uB, NB[0], P.eB - pB, sp.cgx, P.qB[0], oB[0], RB[0]);
     }
     {   // v
         T conv = (xyA - xyAw) * sp.qx;
         conv += (vB - vSA) * (vB + vSA + two * vA) * sp.qy;
         conv += (yzA - C.fvA) * sp.qz;
-        T lap = (vEA + vWA - two * vA) * sp.nx2 + (vB + vSA - two * vA) * sp.ny2;
-        lap += (vTA + C.vbA - two * vA) * sp.nz2;
+        T lap = (vEA + vWA) * sp.nx2 + (vB + vSA) * sp.ny2 + (vTA + C.vbA) * sp.nz2 - sp.lc * vA;
         NA[1] = lap - conv + sp.g[1];
-        mom_update(sp, vA, NA[1], (pB - pA) * sp.idy, P.qA[1], oA[1], RA[1]);
+        mom_update(sp, vA, NA[1], pB - pA, sp.cgy, P.qA[1], oA[1], RA[1]);
         conv = (xyB - xyBw) * sp.qx;
         conv += (vNB - vA) * (vNB + vA + two * vB) * sp.qy;
         conv += (yzB - C.fvB) * sp.qz;
-        lap = (vEB + vWB - two * vB) * sp.nx2 + (vNB + vA - two * vB) * sp.ny2;
-        lap += (vTB + C.vbB - two * vB) * sp.nz2;
+        lap = (vEB + vWB) * sp.nx2 + (vNB + vA) * sp.ny2 + (vTB + C.vbB) * sp.nz2 - sp.lc * vB;
         NB[1] = lap - conv + sp.g[1];
-        mom_update(sp, vB, NB[1], (P.nB - pB) * sp.idy, P.qB[1], oB[1], RB[1]);
+        mom_update(sp, vB, NB[1], P.nB - pB, sp.cgy, P.qB[1], oB[1], RB[1]);
     }
     {   // w
         T conv = (xzA - xzAw) * sp.qx;
         conv += (yzA - yzAs) * sp.qy;
         conv += (wTA - C.wbA) * (wTA + C.wbA + two * wA) * sp.qz;
-        T lap = (wEA + wWA - two * wA) * sp.nx2 + (wB + wSA - two * wA) * sp.ny2;
-        lap += (wTA + C.wbA - two * wA) * sp.nz2;
+        T lap = (wEA + wWA) * sp.nx2 + (wB + wSA) * sp.ny2 + (wTA + C.wbA) * sp.nz2 - sp.lc * wA;
         NA[2] = lap - conv + sp.g[2];
-        mom_update(sp, wA, NA[2], (P.tA - pA) * sp.idz, P.qA[2], oA[2], RA[2]);
+        mom_update(sp, wA, NA[2], P.tA - pA, sp.cgz, P.qA[2], oA[2], RA[2]);
         conv = (xzB - xzBw) * sp.qx;
         conv += (yzB - yzA) * sp.qy;
         conv += (wTB - C.wbB) * (wTB + C.wbB + two * wB) * sp.qz;
-        lap = (wEB + wWB - two * wB) * sp.nx2 + (wNB + wA - two * wB) * sp.ny2;
-        lap += (wTB + C.wbB - two * wB) * sp.nz2;
+        lap = (wEB + wWB) * sp.nx2 + (wNB + wA) * sp.ny2 + (wTB + C.wbB) * sp.nz2 - sp.lc * wB;
         NB[2] = lap - conv + sp.g[2];
-        mom_update(sp, wB, NB[2], (P.tB - pB) * sp.idz, P.qB[2], oB[2], RB[2]);
+        mom_update(sp, wB, NB[2], P.tB - pB, sp.cgz, P.qB[2], oB[2], RB[2]);
     }
     const uint32_t mA = m & 0xffu, mB = (m >> 8) & 0xffu;
     if (__any_sync(0xffffffffu, (mA | mB) & (IBM_MASK_IBM_U | IBM_MASK_IBM_V | IBM_MASK_IBM_W))) {
@@ -387,21 +384,21 @@ __device__ __forceinline__ void mom_plane2(const GridP& g, const MomF<T>& F, con
         T conv = (uEA - uWA) * (uEA + uWA + two * uA) * sp.qx + (xyA - xyAs) * sp.qy;
         T lap = (uEA + uWA - two * uA) * sp.nx2 + (uB + uSA - two * uA) * sp.ny2;
         NA[0] = lap - conv + sp.g[0];
-        mom_update(sp, uA, NA[0], (P.eA - pA) * sp.idx, P.qA[0], oA[0], RA[0]);
+        mom_update(sp, uA, NA[0], P.eA - pA, sp.cgx, P.qA[0], oA[0], RA[0]);
         conv = (uEB - uWB) * (uEB + uWB + two * uB) * sp.qx + (xyB - xyA) * sp.qy;
         lap = (uEB + uWB - two * uB) * sp.nx2 + (uNB + uA - two * uB) * sp.ny2;
         NB[0] = lap - conv + sp.g[0];
-        mom_update(sp, uB, NB[0], (P.eB - pB) * sp.idx, P.qB[0], oB[0], RB[0]);
+        mom_update(sp, uB, NB[0], P.eB - pB, sp.cgx, P.qB[0], oB[0], RB[0]);
     }
     {
         T conv = (xyA - xyAw) * sp.qx + (vB - vSA) * (vB + vSA + two * vA) * sp.qy;
         T lap = (vEA + vWA - two * vA) * sp.nx2 + (vB + vSA - two * vA) * sp.ny2;
         NA[1] = lap - conv + sp.g[1];
-        mom_update(sp, vA, NA[1], (pB - pA) * sp.idy, P.qA[1], oA[1], RA[1]);
+        mom_update(sp, vA, NA[1], pB - pA, sp.cgy, P.qA[1], oA[1], RA[1]);
         conv = (xyB - xyBw) * sp.qx + (vNB - vA) * (vNB + vA + two * vB) * sp.qy;
         lap = (vEB + vWB - two * vB) * sp.nx2 + (vNB + vA - two * vB) * sp.ny2;
         NB[1] = lap - conv + sp.g[1];
-        mom_update(sp, vB, NB[1], (P.nB - pB) * sp.idy, P.qB[1], oB[1], RB[1]);
+        mom_update(sp, vB, NB[1], P.nB - pB, sp.cgy, P.qB[1], oB[1], RB[1]);
     }
     const uint32_t mA = m & 0xffu, mB = (m >> 8) & 0xffu;
     if (__any_sync(0xffffffffu, (mA | mB) & (IBM_MASK_IBM_U | IBM_MASK_IBM_V))) {
@@ -426,8 +423,9 @@ __device__ __forceinline__ void mom_iter3(const GridP& g, const MomF<T>& F, cons
     if (k + 1 < kend) mom_pre(F, S, Pn, g, k + 1, plane, sp.read_prev);
     __syncthreads();
     const int ida = rowA + k * plane;
-    mom_plane3<T, HX, HP>(g, F, sp, ib, S.ta, S.tb, tiles + s0, tiles + s1, C, Pc, mc, k, ida, ida + g.nx, liveA,
-                          liveB, segrow + k * g.ny * g.nsegx, fsum);
+    const T none[3] = {T(0), T(0), T(0)};
+    mom_plane3<T, HX, HP, false>(g, F, sp, ib, S.ta, S.tb, tiles + s0, tiles + s1, C, Pc, none, none, mc, k, ida,
+                                 ida + g.nx, liveA, liveB, segrow + k * g.ny * g.nsegx, fsum);
     const int t = s0;
     s0 = s1;
     s1 = s2;
@@ -874,9 +872,9 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
             }
         }
         const int ida = rowA + k * plane;
-        mom_plane3<T, L::RX, L::CS>(g, F, sp, ib, ta, tb, reinterpret_cast<const T*>(s0),
-                                    reinterpret_cast<const T*>(s1), C, P, mc, k, ida, ida + g.nx, liveA, liveB,
-                                    segrow + k * g.ny * g.nsegx, fsum);
+        mom_plane3<T, L::RX, L::CS, true>(g, F, sp, ib, ta, tb, reinterpret_cast<const T*>(s0),
+                                          reinterpret_cast<const T*>(s1), C, P, ua, ub, mc, k, ida, ida + g.nx,
+                                          liveA, liveB, segrow + k * g.ny * g.nsegx, fsum);
         mc = mn & live_bits;
     }
     if (sp.flux_sum) {
@@ -986,6 +984,8 @@ ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib,
     sp.nx2 = (T)(h->phys.nu / (g.dx * g.dx)); sp.ny2 = (T)(h->phys.nu / (g.dy * g.dy));
     sp.nz2 = (T)(h->phys.nu / (g.dz * g.dz));
     sp.qx = (T)(0.25 / g.dx); sp.qy = (T)(0.25 / g.dy); sp.qz = (T)(0.25 / g.dz);
+    sp.cgx = (T)(dt * RK_C[k] / g.dx); sp.cgy = (T)(dt * RK_C[k] / g.dy); sp.cgz = (T)(dt * RK_C[k] / g.dz);
+    sp.lc = (T)(2.0 * h->phys.nu * (1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy) + 1.0 / (g.dz * g.dz)));
     sp.sig_lo = (T)g.sig_lo;
     sp.sig_hi = (T)g.sig_hi;
     sp.read_prev = k > 0;
