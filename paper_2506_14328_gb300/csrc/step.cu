@@ -276,6 +276,126 @@ __device__ __forceinline__ void tridiag_fp32(const GridP& g, float2* spec, const
     }
 }
 
+// FP64 sweep of one system by a whole warp (ny <= 32 * TW_ROWS).  Both
+// recurrences are first order and affine,
+//   forward  e_j = w_j (d_j - e_{j-1})        (e_{-1} = 0)
+//   backward x_j = e_j - w_j x_{j+1}          (x_{ny} = 0),
+// so each lane composes the maps of its run of consecutive rows, a five-step
+// shuffle scan composes them across the lanes (affine maps compose exactly
+// like the recurrence itself), and each lane replays its rows from the value
+// handed in.  The dependent FP64 chain is about 2 (rows per lane + 5) long
+// instead of 2 ny.  Real and imaginary parts go through together.
+constexpr int TW_ROWS = 8;
+
+template <typename C>
+__device__ __forceinline__ void tridiag_warp64(const GridP& g, C* spec, const double* __restrict__ piv,
+                                               long long base, double scale, bool zero_mode) {
+    constexpr bool F32 = sizeof(C) == sizeof(float2);
+    using S = typename std::conditional<F32, float, double>::type;
+    const int lane = threadIdx.x & 31;
+    const int ny = g.ny;
+    const int E = (ny + 31) / 32;
+    const int j0 = lane * E;
+    const long long st = g.nxh;
+    const float sf = (float)scale;
+    double dr[TW_ROWS], di[TW_ROWS], w[TW_ROWS];
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t) {
+        dr[t] = di[t] = w[t] = 0.0;
+        if (t < E && j0 + t < ny) {
+            const long long o = base + (long long)(j0 + t) * st;
+            const C r = spec[o];
+            // FP32 storage: the scale is applied in FP32 on the input (exact to FP32 rounding)
+            dr[t] = F32 ? (double)((float)r.x * sf) : (double)r.x;
+            di[t] = F32 ? (double)((float)r.y * sf) : (double)r.y;
+            w[t] = piv[o];
+        }
+    }
+    // forward: this lane's map e_out = A + B e_in
+    double Ar = 0.0, Ai = 0.0, B = 1.0;
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t)
+        if (t < E && j0 + t < ny) {
+            Ar = w[t] * (dr[t] - Ar);
+            Ai = w[t] * (di[t] - Ai);
+            B = -w[t] * B;
+        }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {          // inclusive scan: compose with the lanes below
+        const double pr = __shfl_up_sync(0xffffffffu, Ar, off);
+        const double pi = __shfl_up_sync(0xffffffffu, Ai, off);
+        const double pb = __shfl_up_sync(0xffffffffu, B, off);
+        if (lane >= off) {
+            Ar += B * pr;
+            Ai += B * pi;
+            B *= pb;
+        }
+    }
+    double er = __shfl_up_sync(0xffffffffu, Ar, 1), ei = __shfl_up_sync(0xffffffffu, Ai, 1);
+    if (lane == 0) er = ei = 0.0;
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t)
+        if (t < E && j0 + t < ny) {
+            er = w[t] * (dr[t] - er);
+            ei = w[t] * (di[t] - ei);
+            dr[t] = er;
+            di[t] = ei;
+        }
+    // backward: this lane's map x_first = Cm + D x_in, x_in the value above the run
+    double Cr = 0.0, Ci = 0.0, D = 1.0;
+#pragma unroll
+    for (int t = TW_ROWS - 1; t >= 0; --t)
+        if (t < E && j0 + t < ny) {
+            Cr = dr[t] - w[t] * Cr;
+            Ci = di[t] - w[t] * Ci;
+            D = -w[t] * D;
+        }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {          // compose with the lanes above
+        const double pr = __shfl_down_sync(0xffffffffu, Cr, off);
+        const double pi = __shfl_down_sync(0xffffffffu, Ci, off);
+        const double pd = __shfl_down_sync(0xffffffffu, D, off);
+        if (lane + off < 32) {
+            Cr += D * pr;
+            Ci += D * pi;
+            D *= pd;
+        }
+    }
+    double xr = __shfl_down_sync(0xffffffffu, Cr, 1), xi = __shfl_down_sync(0xffffffffu, Ci, 1);
+    if (lane == 31) xr = xi = 0.0;
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int t = TW_ROWS - 1; t >= 0; --t)
+        if (t < E && j0 + t < ny) {
+            xr = dr[t] - w[t] * xr;
+            xi = di[t] - w[t] * xi;
+            dr[t] = F32 ? xr : xr * scale;
+            di[t] = F32 ? xi : xi * scale;
+            sr += xr;
+            si += xi;
+        }
+    double mr = 0.0, mi = 0.0;
+    if (zero_mode) {                                   // box-mean gauge
+        sr = warp_sum(sr);
+        si = warp_sum(si);
+        mr = __shfl_sync(0xffffffffu, sr, 0) / ny * (F32 ? 1.0 : scale);
+        mi = __shfl_sync(0xffffffffu, si, 0) / ny * (F32 ? 1.0 : scale);
+    }
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t)
+        if (t < E && j0 + t < ny) {
+            const long long o = base + (long long)(j0 + t) * st;
+            C r;
+            r.x = (S)dr[t];
+            r.y = (S)di[t];
+            if (zero_mode) {
+                r.x = (S)((double)r.x - mr);
+                r.y = (S)((double)r.y - mi);
+            }
+            spec[o] = r;
+        }
+}
+
 // One warp per block; `order` lists the systems (kz * nxh + kx) with every
 // FP64 system first, so the scarce FP64 pipes of all SMs share the low modes.
 // FP64 systems take two threads (real and imaginary part), FP32 systems one.
@@ -283,7 +403,17 @@ template <typename C>
 __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, const double* __restrict__ piv,
                                                 const float* __restrict__ piv32, const int* __restrict__ order,
                                                 int n64, int nsys, double scale) {
-    const int nb64 = (2 * n64 + 31) / 32;
+    if (g.ny <= 32 * TW_ROWS) {
+        // one warp (block) per FP64 system
+        if ((int)blockIdx.x < n64) {
+            const int sys = order[blockIdx.x];
+            const int kx = sys % g.nxh, kz = sys / g.nxh;
+            const long long base = (long long)kz * g.ny * g.nxh + kx;
+            tridiag_warp64<C>(g, spec, piv, base, scale, kx == 0 && kz == 0);
+            return;
+        }
+    }
+    const int nb64 = g.ny <= 32 * TW_ROWS ? n64 : (2 * n64 + 31) / 32;
     if ((int)blockIdx.x < nb64) {
         const int t = blockIdx.x * 32 + threadIdx.x;
         if (t >= 2 * n64) return;
@@ -445,7 +575,8 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
     timer_end(h, t, "fft_forward");
     double scale = g.dy * g.dy / ((double)g.nx * (double)g.nz);
     const int nsys = g.nz * g.nxh;
-    const int nblk = (2 * h->n64 + 31) / 32 + (nsys - h->n64 + 31) / 32;
+    const int nb64 = g.ny <= 32 * TW_ROWS ? h->n64 : (2 * h->n64 + 31) / 32;
+    const int nblk = nb64 + (nsys - h->n64 + 31) / 32;
     timer_begin(h, "tridiag", &t);
     if (h->prec == IBM_FP64)
         k_tridiag<double2><<<nblk, 32, 0, h->stream>>>(g, (double2*)h->spec, (double2*)h->spec, h->pivots,
