@@ -78,12 +78,16 @@ __device__ __forceinline__ T flux_increment(const FluxCorr<T>& fc, T pic, uint8_
 // ---------------------------------------------------------------------------
 // K4: divergence of the predictor, D u*, in the field precision.  Each block
 // marches g.kzd planes along z carrying w*(k-1) in a register; u*(i-1) comes
-// from the neighbouring lane.
+// from the neighbouring lane.  A thread issues the loads of DZ planes before
+// it uses any of them, so several planes' bytes are in flight per warp.
 // ---------------------------------------------------------------------------
+constexpr int DZ = 4;
+
 template <typename T, bool THREE, bool FLUX>
 __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict__ u, const T* __restrict__ v,
                                                     const T* __restrict__ w, const uint8_t* __restrict__ mask,
                                                     T* __restrict__ rhs, T idx, T idy, T idz, FluxCorr<T> fc) {
+    constexpr int ZB = THREE ? DZ : 1;
     const int lane = threadIdx.x;
     const int i = blockIdx.x * 32 + lane;
     const int j = blockIdx.y * 8 + threadIdx.y;
@@ -99,34 +103,53 @@ __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict
     const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
     T wprev = T(0);
     if (THREE && live) wprev = w[i + g.nx * j + plane * wrapi(kbeg - 1, g.nz)];
-#pragma unroll 2
-    for (int k = kbeg; k < kend; ++k) {
-        const int rowb = g.nx * (j + g.ny * k);
-        const int id = rowb + i;
-        T uc = live ? u[id] : T(0);
-        T ulane0 = u[rowb + il];
-        if (FLUX) {
-            const int rowseg = (j + g.ny * k) * g.nsegx;
-            const uint8_t m = live ? mask[id] : 0;
-            const unsigned b = __ballot_sync(0xffffffffu, (m & IBM_MASK_IBM_U) != 0);
-            if (live) uc += flux_increment(fc, pic, m, b, rowseg + (int)blockIdx.x, lane);
-            const uint8_t ml = il_probe < g.nx ? mask[rowb + il_probe] : 0;
-            const unsigned bl = __ballot_sync(0xffffffffu, (ml & IBM_MASK_IBM_U) != 0);
-            const uint8_t mln = __shfl_sync(0xffffffffu, ml, lanel);
-            ulane0 += flux_increment(fc, pic, mln, bl, rowseg + segl, lanel);
-        }
-        T ul = __shfl_up_sync(0xffffffffu, uc, 1);
-        if (lane == 0) ul = ulane0;
-        if (live) {
-            T d = (uc - ul) * idx;
-            const T vm = j > 0 ? v[id - g.nx] : T(0);
-            d += (v[id] - vm) * idy;
-            if (THREE) {
-                const T wc = w[id];
-                d += (wc - wprev) * idz;
-                wprev = wc;
+    for (int k0 = kbeg; k0 < kend; k0 += ZB) {
+        T uc[ZB], ul0[ZB], vc[ZB], vm[ZB], wc[ZB];
+        uint8_t mc[ZB], ml[ZB];
+#pragma unroll
+        for (int t = 0; t < ZB; ++t) {
+            uc[t] = ul0[t] = vc[t] = vm[t] = wc[t] = T(0);
+            mc[t] = ml[t] = 0;
+            const int k = k0 + t;
+            if (k < kend) {
+                const int rowb = g.nx * (j + g.ny * k);
+                const int id = rowb + i;
+                ul0[t] = u[rowb + il];
+                if (live) {
+                    uc[t] = u[id];
+                    vc[t] = v[id];
+                    if (j > 0) vm[t] = v[id - g.nx];
+                    if (THREE) wc[t] = w[id];
+                    if (FLUX) mc[t] = mask[id];
+                }
+                if (FLUX && il_probe < g.nx) ml[t] = mask[rowb + il_probe];
             }
-            rhs[id] = d;
+        }
+#pragma unroll
+        for (int t = 0; t < ZB; ++t) {
+            const int k = k0 + t;
+            if (k >= kend) break;
+            const int rowb = g.nx * (j + g.ny * k);
+            T ucc = uc[t], ulane0 = ul0[t];
+            if (FLUX) {
+                const int rowseg = (j + g.ny * k) * g.nsegx;
+                const unsigned b = __ballot_sync(0xffffffffu, (mc[t] & IBM_MASK_IBM_U) != 0);
+                if (live) ucc += flux_increment(fc, pic, mc[t], b, rowseg + (int)blockIdx.x, lane);
+                const unsigned bl = __ballot_sync(0xffffffffu, (ml[t] & IBM_MASK_IBM_U) != 0);
+                const uint8_t mln = __shfl_sync(0xffffffffu, ml[t], lanel);
+                ulane0 += flux_increment(fc, pic, mln, bl, rowseg + segl, lanel);
+            }
+            T ul = __shfl_up_sync(0xffffffffu, ucc, 1);
+            if (lane == 0) ul = ulane0;
+            if (live) {
+                T d = (ucc - ul) * idx;
+                d += (vc[t] - vm[t]) * idy;
+                if (THREE) {
+                    d += (wc[t] - wprev) * idz;
+                    wprev = wc[t];
+                }
+                rhs[rowb + i] = d;
+            }
         }
     }
 }
@@ -437,7 +460,7 @@ __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, 
 // K7: u = u* (+ flux correction) - G psi on every non-wall face, p += psi/(c_k dt)
 // (psi = c_k dt phi is what the Poisson solve returns for rhs = D u*).  Blocks
 // march g.kzd planes carrying psi(k+1) into the next plane; psi(i+1) comes from
-// the neighbouring lane.
+// the neighbouring lane.  Loads of DZ planes are issued before any is used.
 // ---------------------------------------------------------------------------
 template <typename T, bool THREE, bool FLUX>
 __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ us0, const T* __restrict__ us1,
@@ -445,6 +468,7 @@ __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ 
                                                  const uint8_t* __restrict__ mask, T* __restrict__ u0,
                                                  T* __restrict__ u1, T* __restrict__ u2, T* __restrict__ p, T idx,
                                                  T idy, T idz, T inv_ckdt, int update_p, FluxCorr<T> fc) {
+    constexpr int ZB = THREE ? DZ : 1;
     const int lane = threadIdx.x;
     const int i = blockIdx.x * 32 + lane;
     const int j = blockIdx.y * 8 + threadIdx.y;
@@ -455,29 +479,52 @@ __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ 
     const int plane = g.nx * g.ny;
     const int ir = (i + 1 < g.nx) ? i + 1 : 0;              // +x neighbour (periodic)
     const bool from_lane = lane < 31 && i + 1 < g.nx;
+    const bool top = j == g.ny - 1;
     const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
     T ph = live ? psi[i + g.nx * j + plane * kbeg] : T(0);
-#pragma unroll 2
-    for (int k = kbeg; k < kend; ++k) {
-        const int rowb = g.nx * (j + g.ny * k);
-        const int id = rowb + i;
-        T pE = __shfl_down_sync(0xffffffffu, ph, 1);
-        T uc = T(0);
-        if (FLUX) {
-            const uint8_t m = live ? mask[id] : 0;
-            const unsigned b = __ballot_sync(0xffffffffu, (m & IBM_MASK_IBM_U) != 0);
-            if (live) uc = flux_increment(fc, pic, m, b, (j + g.ny * k) * g.nsegx + (int)blockIdx.x, lane);
+    for (int k0 = kbeg; k0 < kend; k0 += ZB) {
+        T a0[ZB], a1[ZB], a2[ZB], pT[ZB], pN[ZB], pE[ZB], pp[ZB];
+        uint8_t mc[ZB];
+#pragma unroll
+        for (int t = 0; t < ZB; ++t) {
+            a0[t] = a1[t] = a2[t] = pT[t] = pN[t] = pE[t] = pp[t] = T(0);
+            mc[t] = 0;
+            const int k = k0 + t;
+            if (k < kend && live) {
+                const int rowb = g.nx * (j + g.ny * k);
+                const int id = rowb + i;
+                a0[t] = us0[id];
+                a1[t] = us1[id];
+                if (THREE) {
+                    a2[t] = us2[id];
+                    pT[t] = psi[id + ((k + 1 < g.nz) ? plane : plane - (int)g.N)];
+                }
+                if (!top) pN[t] = psi[id + g.nx];
+                if (!from_lane) pE[t] = psi[rowb + ir];
+                if (FLUX) mc[t] = mask[id];
+                if (update_p) pp[t] = p[id];
+            }
         }
-        T pT = T(0);
-        if (THREE && live) pT = psi[id + ((k + 1 < g.nz) ? plane : plane - (int)g.N)];
-        if (live) {
-            if (!from_lane) pE = psi[rowb + ir];
-            u0[id] = us0[id] + uc - (pE - ph) * idx;
-            u1[id] = j < g.ny - 1 ? us1[id] - (psi[id + g.nx] - ph) * idy : us1[id];
-            if (THREE) u2[id] = us2[id] - (pT - ph) * idz;
-            if (update_p) p[id] += ph * inv_ckdt;
+#pragma unroll
+        for (int t = 0; t < ZB; ++t) {
+            const int k = k0 + t;
+            if (k >= kend) break;
+            const int id = g.nx * (j + g.ny * k) + i;
+            T e = __shfl_down_sync(0xffffffffu, ph, 1);
+            if (!from_lane) e = pE[t];
+            T uc = T(0);
+            if (FLUX) {
+                const unsigned b = __ballot_sync(0xffffffffu, (mc[t] & IBM_MASK_IBM_U) != 0);
+                if (live) uc = flux_increment(fc, pic, mc[t], b, (j + g.ny * k) * g.nsegx + (int)blockIdx.x, lane);
+            }
+            if (live) {
+                u0[id] = a0[t] + uc - (e - ph) * idx;
+                u1[id] = top ? a1[t] : a1[t] - (pN[t] - ph) * idy;
+                if (THREE) u2[id] = a2[t] - (pT[t] - ph) * idz;
+                if (update_p) p[id] = pp[t] + ph * inv_ckdt;
+            }
+            ph = pT[t];
         }
-        ph = pT;
     }
 }
 
