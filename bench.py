@@ -56,6 +56,9 @@ NCU_TRAFFIC = {
 }
 
 
+KERNEL_FILE = {"momentum": "momentum.cu"}   # other kernels of this library live in step.cu
+
+
 def src_hash(name="step.cu") -> str:
     p = os.path.join(ROOT, "paper_2506_14328_gb300", "csrc", name)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
@@ -320,7 +323,7 @@ def run_gpu(args):
         achieved = alg / avg_s / 1e9 if avg_s > 0 else None
         traffic = None
         rec = NCU_TRAFFIC.get(dom)
-        if rec and rec[1] == src_hash():
+        if rec and rec[1] == src_hash(KERNEL_FILE.get(dom, "step.cu")):
             traffic = rec[0]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic, "kernel": dom,
