@@ -14,7 +14,7 @@ namespace {
 thread_local std::string g_last_error;
 
 constexpr size_t ALIGN = 256;
-constexpr int DIAG_PART = 304 * 12;
+constexpr int DIAG_PART = DIAG_BLOCKS * 12;
 constexpr int SCAN_CH = 512 * 8;
 constexpr uint64_t STATE_MAGIC = 0x31534d4249ull;     // "IBMS1"
 

@@ -100,6 +100,160 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // ---------------------------------------------------------------------------
+// Diagnostics accumulated cell by cell, shared by ibm_diagnostics and
+// ibm_diagnostics_noalloc so that the two agree cell by cell.  Results (a[12]):
+//   [0] sum div^2  [1] max |div|  [2..4] max |u_c|  [5..7] sum u_c  [8..10] sum u_c^2
+//   [11] non-finite count;  velocity terms over the internal points of component c.
+// FP64 fields: FP64 per cell.  FP32 fields: the same quantities to about 1e-14
+// relative with FP32 instructions only (GB300's FP64 rate is 1/64 of FP32):
+// differences and products are split exactly into float pairs (two-sum, two-
+// product), sums run in pairs and are folded into FP64 every DIAG_FOLD cells.
+// ---------------------------------------------------------------------------
+constexpr int DIAG_FOLD = 8;
+constexpr int DIAG_BLOCKS = 4 * 304;   // blocks of the diagnostics kernel (12 partials each)
+
+struct FF { float hi, lo; };   // value hi + lo, |lo| <= ulp(hi) / 2
+
+// Each rounding whose error is kept is an explicit _rn operation, so no
+// multiply-add contraction can change it.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ FF ff_norm(float s, float e) {   // fast two-sum: |s| >= |e|
+    FF r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = e - (r.hi - s);
+    return r;
+}
+
+__device__ __forceinline__ FF ff_add(FF a, float bh, float bl) {
+    float s, e;
+    two_sum(a.hi, bh, s, e);
+    return ff_norm(s, e + (a.lo + bl));
+}
+
+__device__ __forceinline__ FF ff_mul(FF a, float bh, float bl) {   // (a.hi + a.lo)(bh + bl), to ~2^-46
+    const float p = __fmul_rn(a.hi, bh);
+    const float pe = fmaf(a.hi, bh, -p) + (a.hi * bl + a.lo * bh);
+    return ff_norm(p, pe);
+}
+
+template <typename T> struct DiagAcc;
+
+template <> struct DiagAcc<double> {
+    double a[12];
+    double vmax[3];
+    __device__ DiagAcc() {
+        for (int q = 0; q < 12; ++q) a[q] = 0.0;
+        vmax[0] = vmax[1] = vmax[2] = 0.0;
+    }
+    __device__ __forceinline__ void cell(int ncomp, const double (&id)[3], double uc, double ul, double vc, double vm,
+                                         double wc, double wm, double pc, uint8_t m) {
+        double d = (uc - ul) * id[0] + (vc - vm) * id[1];
+        if (ncomp == 3) d += (wc - wm) * id[2];
+        a[0] += d * d;
+        a[1] = fmax(a[1], fabs(d));
+        const double x3[3] = {uc, vc, wc};
+        for (int c = 0; c < ncomp; ++c) {
+            const double x = x3[c];
+            if (!isfinite(x)) a[11] += 1.0;
+            if (!((m >> c) & 1u)) continue;
+            vmax[c] = fmax(vmax[c], fabs(x));
+            a[5 + c] += x;
+            a[8 + c] += x * x;
+        }
+        if (!isfinite(pc)) a[11] += 1.0;
+    }
+    __device__ __forceinline__ void finish(double (&out)[12]) {
+        for (int q = 0; q < 12; ++q) out[q] = a[q];
+        for (int c = 0; c < 3; ++c) out[2 + c] = vmax[c];
+    }
+};
+
+template <> struct DiagAcc<float> {
+    double a[12];           // folded sums
+    FF s[7];                // running pairs: sum u_c (0..2), sum u_c^2 (3..5), sum div^2 (6)
+    FF dmax;                // max |div| as a normalised pair (compared exactly)
+    float vmax[3];
+    int nonfinite, n;
+    __device__ DiagAcc() {
+        for (int q = 0; q < 12; ++q) a[q] = 0.0;
+        for (int q = 0; q < 7; ++q) s[q] = FF{0.f, 0.f};
+        dmax = FF{0.f, 0.f};
+        vmax[0] = vmax[1] = vmax[2] = 0.f;
+        nonfinite = n = 0;
+    }
+    __device__ __forceinline__ void fold() {
+        for (int c = 0; c < 3; ++c) {
+            a[5 + c] += (double)s[c].hi + (double)s[c].lo;
+            a[8 + c] += (double)s[3 + c].hi + (double)s[3 + c].lo;
+        }
+        a[0] += (double)s[6].hi + (double)s[6].lo;
+        for (int q = 0; q < 7; ++q) s[q] = FF{0.f, 0.f};
+        n = 0;
+    }
+    // id: the inverse spacings split into float pairs (hi, lo) per direction
+    __device__ __forceinline__ void cell(int ncomp, const float (&id)[6], float uc, float ul, float vc, float vm,
+                                         float wc, float wm, float pc, uint8_t m) {
+        FF t, d;
+        two_sum(uc, -ul, t.hi, t.lo);                  // exact difference
+        d = ff_mul(t, id[0], id[1]);
+        two_sum(vc, -vm, t.hi, t.lo);
+        t = ff_mul(t, id[2], id[3]);
+        d = ff_add(d, t.hi, t.lo);
+        if (ncomp == 3) {
+            two_sum(wc, -wm, t.hi, t.lo);
+            t = ff_mul(t, id[4], id[5]);
+            d = ff_add(d, t.hi, t.lo);
+        }
+        if (!isfinite(d.hi)) d = FF{d.hi, 0.f};
+        const FF d2 = ff_mul(d, d.hi, d.lo);
+        s[6] = ff_add(s[6], d2.hi, d2.lo);
+        const FF ad = d.hi < 0.f ? FF{-d.hi, -d.lo} : d;
+        if (ad.hi > dmax.hi || (ad.hi == dmax.hi && ad.lo > dmax.lo)) dmax = ad;
+        const float x3[3] = {uc, vc, wc};
+        for (int c = 0; c < ncomp; ++c) {
+            const float x = x3[c];
+            if (!isfinite(x)) ++nonfinite;
+            if (!((m >> c) & 1u)) continue;
+            vmax[c] = fmaxf(vmax[c], fabsf(x));
+            s[c] = ff_add(s[c], x, 0.f);
+            const float p = __fmul_rn(x, x);
+            s[3 + c] = ff_add(s[3 + c], p, fmaf(x, x, -p));
+        }
+        if (!isfinite(pc)) ++nonfinite;
+        if (++n == DIAG_FOLD) fold();
+    }
+    __device__ __forceinline__ void finish(double (&out)[12]) {
+        fold();
+        for (int q = 0; q < 12; ++q) out[q] = a[q];
+        out[1] = (double)dmax.hi + (double)dmax.lo;
+        for (int c = 0; c < 3; ++c) out[2 + c] = (double)vmax[c];
+        out[11] = (double)nonfinite;
+    }
+};
+
+// The inverse spacings in the form DiagAcc<T>::cell takes them.
+template <typename T> struct DiagInv;
+template <> struct DiagInv<double> {
+    double v[3];
+    __host__ __device__ DiagInv(double ix, double iy, double iz) { v[0] = ix; v[1] = iy; v[2] = iz; }
+};
+template <> struct DiagInv<float> {
+    float v[6];
+    __host__ __device__ DiagInv(double ix, double iy, double iz) {
+        const double x[3] = {ix, iy, iz};
+        for (int d = 0; d < 3; ++d) {
+            v[2 * d] = (float)x[d];
+            v[2 * d + 1] = (float)(x[d] - (double)v[2 * d]);
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Host-side handle
 // ---------------------------------------------------------------------------
 struct KernelTimer {

@@ -49,32 +49,21 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_partials(GridP g, const 
                                                                  const uint8_t* __restrict__ mask,
                                                                  double* __restrict__ part) {
     __shared__ double sh[NA_VALS][NA_THREADS / 32];
-    double a[NA_VALS];
-    for (int q = 0; q < NA_VALS; ++q) a[q] = 0.0;
+    DiagAcc<T> acc;
+    const DiagInv<T> inv(1.0 / g.dx, 1.0 / g.dy, 1.0 / g.dz);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const T* f[3] = {u, v, w};
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += stride) {
         const int i = (int)(id % g.nx);
         const long long row = id / g.nx;
         const int j = (int)(row % g.ny);
         const int k = (int)(row / g.ny);
-        double d = ((double)u[id] - (double)u[row * g.nx + wrapi(i - 1, g.nx)]) / g.dx;
-        d += ((double)v[id] - (j > 0 ? (double)v[id - g.nx] : 0.0)) / g.dy;
-        if (g.ndim == 3)
-            d += ((double)w[id] - (double)w[i + (long long)g.nx * (j + (long long)g.ny * wrapi(k - 1, g.nz))]) / g.dz;
-        a[0] += d * d;
-        a[1] = fmax(a[1], fabs(d));
-        const uint8_t m = mask[id];
-        for (int c = 0; c < g.ncomp; ++c) {
-            const double x = (double)f[c][id];
-            if (!isfinite(x)) a[11] += 1.0;
-            if (!((m >> c) & 1u)) continue;
-            a[2 + c] = fmax(a[2 + c], fabs(x));
-            a[5 + c] += x;
-            a[8 + c] += x * x;
-        }
-        if (!isfinite((double)p[id])) a[11] += 1.0;
+        const T wc = g.ndim == 3 ? w[id] : T(0);
+        const T wm = g.ndim == 3 ? w[i + (long long)g.nx * (j + (long long)g.ny * wrapi(k - 1, g.nz))] : T(0);
+        acc.cell(g.ncomp, inv.v, u[id], u[row * g.nx + wrapi(i - 1, g.nx)], v[id], j > 0 ? v[id - g.nx] : T(0),
+                 wc, wm, p[id], mask[id]);
     }
+    double a[NA_VALS];
+    acc.finish(a);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int q = 0; q < NA_VALS; ++q) {
         const bool mx = (q == 1 || (q >= 2 && q <= 4));

@@ -550,61 +550,94 @@ __global__ void k_mask_copy(GridP g, const uint8_t* __restrict__ mask, const T* 
 template <typename T>
 __global__ void __launch_bounds__(256) k_diag(GridP g, const T* __restrict__ u, const T* __restrict__ v,
                                               const T* __restrict__ w, const T* __restrict__ p,
-                                              const uint8_t* __restrict__ mask, double* __restrict__ part) {
+                                              const uint8_t* __restrict__ mask, double* __restrict__ part, double idx,
+                                              double idy, double idz) {
+    // A block (32 x 8 threads) takes work tiles of 32 x 8 (x, y) points and up to
+    // DIAG_Z planes; a thread marches its point's column, carrying w(k-1), and
+    // takes u(i-1) from the neighbouring lane.
+    constexpr int DIAG_Z = 8;
     __shared__ double sh[12][8];
-    double a[12];
-    for (int q = 0; q < 12; ++q) a[q] = 0.0;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    const T* f[3] = {u, v, w};
-    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += stride) {
-        int i = (int)(id % g.nx);
-        long long row = id / g.nx;
-        int j = (int)(row % g.ny);
-        int k = (int)(row / g.ny);
-        double d = ((double)u[id] - (double)u[row * g.nx + wrapi(i - 1, g.nx)]) / g.dx;
-        d += ((double)v[id] - (j > 0 ? (double)v[id - g.nx] : 0.0)) / g.dy;
-        if (g.ndim == 3)
-            d += ((double)w[id] - (double)w[i + (long long)g.nx * (j + (long long)g.ny * wrapi(k - 1, g.nz))]) / g.dz;
-        a[0] += d * d;
-        a[1] = fmax(a[1], fabs(d));
-        uint8_t m = mask[id];
-        for (int c = 0; c < g.ncomp; ++c) {
-            double x = (double)f[c][id];
-            if (!isfinite(x)) a[11] += 1.0;
-            if (!((m >> c) & 1u)) continue;
-            a[2 + c] = fmax(a[2 + c], fabs(x));
-            a[5 + c] += x;
-            a[8 + c] += x * x;
+    DiagAcc<T> acc;
+    const DiagInv<T> inv(idx, idy, idz);
+    const int lane = threadIdx.x, wy = threadIdx.y;
+    const int nty = (g.ny + 7) / 8, nzc = (g.nz + DIAG_Z - 1) / DIAG_Z;
+    const long long ntiles = (long long)g.nsegx * nty * nzc;
+    const int plane = g.nx * g.ny;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tx = (int)(t % g.nsegx);
+        const long long r = t / g.nsegx;
+        const int ty = (int)(r % nty);
+        const int kc = (int)(r / nty);
+        const int i = tx * 32 + lane, j = ty * 8 + wy;
+        if (j >= g.ny) continue;                              // whole warp
+        const bool live = i < g.nx;
+        const int il = wrapi(tx * 32 - 1, g.nx);              // left neighbour of lane 0
+        const int kbeg = kc * DIAG_Z, kend = min(kbeg + DIAG_Z, g.nz);
+        T wm = T(0);
+        if (g.ndim == 3 && live) wm = w[i + g.nx * j + plane * wrapi(kbeg - 1, g.nz)];
+        for (int k0 = kbeg; k0 < kend; k0 += DZ) {
+            // the loads of DZ planes go out before any is used
+            T uc[DZ], ul0[DZ], vc[DZ], vm[DZ], wc[DZ], pc[DZ];
+            uint8_t mc[DZ];
+#pragma unroll
+            for (int t = 0; t < DZ; ++t) {
+                uc[t] = ul0[t] = vc[t] = vm[t] = wc[t] = pc[t] = T(0);
+                mc[t] = 0;
+                const int k = k0 + t;
+                if (k < kend) {
+                    const int rowb = g.nx * (j + g.ny * k);
+                    const int id = rowb + i;
+                    if (lane == 0) ul0[t] = u[rowb + il];
+                    if (live) {
+                        uc[t] = u[id];
+                        vc[t] = v[id];
+                        if (j > 0) vm[t] = v[id - g.nx];
+                        if (g.ndim == 3) wc[t] = w[id];
+                        pc[t] = p[id];
+                        mc[t] = mask[id];
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < DZ; ++t) {
+                if (k0 + t >= kend) break;
+                T ul = __shfl_up_sync(0xffffffffu, uc[t], 1);
+                if (lane == 0) ul = ul0[t];
+                if (live) acc.cell(g.ncomp, inv.v, uc[t], ul, vc[t], vm[t], wc[t], wm, pc[t], mc[t]);
+                wm = wc[t];
+            }
         }
-        if (!isfinite((double)p[id])) a[11] += 1.0;
     }
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double a[12];
+    acc.finish(a);
     for (int q = 0; q < 12; ++q) {
         double x = a[q];
         if (q == 1 || (q >= 2 && q <= 4)) x = warp_max(x);
         else x = warp_sum(x);
-        if (lane == 0) sh[q][wid] = x;
+        if (lane == 0) sh[q][wy] = x;
     }
     __syncthreads();
-    if (threadIdx.x < 12) {
-        int q = threadIdx.x;
+    const int tid = lane + 32 * wy;
+    if (tid < 12) {
+        int q = tid;
         double s = 0.0;
-        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww)
+        for (int ww = 0; ww < 8; ++ww)
             s = (q == 1 || (q >= 2 && q <= 4)) ? fmax(s, sh[q][ww]) : s + sh[q][ww];
         part[blockIdx.x * 12 + q] = s;
     }
 }
 
+// one warp per quantity, fixed order: lane-strided partial sums, then a shuffle tree
 __global__ void k_diag_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
-    int q = threadIdx.x;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= 12) return;
+    const bool mx = q == 1 || (q >= 2 && q <= 4);
     double s = 0.0;
-    for (int b = 0; b < nb; ++b)
-        s = (q == 1 || (q >= 2 && q <= 4)) ? fmax(s, part[b * 12 + q]) : s + part[b * 12 + q];
-    out[q] = s;
+    for (int b = lane; b < nb; b += 32) s = mx ? fmax(s, part[b * 12 + q]) : s + part[b * 12 + q];
+    s = mx ? warp_max(s) : warp_sum(s);
+    if (lane == 0) out[q] = s;
 }
 
-constexpr int DIAG_BLOCKS = 304;
 
 // 32 x 8 cells per block, one z plane per blockIdx.z
 dim3 cell_grid(const GridP& g) { return dim3(g.nsegx, (g.ny + 7) / 8, g.nz); }
@@ -757,10 +790,11 @@ template <typename T>
 ibm_status diag_t(ibm_solver* h, double* out) {
     const GridP& g = h->gp;
     const T* w = g.ndim == 3 ? (const T*)h->buf.u[2] : (const T*)h->buf.u[0];
-    k_diag<T><<<DIAG_BLOCKS, 256, 0, h->stream>>>(g, (const T*)h->buf.u[0], (const T*)h->buf.u[1], w,
-                                                  (const T*)h->buf.p, h->mask, h->partials);
+    k_diag<T><<<DIAG_BLOCKS, dim3(32, 8), 0, h->stream>>>(g, (const T*)h->buf.u[0], (const T*)h->buf.u[1], w,
+                                                          (const T*)h->buf.p, h->mask, h->partials, 1.0 / g.dx,
+                                                          1.0 / g.dy, 1.0 / g.dz);
     IBM_LAUNCH_CHECK();
-    k_diag_final<<<1, 32, 0, h->stream>>>(h->partials, DIAG_BLOCKS, h->scal + 4);
+    k_diag_final<<<1, 12 * 32, 0, h->stream>>>(h->partials, DIAG_BLOCKS, h->scal + 4);
     IBM_LAUNCH_CHECK();
     IBM_CUDA_TRY(cudaMemcpyAsync(out, h->scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
