@@ -50,9 +50,9 @@ TRIDIAG_BYTES_PER_SPECTRAL_POINT = 64.0
 # keyed by kernel, with the hash of the source file it was taken on; a changed
 # source makes the figure stale and it is reported as null.
 NCU_TRAFFIC = {
-    # profiles/c3s_wavy_384x256x64_hot_kernels_ncu.md: stage-1 launch on 384x256x64 read 118.5 MB and
-    # wrote 104.6 MB; scaled by cells (x4) to a 384x256x256 launch
-    "momentum": (4.0 * (118.507520e6 + 104.616704e6), "47e5f5aabf29c24a"),
+    # profiles/c3_wavy_384x256x256_momentum_tma_ncu.md: the three stages of one step on the
+    # 384x256x256 grid read+wrote 1025.2, 1325.6 and 1041.6 MB; their mean per launch
+    "momentum": ((1025.195264e6 + 1325.607680e6 + 1041.563136e6) / 3.0, "9d17244a60fed4d0"),
 }
 
 
