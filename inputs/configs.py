@@ -44,6 +44,7 @@ class Case:
     flow_mode: int = FLOW_FORCED
     target_flux: float = 0.0   # volume integral of u over the fluid (FLOW_CONST_FLUX)
     wall_u: tuple = (0.0, 0.0, 0.0)
+    inflow: tuple = (0.0, 0.0, 0.0)   # velocity entering through the -x face (x inflow / outflow boxes)
     precision: str = "fp64"    # "fp64" or "fp32" (FP32 momentum, FP64 tridiagonal/reductions)
     steps: int = 1
     init: dict = field(default_factory=lambda: {"kind": "zero"})
@@ -81,6 +82,24 @@ def couette_case(nx: int = 16, ny: int = 24, a: float = 0.113, b: float = 0.871,
                 bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), geom_kind=GEOM_PLANES,
                 geom_params=(a, b), nu=nu, dt=0.2 * (1.0 / ny) ** 2 / nu,
                 wall_u=(U, 0.0, 0.0), init={"kind": "couette", "a": a, "b": b, "U": U})
+
+
+def cylinder_c2_io(re: float = 40.0, precision: str = "fp64", steps: int = 10, seed: int = 0,
+                   n=(1536, 768)) -> Case:
+    """2D cylinder D=1 at a seeded sub-cell offset from (0, 0) in the box
+    x in [-10, 20], y in [-7.5, 7.5]: uniform inflow U = 1 at x = -10, convective
+    outflow at x = 20, free-slip lateral walls; Re = U D / nu."""
+    from .generators import cell_offset
+    nx, ny = n
+    Lx, Ly = 30.0, 15.0
+    dx = Lx / nx
+    ox, oy = cell_offset(seed, dx)
+    return Case(name=f"c2_cylinder_io_{nx}x{ny}_re{int(re)}", ndim=2, n=(nx, ny, 1), L=(Lx, Ly, 1.0),
+                origin=(-10.0, -7.5, 0.0), bc_lo=(BC_INFLOW, BC_FREESLIP, BC_PERIODIC),
+                bc_hi=(BC_OUTFLOW, BC_FREESLIP, BC_PERIODIC), geom_kind=GEOM_CYLINDER,
+                geom_params=(ox, oy, 0.5, -1.0), nu=1.0 / re, dt=0.004 if re <= 40 else 0.008,
+                inflow=(1.0, 0.0, 0.0), precision=precision, steps=steps, init={"kind": "uniform", "U": 1.0},
+                seed=seed)
 
 
 def cylinder_c2(re: float = 40.0, precision: str = "fp64", steps: int = 10, seed: int = 0,
@@ -149,6 +168,17 @@ def small_case(kind: str, precision: str = "fp64", seed: int = 0) -> Case:
     if kind == "wavy3d":
         c = wavy_c3(precision=precision, steps=2, n=(70, 36, 20), seed=seed)
         return c.with_(name="wavy3d_70x36x20", dt=0.002)
+    if kind == "cylinder2d_io":
+        c = cylinder_c2_io(re=100.0, precision=precision, steps=2, seed=seed, n=(96, 50))
+        return c.with_(name="cylinder2d_io_96x50", dt=0.01,
+                       init={"kind": "uniform_noise", "U": 1.0, "noise": 0.1})
+    if kind == "sphere3d_io":
+        return Case(name="sphere3d_io_48x30x26", ndim=3, n=(48, 30, 26), L=(1.6, 1.0, 1.0),
+                    origin=(0.0, 0.0, 0.0), bc_lo=(BC_INFLOW, BC_NOSLIP, BC_PERIODIC),
+                    bc_hi=(BC_OUTFLOW, BC_FREESLIP, BC_PERIODIC), geom_kind=GEOM_SPHERE,
+                    geom_params=(0.61, 0.47, 0.52, 0.23, -1.0), nu=0.01, dt=0.004, inflow=(0.8, 0.0, 0.0),
+                    precision=precision, steps=2, seed=seed,
+                    init={"kind": "uniform_noise", "U": 0.8, "noise": 0.1})
     if kind == "sphere3d":
         return Case(name="sphere3d_48x30x26", ndim=3, n=(48, 30, 26), L=(1.6, 1.0, 1.0),
                     origin=(0.0, 0.0, 0.0), bc_lo=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC),

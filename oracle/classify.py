@@ -12,8 +12,15 @@
   (Sec. 2.2: the correction applies only to stencils that cross the boundary).
   Neighbours beyond a wall box face are box-boundary ghosts, not arms.
 
+* With an inflow/outflow x direction, the inflow face (x = x_0, not stored)
+  and the outflow face (u at i = n_x - 1, a boundary point) are fluid where
+  phi_u < 0 there: the inflow velocity enters, and the outflow value is read by
+  the stencils and advanced by the convective condition, only on fluid faces.
+
 Packed mask byte per cell (the format the C-ABI returns):
-  bit0..2  u, v, w internal;  bit3  p internal;  bit4..6  u, v, w IBM point.
+  bit0..2  u, v, w internal;  bit3  p internal;  bit4..6  u, v, w IBM point;
+  bit7  (inflow/outflow x only) at i = 0: the inflow face of the row is fluid,
+        at i = n_x - 1: the outflow face of the row is fluid.
 IBM-point lists are sorted by ascending linear index i + nx (j + ny k).
 """
 from __future__ import annotations
@@ -34,6 +41,8 @@ class Classification:
     phi: list               # per component: level-set samples (FP64)
     mask: np.ndarray        # packed uint8
     lists: list             # per component: int64 ascending linear indices of IBM points
+    inflow_fluid: np.ndarray = None    # (nz, ny, 1) bool: inflow face fluid (inflow/outflow x)
+    outflow_fluid: np.ndarray = None   # (nz, ny, 1) bool: outflow face fluid
 
 
 def _neighbour_external(ext: np.ndarray, grid, d: int, s: int) -> np.ndarray:
@@ -110,5 +119,14 @@ def classify(grid, levelset) -> Classification:
         mask |= (ibm[c].astype(np.uint8) << (4 + c))
     mask |= (p_int.astype(np.uint8) << 3)
 
+    inflow_fluid = outflow_fluid = None
+    if grid.xflow:
+        x, y, z = grid.coords(0)
+        x_in = np.full_like(x[..., :1], grid.origin[0])          # u point at i = -1: the inflow face
+        inflow_fluid = np.broadcast_to(levelset.phi(x_in, y, z) < 0.0, grid.shape[:2] + (1,)).copy()
+        outflow_fluid = (phis[0][..., -1:] < 0.0).copy()
+        mask[..., 0] |= (inflow_fluid[..., 0].astype(np.uint8) << 7)
+        mask[..., -1] |= (outflow_fluid[..., 0].astype(np.uint8) << 7)
+
     lists = [np.flatnonzero(ibm[c].ravel()) for c in range(3)]
-    return Classification(internal, external, boundary, p_int, ibm, phis, mask, lists)
+    return Classification(internal, external, boundary, p_int, ibm, phis, mask, lists, inflow_fluid, outflow_fluid)

@@ -8,15 +8,22 @@ sits on the cell's +c face, i.e. its coordinate along c is origin_c+(idx_c+1)d_c
 
 Box boundaries: a periodic direction wraps.  In a non-periodic direction d
 the +d box face carries the stored value of index n_d-1 of component d (a
-prescribed "boundary" point, never solved); the -d box face value is implied
-by the boundary condition (zero for the walls supported here).
+prescribed "boundary" point, never solved by the momentum equation); the -d
+box face value is implied by the boundary condition.
+  * y: walls, no-slip or free-slip; both wall faces carry zero normal velocity.
+  * x: either periodic, or an inflow at the -x face and a convective outflow at
+    the +x face.  The inflow face is not stored: its normal velocity is the
+    inflow velocity on fluid faces and zero on solid ones; tangential
+    velocities are zero there.  The outflow face value u(n_x-1) is advanced by
+    the convective condition (momentum.outflow_update); tangential velocities
+    have zero normal gradient there.
 """
 from __future__ import annotations
 
 import numpy as np
 
 AX = {0: 2, 1: 1, 2: 0}
-BC_PERIODIC, BC_NOSLIP, BC_FREESLIP = 0, 1, 2
+BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW, BC_OUTFLOW = 0, 1, 2, 3, 4
 
 
 class Grid:
@@ -33,9 +40,14 @@ class Grid:
         self.ncomp = 3 if self.ndim == 3 else 2
         if self.ndim == 2 and self.n[2] != 1:
             raise ValueError("2D grids have nz == 1")
-        for dd in (0, 2):
-            if self.bc_lo[dd] != BC_PERIODIC or self.bc_hi[dd] != BC_PERIODIC:
-                raise NotImplementedError("x and z must be periodic (y carries the walls)")
+        if self.bc_lo[2] != BC_PERIODIC or self.bc_hi[2] != BC_PERIODIC:
+            raise NotImplementedError("z must be periodic")
+        xbc = (self.bc_lo[0], self.bc_hi[0])
+        if xbc not in ((BC_PERIODIC, BC_PERIODIC), (BC_INFLOW, BC_OUTFLOW)):
+            raise NotImplementedError("x is periodic or has an inflow at -x and an outflow at +x")
+        if xbc[0] == BC_INFLOW and self.n[0] < 2:
+            raise ValueError("an inflow/outflow x direction needs nx >= 2")
+        self.inflow = tuple(float(v) for v in getattr(case, "inflow", (0.0, 0.0, 0.0)))
         if self.bc_lo[1] not in (BC_NOSLIP, BC_FREESLIP) or self.bc_hi[1] not in (BC_NOSLIP, BC_FREESLIP):
             raise NotImplementedError("y box faces must be no-slip or free-slip walls")
         if self.n[1] < 2:
@@ -80,3 +92,17 @@ class Grid:
         """Ghost factor for tangential velocity beyond a y wall: -1 no-slip, +1 free-slip."""
         bc = self.bc_lo[1] if side == "lo" else self.bc_hi[1]
         return -1.0 if bc == BC_NOSLIP else 1.0
+
+    def ghost_sign(self, d: int, side: str) -> float:
+        """Ghost factor for a tangential velocity beyond the d box face: the y walls as
+        above; -1 at an inflow face (tangential velocity zero on the face), +1 at an
+        outflow face (zero normal gradient)."""
+        if d == 1:
+            return self.wall_sign(side)
+        bc = self.bc_lo[d] if side == "lo" else self.bc_hi[d]
+        return -1.0 if bc == BC_INFLOW else 1.0
+
+    @property
+    def xflow(self) -> bool:
+        """x has an inflow (-x) and a convective outflow (+x) instead of wrapping."""
+        return self.bc_lo[0] == BC_INFLOW

@@ -13,6 +13,13 @@ Right-hand side at internal points (Eq. ns, Eq. semidisc-mom):
   * s_c is the wall-velocity source (zero for walls at rest).
 Box walls in y: tangential velocity ghosts mirror the adjacent value (sign -1
 no-slip, +1 free-slip); the wall-normal velocity on the wall face is zero.
+Inflow/outflow in x (readings; the paper states only that inflow and outflow
+faces exist, Sec. 4): the normal velocity at the inflow face is the inflow
+velocity on fluid faces and zero on solid ones, tangential ghosts are the
+negated adjacent value (zero tangential velocity on the face); at the outflow
+face the stored u(n_x-1) is read, tangential ghosts repeat the adjacent value.
+The outflow value follows the convective condition du/dt + U_c du/dx = 0
+(outflow_update), U_c the inflow flux over the fluid outflow area.
 
 Stage k (Eq. rk3-rai), with the pressure of the incremental projection
 (Sec. 2.1) carried with weight c_k (reading taken):
@@ -28,14 +35,31 @@ import numpy as np
 from .grid import AX
 
 
+def readable(grid, cls, c: int) -> np.ndarray:
+    """Points whose stored value the operators read: internal points, and the fluid
+    outflow face of u.  Everything else (external points, wall faces, solid outflow
+    faces) reads zero."""
+    r = cls.internal[c]
+    if c == 0 and grid.xflow:
+        r = r.copy()
+        r[..., -1] = cls.outflow_fluid[..., 0]
+    return r
+
+
 def masked(grid, cls, fields):
-    """Velocity with every non-internal point read as zero (external and wall faces)."""
-    return [np.where(cls.internal[c], fields[c], 0.0) if c < grid.ncomp else np.zeros(grid.shape)
+    """Velocity with every unreadable point read as zero (external and wall faces)."""
+    return [np.where(readable(grid, cls, c), fields[c], 0.0) if c < grid.ncomp else np.zeros(grid.shape)
             for c in range(3)]
 
 
-def nb(q, grid, c: int, d: int, s: int):
-    """Values of component-c field q at P + s e_d, with the box rules of y walls."""
+def inflow_face(grid, cls) -> np.ndarray:
+    """Normal velocity on the inflow face, shape (nz, ny, 1)."""
+    return np.where(cls.inflow_fluid, grid.inflow[0], 0.0)
+
+
+def nb(q, grid, c: int, d: int, s: int, lo_normal=None):
+    """Values of component-c field q at P + s e_d, with the box rules: y walls, and
+    for an inflow/outflow x the inflow face value lo_normal of the normal component."""
     if grid.periodic(d):
         return np.roll(q, -s, axis=AX[d])
     n = grid.n[d]
@@ -50,17 +74,20 @@ def nb(q, grid, c: int, d: int, s: int):
         dst[ax] = slice(0, n - 1)
         edge_dst[ax] = slice(n - 1, n)
         edge_src[ax] = slice(n - 1, n)
-        sign = grid.wall_sign("hi")
+        sign = grid.ghost_sign(d, "hi")
     else:
         src[ax] = slice(0, n - 1)
         dst[ax] = slice(1, n)
         edge_dst[ax] = slice(0, 1)
         edge_src[ax] = slice(0, 1)
-        sign = grid.wall_sign("lo")
+        sign = grid.ghost_sign(d, "lo")
     out[tuple(dst)] = q[tuple(src)]
     if c == d:
-        # wall-normal component: the value beyond is the wall face (zero)
+        # normal component: the value beyond is the face value (zero on walls and
+        # beyond the outflow face, where it is never read; the inflow value at -x)
         out[tuple(edge_dst)] = 0.0
+        if s < 0 and lo_normal is not None:
+            out[tuple(edge_dst)] = lo_normal
     else:
         out[tuple(edge_dst)] = sign * q[tuple(edge_src)]
     return out
@@ -71,10 +98,11 @@ def rhs(grid, cls, fields, nu: float, g, src):
     U, V, W = masked(grid, cls, fields)
     dx, dy, dz = grid.d
     three = grid.ndim == 3
+    uin = inflow_face(grid, cls) if grid.xflow else None
     out = []
 
     # ---- u ----
-    uE, uW = nb(U, grid, 0, 0, +1), nb(U, grid, 0, 0, -1)
+    uE, uW = nb(U, grid, 0, 0, +1), nb(U, grid, 0, 0, -1, uin)
     uN, uS = nb(U, grid, 0, 1, +1), nb(U, grid, 0, 1, -1)
     cx = (((U + uE) / 2) ** 2 - ((uW + U) / 2) ** 2) / dx
     vN = (V + nb(V, grid, 1, 0, +1)) / 2                       # v(i,j) + v(i+1,j)
@@ -94,7 +122,7 @@ def rhs(grid, cls, fields, nu: float, g, src):
     vE, vW = nb(V, grid, 1, 0, +1), nb(V, grid, 1, 0, -1)
     vNn, vSs = nb(V, grid, 1, 1, +1), nb(V, grid, 1, 1, -1)
     uEe = (U + nb(U, grid, 0, 1, +1)) / 2                      # u(i,j) + u(i,j+1)
-    uWe = (nb(U, grid, 0, 0, -1) + nb(nb(U, grid, 0, 0, -1), grid, 0, 1, +1)) / 2
+    uWe = (nb(U, grid, 0, 0, -1, uin) + nb(nb(U, grid, 0, 0, -1, uin), grid, 0, 1, +1)) / 2
     cx = (uEe * ((V + vE) / 2) - uWe * ((vW + V) / 2)) / dx
     cy = (((V + vNn) / 2) ** 2 - ((vSs + V) / 2) ** 2) / dy
     lap = (vE - 2 * V + vW) / dx ** 2 + (vNn - 2 * V + vSs) / dy ** 2
@@ -113,7 +141,7 @@ def rhs(grid, cls, fields, nu: float, g, src):
         wN, wS = nb(W, grid, 2, 1, +1), nb(W, grid, 2, 1, -1)
         wT, wB = nb(W, grid, 2, 2, +1), nb(W, grid, 2, 2, -1)
         uEe = (U + nb(U, grid, 0, 2, +1)) / 2                  # u(i,j,k) + u(i,j,k+1)
-        uWe = (nb(U, grid, 0, 0, -1) + nb(nb(U, grid, 0, 0, -1), grid, 0, 2, +1)) / 2
+        uWe = (nb(U, grid, 0, 0, -1, uin) + nb(nb(U, grid, 0, 0, -1, uin), grid, 0, 2, +1)) / 2
         cx = (uEe * ((W + wE) / 2) - uWe * ((wW + W) / 2)) / dx
         vNe = (V + nb(V, grid, 1, 2, +1)) / 2                  # v(i,j,k) + v(i,j,k+1)
         vSe = (nb(V, grid, 1, 1, -1) + nb(nb(V, grid, 1, 1, -1), grid, 1, 2, +1)) / 2
@@ -163,3 +191,37 @@ def stage_update(grid, cls, u_prev, N_cur, N_prev, gradp, lam, k: int, dt: float
         ustar = (B * u_prev[c] + R) / (B + x)
         out.append(np.where(cls.internal[c], ustar, 0.0))
     return out
+
+
+# ---- convective outflow (inflow/outflow x) ------------------------------------------
+def outflow_speed(grid, cls) -> float:
+    """U_c: the inflow flux divided by the fluid outflow area (reading: the mean speed
+    through the outflow face, fixed by the geometry)."""
+    n_in = int(np.count_nonzero(cls.inflow_fluid))
+    n_out = int(np.count_nonzero(cls.outflow_fluid))
+    return grid.inflow[0] * n_in / n_out if n_out else 0.0
+
+
+def outflow_update(grid, cls, u_prev, N_prev_b, k: int, dt: float, a, b):
+    """RK3 stage k of du/dt = -U_c (u_b - u_{b-1}) / dx on the fluid outflow faces
+    (u_b = u(n_x-1), u_{b-1} = u(n_x-2) read as the operators read it); the same
+    low-storage combination as the momentum stage, with no pressure and no IBM term.
+    Returns u*_b and N_b, each of shape (nz, ny, 1); zero on solid outflow faces."""
+    Uc = outflow_speed(grid, cls)
+    ub = u_prev[0][..., -1:]
+    um = np.where(cls.internal[0][..., -2:-1], u_prev[0][..., -2:-1], 0.0)
+    Nb = -Uc * (ub - um) / grid.d[0]
+    R = dt * a[k] * Nb + dt * b[k] * N_prev_b
+    return np.where(cls.outflow_fluid, ub + R, 0.0), np.where(cls.outflow_fluid, Nb, 0.0)
+
+
+def outflow_balance(grid, cls, ub):
+    """Shift the fluid outflow face velocities by one constant so that the outflow flux
+    equals the inflow flux (reading; the Poisson problem with prescribed normal velocity
+    on every box face is solvable only then)."""
+    n_in = int(np.count_nonzero(cls.inflow_fluid))
+    n_out = int(np.count_nonzero(cls.outflow_fluid))
+    if n_out == 0:
+        return ub
+    shift = (grid.inflow[0] * n_in - np.sum(np.where(cls.outflow_fluid, ub, 0.0))) / n_out
+    return np.where(cls.outflow_fluid, ub + shift, 0.0)

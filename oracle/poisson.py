@@ -8,7 +8,10 @@ solved everywhere "as though there was no boundary".  Reading taken (the
 box, with the box boundary conditions only:
   * periodic directions wrap;
   * wall directions: the wall-normal velocity is prescribed, so G phi is not
-    applied on wall faces (homogeneous Neumann for phi).
+    applied on wall faces (homogeneous Neumann for phi);
+  * an inflow/outflow x direction likewise: the inflow velocity and the
+    (balanced) outflow velocity are prescribed, G phi is not applied on the
+    outflow face, and phi is homogeneous Neumann in x.
 The correction u = u* - c_k Delta t G phi is applied on every non-wall face
 and p += phi in every cell.  The operator is singular (constants); the gauge
 is: mean of phi over the box = 0.
@@ -19,8 +22,11 @@ Two solvers, which must agree:
   * solve_spectral: FFT (numpy, a library primitive) in the periodic
     directions x and z and a Thomas solve along y for every wavenumber pair,
     with the modified wavenumbers 4 sin^2(pi k/n)/Delta^2 of the 3-point
-    second difference.  The (0,0) mode fixes phi_0 = 0, solves the rest and
-    then removes the mean over y.
+    second difference.  A Neumann x direction takes the type-II discrete
+    cosine transform instead (scipy, a library primitive), whose cosines
+    cos(pi k (2i+1) / 2n) diagonalise the cell-centred Neumann second
+    difference with eigenvalues 4 sin^2(pi k / 2n)/Delta^2.  The (0,0) mode
+    fixes phi_0 = 0, solves the rest and then removes the mean over y.
 """
 from __future__ import annotations
 
@@ -31,8 +37,9 @@ import scipy.sparse.linalg as spla
 from .grid import AX
 
 
-def divergence(grid, vel):
-    """(D u) at every cell: sum_d (u_d(idx) - u_d(idx - e_d)) / Delta_d; the -y wall face is 0."""
+def divergence(grid, vel, inflow_face=None):
+    """(D u) at every cell: sum_d (u_d(idx) - u_d(idx - e_d)) / Delta_d; the -y wall face
+    is 0, the -x face of an inflow/outflow box carries inflow_face (nz, ny, 1)."""
     out = np.zeros(grid.shape)
     for d in range(grid.ncomp):
         q = vel[d]
@@ -40,6 +47,8 @@ def divergence(grid, vel):
             qm = np.roll(q, 1, axis=AX[d])
         else:
             qm = np.zeros_like(q)
+            if d == 0 and inflow_face is not None:
+                qm[..., :1] = inflow_face
             n = grid.n[d]
             a = [slice(None)] * 3
             b = [slice(None)] * 3
@@ -103,11 +112,21 @@ def modified_wavenumbers(n: int, Delta: float) -> np.ndarray:
     return 4.0 * np.sin(np.pi * k / n) ** 2 / Delta ** 2
 
 
+def neumann_wavenumbers(n: int, Delta: float) -> np.ndarray:
+    k = np.arange(n)
+    return 4.0 * np.sin(np.pi * k / (2 * n)) ** 2 / Delta ** 2
+
+
 def solve_spectral(grid, rhs):
     nx, ny, nz = grid.n
     dy = grid.d[1]
-    rh = np.fft.fft2(rhs, axes=(0, 2))                 # (kz, y, kx)
-    K = modified_wavenumbers(nx, grid.d[0])[None, :]
+    if not grid.periodic(0):
+        import scipy.fft as sf
+        rh = np.fft.fft(sf.dct(rhs, type=2, axis=2), axis=0)      # (kz, y, kx)
+        K = neumann_wavenumbers(nx, grid.d[0])[None, :]
+    else:
+        rh = np.fft.fft2(rhs, axes=(0, 2))                 # (kz, y, kx)
+        K = modified_wavenumbers(nx, grid.d[0])[None, :]
     if grid.ndim == 3:
         K = K + modified_wavenumbers(nz, grid.d[2])[:, None]
     else:
@@ -139,6 +158,9 @@ def solve_spectral(grid, rhs):
         x -= x.mean()
         sol[:, kz, kx] = x
     ph = np.moveaxis(sol, 0, 1)
+    if not grid.periodic(0):
+        import scipy.fft as sf
+        return sf.idct(np.real(np.fft.ifft(ph, axis=0)), type=2, axis=2)
     return np.real(np.fft.ifft2(ph, axes=(0, 2)))
 
 

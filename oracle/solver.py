@@ -23,7 +23,8 @@ from .grid import Grid
 from .geometry import LevelSet
 from .classify import classify
 from .weights import build_weights, B_of_x, RK3_A, RK3_B, RK3_C
-from .momentum import rhs, stage_update, pressure_gradient, masked
+from .momentum import (rhs, stage_update, pressure_gradient, masked, inflow_face, outflow_update,
+                       outflow_balance)
 from .poisson import divergence, gradient, solve_spectral, solve_direct
 
 FLOW_FORCED, FLOW_CONST_FLUX = 0, 1
@@ -42,6 +43,8 @@ class OracleSolver:
         self.flow_mode = int(case.flow_mode)
         self.target_flux = float(case.target_flux)
         self.w = build_weights(self.grid, self.levelset, self.cls, self.nu, case.wall_u, no_ibm=no_ibm)
+        if self.grid.xflow and self.flow_mode == FLOW_CONST_FLUX:
+            raise ValueError("a constant flow rate needs a periodic x direction")
         self.poisson = solve_spectral if poisson == "spectral" else solve_direct
         z = np.zeros(self.grid.shape)
         self.u = [z.copy(), z.copy(), z.copy()]
@@ -67,6 +70,12 @@ class OracleSolver:
         um = masked(g, cls, self.u)
         ustar = stage_update(g, cls, um, N, self.Nprev, gp, self.w.lam, k, self.dt,
                              self.bmode, RK3_A, RK3_B, RK3_C, B_of_x)
+        if g.xflow:
+            # the outflow face: convective condition, then the flux balance
+            ub, Nb = outflow_update(g, cls, self.u, self.Nprev[0][..., -1:], k, self.dt, RK3_A, RK3_B)
+            ustar[0][..., -1:] = outflow_balance(g, cls, ub)
+            N[0] = N[0].copy()
+            N[0][..., -1:] = Nb
         self.Nprev = N
         if self.flow_mode == FLOW_CONST_FLUX:
             ckdt = RK3_C[k] * self.dt
@@ -85,7 +94,7 @@ class OracleSolver:
 
     def _project(self, ustar, ckdt: float, update_p: bool):
         g = self.grid
-        r = divergence(g, ustar) / ckdt
+        r = divergence(g, ustar, inflow_face(g, self.cls) if g.xflow else None) / ckdt
         phi = self.poisson(g, r)
         G = gradient(g, phi)
         self.u = [ustar[c] - ckdt * G[c] for c in range(3)]
@@ -101,13 +110,17 @@ class OracleSolver:
             self.step_count += 1
 
     def project(self):
-        """Initial-condition projection: zero the non-internal velocities, then project (p unchanged)."""
+        """Initial-condition projection: zero the unreadable velocities, balance the outflow
+        (inflow/outflow x), then project (p unchanged)."""
         um = masked(self.grid, self.cls, self.u)
+        if self.grid.xflow:
+            um[0] = um[0].copy()
+            um[0][..., -1:] = outflow_balance(self.grid, self.cls, um[0][..., -1:])
         self._project(um, 1.0, update_p=False)
 
     def diagnostics(self) -> dict:
         g, cls = self.grid, self.cls
-        div = divergence(g, self.u)
+        div = divergence(g, self.u, inflow_face(g, cls) if g.xflow else None)
         dV = g.cell_volume()
         out = {"div_l2": float(np.sqrt(np.mean(div ** 2))), "div_linf": float(np.max(np.abs(div)))}
         cfl = 0.0

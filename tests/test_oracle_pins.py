@@ -453,3 +453,72 @@ def test_temporal_order_exact_B_vs_euler():
         e = [abs(_startup_flux(dt, mode, T=T) - ref) for dt in dts]
         p = math.log2(e[1] / e[2])
         assert lo < p < hi, (mode, p)
+
+
+# ---- inflow / convective outflow in x, Neumann (DCT) Poisson direction --------------------
+
+@pytest.mark.parametrize("name", ["cylinder2d_io", "sphere3d_io"])
+def test_neumann_x_spectral_poisson_equals_direct_solve(name):
+    """The DCT-II + FFT + Thomas solve equals the sparse direct solve of the same D G with
+    homogeneous Neumann x and y faces (a different route to the same definition)."""
+    from oracle import solve_direct
+    from oracle.grid import Grid
+    case = small_case(name)
+    g = Grid(case)
+    r = np.random.default_rng(5).standard_normal(g.shape)
+    r -= r.mean()
+    a = solve_spectral(g, r)
+    b = solve_direct(g, r)
+    assert np.abs(a - b).max() < 1e-11 * np.abs(b).max()
+
+
+def test_uniform_stream_is_a_fixed_point_of_an_inflow_outflow_channel():
+    """No body, free-slip walls, inflow U: u = U, v = p = 0 is an exact solution (its convection
+    and diffusion vanish, the outflow condition sees no gradient, the flux balances), so two
+    full steps leave it unchanged to round-off.  A wrong inflow face value, outflow speed or
+    balance breaks this."""
+    from inputs import GEOM_NONE
+    case = small_case("cylinder2d_io").with_(geom_kind=GEOM_NONE, geom_params=(), inflow=(1.3, 0.0, 0.0))
+    o = OracleSolver(case)
+    shape = o.grid.shape
+    o.set_state(np.full(shape, 1.3), np.zeros(shape), np.zeros(shape), np.zeros(shape))
+    o.step(2)
+    assert np.abs(o.u[0] - 1.3).max() < 1e-13
+    assert np.abs(o.u[1]).max() < 1e-13
+    assert np.abs(o.p).max() < 1e-10
+
+
+@pytest.mark.parametrize("name", ["cylinder2d_io", "sphere3d_io"])
+def test_inflow_outflow_steps_are_solenoidal_and_balanced(name):
+    """After the projection the discrete divergence (with the inflow face) is round-off at
+    every cell, and the fluid outflow flux equals the inflow flux."""
+    from oracle.momentum import inflow_face
+    from oracle.poisson import divergence
+    case = small_case(name)
+    o = OracleSolver(case)
+    f = initial_field(case)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    o.project()
+    o.step(2)
+    d = divergence(o.grid, o.u, inflow_face(o.grid, o.cls))
+    umax = max(np.abs(o.u[c]).max() for c in range(o.grid.ncomp))
+    assert np.abs(d).max() < 1e-12 * umax / min(o.grid.d[:o.grid.ndim])
+    q_in = case.inflow[0] * np.count_nonzero(o.cls.inflow_fluid)
+    q_out = np.sum(o.u[0][..., -1][o.cls.outflow_fluid[..., 0]])
+    assert abs(q_out - q_in) < 1e-12 * q_in
+
+
+def test_inflow_outflow_cylinder_stays_mirror_symmetric():
+    """A cylinder centred on the channel axis with a uniform inflow and a mirror-symmetric
+    start stays mirror-symmetric in y: u even, v odd (sign and index errors across the
+    lateral walls or in the body's weights break it)."""
+    case = small_case("cylinder2d_io").with_(geom_params=(0.0, 0.0, 0.5, -1.0), init={"kind": "uniform", "U": 1.0})
+    o = OracleSolver(case)
+    f = initial_field(case)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    o.project()
+    o.step(3)
+    u, v = o.u[0][0], o.u[1][0]
+    # y mirror: u(j) <-> u(ny-1-j); v sits on +y faces, so v(j) <-> -v(ny-2-j), v(ny-1) is the wall face
+    assert np.abs(u - u[::-1, :]).max() < 1e-12 * np.abs(u).max()
+    assert np.abs(v[:-1] + v[:-1][::-1, :]).max() < 1e-12 * np.abs(u).max()
