@@ -17,8 +17,14 @@
  *     Cell (i,j,k) has its centre at origin + ((i+1/2)dx, (j+1/2)dy, (k+1/2)dz),
  *     dx = L[0]/n[0] etc.; u(i,j,k) sits on the cell's +x face, v on its +y
  *     face, w on its +z face.  In 2D, nz = 1 and w is absent.
- *   - x and z must be periodic; y is bounded by box walls (no-slip or
- *     free-slip).  v(i, ny-1, k) lies on the +y wall and is held at zero.
+ *   - z must be periodic; y is bounded by box walls (no-slip or free-slip),
+ *     and v(i, ny-1, k) lies on the +y wall and is held at zero.  x is either
+ *     periodic, or has an inflow at -x (bc_lo[0] = IBM_BC_INFLOW, velocity
+ *     inflow[0] on the fluid part of the face, zero tangential velocity) and a
+ *     convective outflow at +x (bc_hi[0] = IBM_BC_OUTFLOW): u(nx-1, j, k) lies
+ *     on the outflow face and follows du/dt + U_c du/dx = 0, U_c the inflow
+ *     flux over the fluid outflow area, shifted each substage so that outflow
+ *     and inflow fluxes balance; the Poisson problem is then Neumann in x.
  *     Other combinations return IBM_E_UNSUPPORTED.
  *   - Memory: the caller allocates every device buffer (fields, workspace,
  *     weights) and keeps it alive until ibm_destroy.  The library never
@@ -82,7 +88,10 @@ enum {
 };
 /* packed mask bits returned by ibm_get_classification */
 enum { IBM_MASK_U = 1, IBM_MASK_V = 2, IBM_MASK_W = 4, IBM_MASK_P = 8,
-       IBM_MASK_IBM_U = 16, IBM_MASK_IBM_V = 32, IBM_MASK_IBM_W = 64 };
+       IBM_MASK_IBM_U = 16, IBM_MASK_IBM_V = 32, IBM_MASK_IBM_W = 64,
+       /* x inflow/outflow only: at i = 0 the inflow face of the row is fluid, at
+        * i = nx-1 the outflow face (u there) is fluid */
+       IBM_MASK_FACE = 128 };
 
 typedef struct {
     int ndim;           /* 2 or 3 */
@@ -92,6 +101,8 @@ typedef struct {
     int bc_lo[3];       /* IBM_BC_* per direction, low face */
     int bc_hi[3];       /* IBM_BC_* per direction, high face */
     int precision;      /* IBM_FP64 or IBM_FP32 */
+    double inflow[3];   /* x = IBM_BC_INFLOW / IBM_BC_OUTFLOW: velocity through the inflow face
+                         * (inflow[0] used; uniform on the fluid part of the face) */
 } ibm_grid_desc;
 
 typedef struct {
@@ -258,7 +269,7 @@ ibm_status ibm_launch_count(const ibm_solver* h, long long* count);
  *     library's own device memory (196,736 bytes, present on every GPU that
  *     loads the library until the process exits); nothing is allocated.
  *   - Limit: grids of at most 134,217,728 cells; larger ones return
- *     IBM_E_INVALID with a message.  x and z must be periodic.
+ *     IBM_E_INVALID with a message.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture on the device.

@@ -35,7 +35,8 @@ EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_g
 
 class ibm_grid_desc(C.Structure):
     _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3), ("origin", C.c_double * 3),
-                ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3), ("precision", C.c_int)]
+                ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3), ("precision", C.c_int),
+                ("inflow", C.c_double * 3)]
 
 
 class ibm_geom_desc(C.Structure):

@@ -2,6 +2,7 @@
 // carve-out, cuFFT plans, stream capture, event timing and state export.
 #include "common.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -33,9 +34,14 @@ ibm_status check_grid(const ibm_grid_desc* d) {
     long long N = (long long)d->n[0] * d->n[1] * d->n[2];
     if (N >= (1ll << 31)) return ibm_set_error(IBM_E_INVALID, "more than 2^31-1 cells");
     if (d->precision != IBM_FP64 && d->precision != IBM_FP32) return ibm_set_error(IBM_E_INVALID, "bad precision");
-    for (int dd : {0, 2})
-        if (d->bc_lo[dd] != IBM_BC_PERIODIC || d->bc_hi[dd] != IBM_BC_PERIODIC)
-            return ibm_set_error(IBM_E_UNSUPPORTED, "x and z must be periodic in this build");
+    if (d->bc_lo[2] != IBM_BC_PERIODIC || d->bc_hi[2] != IBM_BC_PERIODIC)
+        return ibm_set_error(IBM_E_UNSUPPORTED, "z must be periodic in this build");
+    const bool xper = d->bc_lo[0] == IBM_BC_PERIODIC && d->bc_hi[0] == IBM_BC_PERIODIC;
+    const bool xflow = d->bc_lo[0] == IBM_BC_INFLOW && d->bc_hi[0] == IBM_BC_OUTFLOW;
+    if (!xper && !xflow)
+        return ibm_set_error(IBM_E_UNSUPPORTED, "x must be periodic, or an inflow at -x with an outflow at +x");
+    if (xflow && (d->n[0] < 2 || !std::isfinite(d->inflow[0])))
+        return ibm_set_error(IBM_E_INVALID, "an inflow/outflow x needs nx >= 2 and a finite inflow velocity");
     for (int b : {d->bc_lo[1], d->bc_hi[1]})
         if (b != IBM_BC_NOSLIP && b != IBM_BC_FREESLIP)
             return ibm_set_error(IBM_E_UNSUPPORTED, "y faces must be no-slip or free-slip walls in this build");
@@ -50,7 +56,12 @@ GridP make_gridp(const ibm_grid_desc* d) {
     g.ndim = d->ndim;
     g.ncomp = d->ndim == 3 ? 3 : 2;
     g.nsegx = (g.nx + IBM_WARP - 1) / IBM_WARP;
-    g.nxh = g.nx / 2 + 1;
+    g.xper = d->bc_lo[0] != IBM_BC_INFLOW;
+    // spectrum extents: periodic x: half complex in x, full in z; Neumann x: all DCT modes
+    // in x, half complex in z (3D)
+    g.nxh = g.xper ? g.nx / 2 + 1 : g.nx;
+    g.nzs = g.xper ? g.nz : (g.nz > 1 ? g.nz / 2 + 1 : 1);
+    g.uin = g.xper ? 0.0 : d->inflow[0];
     g.N = (long long)g.nx * g.ny * g.nz;
     g.dx = d->L[0] / d->n[0];
     g.dy = d->L[1] / d->n[1];
@@ -71,37 +82,62 @@ int momentum_blocks(const GridP& g) {
     return (int)(d.x * d.y * d.z);
 }
 
-// Creates forward/inverse plans with auto-allocation off; returns the larger work size.
-ibm_status make_plans(const GridP& g, int prec, cufftHandle* pf, cufftHandle* pi, size_t* work) {
+// Creates the transform plans with auto-allocation off; returns the largest work size.
+// Periodic x: one 2D (z, x) R2C / C2R pair (1D in x for 2D grids), *pfz = *piz = 0.
+// Neumann x: an R2C / C2R pair along x (the FFT inside the DCT) and, in 3D, a strided
+// R2C / C2R pair along z over the real DCT coefficients.
+ibm_status make_plans(const GridP& g, int prec, cufftHandle* pf, cufftHandle* pi, cufftHandle* pfz,
+                      cufftHandle* piz, size_t* work) {
     cufftType tf = prec == IBM_FP64 ? CUFFT_D2Z : CUFFT_R2C;
     cufftType ti = prec == IBM_FP64 ? CUFFT_Z2D : CUFFT_C2R;
-    long long nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
-    size_t wf = 0, wi = 0;
+    long long nx = g.nx, ny = g.ny, nz = g.nz;
+    size_t wf = 0, wi = 0, wfz = 0, wiz = 0;
+    *pfz = *piz = 0;
     if (cufftCreate(pf) != CUFFT_SUCCESS || cufftCreate(pi) != CUFFT_SUCCESS)
         return ibm_set_error(IBM_E_CUDA, "cufftCreate failed");
     cufftSetAutoAllocation(*pf, 0);
     cufftSetAutoAllocation(*pi, 0);
-    cufftResult r1, r2;
-    if (g.nz > 1) {
+    cufftResult r1 = CUFFT_SUCCESS, r2 = CUFFT_SUCCESS, r3 = CUFFT_SUCCESS, r4 = CUFFT_SUCCESS;
+    if (g.xper && g.nz > 1) {
+        long long nxh = g.nxh;
         long long n[2] = {nz, nx};
         long long ie[2] = {nz, ny * nx};
         long long oe[2] = {nz, ny * nxh};
         r1 = cufftMakePlanMany64(*pf, 2, n, ie, 1, nx, oe, 1, nxh, tf, ny, &wf);
         r2 = cufftMakePlanMany64(*pi, 2, n, oe, 1, nxh, ie, 1, nx, ti, ny, &wi);
     } else {
+        long long nxr = nx / 2 + 1;   // half spectrum of a real row
         long long n[1] = {nx};
         long long ie[1] = {nx};
-        long long oe[1] = {nxh};
-        r1 = cufftMakePlanMany64(*pf, 1, n, ie, 1, nx, oe, 1, nxh, tf, ny * nz, &wf);
-        r2 = cufftMakePlanMany64(*pi, 1, n, oe, 1, nxh, ie, 1, nx, ti, ny * nz, &wi);
+        long long oe[1] = {nxr};
+        r1 = cufftMakePlanMany64(*pf, 1, n, ie, 1, nx, oe, 1, nxr, tf, ny * nz, &wf);
+        r2 = cufftMakePlanMany64(*pi, 1, n, oe, 1, nxr, ie, 1, nx, ti, ny * nz, &wi);
+        if (!g.xper && g.nz > 1) {
+            if (cufftCreate(pfz) != CUFFT_SUCCESS || cufftCreate(piz) != CUFFT_SUCCESS)
+                return ibm_set_error(IBM_E_CUDA, "cufftCreate failed");
+            cufftSetAutoAllocation(*pfz, 0);
+            cufftSetAutoAllocation(*piz, 0);
+            long long nzn[1] = {nz};
+            long long ize[1] = {nz};
+            long long oze[1] = {nz / 2 + 1};
+            r3 = cufftMakePlanMany64(*pfz, 1, nzn, ize, ny * nx, 1, oze, ny * nx, 1, tf, ny * nx, &wfz);
+            r4 = cufftMakePlanMany64(*piz, 1, nzn, oze, ny * nx, 1, ize, ny * nx, 1, ti, ny * nx, &wiz);
+        }
     }
-    if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS) {
+    if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS || r3 != CUFFT_SUCCESS || r4 != CUFFT_SUCCESS) {
         cufftDestroy(*pf);
         cufftDestroy(*pi);
-        return ibm_set_error(IBM_E_CUDA, "cufftMakePlanMany64 failed (code " + std::to_string((int)r1) + "/" +
-                                             std::to_string((int)r2) + ")");
+        if (*pfz) cufftDestroy(*pfz);
+        if (*piz) cufftDestroy(*piz);
+        *pfz = *piz = 0;
+        return ibm_set_error(IBM_E_CUDA, "cufftMakePlanMany64 failed (codes " + std::to_string((int)r1) + "/" +
+                                             std::to_string((int)r2) + "/" + std::to_string((int)r3) + "/" +
+                                             std::to_string((int)r4) + ")");
     }
-    *work = wf > wi ? wf : wi;
+    size_t w = wf > wi ? wf : wi;
+    w = w > wfz ? w : wfz;
+    w = w > wiz ? w : wiz;
+    *work = w;
     return IBM_OK;
 }
 
@@ -110,7 +146,9 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
     size_t off = 0;
     size_t esz = prec == IBM_FP64 ? 8 : 4;
     long long nseg = (long long)g.nsegx * g.ny * g.nz;
-    long long nspec = (long long)g.nz * g.ny * g.nxh;
+    long long nspec = (long long)g.nzs * g.ny * g.nxh;
+    // the spectrum buffer also holds the half spectra of the x rows inside the DCT (Neumann x)
+    long long nspec_buf = g.xper ? nspec : std::max(nspec, (long long)g.nz * g.ny * (g.nx / 2 + 1));
     int nscanb = (int)((nseg + SCAN_CH - 1) / SCAN_CH);
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -124,17 +162,19 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
     for (int c = 0; c < 3; ++c) segcnt[c] = take(nseg * sizeof(int));
     for (int c = 0; c < 3; ++c) segoff[c] = take(nseg * sizeof(int));
     char* scan_tmp = take(3 * (size_t)nscanb * sizeof(int));
-    char* counts = take(4 * sizeof(int));
+    char* counts = take(8 * sizeof(int));
     char* ustar[3] = {nullptr, nullptr, nullptr};
     char* Nh[3] = {nullptr, nullptr, nullptr};
     for (int c = 0; c < g.ncomp; ++c) ustar[c] = take(g.N * esz);
     for (int c = 0; c < g.ncomp; ++c) Nh[c] = take(g.N * esz);
     char* rhs = take(g.N * esz);
-    char* spec = take(nspec * 2 * esz);
+    char* spec = take(nspec_buf * 2 * esz);
     char* piv = take(nspec * sizeof(double));
     char* piv32 = take(nspec * sizeof(float));
-    char* use32 = take((size_t)g.nz * g.nxh);
-    char* order = take((size_t)g.nz * g.nxh * sizeof(int));
+    char* use32 = take((size_t)g.nzs * g.nxh);
+    char* order = take((size_t)g.nzs * g.nxh * sizeof(int));
+    char* rtmp = g.xper ? nullptr : take(g.N * esz);            // reordered rows of the DCT
+    char* twid = g.xper ? nullptr : take((size_t)g.nx * 2 * esz);   // cos, sin of pi k / 2nx
     char* dtemp = prec == IBM_FP32 ? take(nspec * 2 * sizeof(double)) : nullptr;
     char* fftw = take(fft_work);
     int npart = momentum_blocks(g);
@@ -160,6 +200,8 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
         h->use32 = (uint8_t*)use32;
         h->sys_order = (int*)order;
         h->dtemp = dtemp;
+        h->rtmp = rtmp;
+        h->twid = twid;
         h->fft_work = fftw;
         h->partials = (double*)partials;
         h->npartials = npart;
@@ -237,11 +279,12 @@ ibm_status ibm_workspace_bytes(const ibm_grid_desc* grid, size_t* bytes) {
     if (st != IBM_OK) return st;
     if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");
     GridP g = make_gridp(grid);
-    // cuFFT's work size depends only on the transform shape and precision; remember it
+    // cuFFT's work size depends only on the transform shapes (grid, periodic or Neumann x) and
+    // the precision; remember it
     // so that repeated queries (a server admitting many solves) build no temporary plans
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int>, size_t> known;
-    const auto key = std::make_tuple(g.nx, g.ny, g.nz, grid->precision);
+    static std::map<std::tuple<int, int, int, int, int>, size_t> known;
+    const auto key = std::make_tuple(g.nx, g.ny, g.nz, grid->precision, g.xper);
     size_t work = 0;
     bool hit = false;
     {
@@ -250,11 +293,13 @@ ibm_status ibm_workspace_bytes(const ibm_grid_desc* grid, size_t* bytes) {
         if (it != known.end()) { work = it->second; hit = true; }
     }
     if (!hit) {
-        cufftHandle pf, pi;
-        st = make_plans(g, grid->precision, &pf, &pi, &work);
+        cufftHandle pf, pi, pfz, piz;
+        st = make_plans(g, grid->precision, &pf, &pi, &pfz, &piz, &work);
         if (st != IBM_OK) return st;
         cufftDestroy(pf);
         cufftDestroy(pi);
+        if (pfz) cufftDestroy(pfz);
+        if (piz) cufftDestroy(piz);
         std::lock_guard<std::mutex> lock(mu);
         known[key] = work;
     }
@@ -298,11 +343,11 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     h->prec = grid->precision;
     h->esz = grid->precision == IBM_FP64 ? 8 : 4;
     h->N = g.N;
-    h->nspec = (long long)g.nz * g.ny * g.nxh;
+    h->nspec = (long long)g.nzs * g.ny * g.nxh;
     h->nseg = (long long)g.nsegx * g.ny * g.nz;
 
     size_t work = 0;
-    st = make_plans(g, h->prec, &h->plan_f, &h->plan_i, &work);
+    st = make_plans(g, h->prec, &h->plan_f, &h->plan_i, &h->plan_fz, &h->plan_iz, &work);
     if (st != IBM_OK) { delete h; return st; }
     h->plans = true;
     size_t need_bytes = carve(nullptr, g, h->prec, work, nullptr);
@@ -314,14 +359,17 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     h->fft_work_bytes = work;
     momentum_prepare(h);
     h->gp.kzm = momentum_default_kzm(h->gp, h->prec, momentum_uses_tma(h));
-    if (cufftSetWorkArea(h->plan_f, h->fft_work) != CUFFT_SUCCESS ||
-        cufftSetWorkArea(h->plan_i, h->fft_work) != CUFFT_SUCCESS ||
-        cufftSetStream(h->plan_f, h->stream) != CUFFT_SUCCESS || cufftSetStream(h->plan_i, h->stream) != CUFFT_SUCCESS) {
+    bool plan_ok = true;
+    for (cufftHandle p : {h->plan_f, h->plan_i, h->plan_fz, h->plan_iz})
+        if (p && (cufftSetWorkArea(p, h->fft_work) != CUFFT_SUCCESS || cufftSetStream(p, h->stream) != CUFFT_SUCCESS))
+            plan_ok = false;
+    if (!plan_ok) {
         ibm_destroy(h);
         return ibm_set_error(IBM_E_CUDA, "cufft work area / stream setup failed");
     }
     st = geom_classify(h);
     if (st == IBM_OK) st = geom_pivots(h);
+    if (st == IBM_OK) st = poisson_prepare(h);
     if (st == IBM_OK) {
         cudaError_t e = cudaMemsetAsync(h->scal, 0, 16 * sizeof(double), h->stream);
         if (e != cudaSuccess) st = ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e));
@@ -351,6 +399,8 @@ ibm_status ibm_build_weights(ibm_solver* h, const ibm_physics* phys, void* weigh
     if (phys->bmode < IBM_B_EXACT || phys->bmode > IBM_B_TAYLOR2) return ibm_set_error(IBM_E_INVALID, "bad bmode");
     if (phys->flow_mode != IBM_FLOW_FORCED && phys->flow_mode != IBM_FLOW_CONST_FLUX)
         return ibm_set_error(IBM_E_INVALID, "bad flow_mode");
+    if (phys->flow_mode == IBM_FLOW_CONST_FLUX && !h->gp.xper)
+        return ibm_set_error(IBM_E_INVALID, "a constant flow rate needs a periodic x direction");
     if ((uintptr_t)weights % ALIGN) return ibm_set_error(IBM_E_INVALID, "weights must be 256-byte aligned");
     size_t need = weights_layout(h, nullptr);
     if (weights_bytes < need) return ibm_set_error(IBM_E_NOMEM, "weights buffer too small: need " + std::to_string(need));
@@ -733,6 +783,8 @@ void ibm_destroy(ibm_solver* h) {
     if (h->plans) {
         cufftDestroy(h->plan_f);
         cufftDestroy(h->plan_i);
+        if (h->plan_fz) cufftDestroy(h->plan_fz);
+        if (h->plan_iz) cufftDestroy(h->plan_iz);
     }
     momentum_release(h);
     delete h;

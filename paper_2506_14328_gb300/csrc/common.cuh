@@ -19,7 +19,10 @@ struct GridP {
     int nx, ny, nz;
     int ndim, ncomp;
     int nsegx;              // x segments of 32 points per row
-    int nxh;                // nx/2 + 1 (half spectrum)
+    int nxh;                // spectrum extent in x: nx/2 + 1 (periodic x), nx (Neumann x, DCT modes)
+    int nzs;                // spectrum extent in z: nz (periodic x), nz/2 + 1 or 1 (Neumann x)
+    int xper;               // 1: x periodic; 0: inflow at -x, convective outflow at +x
+    double uin;             // inflow velocity (x inflow/outflow)
     long long N;            // cells
     double dx, dy, dz;
     double ox, oy, oz;
@@ -54,6 +57,7 @@ template <typename T> struct StageP {
     T qx, qy, qz;      // 1/(4 dx) ...: the two-point averages' 1/2 squared, over the spacing
     T cgx, cgy, cgz;   // c_k dt / dx ...: pressure-gradient factors
     T lc;              // 2 (nu/dx^2 + nu/dy^2 + nu/dz^2): the Laplacian's centre weight (3D)
+    T uin;             // inflow velocity (inflow/outflow x)
     int read_prev;     // stage k > 1: add b_k N^{k-2}
     int write_n;       // stage k < 3: store N^{k-1}
     int flux_sum;      // accumulate the predictor flux (constant flow rate)
@@ -298,6 +302,7 @@ struct ibm_solver {
     int npartials = 0;
 
     int counts[3] = {0, 0, 0};
+    int nfaces[2] = {0, 0};    // inflow/outflow x: fluid inflow and outflow faces
 
     // weights
     bool weights_ready = false;
@@ -310,6 +315,9 @@ struct ibm_solver {
     double last_pi = 0.0;
 
     cufftHandle plan_f = 0, plan_i = 0;
+    cufftHandle plan_fz = 0, plan_iz = 0;   // Neumann x, 3D: transforms along z
+    void* rtmp = nullptr;                    // Neumann x: reordered rows of the DCT (N reals)
+    void* twid = nullptr;                    // Neumann x: cos, sin of pi k / 2nx (field precision)
     bool plans = false;
 
     bool failed = false;
@@ -365,6 +373,7 @@ bool momentum_uses_tma(const ibm_solver* h);
 ibm_status run_project(ibm_solver* h);
 ibm_status run_poisson(ibm_solver* h, void* rhs_inout);
 ibm_status run_diagnostics(ibm_solver* h, double* out11);
+ibm_status poisson_prepare(ibm_solver* h);   // Neumann x: the DCT twiddle table
 
 // timing hooks used by both
 void timer_begin(ibm_solver* h, const char* name, cudaEvent_t* ev);

@@ -52,8 +52,11 @@ __device__ __forceinline__ double coord(const GridP& g, int d, int idx, int c) {
     return __dadd_rn(o, __dmul_rn(__dadd_rn((double)idx, off), D));
 }
 
-// Is (i,j,k) of component c a prescribed wall-face point (v on the +y wall)?
-__device__ __forceinline__ bool wall_face(const GridP& g, int c, int j) { return c == 1 && j == g.ny - 1; }
+// Is (i,j,k) of component c a prescribed box-face point: v on the +y wall, or u
+// on the outflow face of an inflow/outflow x?  Such points are never solved.
+__device__ __forceinline__ bool bface(const GridP& g, int c, int i, int j) {
+    return (c == 1 && j == g.ny - 1) || (c == 0 && !g.xper && i == g.nx - 1);
+}
 
 // ---------------------------------------------------------------------------
 // Classification
@@ -66,9 +69,16 @@ __global__ void k_classify_vel(GridP g, GeomP geo, uint8_t* __restrict__ velbits
     int k = (int)(id / ((long long)g.nx * g.ny));
     uint8_t b = 0;
     for (int c = 0; c < g.ncomp; ++c) {
-        if (wall_face(g, c, j)) continue;
+        if (bface(g, c, i, j)) continue;
         double x = coord(g, 0, i, c), y = coord(g, 1, j, c), z = coord(g, 2, k, c);
         if (phi_at(geo, x, y, z) < 0.0) b |= (uint8_t)(1u << c);
+    }
+    if (!g.xper) {
+        // bit 7: the inflow face (u at i = -1, i.e. x = origin) of row (j, k) is fluid at i = 0,
+        // the outflow face (u at i = nx-1) is fluid at i = nx-1
+        double yy = coord(g, 1, j, 0), zz = coord(g, 2, k, 0);
+        if (i == 0 && phi_at(geo, coord(g, 0, -1, 0), yy, zz) < 0.0) b |= IBM_MASK_FACE;
+        if (i == g.nx - 1 && phi_at(geo, coord(g, 0, i, 0), yy, zz) < 0.0) b |= IBM_MASK_FACE;
     }
     velbits[id] = b;
 }
@@ -77,15 +87,19 @@ __device__ __forceinline__ bool vel_internal(const GridP& g, const uint8_t* vb, 
     return (vb[i + (long long)g.nx * (j + (long long)g.ny * k)] >> c) & 1u;
 }
 
-// external = a stored, non-wall-face point that is not internal
+// external = a stored point, not on a box face, that is not internal
 __device__ __forceinline__ bool vel_external(const GridP& g, const uint8_t* vb, int c, int i, int j, int k) {
-    if (wall_face(g, c, j)) return false;
+    if (bface(g, c, i, j)) return false;
     return !vel_internal(g, vb, c, i, j, k);
 }
 
-// Neighbour of (i,j,k) along d by s on component c's grid; false if beyond a wall face.
+// Neighbour of (i,j,k) along d by s on component c's grid; false if beyond a box face.
 __device__ __forceinline__ bool neighbour(const GridP& g, int d, int s, int& i, int& j, int& k) {
-    if (d == 0) { i = wrapi(i + s, g.nx); return true; }
+    if (d == 0) {
+        if (g.xper) { i = wrapi(i + s, g.nx); return true; }
+        i += s;
+        return i >= 0 && i < g.nx;
+    }
     if (d == 2) { k = wrapi(k + s, g.nz); return true; }
     j += s;
     return j >= 0 && j < g.ny;
@@ -99,11 +113,14 @@ __global__ void k_classify_final(GridP g, const uint8_t* __restrict__ vb, uint8_
     int k = (int)(id / ((long long)g.nx * g.ny));
     uint8_t own = vb[id];
     uint8_t m = own;
-    // internal pressure: any of the cell's face velocities internal
-    bool pint = own != 0;
+    // internal pressure: any of the cell's face velocities internal (the inflow face is not one)
+    bool pint = (own & 7u) != 0;
     for (int c = 0; c < g.ncomp && !pint; ++c) {
         int ii = i, jj = j, kk = k;
-        if (c == 0) ii = wrapi(i - 1, g.nx);
+        if (c == 0) {
+            ii = g.xper ? wrapi(i - 1, g.nx) : i - 1;
+            if (ii < 0) continue;
+        }
         else if (c == 2) kk = wrapi(k - 1, g.nz);
         else { jj = j - 1; if (jj < 0) continue; }
         if (vel_internal(g, vb, c, ii, jj, kk)) pint = true;
@@ -329,7 +346,7 @@ __global__ void k_weights(GridP g, GeomP geo, WeightArgs a, const uint8_t* __res
             for (int s = 1; s >= -1; s -= 2) {
                 int ii = i, jj = j, kk = k;
                 if (!neighbour(g, d, s, ii, jj, kk)) continue;
-                if (wall_face(g, c, jj)) continue;
+                if (bface(g, c, ii, jj)) continue;
                 long long q = ii + (long long)g.nx * (jj + (long long)g.ny * kk);
                 if ((mask[q] >> c) & 1u) continue;       // internal neighbour
                 double phiQ = phi_at(geo, coord(g, 0, ii, c), coord(g, 1, jj, c), coord(g, 2, kk, c));
@@ -422,17 +439,28 @@ __global__ void k_flux_response(GridP g, const uint8_t* __restrict__ mask, const
 }
 
 // ---------------------------------------------------------------------------
+// Fluid inflow and outflow faces of an inflow/outflow x: out[0] += inflow faces,
+// out[1] += outflow faces (integer counts, exact)
+__global__ void k_face_count(GridP g, const uint8_t* __restrict__ mask, int* __restrict__ out) {
+    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;   // row (j, k)
+    if (r >= (long long)g.ny * g.nz) return;
+    const long long base = r * g.nx;
+    if (mask[base] & IBM_MASK_FACE) atomicAdd(out, 1);
+    if (mask[base + g.nx - 1] & IBM_MASK_FACE) atomicAdd(out + 1, 1);
+}
+
 // Thomas pivots of the y systems, one thread per (kz, kx)
 // ---------------------------------------------------------------------------
 __global__ void k_pivots(GridP g, double* __restrict__ piv, float* __restrict__ piv32, uint8_t* __restrict__ use32,
                          double tau) {
     long long sys = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long nsys = (long long)g.nz * g.nxh;
+    long long nsys = (long long)g.nzs * g.nxh;
     if (sys >= nsys) return;
     int kx = (int)(sys % g.nxh);
     int kz = (int)(sys / g.nxh);
     const double PI = 3.141592653589793;
-    double sx = sin(PI * kx / g.nx);
+    // periodic x: Fourier modes, 4 sin^2(pi k/n)/dx^2; Neumann x: cosine modes, 4 sin^2(pi k/2n)/dx^2
+    double sx = g.xper ? sin(PI * kx / g.nx) : sin(PI * kx / (2.0 * g.nx));
     double K = 4.0 * sx * sx / (g.dx * g.dx);
     if (g.ndim == 3 && g.nz > 1) {
         double sz = sin(PI * kz / g.nz);
@@ -482,8 +510,18 @@ ibm_status geom_classify(ibm_solver* h) {
     IBM_LAUNCH_CHECK();
     k_scan_apply<<<dim3(nblocks, 3), SCAN_T, 0, h->stream>>>(sa, h->nseg, h->scan_tmp, nblocks);
     IBM_LAUNCH_CHECK();
+    int faces[2] = {0, 0};
+    if (!g.xper) {
+        IBM_CUDA_TRY(cudaMemsetAsync(h->d_counts + 4, 0, 2 * sizeof(int), h->stream));
+        const long long rows = (long long)g.ny * g.nz;
+        k_face_count<<<(int)((rows + 255) / 256), 256, 0, h->stream>>>(g, h->mask, h->d_counts + 4);
+        IBM_LAUNCH_CHECK();
+        IBM_CUDA_TRY(cudaMemcpyAsync(faces, h->d_counts + 4, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    }
     IBM_CUDA_TRY(cudaMemcpyAsync(h->counts, h->d_counts, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->nfaces[0] = faces[0];
+    h->nfaces[1] = faces[1];
     return IBM_OK;
 }
 
@@ -553,7 +591,7 @@ ibm_status geom_stage_coefficients(ibm_solver* h) {
 }
 
 ibm_status geom_pivots(ibm_solver* h) {
-    long long nsys = (long long)h->gp.nz * h->gp.nxh;
+    long long nsys = (long long)h->gp.nzs * h->gp.nxh;
     // FP32 sweeps only in FP32 mode, for systems with K dy^2 >= 1
     double tau = h->prec == IBM_FP32 ? 1.0 : 1e300;
     k_pivots<<<(int)((nsys + 127) / 128), 128, 0, h->stream>>>(h->gp, h->pivots, h->pivots32, h->use32, tau);

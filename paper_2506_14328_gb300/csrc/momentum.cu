@@ -69,7 +69,21 @@ struct MomSrc {
     bool hh;                 // this thread loads a halo point
     bool ga, gb, gh;         // beyond a y wall: v reads 0, u and w read f * (adjacent)
     T fa, fb, fh;
+    // inflow/outflow x: xa (cells A, B) and xh (halo) are 1 beyond the inflow face, 2 beyond
+    // the outflow face, else 0; outa / outh: the point is the outflow face column of u
+    int xa, xh;
+    bool outa, outh;
 };
+
+// Source column of tile column i: wrapped (periodic x), or the adjacent column with
+// a ghost kind beyond an inflow (1) or outflow (2) face.
+__device__ __forceinline__ int mom_col(const GridP& g, int i, int& xk) {
+    xk = 0;
+    if (g.xper) return ((i % g.nx) + g.nx) % g.nx;
+    if (i < 0) { xk = 1; return 0; }
+    if (i >= g.nx) { xk = 2; return g.nx - 1; }
+    return i;
+}
 
 template <typename T, int NC>
 struct MomRegs {
@@ -100,7 +114,8 @@ __device__ __forceinline__ int mom_row(const GridP& g, int j, T sig_lo, T sig_hi
 template <typename T>
 __device__ __forceinline__ void mom_sources(const GridP& g, MomSrc<T>& S, int i0, int j0, T sig_lo, T sig_hi) {
     const int tx = threadIdx.x, w = threadIdx.y;
-    const int ix = (i0 + tx) % g.nx;
+    const int ix = mom_col(g, i0 + tx, S.xa);
+    S.outa = !g.xper && S.xa == 0 && ix == g.nx - 1;
     const int ixe = (ix + 1 < g.nx) ? ix + 1 : 0;
     const int ja = mom_row(g, j0 + 2 * w, sig_lo, sig_hi, S.fa, S.ga);
     const int jb = mom_row(g, j0 + 2 * w + 1, sig_lo, sig_hi, S.fb, S.gb);
@@ -117,6 +132,8 @@ __device__ __forceinline__ void mom_sources(const GridP& g, MomSrc<T>& S, int i0
     S.th = 0;
     S.fh = T(1);
     S.gh = false;
+    S.xh = S.xa;
+    S.outh = S.outa;
     if (w == 0 || w == 1) {                       // halo rows below and above the tile
         const int jh = mom_row(g, w == 0 ? j0 - 1 : j0 + MY, sig_lo, sig_hi, S.fh, S.gh);
         S.hh = true;
@@ -124,7 +141,8 @@ __device__ __forceinline__ void mom_sources(const GridP& g, MomSrc<T>& S, int i0
         S.th = (w == 0 ? 0 : (HY - 1) * HX) + tx + 1;
     } else if ((w == 2 || w == 3) && tx < HY) {   // halo columns left and right (with corners)
         const int jh = mom_row(g, j0 - 1 + tx, sig_lo, sig_hi, S.fh, S.gh);
-        const int ih = w == 2 ? (i0 - 1 + g.nx) % g.nx : (i0 + MX) % g.nx;
+        const int ih = mom_col(g, w == 2 ? i0 - 1 : i0 + MX, S.xh);
+        S.outh = !g.xper && S.xh == 0 && ih == g.nx - 1;
         S.hh = true;
         S.oh = ih + g.nx * jh;
         S.th = tx * HX + (w == 2 ? 0 : HX - 1);
@@ -149,28 +167,37 @@ __device__ __forceinline__ void mom_fetch(const MomF<T>& F, const MomSrc<T>& S, 
     R.m = ma | (mb << 8) | (mh << 16);
 }
 
-// value as the operator reads it: 0 unless internal; the ghost rule beyond a wall
+// value as the operator reads it: 0 unless internal (or the fluid outflow face
+// of u); beyond an inflow face u reads the inflow velocity and v, w the negated
+// adjacent value, beyond an outflow face v, w repeat it; then the y-wall rule.
+// sh selects the point's mask byte in m.
 template <typename T, bool EDGE>
-__device__ __forceinline__ T mom_masked(T x, uint32_t m, int bit, int c, bool beyond, T f) {
-    x = ((m >> bit) & 1u) ? x : T(0);
+__device__ __forceinline__ T mom_masked(T x, uint32_t m, int sh, int c, bool beyond, T f, int xk, bool outc, T uin) {
+    const uint32_t mb = (m >> sh) & 0xffu;
+    bool rd = (mb >> c) & 1u;
+    if (EDGE && c == 0 && outc) rd = (mb & IBM_MASK_FACE) != 0;
+    x = rd ? x : T(0);
+    if (EDGE && xk == 1) x = (c == 0) ? ((mb & IBM_MASK_FACE) ? uin : T(0)) : -x;
+    else if (EDGE && xk == 2) x = (c == 0) ? T(0) : x;
     if (EDGE && beyond) x = (c == 1) ? T(0) : f * x;
     return x;
 }
 
 template <typename T, int NC, bool EDGE>
-__device__ __forceinline__ void mom_store(T* tile, const MomSrc<T>& S, const MomRegs<T, NC>& R) {
+__device__ __forceinline__ void mom_store(T* tile, const MomSrc<T>& S, const MomRegs<T, NC>& R, T uin) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        tile[c * HP + S.ta] = mom_masked<T, EDGE>(R.a[c], R.m, c, c, S.ga, S.fa);
-        tile[c * HP + S.tb] = mom_masked<T, EDGE>(R.b[c], R.m, 8 + c, c, S.gb, S.fb);
-        if (S.hh) tile[c * HP + S.th] = mom_masked<T, EDGE>(R.h[c], R.m, 16 + c, c, S.gh, S.fh);
+        tile[c * HP + S.ta] = mom_masked<T, EDGE>(R.a[c], R.m, 0, c, S.ga, S.fa, S.xa, S.outa, uin);
+        tile[c * HP + S.tb] = mom_masked<T, EDGE>(R.b[c], R.m, 8, c, S.gb, S.fb, S.xa, S.outa, uin);
+        if (S.hh) tile[c * HP + S.th] = mom_masked<T, EDGE>(R.h[c], R.m, 16, c, S.gh, S.fh, S.xh, S.outh, uin);
     }
 }
 
 template <typename T, int NC>
-__device__ __forceinline__ void mom_store_plane(T* tile, const MomSrc<T>& S, const MomRegs<T, NC>& R, bool yedge) {
-    if (yedge) mom_store<T, NC, true>(tile, S, R);
-    else mom_store<T, NC, false>(tile, S, R);
+__device__ __forceinline__ void mom_store_plane(T* tile, const MomSrc<T>& S, const MomRegs<T, NC>& R, bool edge,
+                                                T uin) {
+    if (edge) mom_store<T, NC, true>(tile, S, R, uin);
+    else mom_store<T, NC, false>(tile, S, R, uin);
 }
 
 template <typename T>
@@ -238,9 +265,10 @@ __device__ __forceinline__ void mom_ibm_fix(const IbmStage<T>& ib, const StageP<
 template <typename T, int NC>
 __device__ __forceinline__ void mom_write(const MomF<T>& F, const StageP<T>& sp, int ida, int idb, bool liveA,
                                           bool liveB, uint32_t mA, uint32_t mB, T (&oA)[3], T (&oB)[3], T (&NA)[3],
-                                          T (&NB)[3], T& fsum) {
+                                          T (&NB)[3], T& fsum, bool outcol) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
+        if (c == 0 && outcol) continue;   // u on the outflow face: the outflow update writes it
         const bool ia = (mA >> c) & 1u, ibb = (mB >> c) & 1u;
         oA[c] = ia ? oA[c] : T(0);
         oB[c] = ibb ? oB[c] : T(0);
@@ -263,7 +291,7 @@ __device__ __forceinline__ void mom_plane3(const GridP& g, const MomF<T>& F, con
                                            const IbmStage<T>& ib, int a, int b, const T* __restrict__ t0,
                                            const T* __restrict__ t1, MomCarry<T>& C, const MomPre<T>& P,
                                            const T (&ownA)[3], const T (&ownB)[3], uint32_t m, int k, int ida,
-                                           int idb, bool liveA, bool liveB, int segA, T& fsum) {
+                                           int idb, bool liveA, bool liveB, int segA, T& fsum, bool outcol) {
     constexpr int HX = RS;
     const T* U0 = t0;
     const T* V0 = t0 + CS;
@@ -350,7 +378,7 @@ __device__ __forceinline__ void mom_plane3(const GridP& g, const MomF<T>& F, con
         const T ua3[3] = {uA, vA, wA}, ub3[3] = {uB, vB, wB};
         mom_ibm_fix<T, 3>(ib, sp, mA, mB, segA, segA + g.nsegx, ua3, ub3, RA, RB, oA, oB, NA, NB);
     }
-    mom_write<T, 3>(F, sp, ida, idb, liveA, liveB, mA, mB, oA, oB, NA, NB, fsum);
+    mom_write<T, 3>(F, sp, ida, idb, liveA, liveB, mA, mB, oA, oB, NA, NB, fsum, outcol);
 
     // carry this column into the next plane
     C.ubA = uA; C.ubB = uB; C.vbA = vA; C.vbB = vB; C.wbA = wA; C.wbB = wB;
@@ -365,7 +393,7 @@ template <typename T>
 __device__ __forceinline__ void mom_plane2(const GridP& g, const MomF<T>& F, const StageP<T>& sp,
                                            const IbmStage<T>& ib, const MomSrc<T>& S, const T* __restrict__ t0,
                                            const MomPre<T>& P, T pA, T pB, uint32_t m, int ida, int idb,
-                                           bool liveA, bool liveB, int segA, T& fsum) {
+                                           bool liveA, bool liveB, int segA, T& fsum, bool outcol) {
     const int a = S.ta, b = S.tb;
     const T* U0 = t0;
     const T* V0 = t0 + HP;
@@ -405,7 +433,7 @@ __device__ __forceinline__ void mom_plane2(const GridP& g, const MomF<T>& F, con
         const T ua3[3] = {uA, vA, T(0)}, ub3[3] = {uB, vB, T(0)};
         mom_ibm_fix<T, 2>(ib, sp, mA, mB, segA, segA + g.nsegx, ua3, ub3, RA, RB, oA, oB, NA, NB);
     }
-    mom_write<T, 2>(F, sp, ida, idb, liveA, liveB, mA, mB, oA, oB, NA, NB, fsum);
+    mom_write<T, 2>(F, sp, ida, idb, liveA, liveB, mA, mB, oA, oB, NA, NB, fsum, outcol);
 }
 
 // One step of the 3D plane loop: store plane k+1 (register set R) into its
@@ -417,7 +445,7 @@ __device__ __forceinline__ void mom_iter3(const GridP& g, const MomF<T>& F, cons
                                           int& s2, MomRegs<T, 3>& R, MomPre<T>& Pc, MomPre<T>& Pn, uint32_t& mc,
                                           uint32_t& mn, MomCarry<T>& C, int k, int kend, int plane, bool yedge,
                                           int rowA, bool liveA, bool liveB, int segrow, T& fsum) {
-    mom_store_plane<T, 3>(tiles + s1, S, R, yedge);               // plane k+1
+    mom_store_plane<T, 3>(tiles + s1, S, R, yedge, sp.uin);       // plane k+1
     mn = R.m & 0xffffu;
     if (k + 3 <= kend) mom_fetch<T, 3>(F, S, R, wrapi(k + 3, g.nz) * plane);
     if (k + 1 < kend) mom_pre(F, S, Pn, g, k + 1, plane, sp.read_prev);
@@ -425,7 +453,7 @@ __device__ __forceinline__ void mom_iter3(const GridP& g, const MomF<T>& F, cons
     const int ida = rowA + k * plane;
     const T none[3] = {T(0), T(0), T(0)};
     mom_plane3<T, HX, HP, false>(g, F, sp, ib, S.ta, S.tb, tiles + s0, tiles + s1, C, Pc, none, none, mc, k, ida,
-                                 ida + g.nx, liveA, liveB, segrow + k * g.ny * g.nsegx, fsum);
+                                 ida + g.nx, liveA, liveB, segrow + k * g.ny * g.nsegx, fsum, S.outa);
     const int t = s0;
     s0 = s1;
     s1 = s2;
@@ -445,7 +473,8 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
     const int i = i0 + tx, jA = j0 + 2 * ty;
     const bool liveA = i < g.nx && jA < g.ny;
     const bool liveB = i < g.nx && jA + 1 < g.ny;
-    const bool yedge = j0 == 0 || j0 + MY >= g.ny;
+    // blocks that touch a y wall, or an x face of an inflow/outflow box, apply the ghost rules
+    const bool yedge = j0 == 0 || j0 + MY >= g.ny || (!g.xper && (i0 == 0 || i0 + MX >= g.nx));
     const int plane = g.nx * g.ny;
     const int rowA = i + g.nx * jA;               // in-plane index of A (B: + nx)
     const int segrow = jA * g.nsegx + blockIdx.x;  // row segment of A at plane 0
@@ -471,8 +500,8 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
         MomCarry<T> C;
         C.pA = F.p[kbeg * plane + S.oa];
         C.pB = F.p[kbeg * plane + S.ob];
-        mom_store_plane<T, 3>(tiles + s2, S, X, yedge);
-        mom_store_plane<T, 3>(tiles + s0, S, Y, yedge);
+        mom_store_plane<T, 3>(tiles + s2, S, X, yedge, sp.uin);
+        mom_store_plane<T, 3>(tiles + s0, S, Y, yedge, sp.uin);
         uint32_t m0 = Y.m & live_bits, m1 = 0;
         __syncthreads();
         {
@@ -506,10 +535,10 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
         mom_fetch<T, NC>(F, S, X, 0);
         mom_pre(F, S, P0, g, 0, plane, sp.read_prev);
         const T pA = F.p[S.oa], pB = F.p[S.ob];
-        mom_store_plane<T, NC>(tiles, S, X, yedge);
+        mom_store_plane<T, NC>(tiles, S, X, yedge, sp.uin);
         __syncthreads();
         mom_plane2<T>(g, F, sp, ib, S, tiles, P0, pA, pB, X.m & live_bits, rowA, rowA + g.nx, liveA, liveB, segrow,
-                      fsum);
+                      fsum, S.outa);
     }
     if (sp.flux_sum) {
         // FP32 sums within a warp, FP64 across warps and blocks
@@ -874,7 +903,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
         const int ida = rowA + k * plane;
         mom_plane3<T, L::RX, L::CS, true>(g, F, sp, ib, ta, tb, reinterpret_cast<const T*>(s0),
                                           reinterpret_cast<const T*>(s1), C, P, ua, ub, mc, k, ida, ida + g.nx,
-                                          liveA, liveB, segrow + k * g.ny * g.nsegx, fsum);
+                                          liveA, liveB, segrow + k * g.ny * g.nsegx, fsum, false);
         mc = mn & live_bits;
     }
     if (sp.flux_sum) {
@@ -986,6 +1015,7 @@ ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib,
     sp.qx = (T)(0.25 / g.dx); sp.qy = (T)(0.25 / g.dy); sp.qz = (T)(0.25 / g.dz);
     sp.cgx = (T)(dt * RK_C[k] / g.dx); sp.cgy = (T)(dt * RK_C[k] / g.dy); sp.cgz = (T)(dt * RK_C[k] / g.dz);
     sp.lc = (T)(2.0 * h->phys.nu * (1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy) + 1.0 / (g.dz * g.dz)));
+    sp.uin = (T)g.uin;
     sp.sig_lo = (T)g.sig_lo;
     sp.sig_hi = (T)g.sig_hi;
     sp.read_prev = k > 0;
@@ -1012,7 +1042,8 @@ void momentum_release(ibm_solver* h) {
 
 void momentum_prepare(ibm_solver* h) {
     momentum_release(h);
-    if (h->gp.ndim != 3 || h->gp.nx % 16 != 0) return;
+    // the TMA form covers 3D grids with a periodic x whose extent is a multiple of 16
+    if (h->gp.ndim != 3 || h->gp.nx % 16 != 0 || !h->gp.xper) return;
     h->mom_maps = h->prec == IBM_FP64 ? static_cast<void*>(build_maps<double>(h))
                                       : static_cast<void*>(build_maps<float>(h));
 }

@@ -59,8 +59,10 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_partials(GridP g, const 
         const int k = (int)(row / g.ny);
         const T wc = g.ndim == 3 ? w[id] : T(0);
         const T wm = g.ndim == 3 ? w[i + (long long)g.nx * (j + (long long)g.ny * wrapi(k - 1, g.nz))] : T(0);
-        acc.cell(g.ncomp, inv.v, u[id], u[row * g.nx + wrapi(i - 1, g.nx)], v[id], j > 0 ? v[id - g.nx] : T(0),
-                 wc, wm, p[id], mask[id]);
+        // the -x face of the first cell is the inflow face in an inflow/outflow box
+        const T uw = (g.xper || i > 0) ? u[row * g.nx + wrapi(i - 1, g.nx)]
+                                       : ((mask[id] & IBM_MASK_FACE) ? (T)g.uin : T(0));
+        acc.cell(g.ncomp, inv.v, u[id], uw, v[id], j > 0 ? v[id - g.nx] : T(0), wc, wm, p[id], mask[id]);
     }
     double a[NA_VALS];
     acc.finish(a);
@@ -163,6 +165,8 @@ extern "C" ibm_status ibm_diagnostics_noalloc(const ibm_grid_desc* grid, const v
     g.dx = grid->L[0] / grid->n[0];
     g.dy = grid->L[1] / grid->n[1];
     g.dz = grid->L[2] / grid->n[2];
+    g.xper = grid->bc_lo[0] != IBM_BC_INFLOW;
+    g.uin = g.xper ? 0.0 : grid->inflow[0];
     double s[NA_VALS];
     st = grid->precision == IBM_FP64
              ? noalloc_run<double>(g, u, v, w, p, mask, (cudaStream_t)stream, scratch, s)

@@ -83,7 +83,7 @@ __device__ __forceinline__ T flux_increment(const FluxCorr<T>& fc, T pic, uint8_
 // ---------------------------------------------------------------------------
 constexpr int DZ = 4;
 
-template <typename T, bool THREE, bool FLUX>
+template <typename T, bool THREE, bool FLUX, bool XF>
 __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict__ u, const T* __restrict__ v,
                                                     const T* __restrict__ w, const uint8_t* __restrict__ mask,
                                                     T* __restrict__ rhs, T idx, T idy, T idz, FluxCorr<T> fc) {
@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict
     const int segl = il / 32, lanel = il % 32;
     const int il_probe = segl * 32 + lane;                  // the warp reads that segment's mask bits
     const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
+    // the first segment of an inflow/outflow x: lane 0 (cell 0) reads the inflow face
+    const bool inflow_seg = XF && blockIdx.x == 0;
     T wprev = T(0);
     if (THREE && live) wprev = w[i + g.nx * j + plane * wrapi(kbeg - 1, g.nz)];
     for (int k0 = kbeg; k0 < kend; k0 += ZB) {
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict
                     vc[t] = v[id];
                     if (j > 0) vm[t] = v[id - g.nx];
                     if (THREE) wc[t] = w[id];
-                    if (FLUX) mc[t] = mask[id];
+                    if (FLUX || inflow_seg) mc[t] = mask[id];
                 }
                 if (FLUX && il_probe < g.nx) ml[t] = mask[rowb + il_probe];
             }
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict
                 ulane0 += flux_increment(fc, pic, mln, bl, rowseg + segl, lanel);
             }
             T ul = __shfl_up_sync(0xffffffffu, ucc, 1);
-            if (lane == 0) ul = ulane0;
+            if (lane == 0) ul = inflow_seg ? ((mc[t] & IBM_MASK_FACE) ? (T)g.uin : T(0)) : ulane0;   // inflow face
             if (live) {
                 T d = (ucc - ul) * idx;
                 d += (vc[t] - vm[t]) * idy;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, 
 // march g.kzd planes carrying psi(k+1) into the next plane; psi(i+1) comes from
 // the neighbouring lane.  Loads of DZ planes are issued before any is used.
 // ---------------------------------------------------------------------------
-template <typename T, bool THREE, bool FLUX>
+template <typename T, bool THREE, bool FLUX, bool XF>
 __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ us0, const T* __restrict__ us1,
                                                  const T* __restrict__ us2, const T* __restrict__ psi,
                                                  const uint8_t* __restrict__ mask, T* __restrict__ u0,
@@ -480,6 +482,7 @@ __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ 
     const int ir = (i + 1 < g.nx) ? i + 1 : 0;              // +x neighbour (periodic)
     const bool from_lane = lane < 31 && i + 1 < g.nx;
     const bool top = j == g.ny - 1;
+    const bool outface = XF && i == g.nx - 1;               // the outflow face keeps u*
     const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
     T ph = live ? psi[i + g.nx * j + plane * kbeg] : T(0);
     for (int k0 = kbeg; k0 < kend; k0 += ZB) {
@@ -518,7 +521,7 @@ __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ 
                 if (live) uc = flux_increment(fc, pic, mc[t], b, (j + g.ny * k) * g.nsegx + (int)blockIdx.x, lane);
             }
             if (live) {
-                u0[id] = a0[t] + uc - (e - ph) * idx;
+                u0[id] = outface ? a0[t] : a0[t] + uc - (e - ph) * idx;
                 u1[id] = top ? a1[t] : a1[t] - (pN[t] - ph) * idy;
                 if (THREE) u2[id] = a2[t] - (pT[t] - ph) * idz;
                 if (update_p) p[id] = pp[t] + ph * inv_ckdt;
@@ -538,7 +541,8 @@ __global__ void k_mask_copy(GridP g, const uint8_t* __restrict__ mask, const T* 
     if (i >= g.nx || j >= g.ny) return;
     const long long id = i + (long long)g.nx * (j + (long long)g.ny * blockIdx.z);
     uint8_t m = mask[id];
-    b0[id] = (m & IBM_MASK_U) ? a0[id] : T(0);
+    const bool readable_u = (m & IBM_MASK_U) || (!g.xper && i == g.nx - 1 && (m & IBM_MASK_FACE));
+    b0[id] = readable_u ? a0[id] : T(0);
     b1[id] = (m & IBM_MASK_V) ? a1[id] : T(0);
     if (g.ndim == 3) b2[id] = (m & IBM_MASK_W) ? a2[id] : T(0);
 }
@@ -587,7 +591,10 @@ __global__ void __launch_bounds__(256) k_diag(GridP g, const T* __restrict__ u, 
                 if (k < kend) {
                     const int rowb = g.nx * (j + g.ny * k);
                     const int id = rowb + i;
-                    if (lane == 0) ul0[t] = u[rowb + il];
+                    if (lane == 0) {
+                        if (g.xper || tx != 0) ul0[t] = u[rowb + il];
+                        else ul0[t] = (mask[rowb] & IBM_MASK_FACE) ? (T)g.uin : T(0);   // the inflow face
+                    }
                     if (live) {
                         uc[t] = u[id];
                         vc[t] = v[id];
@@ -643,18 +650,195 @@ __global__ void k_diag_final(const double* __restrict__ part, int nb, double* __
 dim3 cell_grid(const GridP& g) { return dim3(g.nsegx, (g.ny + 7) / 8, g.nz); }
 
 
+// ---------------------------------------------------------------------------
+// Neumann x (inflow/outflow): the type-II DCT of every x row,
+//   X[k] = sum_n x[n] cos(pi k (2n+1) / 2nx),
+// through one nx-point real FFT (Makhoul's reordering), and its inverse.
+//   forward:  v[pos(n)] = x[n], even n ascending and odd n descending;
+//             V = FFT(v);  X[k] = Re(e^{-i pi k/2nx} V[k])  (V[k] = conj V[nx-k] past nx/2)
+//   inverse:  V[k] = e^{i pi k/2nx} (X[k] - i X[nx-k])  (X[nx] = 0),  v = IFFT(V),  x[n] = v[pos(n)]
+// The 1/nx of the inverse sits in the tridiagonal's scale with the 1/nz of z.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int dct_pos(int n, int N) { return (n & 1) ? N - 1 - (n >> 1) : (n >> 1); }
+
+template <typename T>
+__global__ void k_dct_reorder(GridP g, const T* __restrict__ in, T* __restrict__ out, int inverse) {
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    const int n = (int)(id % g.nx);
+    const long long m = id - n + dct_pos(n, g.nx);
+    if (inverse) out[id] = in[m];
+    else out[m] = in[id];
+}
+
+template <typename T>
+__global__ void k_dct_twiddles(int nx, T* __restrict__ tw) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nx) return;
+    double sn, cs;
+    sincospi((double)k / (2.0 * nx), &sn, &cs);
+    tw[2 * k] = (T)cs;
+    tw[2 * k + 1] = (T)sn;
+}
+
+template <typename T, typename C>
+__global__ void k_dct_post(GridP g, const C* __restrict__ V, T* __restrict__ X, const T* __restrict__ tw) {
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    const int k = (int)(id % g.nx);
+    const long long row = id / g.nx;
+    const int nxr = g.nx / 2 + 1;
+    C v;
+    if (k < nxr) {
+        v = V[row * nxr + k];
+    } else {
+        v = V[row * nxr + g.nx - k];
+        v.y = -v.y;
+    }
+    X[id] = tw[2 * k] * v.x + tw[2 * k + 1] * v.y;
+}
+
+template <typename T, typename C>
+__global__ void k_idct_pre(GridP g, const T* __restrict__ X, C* __restrict__ V, const T* __restrict__ tw) {
+    const int nxr = g.nx / 2 + 1;
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= (long long)g.ny * g.nz * nxr) return;
+    const int k = (int)(id % nxr);
+    const long long row = id / nxr;
+    const T a = X[row * g.nx + k];
+    const T b = k == 0 ? T(0) : X[row * g.nx + g.nx - k];
+    const T c = tw[2 * k], sn = tw[2 * k + 1];
+    C v;
+    v.x = c * a + sn * b;
+    v.y = sn * a - c * b;
+    V[id] = v;
+}
+
+template <typename T, typename C>
+__global__ void k_pack_real(long long n, const T* __restrict__ x, C* __restrict__ y) {
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    C v;
+    v.x = x[id];
+    v.y = T(0);
+    y[id] = v;
+}
+
+template <typename T, typename C>
+__global__ void k_unpack_real(long long n, const C* __restrict__ y, T* __restrict__ x) {
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    x[id] = y[id].x;
+}
+
+// ---------------------------------------------------------------------------
+// Convective outflow (inflow/outflow x), readings as in the header: on every
+// fluid outflow face u_b = u(nx-1) the RK3 stage of du/dt = -U_c (u_b - u_{b-1})/dx,
+// with the momentum stage's combination (dt a_k N + dt b_k N^{k-2}) and no
+// pressure or IBM term; then one constant shift of all fluid outflow faces so
+// that the outflow flux equals the inflow flux.  With update = 0 the first
+// kernel only sums the present outflow values (initial projection).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_outflow(GridP g, const T* __restrict__ u, const uint8_t* __restrict__ mask,
+                                                 T* __restrict__ us, T* __restrict__ Nh, T dta, T dtb, T ucx,
+                                                 int read_prev, int write_n, int update, double* __restrict__ part) {
+    __shared__ double sh[8];
+    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;   // row (j, k)
+    double s = 0.0;
+    if (r < (long long)g.ny * g.nz) {
+        const long long ib = r * g.nx + g.nx - 1;
+        const bool fluid = mask[ib] & IBM_MASK_FACE;
+        if (update) {
+            T o = T(0), Nb = T(0);
+            if (fluid) {
+                const T ub = u[ib];
+                const T um = (mask[ib - 1] & IBM_MASK_U) ? u[ib - 1] : T(0);
+                Nb = -ucx * (ub - um);
+                T R = dta * Nb;
+                if (read_prev) R += dtb * Nh[ib];
+                o = ub + R;
+            }
+            us[ib] = o;
+            if (write_n) Nh[ib] = Nb;
+            s = (double)o;
+        } else if (fluid) {
+            s = (double)us[ib];
+        }
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_outflow_fix(GridP g, const uint8_t* __restrict__ mask, T* __restrict__ us,
+                                                      const double* __restrict__ part, int nparts, double qin,
+                                                      int nout) {
+    __shared__ double sh[32];
+    __shared__ double shift;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += part[b];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 32; ++w) t += sh[w];
+        shift = nout > 0 ? (qin - t) / nout : 0.0;
+    }
+    __syncthreads();
+    const T sh_t = (T)shift;
+    for (long long r = threadIdx.x; r < (long long)g.ny * g.nz; r += blockDim.x) {
+        const long long ib = r * g.nx + g.nx - 1;
+        if (mask[ib] & IBM_MASK_FACE) us[ib] += sh_t;
+    }
+}
+
 template <typename T>
 ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
+    using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
     const GridP& g = h->gp;
     cudaEvent_t t;
+    const int nbN = (int)((g.N + 255) / 256);
+    auto fwd = [&](cufftHandle p, void* in, void* out) {
+        return h->prec == IBM_FP64 ? cufftExecD2Z(p, (cufftDoubleReal*)in, (cufftDoubleComplex*)out)
+                                   : cufftExecR2C(p, (cufftReal*)in, (cufftComplex*)out);
+    };
+    auto inv = [&](cufftHandle p, void* in, void* out) {
+        return h->prec == IBM_FP64 ? cufftExecZ2D(p, (cufftDoubleComplex*)in, (cufftDoubleReal*)out)
+                                   : cufftExecC2R(p, (cufftComplex*)in, (cufftReal*)out);
+    };
     timer_begin(h, "fft_forward", &t);
-    cufftResult r;
-    if (h->prec == IBM_FP64) r = cufftExecD2Z(h->plan_f, (cufftDoubleReal*)rhs_inout, (cufftDoubleComplex*)h->spec);
-    else r = cufftExecR2C(h->plan_f, (cufftReal*)rhs_inout, (cufftComplex*)h->spec);
+    cufftResult r = CUFFT_SUCCESS;
+    if (g.xper) {
+        r = fwd(h->plan_f, rhs_inout, h->spec);
+    } else {
+        // DCT of the x rows into rhs, then (3D) the real FFT along z into the spectrum
+        T* x = (T*)rhs_inout;
+        k_dct_reorder<T><<<nbN, 256, 0, h->stream>>>(g, x, (T*)h->rtmp, 0);
+        IBM_LAUNCH_CHECK();
+        r = fwd(h->plan_f, h->rtmp, h->spec);
+        if (r == CUFFT_SUCCESS) {
+            k_dct_post<T, C><<<nbN, 256, 0, h->stream>>>(g, (const C*)h->spec, x, (const T*)h->twid);
+            IBM_LAUNCH_CHECK();
+            if (g.nz > 1) {
+                r = fwd(h->plan_fz, x, h->spec);
+            } else {
+                k_pack_real<T, C><<<nbN, 256, 0, h->stream>>>(g.N, x, (C*)h->spec);
+                IBM_LAUNCH_CHECK();
+            }
+        }
+    }
     if (r != CUFFT_SUCCESS) { h->failed = true; return ibm_set_error(IBM_E_CUDA, "cufft forward failed"); }
     timer_end(h, t, "fft_forward");
     double scale = g.dy * g.dy / ((double)g.nx * (double)g.nz);
-    const int nsys = g.nz * g.nxh;
+    const int nsys = g.nzs * g.nxh;
     const int nb64 = g.ny <= 32 * TW_ROWS ? h->n64 : (2 * h->n64 + 31) / 32;
     const int nblk = nb64 + (nsys - h->n64 + 31) / 32;
     timer_begin(h, "tridiag", &t);
@@ -667,8 +851,27 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
     IBM_LAUNCH_CHECK();
     timer_end(h, t, "tridiag");
     timer_begin(h, "fft_inverse", &t);
-    if (h->prec == IBM_FP64) r = cufftExecZ2D(h->plan_i, (cufftDoubleComplex*)h->spec, (cufftDoubleReal*)rhs_inout);
-    else r = cufftExecC2R(h->plan_i, (cufftComplex*)h->spec, (cufftReal*)rhs_inout);
+    if (g.xper) {
+        r = inv(h->plan_i, h->spec, rhs_inout);
+    } else {
+        T* x = (T*)rhs_inout;
+        if (g.nz > 1) {
+            r = inv(h->plan_iz, h->spec, x);
+        } else {
+            k_unpack_real<T, C><<<nbN, 256, 0, h->stream>>>(g.N, (const C*)h->spec, x);
+            IBM_LAUNCH_CHECK();
+        }
+        if (r == CUFFT_SUCCESS) {
+            const long long nh = (long long)g.ny * g.nz * (g.nx / 2 + 1);
+            k_idct_pre<T, C><<<(int)((nh + 255) / 256), 256, 0, h->stream>>>(g, x, (C*)h->spec, (const T*)h->twid);
+            IBM_LAUNCH_CHECK();
+            r = inv(h->plan_i, h->spec, h->rtmp);
+            if (r == CUFFT_SUCCESS) {
+                k_dct_reorder<T><<<nbN, 256, 0, h->stream>>>(g, (const T*)h->rtmp, x, 1);
+                IBM_LAUNCH_CHECK();
+            }
+        }
+    }
     if (r != CUFFT_SUCCESS) { h->failed = true; return ibm_set_error(IBM_E_CUDA, "cufft inverse failed"); }
     timer_end(h, t, "fft_inverse");
     return IBM_OK;
@@ -696,12 +899,16 @@ ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const 
     const T ix = (T)(1.0 / g.dx), iy = (T)(1.0 / g.dy), iz = (T)(1.0 / g.dz);
     const dim3 grd = zmarch_grid(g), blk(32, 8);
     T* rhs = (T*)h->rhs;
-    if (g.ndim == 3) {
-        if (flux) k_divergence<T, true, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us[2], h->mask, rhs, ix, iy, iz, fc);
-        else k_divergence<T, true, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us[2], h->mask, rhs, ix, iy, iz, fc);
+    T* w = g.ndim == 3 ? us[2] : us[0];
+    if (!g.xper) {   // inflow/outflow x (no constant flow rate)
+        if (g.ndim == 3) k_divergence<T, true, false, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], w, h->mask, rhs, ix, iy, iz, fc);
+        else k_divergence<T, false, false, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], w, h->mask, rhs, ix, iy, iz, fc);
+    } else if (g.ndim == 3) {
+        if (flux) k_divergence<T, true, true, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], w, h->mask, rhs, ix, iy, iz, fc);
+        else k_divergence<T, true, false, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], w, h->mask, rhs, ix, iy, iz, fc);
     } else {
-        if (flux) k_divergence<T, false, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us[0], h->mask, rhs, ix, iy, iz, fc);
-        else k_divergence<T, false, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us[0], h->mask, rhs, ix, iy, iz, fc);
+        if (flux) k_divergence<T, false, true, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], w, h->mask, rhs, ix, iy, iz, fc);
+        else k_divergence<T, false, false, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], w, h->mask, rhs, ix, iy, iz, fc);
     }
     IBM_LAUNCH_CHECK();
     timer_end(h, t, "divergence");
@@ -719,17 +926,43 @@ ibm_status launch_correct(ibm_solver* h, T* const us[3], T inv_ckdt, int update_
     T* u2 = g.ndim == 3 ? (T*)h->buf.u[2] : u0;
     T* us2 = g.ndim == 3 ? us[2] : us[0];
     T* p = (T*)h->buf.p;
-    if (g.ndim == 3) {
-        if (flux) k_correct<T, true, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy, iz, inv_ckdt, update_p, fc);
-        else k_correct<T, true, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy, iz, inv_ckdt, update_p, fc);
+#define IBM_CORRECT(THREE_, FLUX_, XF_)                                                                        \
+    k_correct<T, THREE_, FLUX_, XF_><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, \
+                                                                 ix, iy, iz, inv_ckdt, update_p, fc)
+    if (!g.xper) {   // inflow/outflow x (no constant flow rate)
+        if (g.ndim == 3) IBM_CORRECT(true, false, true);
+        else IBM_CORRECT(false, false, true);
+    } else if (g.ndim == 3) {
+        if (flux) IBM_CORRECT(true, true, false);
+        else IBM_CORRECT(true, false, false);
     } else {
-        if (flux) k_correct<T, false, true><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy, iz, inv_ckdt, update_p, fc);
-        else k_correct<T, false, false><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy, iz, inv_ckdt, update_p, fc);
+        if (flux) IBM_CORRECT(false, true, false);
+        else IBM_CORRECT(false, false, false);
     }
+#undef IBM_CORRECT
     IBM_LAUNCH_CHECK();
     return IBM_OK;
 }
 
+
+// Outflow face of stage k (update) or, for the initial projection, only the flux balance.
+template <typename T>
+ibm_status outflow_t(ibm_solver* h, int k, bool update) {
+    const GridP& g = h->gp;
+    const long long rows = (long long)g.ny * g.nz;
+    const int nb = (int)((rows + 255) / 256);
+    if (nb > h->npartials) return ibm_set_error(IBM_E_INVALID, "too many outflow rows for the partials buffer");
+    const double dt = h->phys.dt;
+    const double ucx = h->nfaces[1] > 0 ? g.uin * h->nfaces[0] / (double)h->nfaces[1] / g.dx : 0.0;
+    k_outflow<T><<<nb, 256, 0, h->stream>>>(g, (const T*)h->buf.u[0], h->mask, (T*)h->ustar[0], (T*)h->Nh[0],
+                                           (T)(dt * RK_A[k]), (T)(dt * RK_B[k]), (T)ucx, k > 0, k < 2, update ? 1 : 0,
+                                           h->partials);
+    IBM_LAUNCH_CHECK();
+    k_outflow_fix<T><<<1, 1024, 0, h->stream>>>(g, h->mask, (T*)h->ustar[0], h->partials, nb,
+                                               g.uin * (double)h->nfaces[0], h->nfaces[1]);
+    IBM_LAUNCH_CHECK();
+    return IBM_OK;
+}
 
 template <typename T>
 ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
@@ -742,6 +975,12 @@ ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
     ibm_status st0 = momentum_launch(h, k, &nparts);
     if (st0 != IBM_OK) return st0;
     timer_end(h, t, "momentum");
+    if (!g.xper) {
+        timer_begin(h, "outflow", &t);
+        st0 = outflow_t<T>(h, k, true);
+        if (st0 != IBM_OK) return st0;
+        timer_end(h, t, "outflow");
+    }
     if (cflux) {
         double dV = g.dx * g.dy * (g.ndim == 3 ? g.dz : 1.0);
         timer_begin(h, "flux_control", &t);
@@ -780,6 +1019,10 @@ ibm_status project_t(ibm_solver* h) {
     k_mask_copy<T><<<cell_grid(g), dim3(32, 8), 0, h->stream>>>(g, h->mask, (const T*)h->buf.u[0], (const T*)h->buf.u[1], u2, us[0],
                                               us[1], us[2]);
     IBM_LAUNCH_CHECK();
+    if (!g.xper) {
+        ibm_status st0 = outflow_t<T>(h, 0, false);
+        if (st0 != IBM_OK) return st0;
+    }
     const FluxCorr<T> fc = flux_corr<T>(h, 0);
     ibm_status st = divergence_and_solve<T>(h, us, false, fc);
     if (st != IBM_OK) return st;
@@ -844,7 +1087,7 @@ ibm_status autotune_t(ibm_solver* h, int* kzm_out, int* kzd_out) {
         if (kz > 2 * g.nz && kz != KZD_CHOICES[0]) continue;
         g.kzd = kz;
         float ms = time_it([&] {
-            k_divergence<T, true, false><<<zmarch_grid(g), dim3(32, 8), 0, h->stream>>>(
+            k_divergence<T, true, false, false><<<zmarch_grid(g), dim3(32, 8), 0, h->stream>>>(
                 g, us[0], us[1], us[2], h->mask, (T*)h->rhs, ix, iy, iz, fc);
         });
         if (ms < best) { best = ms; best_kzd = kz; }
@@ -866,6 +1109,15 @@ ibm_status autotune_t(ibm_solver* h, int* kzm_out, int* kzd_out) {
 }  // namespace
 
 int diag_blocks() { return DIAG_BLOCKS; }
+
+ibm_status poisson_prepare(ibm_solver* h) {
+    if (h->gp.xper) return IBM_OK;
+    const int nb = (h->gp.nx + 255) / 256;
+    if (h->prec == IBM_FP64) k_dct_twiddles<double><<<nb, 256, 0, h->stream>>>(h->gp.nx, (double*)h->twid);
+    else k_dct_twiddles<float><<<nb, 256, 0, h->stream>>>(h->gp.nx, (float*)h->twid);
+    IBM_LAUNCH_CHECK();
+    return IBM_OK;
+}
 
 
 ibm_status run_autotune(ibm_solver* h, int* kzm, int* kzd) {

@@ -22,11 +22,11 @@ class Solver:
 
     Parameters mirror the C structs: ndim, n=(nx,ny,nz), L, origin, bc_lo,
     bc_hi, precision ('fp64'|'fp32'), geom_kind, geom_params, and physics
-    nu, dt, g, bmode, flow_mode, target_flux, wall_u, no_ibm."""
+    nu, dt, g, bmode, flow_mode, target_flux, wall_u, no_ibm; inflow (x inflow/outflow)."""
 
     def __init__(self, *, ndim, n, L, origin, bc_lo, bc_hi, precision, geom_kind, geom_params, nu, dt,
                  g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0, wall_u=(0.0, 0.0, 0.0), no_ibm=False,
-                 device="cuda", stream=None):
+                 inflow=(0.0, 0.0, 0.0), device="cuda", stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("the IBM solver needs a CUDA device")
         self.device = torch.device(device)
@@ -48,6 +48,8 @@ class Solver:
             gd.bc_lo[d] = int(bc_lo[d])
             gd.bc_hi[d] = int(bc_hi[d])
         gd.precision = IBM_FP64 if precision == "fp64" else IBM_FP32
+        for d in range(3):
+            gd.inflow[d] = float(inflow[d])
         self.grid = gd
         geo = ibm_geom_desc()
         geo.kind = int(geom_kind)
@@ -82,7 +84,8 @@ class Solver:
         return cls(ndim=case.ndim, n=case.n, L=case.L, origin=case.origin, bc_lo=case.bc_lo, bc_hi=case.bc_hi,
                    precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,
                    nu=case.nu, dt=case.dt, g=case.g, bmode=case.bmode, flow_mode=case.flow_mode,
-                   target_flux=case.target_flux, wall_u=case.wall_u, no_ibm=no_ibm, **kw)
+                   target_flux=case.target_flux, wall_u=case.wall_u, no_ibm=no_ibm,
+                   inflow=getattr(case, "inflow", (0.0, 0.0, 0.0)), **kw)
 
     def set_physics(self, *, nu, dt, g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0,
                     wall_u=(0.0, 0.0, 0.0), no_ibm=False):

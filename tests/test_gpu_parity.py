@@ -19,7 +19,7 @@ from inputs import (small_case, channel_c1, couette_case, wavy_c3, pipe_case, in
                     B_EULER, B_TAYLOR2, GEOM_NONE)
 from oracle import OracleSolver, solve_spectral  # noqa: E402
 
-CASES = ["channel2d", "wavy3d", "sphere3d", "cylinder2d"]
+CASES = ["channel2d", "wavy3d", "sphere3d", "cylinder2d", "cylinder2d_io", "sphere3d_io"]
 TOL64 = 1e-12
 
 
@@ -352,3 +352,27 @@ def test_tma_and_register_momentum_forms_agree(precision):
     tol = TOL64 if precision == "fp64" else 1e-5
     for c in range(3):
         assert _rel(o, runs[0][0][c], runs[1][0][c], c) < tol, c
+
+
+@pytest.mark.parametrize("name", ["cylinder2d_io", "sphere3d_io"])
+def test_inflow_outflow_faces_and_balance_match_oracle(name):
+    """Inflow / convective outflow: the outflow face values (boundary points the parity helper
+    skips) match the oracle to 1e-12 after full steps, their flux equals the inflow flux, and
+    the divergence with the inflow face is round-off."""
+    case = small_case(name)
+    g, o = _pair(case)
+    g.project()
+    o.project()
+    for _ in range(case.steps):
+        g.step(1)
+        o.step(1)
+    ug, _ = g.state()
+    fl = o.cls.outflow_fluid[..., 0]
+    ref = o.u[0][..., -1]
+    got = ug[0][..., -1]
+    assert np.abs(got[fl] - ref[fl]).max() <= TOL64 * np.abs(ref[fl]).max()
+    assert np.all(got[~fl] == 0.0)
+    q_in = case.inflow[0] * np.count_nonzero(o.cls.inflow_fluid)
+    assert abs(got[fl].sum() - q_in) < 1e-12 * q_in
+    d = g.diagnostics()
+    assert d["div_linf"] < 1e-11 * case.inflow[0] / min(o.grid.d[:o.grid.ndim])
