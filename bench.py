@@ -6,7 +6,7 @@ rate (see inputs.configs.wavy_c3).  A "step" is one full RK3 time step: three
 substages, each a momentum predictor with the implicit IBM division followed
 by the projection.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c3s|c3_fp64|c1|c2] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c3s|c3_fp64|c1|c2|c2_fp64|c2_periodic] [--impl reference]
 
 One JSON line on stdout (rank 0).  `value` is cells x steps / time over all
 ranks (replicas: every rank advances its own copy of the workload, no
@@ -73,7 +73,7 @@ def measured_peaks() -> dict:
 
 
 def workload(name: str):
-    from inputs import wavy_c3, channel_c1, cylinder_c2
+    from inputs import wavy_c3, channel_c1, cylinder_c2, cylinder_c2_io
     if name == "c3":
         return wavy_c3(precision="fp32")
     if name == "c3_fp64":
@@ -82,7 +82,11 @@ def workload(name: str):
         return wavy_c3(precision="fp32", n=(384, 256, 64))
     if name == "c1":
         return channel_c1(precision="fp64")
-    if name == "c2":
+    if name == "c2":         # uniform inflow, convective outflow, free-slip lateral walls
+        return cylinder_c2_io(re=100.0, precision="fp32")
+    if name == "c2_fp64":
+        return cylinder_c2_io(re=100.0, precision="fp64")
+    if name == "c2_periodic":  # the periodic-x stand-in with a constant flow rate
         return cylinder_c2(re=100.0, precision="fp32")
     raise SystemExit(f"unknown workload {name}")
 

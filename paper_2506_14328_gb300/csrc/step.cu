@@ -301,7 +301,7 @@ __device__ __forceinline__ void tridiag_fp32(const GridP& g, float2* spec, const
     }
 }
 
-// FP64 sweep of one system by a whole warp (ny <= 32 * TW_ROWS).  Both
+// FP64 sweep of one system by a whole warp (ny <= 32 * TW_ROWS rows per lane).  Both
 // recurrences are first order and affine,
 //   forward  e_j = w_j (d_j - e_{j-1})        (e_{-1} = 0)
 //   backward x_j = e_j - w_j x_{j+1}          (x_{ny} = 0),
@@ -310,9 +310,9 @@ __device__ __forceinline__ void tridiag_fp32(const GridP& g, float2* spec, const
 // like the recurrence itself), and each lane replays its rows from the value
 // handed in.  The dependent FP64 chain is about 2 (rows per lane + 5) long
 // instead of 2 ny.  Real and imaginary parts go through together.
-constexpr int TW_ROWS = 8;
+constexpr int TW_ROWS = 32;   // rows per lane at most: the warp path covers ny <= 1024
 
-template <typename C>
+template <typename C, int TW_ROWS>
 __device__ __forceinline__ void tridiag_warp64(const GridP& g, C* spec, const double* __restrict__ piv,
                                                long long base, double scale, bool zero_mode) {
     constexpr bool F32 = sizeof(C) == sizeof(float2);
@@ -424,21 +424,22 @@ __device__ __forceinline__ void tridiag_warp64(const GridP& g, C* spec, const do
 // One warp per block; `order` lists the systems (kz * nxh + kx) with every
 // FP64 system first, so the scarce FP64 pipes of all SMs share the low modes.
 // FP64 systems take two threads (real and imaginary part), FP32 systems one.
-template <typename C>
+// R: rows per lane of the warp-per-system FP64 path (ny <= 32 R); 0 when ny > 32 * TW_ROWS.
+template <typename C, int R>
 __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, const double* __restrict__ piv,
                                                 const float* __restrict__ piv32, const int* __restrict__ order,
                                                 int n64, int nsys, double scale) {
-    if (g.ny <= 32 * TW_ROWS) {
+    if constexpr (R > 0) {
         // one warp (block) per FP64 system
         if ((int)blockIdx.x < n64) {
             const int sys = order[blockIdx.x];
             const int kx = sys % g.nxh, kz = sys / g.nxh;
             const long long base = (long long)kz * g.ny * g.nxh + kx;
-            tridiag_warp64<C>(g, spec, piv, base, scale, kx == 0 && kz == 0);
+            tridiag_warp64<C, R>(g, spec, piv, base, scale, kx == 0 && kz == 0);
             return;
         }
     }
-    const int nb64 = g.ny <= 32 * TW_ROWS ? n64 : (2 * n64 + 31) / 32;
+    const int nb64 = R > 0 ? n64 : (2 * n64 + 31) / 32;
     if ((int)blockIdx.x < nb64) {
         const int t = blockIdx.x * 32 + threadIdx.x;
         if (t >= 2 * n64) return;
@@ -842,12 +843,22 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
     const int nb64 = g.ny <= 32 * TW_ROWS ? h->n64 : (2 * h->n64 + 31) / 32;
     const int nblk = nb64 + (nsys - h->n64 + 31) / 32;
     timer_begin(h, "tridiag", &t);
-    if (h->prec == IBM_FP64)
-        k_tridiag<double2><<<nblk, 32, 0, h->stream>>>(g, (double2*)h->spec, (double2*)h->spec, h->pivots,
-                                                       h->pivots32, h->sys_order, h->n64, nsys, scale);
-    else
-        k_tridiag<float2><<<nblk, 32, 0, h->stream>>>(g, (float2*)h->spec, (double2*)h->dtemp, h->pivots,
-                                                      h->pivots32, h->sys_order, h->n64, nsys, scale);
+    // rows per lane of the warp path, rounded up to a compiled size
+#define IBM_TRIDIAG(RR)                                                                                          \
+    do {                                                                                                         \
+        if (h->prec == IBM_FP64)                                                                                 \
+            k_tridiag<double2, RR><<<nblk, 32, 0, h->stream>>>(g, (double2*)h->spec, (double2*)h->spec, h->pivots, \
+                                                               h->pivots32, h->sys_order, h->n64, nsys, scale);  \
+        else                                                                                                     \
+            k_tridiag<float2, RR><<<nblk, 32, 0, h->stream>>>(g, (float2*)h->spec, (double2*)h->dtemp, h->pivots,  \
+                                                              h->pivots32, h->sys_order, h->n64, nsys, scale);   \
+    } while (0)
+    if (g.ny <= 32 * 8) IBM_TRIDIAG(8);
+    else if (g.ny <= 32 * 16) IBM_TRIDIAG(16);
+    else if (g.ny <= 32 * 24) IBM_TRIDIAG(24);
+    else if (g.ny <= 32 * 32) IBM_TRIDIAG(32);
+    else IBM_TRIDIAG(0);
+#undef IBM_TRIDIAG
     IBM_LAUNCH_CHECK();
     timer_end(h, t, "tridiag");
     timer_begin(h, "fft_inverse", &t);

@@ -228,7 +228,7 @@ def test_checkpoint_resume_is_bitwise():
     assert g2.diagnostics()["step"] == 4
 
 
-@pytest.mark.parametrize("name", ["channel2d", "wavy3d", "sphere3d"])
+@pytest.mark.parametrize("name", ["channel2d", "wavy3d", "sphere3d", "cylinder2d_io", "sphere3d_io"])
 def test_fp32_error_against_fp64(name):
     """FP32 momentum / FP32 FFT / FP64 tridiagonal against the FP64 path after the case's steps."""
     case = small_case(name)
