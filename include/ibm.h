@@ -74,7 +74,11 @@ enum {
     IBM_GEOM_SPHERE = 3,    /* param = {xc, yc, zc, R, s}                                    */
     IBM_GEOM_SINE_WALL = 4, /* param = {y0, A, lam, ytop}: fluid for
                                y0 + A sin(2 pi x/lam) < y < ytop; the wavy wall moves         */
-    IBM_GEOM_TUBES = 5,     /* reserved (IBM_E_UNSUPPORTED)                                   */
+    IBM_GEOM_TUBES = 5,     /* union of tubes: data = {ntubes, npts, then per tube npts points
+                             * (x, y, z, r)}, ntubes <= 12, 2 <= npts <= 32; fluid inside.
+                             * phi = min over tubes and segments of |X - C| - r(t), with C the
+                             * projection of X on the segment, t in [0,1] its position and r
+                             * interpolated linearly between the segment's end radii        */
     IBM_GEOM_SAMPLED = 6    /* reserved (IBM_E_UNSUPPORTED)                                   */
 };
 /* B(x) of Eq. (Bexpr), x = lambda c_k dt */
@@ -109,6 +113,9 @@ typedef struct {
     int kind;           /* IBM_GEOM_* */
     int nparam;         /* number of valid entries in param */
     double param[32];   /* kind-specific parameters (see the enum) */
+    const double* data; /* IBM_GEOM_TUBES: host array of ndata doubles (see the enum), read at
+                         * setup; NULL for the other kinds */
+    int ndata;
 } ibm_geom_desc;
 
 typedef struct {

@@ -21,6 +21,10 @@ Level sets (parameters as in include/ibm.h):
   SPHERE    [xc, yc, zc, R, s]: phi = s((x-xc)^2 + (y-yc)^2 + (z-zc)^2 - R^2)
             s = +1: fluid inside (pipe);  s = -1: fluid outside (body)
   SINE_WALL [y0, A, lam, ytop]: y_w = y0 + A sin(2 pi (x/lam)); phi = max(y_w - y, y - ytop)
+  TUBES     [ntubes, npts, then per tube npts points (x, y, z, r)]: a union of tubes
+            along polylines; phi = min over tubes and segments [A, B] of |X - C| - r(t),
+            C = A + t (B - A) the projection of X clamped to t in [0, 1], r(t) linear
+            between the end radii (fluid inside).  No closed form for delta: bisection.
   SAMPLED   phi given at the points; delta by linear interpolation
             delta = Delta phi_P / (phi_P - phi_Q)
 """
@@ -39,7 +43,8 @@ class LevelSet:
         self.p = tuple(float(v) for v in params)
         self.samples = samples  # SAMPLED: list of 3 arrays of shape (nz, ny, nx)
         if self.kind == TUBES:
-            raise NotImplementedError("tube-union geometry is not in this oracle")
+            nt, npts = int(self.p[0]), int(self.p[1])
+            self.tubes = np.asarray(self.p[2:2 + nt * npts * 4], dtype=np.float64).reshape(nt, npts, 4)
 
     # phi at arbitrary broadcastable coordinates (FP64, evaluated in the written order)
     def phi(self, x, y, z):
@@ -64,7 +69,47 @@ class LevelSet:
             y0, A, lam, ytop = p[0], p[1], p[2], p[3]
             yw = y0 + A * np.sin(TWO_PI * (x / lam))
             return np.maximum(yw - y, y - ytop) + 0.0 * z
+        if k == TUBES:
+            x, y, z = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64),
+                                          np.asarray(z, dtype=np.float64))
+            if x.size == 1:
+                return self._tubes_point(float(x.ravel()[0]), float(y.ravel()[0]), float(z.ravel()[0]))
+            best = np.full(x.shape, 1e300)
+            for tube in self.tubes:
+                for a, b in zip(tube[:-1], tube[1:]):
+                    ex, ey, ez = b[0] - a[0], b[1] - a[1], b[2] - a[2]
+                    ee = (ex * ex + ey * ey) + ez * ez
+                    wx, wy, wz = x - a[0], y - a[1], z - a[2]
+                    we = (wx * ex + wy * ey) + wz * ez
+                    t = np.minimum(np.maximum(we / ee, 0.0), 1.0)
+                    dx = x - (a[0] + t * ex)
+                    dy = y - (a[1] + t * ey)
+                    dz = z - (a[2] + t * ez)
+                    dist = np.sqrt((dx * dx + dy * dy) + dz * dz)
+                    r = a[3] + t * (b[3] - a[3])
+                    best = np.minimum(best, dist - r)
+            return best
         raise ValueError(f"phi not defined for kind {k}")
+
+    def _tubes_point(self, x: float, y: float, z: float) -> float:
+        """phi of TUBES at one point: the same per-segment arithmetic as phi, with the
+        segments of all tubes taken as one array."""
+        if not hasattr(self, "_seg"):
+            a = self.tubes[:, :-1, :].reshape(-1, 4)
+            b = self.tubes[:, 1:, :].reshape(-1, 4)
+            self._seg = (a, b)
+        a, b = self._seg
+        ex, ey, ez = b[:, 0] - a[:, 0], b[:, 1] - a[:, 1], b[:, 2] - a[:, 2]
+        ee = (ex * ex + ey * ey) + ez * ez
+        wx, wy, wz = x - a[:, 0], y - a[:, 1], z - a[:, 2]
+        we = (wx * ex + wy * ey) + wz * ez
+        t = np.minimum(np.maximum(we / ee, 0.0), 1.0)
+        dx = x - (a[:, 0] + t * ex)
+        dy = y - (a[:, 1] + t * ey)
+        dz = z - (a[:, 2] + t * ez)
+        dist = np.sqrt((dx * dx + dy * dy) + dz * dz)
+        r = a[:, 3] + t * (b[:, 3] - a[:, 3])
+        return float(np.min(dist - r))
 
     def phi_points(self, grid, c: int) -> np.ndarray:
         if self.kind == SAMPLED:
@@ -84,6 +129,50 @@ class LevelSet:
             if dl is None:
                 dl = self._bisect(P, d, s, Delta)
         return min(max(dl, 1e-12 * Delta), Delta)
+
+    def delta_many(self, P, d, s, Delta, phiP, phiQ) -> np.ndarray:
+        """delta for many arms at once (P: (m, 3)); each value equals delta(P[q], d[q], ...):
+        the closed forms and the sampled interpolation arm by arm, the bisection for all
+        remaining arms together (the same steps, stopped arm by arm)."""
+        m = len(Delta)
+        out = np.zeros(m)
+        todo = []
+        for q in range(m):
+            if phiQ[q] == 0.0:
+                out[q] = Delta[q]
+            elif self.kind == SAMPLED:
+                out[q] = Delta[q] * (phiP[q] / (phiP[q] - phiQ[q]))
+            else:
+                dl = self._closed_form(list(P[q]), int(d[q]), int(s[q]), float(Delta[q]))
+                if dl is None:
+                    todo.append(q)
+                else:
+                    out[q] = dl
+        if todo:
+            t = np.array(todo)
+            out[t] = self._bisect_many(P[t], d[t], s[t], Delta[t])
+        return np.minimum(np.maximum(out, 1e-12 * Delta), Delta)
+
+    def _bisect_many(self, P, d, s, Delta):
+        """_bisect for many arms: every arm takes the same midpoints and stops where its
+        own bracket cannot shrink."""
+        m = len(Delta)
+        lo = np.zeros(m)
+        hi = np.array(Delta, dtype=np.float64)
+        active = np.ones(m, dtype=bool)
+        rows = np.arange(m)
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            active &= ~((mid <= lo) | (mid >= hi))
+            if not active.any():
+                break
+            a = rows[active]
+            Q = P[a].copy()
+            Q[np.arange(len(a)), d[a]] = P[a, d[a]] + s[a] * mid[a]
+            inside = np.asarray(self.phi(Q[:, 0], Q[:, 1], Q[:, 2])) < 0.0
+            lo[a[inside]] = mid[a[inside]]
+            hi[a[~inside]] = mid[a[~inside]]
+        return hi
 
     def _closed_form(self, P, d, s, Delta):
         k, p = self.kind, self.p

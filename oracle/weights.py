@@ -61,6 +61,9 @@ class Weights:
 
 
 def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm: bool = False) -> Weights:
+    """lambda and the wall source at every IBM point, arms taken in the order d = x, y, z
+    and s = +1, -1 (the distance of every crossed arm comes from levelset.delta_many,
+    which gives each arm the same value as levelset.delta)."""
     lam, src, lam_list, src_list = [], [], [], []
     nx, ny, nz = grid.n
     for c in range(3):
@@ -69,19 +72,18 @@ def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm
         lst = cls.lists[c]
         ll = np.zeros(len(lst))
         sl = np.zeros(len(lst))
-        if c < grid.ncomp and not no_ibm:
+        if c < grid.ncomp and not no_ibm and len(lst):
             ext = cls.external[c]
             phi = cls.phi[c]
+            # pass 1: the crossed arms of every IBM point, in accumulation order
+            arms = []          # (m, P, d, s, Delta, phiP, phiQ)
             for m, lin in enumerate(lst):
                 i = lin % nx
                 j = (lin // nx) % ny
                 k = lin // (nx * ny)
                 idx = [i, j, k]
                 P = [grid.origin[d] + (idx[d] + (1.0 if d == c else 0.5)) * grid.d[d] for d in range(3)]
-                lam_p = 0.0
-                src_p = 0.0
                 for d in range(grid.ndim):
-                    Dd = grid.d[d]
                     for s in (+1, -1):
                         q = list(idx)
                         q[d] = q[d] + s
@@ -92,14 +94,28 @@ def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm
                         qk = (q[2], q[1], q[0])
                         if not ext[qk]:
                             continue
-                        delta = levelset.delta(P, d, s, Dd, float(phi[k, j, i]), float(phi[qk]))
-                        lam_p += nu * (Dd - delta) / (delta * Dd * Dd)
-                        uw = wall_u[c] * levelset.wall_velocity_factor(d, s)
-                        src_p += nu * uw / (delta * Dd)
-                ll[m] = lam_p
-                sl[m] = src_p
-                L[k, j, i] = lam_p
-                S[k, j, i] = src_p
+                        arms.append((m, P, d, s, grid.d[d], float(phi[k, j, i]), float(phi[qk])))
+            deltas = levelset.delta_many(np.array([a[1] for a in arms]).reshape(-1, 3),
+                                         np.array([a[2] for a in arms], dtype=int),
+                                         np.array([a[3] for a in arms], dtype=int),
+                                         np.array([a[4] for a in arms], dtype=np.float64),
+                                         np.array([a[5] for a in arms], dtype=np.float64),
+                                         np.array([a[6] for a in arms], dtype=np.float64))
+            # pass 2: lambda and the source, summed arm by arm
+            lam_p = np.zeros(len(lst))
+            src_p = np.zeros(len(lst))
+            for (m, P, d, s, Dd, _, _), delta in zip(arms, deltas):
+                lam_p[m] += nu * (Dd - delta) / (delta * Dd * Dd)
+                uw = wall_u[c] * levelset.wall_velocity_factor(d, s)
+                src_p[m] += nu * uw / (delta * Dd)
+            for m, lin in enumerate(lst):
+                i = lin % nx
+                j = (lin // nx) % ny
+                k = lin // (nx * ny)
+                ll[m] = lam_p[m]
+                sl[m] = src_p[m]
+                L[k, j, i] = lam_p[m]
+                S[k, j, i] = src_p[m]
         lam.append(L)
         src.append(S)
         lam_list.append(ll)

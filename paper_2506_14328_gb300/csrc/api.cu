@@ -316,8 +316,16 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     int kind = geom->kind;
     int need = kind == IBM_GEOM_PLANES ? 2 : kind == IBM_GEOM_CYLINDER ? 4 : kind == IBM_GEOM_SPHERE ? 5
              : kind == IBM_GEOM_SINE_WALL ? 4 : 0;
-    if (kind == IBM_GEOM_TUBES || kind == IBM_GEOM_SAMPLED)
-        return ibm_set_error(IBM_E_UNSUPPORTED, "geometry kind not built");
+    if (kind == IBM_GEOM_SAMPLED) return ibm_set_error(IBM_E_UNSUPPORTED, "geometry kind not built");
+    if (kind == IBM_GEOM_TUBES) {
+        if (!geom->data || geom->ndata < 2) return ibm_set_error(IBM_E_INVALID, "tubes: data is missing");
+        const double nt = geom->data[0], np = geom->data[1];
+        if (!(nt >= 1 && nt <= TUBE_MAX && nt == (int)nt) || !(np >= 2 && np <= TUBE_PTS && np == (int)np))
+            return ibm_set_error(IBM_E_INVALID, "tubes: need 1..12 tubes of 2..32 points");
+        if (geom->ndata != 2 + (int)nt * (int)np * 4) return ibm_set_error(IBM_E_INVALID, "tubes: ndata mismatch");
+        for (int q = 2; q < geom->ndata; ++q)
+            if (!std::isfinite(geom->data[q])) return ibm_set_error(IBM_E_INVALID, "tubes: non-finite data");
+    }
     if (kind < IBM_GEOM_NONE || kind > IBM_GEOM_SAMPLED) return ibm_set_error(IBM_E_INVALID, "bad geometry kind");
     if (geom->nparam < need) return ibm_set_error(IBM_E_INVALID, "too few geometry parameters");
     if (kind == IBM_GEOM_SINE_WALL && !(geom->param[2] != 0.0))
@@ -340,6 +348,15 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     h->gp = g;
     h->geo.kind = kind;
     for (int q = 0; q < 8; ++q) h->geo.p[q] = q < geom->nparam ? geom->param[q] : 0.0;
+    h->geo.ntubes = h->geo.npts = 0;
+    std::memset(h->geo.tube, 0, sizeof(h->geo.tube));
+    if (kind == IBM_GEOM_TUBES) {
+        h->geo.ntubes = (int)geom->data[0];
+        h->geo.npts = (int)geom->data[1];
+        std::memcpy(h->geo.tube, geom->data + 2, (size_t)h->geo.ntubes * h->geo.npts * 4 * sizeof(double));
+    }
+    h->geom.data = nullptr;   // the caller's array is not kept
+    h->geom.ndata = 0;
     h->prec = grid->precision;
     h->esz = grid->precision == IBM_FP64 ? 8 : 4;
     h->N = g.N;

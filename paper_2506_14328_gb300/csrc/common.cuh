@@ -31,9 +31,15 @@ struct GridP {
     int kzd;                // z planes one divergence / correction block marches (autotuned)
 };
 
+// Union of tubes (IBM_GEOM_TUBES): polylines of (x, y, z, r) points, at most
+// TUBE_MAX tubes of TUBE_PTS points; passed by value with the other parameters.
+constexpr int TUBE_MAX = 12, TUBE_PTS = 32;
+
 struct GeomP {
     int kind;
     double p[8];
+    int ntubes, npts;
+    double tube[TUBE_MAX * TUBE_PTS * 4];
 };
 
 // The IBM coefficients of one stage for one component: indexed by list

@@ -39,6 +39,31 @@ __device__ double phi_at(const GeomP& g, double x, double y, double z) {
             double yw = __dadd_rn(p[0], __dmul_rn(p[1], sin(__dmul_rn(TWO_PI, __ddiv_rn(x, p[2])))));
             return fmax(__dsub_rn(yw, y), __dsub_rn(y, p[3]));
         }
+        case IBM_GEOM_TUBES: {
+            // min over tubes and segments of |X - C| - r(t): C the projection of X on the
+            // segment [A, B], t in [0,1] its position, r linear between the end radii
+            double best = 1e300;
+            for (int tb = 0; tb < g.ntubes; ++tb) {
+                const double* q = g.tube + tb * g.npts * 4;
+                for (int sgi = 0; sgi + 1 < g.npts; ++sgi) {
+                    const double* a = q + 4 * sgi;
+                    const double* b = a + 4;
+                    const double ex = __dsub_rn(b[0], a[0]), ey = __dsub_rn(b[1], a[1]), ez = __dsub_rn(b[2], a[2]);
+                    const double ee = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+                    const double wx = __dsub_rn(x, a[0]), wy = __dsub_rn(y, a[1]), wz = __dsub_rn(z, a[2]);
+                    const double we = __dadd_rn(__dadd_rn(__dmul_rn(wx, ex), __dmul_rn(wy, ey)), __dmul_rn(wz, ez));
+                    const double t = fmin(fmax(__ddiv_rn(we, ee), 0.0), 1.0);
+                    const double dx = __dsub_rn(x, __dadd_rn(a[0], __dmul_rn(t, ex)));
+                    const double dy = __dsub_rn(y, __dadd_rn(a[1], __dmul_rn(t, ey)));
+                    const double dz = __dsub_rn(z, __dadd_rn(a[2], __dmul_rn(t, ez)));
+                    const double dist = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                                             __dmul_rn(dz, dz)));
+                    const double r = __dadd_rn(a[3], __dmul_rn(t, __dsub_rn(b[3], a[3])));
+                    best = fmin(best, __dsub_rn(dist, r));
+                }
+            }
+            return best;
+        }
         default:
             return -1.0;
     }

@@ -6,6 +6,8 @@ fields are plain numpy arrays of shape (nz, ny, nx).
 """
 from __future__ import annotations
 
+import ctypes as C
+
 import numpy as np
 import torch
 
@@ -53,9 +55,15 @@ class Solver:
         self.grid = gd
         geo = ibm_geom_desc()
         geo.kind = int(geom_kind)
-        geo.nparam = len(geom_params)
-        for q, v in enumerate(geom_params):
-            geo.param[q] = float(v)
+        if geo.kind == 5:      # IBM_GEOM_TUBES: the parameters are the tube data array
+            self._geom_data = (C.c_double * len(geom_params))(*[float(v) for v in geom_params])
+            geo.data = C.cast(self._geom_data, C.POINTER(C.c_double))
+            geo.ndata = len(geom_params)
+            geo.nparam = 0
+        else:
+            geo.nparam = len(geom_params)
+            for q, v in enumerate(geom_params):
+                geo.param[q] = float(v)
         self.geom = geo
         # every torch operation of this solver runs on its own stream, so setting up
         # one solve never waits for work that other solves have on the device
