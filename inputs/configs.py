@@ -146,6 +146,26 @@ def wavy_c3(precision: str = "fp32", steps: int = 10, n=(384, 256, 256), seed: i
                 seed=seed)
 
 
+def airway_c4(precision: str = "fp32", steps: int = 10, n=(512, 384, 256), seed: int = 0,
+              re: float = 1000.0) -> Case:
+    """3D airway-like duct: a seeded union of 6-12 tubes (radius 0.05-0.2, seeded
+    Catmull-Rom centre lines, radius bumps of 10%) in the box [0,1]x[0,0.75]x[0,0.5].
+    Uniform inflow U = 1 on the fluid part of x = 0, convective outflow at x = 1; the
+    y and z faces lie in the solid (no-slip y walls, periodic z).  Re = U D / nu on the
+    inlet diameter D; dt at a Courant number 0.5 for a peak speed 2U."""
+    from .generators import tube_union
+    nx, ny, nz = n
+    L = (1.0, 0.75, 0.5)
+    geo = tube_union(seed, L=L)
+    d_in = 2.0 * geo[2 + 3]              # twice the trunk's radius at its first point
+    dx = L[0] / nx
+    return Case(name=f"c4_airway_{nx}x{ny}x{nz}", ndim=3, n=(nx, ny, nz), L=L, origin=(0.0, 0.0, 0.0),
+                bc_lo=(BC_INFLOW, BC_NOSLIP, BC_PERIODIC), bc_hi=(BC_OUTFLOW, BC_NOSLIP, BC_PERIODIC),
+                geom_kind=GEOM_TUBES, geom_params=geo, nu=1.0 * d_in / re, dt=0.25 * dx,
+                inflow=(1.0, 0.0, 0.0), precision=precision, steps=steps,
+                init={"kind": "uniform", "U": 1.0}, seed=seed)
+
+
 def pipe_case(N: int = 40, R: float = 1.0, nu: float = 1.0, nz: int = 1) -> Case:
     """Straight circular pipe along z on a 2.5R square of N x N cells (Sec. 2.3 example)."""
     L = 2.5 * R
@@ -179,6 +199,10 @@ def small_case(kind: str, precision: str = "fp64", seed: int = 0) -> Case:
                     geom_params=(0.61, 0.47, 0.52, 0.23, -1.0), nu=0.01, dt=0.004, inflow=(0.8, 0.0, 0.0),
                     precision=precision, steps=2, seed=seed,
                     init={"kind": "uniform_noise", "U": 0.8, "noise": 0.1})
+    if kind == "tubes3d_io":
+        c = airway_c4(precision=precision, steps=2, n=(64, 48, 32), seed=seed)
+        return c.with_(name="tubes3d_io_64x48x32", nu=0.01, dt=0.002,
+                       init={"kind": "uniform_noise", "U": 1.0, "noise": 0.1})
     if kind == "sphere3d":
         return Case(name="sphere3d_48x30x26", ndim=3, n=(48, 30, 26), L=(1.6, 1.0, 1.0),
                     origin=(0.0, 0.0, 0.0), bc_lo=(BC_PERIODIC, BC_FREESLIP, BC_PERIODIC),

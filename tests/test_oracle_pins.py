@@ -488,7 +488,7 @@ def test_uniform_stream_is_a_fixed_point_of_an_inflow_outflow_channel():
     assert np.abs(o.p).max() < 1e-10
 
 
-@pytest.mark.parametrize("name", ["cylinder2d_io", "sphere3d_io"])
+@pytest.mark.parametrize("name", ["cylinder2d_io", "sphere3d_io", "tubes3d_io"])
 def test_inflow_outflow_steps_are_solenoidal_and_balanced(name):
     """After the projection the discrete divergence (with the inflow face) is round-off at
     every cell, and the fluid outflow flux equals the inflow flux."""
@@ -522,3 +522,78 @@ def test_inflow_outflow_cylinder_stays_mirror_symmetric():
     # y mirror: u(j) <-> u(ny-1-j); v sits on +y faces, so v(j) <-> -v(ny-2-j), v(ny-1) is the wall face
     assert np.abs(u - u[::-1, :]).max() < 1e-12 * np.abs(u).max()
     assert np.abs(v[:-1] + v[:-1][::-1, :]).max() < 1e-12 * np.abs(u).max()
+
+
+# ---- tube-union geometry ------------------------------------------------------------------
+
+def test_straight_tube_equals_the_circular_pipe():
+    """One straight tube of constant radius R along z is the pipe x^2 + y^2 < R^2: the same
+    fluid points, IBM points and (bisection against closed form) the same lambda."""
+    from inputs import GEOM_TUBES
+    pipe = pipe_case(N=29, nz=3)
+    tube = pipe.with_(geom_kind=GEOM_TUBES, geom_params=(1.0, 2.0, 0.0, 0.0, -5.0, 1.0, 0.0, 0.0, 5.0, 1.0))
+    ga, _, ca, wa = _setup(pipe)
+    gb, _, cb, wb = _setup(tube)
+    for c in range(3):
+        assert np.array_equal(ca.internal[c], cb.internal[c])
+        assert np.array_equal(ca.lists[c], cb.lists[c])
+        if len(wa.lam_list[c]):
+            scale = np.abs(wa.lam_list[c]).max()
+            assert np.abs(wa.lam_list[c] - wb.lam_list[c]).max() < 1e-9 * scale
+    assert sum(len(ca.lists[c]) for c in range(2)) > 100
+
+
+def test_tube_phi_matches_a_brute_force_nearest_point_search():
+    """phi of a seeded tube union against a search over 4000 points per segment: the
+    nearest sampled centre-line point S of every segment, |X - S| - r(S), minimised over
+    segments and tubes.  The sampling error is below half a sample spacing."""
+    from inputs import GEOM_TUBES, tube_union
+    geo = tube_union(3)
+    ls = LevelSet(GEOM_TUBES, geo)
+    nt, npts = int(geo[0]), int(geo[1])
+    tubes = np.array(geo[2:]).reshape(nt, npts, 4)
+    rng = np.random.default_rng(11)
+    X = rng.random((300, 3)) * np.array([1.0, 0.75, 0.5])
+    # half the points near the centre lines, where the clamping and the radius matter
+    near = tubes[rng.integers(nt, size=150), rng.integers(npts, size=150), :3]
+    X[:150] = near + 0.08 * (rng.random((150, 3)) - 0.5)
+    K = 4000
+    t = (np.arange(K) + 0.5) / K
+    best = np.full(len(X), np.inf)
+    seglen = 0.0
+    for tb in tubes:
+        for a, b in zip(tb[:-1], tb[1:]):
+            S = a[None, :3] + t[:, None] * (b[:3] - a[:3])[None, :]
+            r = a[3] + t * (b[3] - a[3])
+            d2 = ((X[:, None, :] - S[None, :, :]) ** 2).sum(axis=2)
+            kmin = np.argmin(d2, axis=1)
+            best = np.minimum(best, np.sqrt(d2[np.arange(len(X)), kmin]) - r[kmin])
+            seglen = max(seglen, np.linalg.norm(b[:3] - a[:3]) + abs(b[3] - a[3]))
+    phi = np.asarray(ls.phi(X[:, 0], X[:, 1], X[:, 2]))
+    assert np.abs(phi - best).max() < 2.0 / K * seglen
+    assert (phi < 0).sum() > 50 and (phi > 0).sum() > 50
+    # the single-point path agrees with the array path bit for bit
+    for q in range(0, 300, 37):
+        assert float(ls.phi(X[q, 0], X[q, 1], X[q, 2])) == phi[q]
+
+
+def test_tube_union_trunk_crosses_the_x_faces_and_the_other_faces_are_solid():
+    """The generated airway: fluid on the x = 0 and x = 1 faces (the trunk's ends), solid on
+    the y and z faces of the box, and 6-12 tubes with radii in 0.05-0.2 up to the 10% bumps."""
+    from inputs import GEOM_TUBES, tube_union
+    for seed in range(3):
+        geo = tube_union(seed)
+        nt, npts = int(geo[0]), int(geo[1])
+        assert 6 <= nt <= 12
+        r = np.array(geo[2:]).reshape(nt, npts, 4)[..., 3]
+        assert r.min() >= 0.9 * 0.05 - 1e-12 and r.max() <= 1.1 * 0.2 + 1e-12
+        ls = LevelSet(GEOM_TUBES, geo)
+        s = np.linspace(0.0, 1.0, 41)
+        a, b = np.meshgrid(s, s, indexing="ij")
+        a, b = a.ravel(), b.ravel()
+        for x in (0.0, 1.0):
+            assert (np.asarray(ls.phi(np.full_like(a, x), 0.75 * a, 0.5 * b)) < 0).any()
+        for y in (0.0, 0.75):
+            assert (np.asarray(ls.phi(a, np.full_like(a, y), 0.5 * b)) > 0).all()
+        for z in (0.0, 0.5):
+            assert (np.asarray(ls.phi(a, 0.75 * b, np.full_like(a, z))) > 0).all()
