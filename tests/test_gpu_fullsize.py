@@ -1,6 +1,8 @@
-"""The momentum predictor at the full 384 x 256 x 256 wavy-channel size, in the launch
-configuration the benchmark times (FP32, TMA form, default z-chunk), against the FP64
-oracle on sampled points.
+"""The momentum predictor at the full 384 x 256 x 256 wavy-channel and 512 x 384 x 256
+airway sizes, in the launch configuration the benchmark times (FP32, default z-chunk;
+the TMA form on the periodic channel, the register form on the inflow/outflow duct),
+against the FP64 oracle on sampled points; on the airway also the classification byte
+and lambda of the device-built weights at the sampled points.
 
 The predictor at a point depends only on its 3 x 3 x 3 neighbourhood, its IBM weight
 and the pressure next to it, so the oracle evaluates each sample on a 7-point window
@@ -19,7 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
 
-from inputs import wavy_c3, initial_field, FLOW_FORCED, BC_PERIODIC, BC_NOSLIP  # noqa: E402
+from inputs import wavy_c3, airway_c4, initial_field, FLOW_FORCED, BC_PERIODIC, BC_NOSLIP  # noqa: E402
 from oracle import OracleSolver, Grid, LevelSet, classify  # noqa: E402
 
 R = 3   # window half-width
@@ -34,7 +36,8 @@ def _window_case(case, i, j, k):
     n = (2 * R + 1, jhi - jlo, 2 * R + 1)
     origin = (case.origin[0] + (i - R) * d[0], case.origin[1] + jlo * d[1], case.origin[2] + (k - R) * d[2])
     L = (n[0] * d[0], n[1] * d[1], n[2] * d[2])
-    w = case.with_(n=n, origin=origin, L=L, bc_lo=bc_lo, bc_hi=bc_hi, name="window")
+    # samples keep R cells from the x faces, so the window is periodic in x and sees no inflow
+    w = case.with_(n=n, origin=origin, L=L, bc_lo=bc_lo, bc_hi=bc_hi, inflow=(0.0, 0.0, 0.0), name="window")
     ii = (i - R + np.arange(n[0])) % nx
     jj = np.arange(jlo, jhi)
     kk = (k - R + np.arange(n[2])) % nz
@@ -93,3 +96,72 @@ def test_predictor_full_size_sampled_against_oracle():
             worst = max(worst, err)
             assert err < 2e-6, ((i, j, k), c, err)
     assert worst > 0.0     # FP32 arithmetic leaves a trace; an exact match would mean nothing ran
+
+
+def _airway_samples(case, ls, kzm, rng):
+    """Cells near the tube walls (|phi| < 2 cells at the centre), a few deep in the fluid,
+    a few on the 32 x 16 tile and z-chunk edges, and a few anywhere (mostly solid).  Every
+    sample keeps R cells from the x faces.  Chosen with the oracle's level set alone."""
+    nx, ny, nz = case.n
+    h = case.L[0] / nx
+    cand = np.stack([rng.integers(R, nx - R, 40000), rng.integers(ny, size=40000), rng.integers(nz, size=40000)], 1)
+    xc = (cand + 0.5) * h
+    phi = np.asarray(ls.phi(xc[:, 0], xc[:, 1], xc[:, 2]))
+    near = cand[np.abs(phi) < 2 * h]
+    deep = cand[phi < -3 * h]
+    edge = near[((near[:, 0] % 32 == 0) | (near[:, 0] % 32 == 31)) | ((near[:, 1] % 16 == 0) | (near[:, 1] % 16 == 15))
+                | ((near[:, 2] % kzm == 0) | (near[:, 2] % kzm == kzm - 1))]
+    pts = set()
+    for arr, m in ((near, 200), (deep, 30), (edge, 40), (cand, 30)):
+        for q in rng.permutation(len(arr))[:m]:
+            pts.add(tuple(int(v) for v in arr[q]))
+    return sorted(pts)
+
+
+def test_airway_full_size_sampled_against_oracle():
+    from paper_2506_14328_gb300.solver import Solver
+    from oracle import LevelSet as LS
+    case = airway_c4(precision="fp32", steps=1).with_(init={"kind": "uniform_noise", "U": 1.0, "noise": 0.1})
+    nx, ny, nz = case.n
+    f = initial_field(case)
+    f32 = {q: np.asarray(f[q], dtype=np.float32).astype(np.float64) for q in ("u", "v", "w", "p")}
+    del f
+    g = Solver.from_case(case)
+    kzm, _, tma = g.tiles()
+    assert not tma, "an inflow/outflow x runs the register form"
+    mask, lists = g.classification()
+    lam, _ = g.weights_lists()
+    g.set_state(f32["u"], f32["v"], f32["w"], f32["p"])
+    g.step(1, flags=1)                     # IBM_STEP_PREDICTOR_ONLY: u* of stage 1
+    us, _ = g.state()
+    g.close()
+    ls = LS(case.geom_kind, case.geom_params)
+    pts = _airway_samples(case, ls, kzm, np.random.default_rng(7))
+    assert len(pts) >= 200
+    umax = max(np.abs(f32[q]).max() for q in ("u", "v", "w"))
+    worst, nibm, nint = 0.0, 0, 0
+    for (i, j, k) in pts:
+        wc, (ii, jj, kk), (ci, cj, ck) = _window_case(case, i, j, k)
+        o = OracleSolver(wc)
+        # the grid spacing is a power of two, so the window's coordinates are the box's bit for bit
+        assert mask[k, j, i] == o.cls.mask[ck, cj, ci], (i, j, k)
+        sub = {q: f32[q][np.ix_(kk, jj, ii)] for q in ("u", "v", "w", "p")}
+        o.set_state(sub["u"], sub["v"], sub["w"], sub["p"])
+        o.substage(0, predictor_only=True)
+        lin = (k * ny + j) * nx + i
+        wlin = (ck * wc.n[1] + cj) * wc.n[0] + ci
+        for c in range(3):
+            if mask[k, j, i] & (16 << c):
+                pos = int(np.searchsorted(lists[c], lin))
+                wpos = int(np.searchsorted(o.cls.lists[c], wlin))
+                ref = o.w.lam_list[c][wpos]
+                assert abs(lam[c][pos] - ref) <= 1e-12 * abs(ref), ((i, j, k), c)
+                nibm += 1
+            if not o.cls.internal[c][ck, cj, ci]:
+                continue
+            nint += 1
+            err = abs(us[c][k, j, i] - o.u[c][ck, cj, ci]) / umax
+            worst = max(worst, err)
+            assert err < 2e-6, ((i, j, k), c, err)
+    assert nibm >= 80 and nint >= 300
+    assert worst > 0.0

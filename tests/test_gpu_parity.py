@@ -19,7 +19,7 @@ from inputs import (small_case, channel_c1, couette_case, wavy_c3, pipe_case, in
                     B_EULER, B_TAYLOR2, GEOM_NONE)
 from oracle import OracleSolver, solve_spectral  # noqa: E402
 
-CASES = ["channel2d", "wavy3d", "sphere3d", "cylinder2d", "cylinder2d_io", "sphere3d_io"]
+CASES = ["channel2d", "wavy3d", "sphere3d", "cylinder2d", "cylinder2d_io", "sphere3d_io", "tubes3d_io"]
 TOL64 = 1e-12
 
 
@@ -228,7 +228,7 @@ def test_checkpoint_resume_is_bitwise():
     assert g2.diagnostics()["step"] == 4
 
 
-@pytest.mark.parametrize("name", ["channel2d", "wavy3d", "sphere3d", "cylinder2d_io", "sphere3d_io"])
+@pytest.mark.parametrize("name", ["channel2d", "wavy3d", "sphere3d", "cylinder2d_io", "sphere3d_io", "tubes3d_io"])
 def test_fp32_error_against_fp64(name):
     """FP32 momentum / FP32 FFT / FP64 tridiagonal against the FP64 path after the case's steps."""
     case = small_case(name)
@@ -354,7 +354,7 @@ def test_tma_and_register_momentum_forms_agree(precision):
         assert _rel(o, runs[0][0][c], runs[1][0][c], c) < tol, c
 
 
-@pytest.mark.parametrize("name", ["cylinder2d_io", "sphere3d_io"])
+@pytest.mark.parametrize("name", ["cylinder2d_io", "sphere3d_io", "tubes3d_io"])
 def test_inflow_outflow_faces_and_balance_match_oracle(name):
     """Inflow / convective outflow: the outflow face values (boundary points the parity helper
     skips) match the oracle to 1e-12 after full steps, their flux equals the inflow flux, and
