@@ -568,9 +568,11 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
 //   N^{k-2}  32 x 16 at (i0, j0)       (stages 2 and 3; planes kbeg..kend-1)
 // Rows or columns outside the box read 0 (the copy's fill).  Periodic x is
 // completed from small wrap boxes (the last 4 / 16 columns for the block at
-// x = 0, the first ones for the block that reaches nx).  Before a plane is
-// computed its u, v, w tile is rewritten in place into the form the operator
-// reads (non-internal -> 0, ghost rows beyond a y wall, wrapped columns), and
+// x = 0, the first ones for the block that reaches nx); an inflow/outflow x
+// takes its ghost columns from the box's own first or last grid column.  Before
+// a plane is computed its u, v, w tile is rewritten in place into the form the
+// operator reads (non-internal -> 0, ghost rows beyond a y wall, wrapped or
+// ghost columns, the outflow face of u), and
 // the thread keeps its own two cells' values and masks in registers.  Plane
 // k+D-1 is requested while plane k is computed (D = 3 for FP32, 4 for FP64),
 // so two or three planes of every block are in flight without register cost.
@@ -691,9 +693,11 @@ struct TmaPt {
     int d, so, cs, mo;
     bool ghost;      // beyond a y wall: v reads 0, u and w read f * (adjacent)
     T f;
+    int xk;          // inflow/outflow x: 1 beyond the inflow face, 2 beyond the outflow face
+    bool outc;       // the u point is the outflow face (readable where the face is fluid)
 };
 
-template <typename T>
+template <typename T, bool XP>
 __device__ __forceinline__ TmaPt<T> tma_point(const GridP& g, int i0, int j0, int rx, int ry, T sig_lo, T sig_hi) {
     using L = TmaLay<T>;
     TmaPt<T> q;
@@ -704,7 +708,16 @@ __device__ __forceinline__ TmaPt<T> tma_point(const GridP& g, int i0, int j0, in
     q.ghost = j != jc;
     q.f = j < 0 ? sig_lo : (j >= g.ny ? sig_hi : T(1));
     const int i = i0 - 4 + rx;
-    if (i < 0) {                      // x = -1: the last column, from the left wrap box
+    q.xk = 0;
+    q.outc = false;
+    if (!XP) {                        // ghost columns repeat the first or last grid column
+        const int ic = i < 0 ? 0 : (i >= g.nx ? g.nx - 1 : i);
+        q.xk = i < 0 ? 1 : (i >= g.nx ? 2 : 0);
+        q.outc = i == g.nx - 1;
+        q.so = sry * L::RX + ic - i0 + 4;
+        q.cs = L::CS;
+        q.mo = L::oM + sry * L::MXB + ic - i0 + 16;
+    } else if (i < 0) {               // x = -1: the last column, from the left wrap box
         q.so = L::oWL / L::es + sry * L::WX + L::WX - 1;
         q.cs = L::WCSB / L::es;
         q.mo = L::oWML + sry * L::WMX + L::WMX - 1;
@@ -721,15 +734,22 @@ __device__ __forceinline__ TmaPt<T> tma_point(const GridP& g, int i0, int j0, in
 }
 
 // Rewrites one point in place; returns its mask byte and its three values.
-template <typename T, bool GEN>
-__device__ __forceinline__ uint32_t tma_mask_pt(unsigned char* st, const TmaPt<T>& q, T (&out)[3]) {
+// A ghost column may read a grid column that its own thread rewrites at the
+// same time: the rule below re-applies that column's mask, so the raw and the
+// rewritten value give the same result.
+template <typename T, bool GEN, bool XP>
+__device__ __forceinline__ uint32_t tma_mask_pt(unsigned char* st, const TmaPt<T>& q, T uin, T (&out)[3]) {
     using L = TmaLay<T>;
     T* f = reinterpret_cast<T*>(st);
     const uint32_t m = st[q.mo];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         T x = GEN ? f[q.so + c * q.cs] : f[q.d + c * L::CS];
-        x = ((m >> c) & 1u) ? x : T(0);
+        bool rd = (m >> c) & 1u;
+        if (!XP && GEN && c == 0 && q.outc) rd = (m & IBM_MASK_FACE) != 0;
+        x = rd ? x : T(0);
+        if (!XP && GEN && q.xk == 1) x = (c == 0) ? ((m & IBM_MASK_FACE) ? uin : T(0)) : -x;
+        else if (!XP && GEN && q.xk == 2) x = (c == 0) ? T(0) : x;
         if (GEN && q.ghost) x = (c == 1) ? T(0) : q.f * x;
         f[q.d + c * L::CS] = x;
         out[c] = x;
@@ -740,22 +760,22 @@ __device__ __forceinline__ uint32_t tma_mask_pt(unsigned char* st, const TmaPt<T
 // The operator-form pass over one stage: this thread's cells A and B (fast
 // path unless the block is ragged), its halo point, and the wrapped +x
 // pressure column of the block that reaches nx.  Returns A | B << 8.
-template <typename T>
+template <typename T, bool XP>
 __device__ __forceinline__ uint32_t tma_pass(unsigned char* st, const TmaPt<T>& qa, const TmaPt<T>& qb,
                                              const TmaPt<T>& qh, bool own_gen, bool has_h, int pfix_row,
-                                             int pfix_col, T (&ua)[3], T (&ub)[3]) {
+                                             int pfix_col, T uin, T (&ua)[3], T (&ub)[3]) {
     using L = TmaLay<T>;
     uint32_t ma, mb;
     if (own_gen) {
-        ma = tma_mask_pt<T, true>(st, qa, ua);
-        mb = tma_mask_pt<T, true>(st, qb, ub);
+        ma = tma_mask_pt<T, true, XP>(st, qa, uin, ua);
+        mb = tma_mask_pt<T, true, XP>(st, qb, uin, ub);
     } else {
-        ma = tma_mask_pt<T, false>(st, qa, ua);
-        mb = tma_mask_pt<T, false>(st, qb, ub);
+        ma = tma_mask_pt<T, false, XP>(st, qa, uin, ua);
+        mb = tma_mask_pt<T, false, XP>(st, qb, uin, ub);
     }
     if (has_h) {
         T uh[3];
-        tma_mask_pt<T, true>(st, qh, uh);
+        tma_mask_pt<T, true, XP>(st, qh, uin, uh);
     }
     if (pfix_row >= 0) {
         T* P = reinterpret_cast<T*>(st + L::oP);
@@ -765,7 +785,8 @@ __device__ __forceinline__ uint32_t tma_pass(unsigned char* st, const TmaPt<T>& 
     return ma | (mb << 8);
 }
 
-template <typename T>
+// XP: periodic x (wrap boxes) or inflow/outflow x (ghost columns from the box)
+template <typename T, bool XP>
 __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
     k_momentum_tma(GridP g, MomF<T> F, StageP<T> sp, IbmStage<T> ib, double* __restrict__ flux_part,
                    double* __restrict__ status, const __grid_constant__ MomMaps maps) {
@@ -783,23 +804,26 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
     const int plane = g.nx * g.ny;
     const int rowA = i + g.nx * jA;
     const int segrow = jA * g.nsegx + blockIdx.x;
-    const bool xl = i0 == 0, xr = i0 + MX >= g.nx;
-    const bool own_gen = i0 + MX > g.nx || j0 + MY > g.ny;
+    // wrap boxes only for a periodic x; an inflow/outflow x rewrites the block holding the
+    // outflow column in the general form
+    const bool xl = XP && i0 == 0, xr = XP && i0 + MX >= g.nx;
+    const bool own_gen = i0 + MX > g.nx || j0 + MY > g.ny || (!XP && i0 + MX >= g.nx);
+    const bool outcol = !XP && i == g.nx - 1;
     const int kbeg = blockIdx.z * g.kzm;
     const int kend = min(kbeg + g.kzm, g.nz);
     const int nrel = kend - kbeg + 2;          // planes kbeg-1 .. kend
 
     // this thread's points in the u, v, w tile (raw x = i - i0 + 4, raw y = j - j0 + 1)
-    const TmaPt<T> qa = tma_point<T>(g, i0, j0, tx + 4, 2 * w + 1, sp.sig_lo, sp.sig_hi);
-    const TmaPt<T> qb = tma_point<T>(g, i0, j0, tx + 4, 2 * w + 2, sp.sig_lo, sp.sig_hi);
+    const TmaPt<T> qa = tma_point<T, XP>(g, i0, j0, tx + 4, 2 * w + 1, sp.sig_lo, sp.sig_hi);
+    const TmaPt<T> qb = tma_point<T, XP>(g, i0, j0, tx + 4, 2 * w + 2, sp.sig_lo, sp.sig_hi);
     bool has_h = false;
     TmaPt<T> qh = qa;
     if (w == 0 || w == 1) {
         has_h = true;
-        qh = tma_point<T>(g, i0, j0, tx + 4, w == 0 ? 0 : L::RY - 1, sp.sig_lo, sp.sig_hi);
+        qh = tma_point<T, XP>(g, i0, j0, tx + 4, w == 0 ? 0 : L::RY - 1, sp.sig_lo, sp.sig_hi);
     } else if ((w == 2 || w == 3) && tx < L::RY) {
         has_h = true;
-        qh = tma_point<T>(g, i0, j0, w == 2 ? 3 : 4 + MX, tx, sp.sig_lo, sp.sig_hi);
+        qh = tma_point<T, XP>(g, i0, j0, w == 2 ? 3 : 4 + MX, tx, sp.sig_lo, sp.sig_hi);
     }
     // the block that reaches nx copies p(x = 0) next to its last column
     const int pfix_row = (xr && w == 4 && tx < L::PY) ? tx : -1;
@@ -836,10 +860,10 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
     // prologue: planes kbeg-1 (rel 0) and kbeg (rel 1)
     T ua[3], ub[3];
     bool ok = mbar_wait_bounded(&full[0], 0);
-    if (ok) tma_pass<T>(stage(0), qa, qb, qh, own_gen, has_h, -1, 0, ua, ub);
+    if (ok) tma_pass<T, XP>(stage(0), qa, qb, qh, own_gen, has_h, -1, 0, sp.uin, ua, ub);
     ok = ok && mbar_wait_bounded(&full[1], 0);
     uint32_t mc = 0;
-    if (ok) mc = tma_pass<T>(stage(1), qa, qb, qh, own_gen, has_h, pfix_row, pfix_col, ua, ub) & live_bits;
+    if (ok) mc = tma_pass<T, XP>(stage(1), qa, qb, qh, own_gen, has_h, pfix_row, pfix_col, sp.uin, ua, ub) & live_bits;
     fence_proxy_async();
     if (__syncthreads_or(!ok)) {
         abort_block(0);
@@ -875,7 +899,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
         // plane k+1 into operator form
         ok = mbar_wait_bounded(&full[(rel + 1) % L::D], ((rel + 1) / L::D) & 1);
         uint32_t mn = 0;
-        if (ok) mn = tma_pass<T>(stage(rel + 1), qa, qb, qh, own_gen, has_h, pfix_row, pfix_col, ua, ub);
+        if (ok) mn = tma_pass<T, XP>(stage(rel + 1), qa, qb, qh, own_gen, has_h, pfix_row, pfix_col, sp.uin, ua, ub);
         fence_proxy_async();
         if (__syncthreads_or(!ok)) {
             abort_block(rel + 1);
@@ -903,7 +927,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
         const int ida = rowA + k * plane;
         mom_plane3<T, L::RX, L::CS, true>(g, F, sp, ib, ta, tb, reinterpret_cast<const T*>(s0),
                                           reinterpret_cast<const T*>(s1), C, P, ua, ub, mc, k, ida, ida + g.nx,
-                                          liveA, liveB, segrow + k * g.ny * g.nsegx, fsum, false);
+                                          liveA, liveB, segrow + k * g.ny * g.nsegx, fsum, outcol);
         mc = mn & live_bits;
     }
     if (sp.flux_sum) {
@@ -982,10 +1006,11 @@ bool tma_smem_ready() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
     if (state[dev] == 0) {
-        state[dev] = cudaFuncSetAttribute(k_momentum_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          TmaLay<T>::SMEM) == cudaSuccess
-                         ? 1
-                         : -1;
+        const bool ok = cudaFuncSetAttribute(k_momentum_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TmaLay<T>::SMEM) == cudaSuccess &&
+                        cudaFuncSetAttribute(k_momentum_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TmaLay<T>::SMEM) == cudaSuccess;
+        state[dev] = ok ? 1 : -1;
         cudaGetLastError();
     }
     return state[dev] == 1;
@@ -1024,9 +1049,14 @@ ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib,
     ib = stage_coefs<T>(h, k);
     dim3 blk(MX, MW, 1);
     grd = momentum_grid(g);
-    if (g.ndim == 3 && h->mom_maps && h->mom_tma && tma_smem_ready<T>())
-        k_momentum_tma<T><<<grd, blk, TmaLay<T>::SMEM, h->stream>>>(g, F, sp, ib, h->partials, h->scal,
-                                                                     *static_cast<const MomMaps*>(h->mom_maps));
+    if (g.ndim == 3 && h->mom_maps && h->mom_tma && tma_smem_ready<T>()) {
+        const MomMaps& maps = *static_cast<const MomMaps*>(h->mom_maps);
+        if (g.xper)
+            k_momentum_tma<T, true><<<grd, blk, TmaLay<T>::SMEM, h->stream>>>(g, F, sp, ib, h->partials, h->scal, maps);
+        else
+            k_momentum_tma<T, false><<<grd, blk, TmaLay<T>::SMEM, h->stream>>>(g, F, sp, ib, h->partials, h->scal,
+                                                                               maps);
+    }
     else if (g.ndim == 3) k_momentum<T, true><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, h->partials);
     else k_momentum<T, false><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, h->partials);
     IBM_LAUNCH_CHECK();
@@ -1042,8 +1072,8 @@ void momentum_release(ibm_solver* h) {
 
 void momentum_prepare(ibm_solver* h) {
     momentum_release(h);
-    // the TMA form covers 3D grids with a periodic x whose extent is a multiple of 16
-    if (h->gp.ndim != 3 || h->gp.nx % 16 != 0 || !h->gp.xper) return;
+    // the TMA form covers 3D grids whose x extent is a multiple of 16
+    if (h->gp.ndim != 3 || h->gp.nx % 16 != 0) return;
     h->mom_maps = h->prec == IBM_FP64 ? static_cast<void*>(build_maps<double>(h))
                                       : static_cast<void*>(build_maps<float>(h));
 }
@@ -1078,9 +1108,9 @@ int momentum_default_kzm(const GridP& g, int prec, bool tma) {
         sms = 0;
     cudaError_t e;
     if (tma)
-        e = prec == IBM_FP64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_momentum_tma<double>, threads,
+        e = prec == IBM_FP64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_momentum_tma<double, true>, threads,
                                                                             TmaLay<double>::SMEM)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_momentum_tma<float>, threads,
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_momentum_tma<float, true>, threads,
                                                                             TmaLay<float>::SMEM);
     else
         e = prec == IBM_FP64

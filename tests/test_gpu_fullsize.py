@@ -1,6 +1,6 @@
 """The momentum predictor at the full 384 x 256 x 256 wavy-channel and 512 x 384 x 256
-airway sizes, in the launch configuration the benchmark times (FP32, default z-chunk;
-the TMA form on the periodic channel, the register form on the inflow/outflow duct),
+airway sizes, in the launch configuration the benchmark times (FP32, default z-chunk, the TMA form:
+wrap boxes on the periodic channel, ghost columns on the inflow/outflow duct),
 against the FP64 oracle on sampled points; on the airway also the classification byte
 and lambda of the device-built weights at the sampled points.
 
@@ -128,7 +128,7 @@ def test_airway_full_size_sampled_against_oracle():
     del f
     g = Solver.from_case(case)
     kzm, _, tma = g.tiles()
-    assert not tma, "an inflow/outflow x runs the register form"
+    assert tma, "the full-size FP32 duct runs the TMA form (x a multiple of 16)"
     mask, lists = g.classification()
     lam, _ = g.weights_lists()
     g.set_state(f32["u"], f32["v"], f32["w"], f32["p"])

@@ -299,15 +299,18 @@ def test_full_size_wavy_channel_launch_configuration():
 
 
 @pytest.mark.parametrize("nx", [70, 64])
-@pytest.mark.parametrize("flow", ["forced", "const_flux"])
+@pytest.mark.parametrize("flow", ["forced", "const_flux", "inflow"])
 def test_predictor_every_z_chunk_matches_oracle(flow, nx):
     """The momentum predictor at every z-chunk the autotuner may pick, on a grid whose
     z extent (23) leaves odd and short chunks, against the oracle to 1e-12.  nx = 64 runs
-    the TMA form (x a multiple of 16), nx = 70 the register form.  With a forced flow u*
-    is also the same bit for bit at every chunk; under the constant flow rate the forcing
-    sums per-block partials, whose grouping follows the chunking."""
+    the TMA form (x a multiple of 16), nx = 70 the register form.  With a forced flow or an
+    inflow/outflow x, u* is also the same bit for bit at every chunk; under the constant
+    flow rate the forcing sums per-block partials, whose grouping follows the chunking."""
     from inputs import FLOW_FORCED
-    case = small_case("wavy3d").with_(n=(nx, 36, 23), name=f"wavy3d_{nx}x36x23")
+    if flow == "inflow":
+        case = small_case("sphere3d_io").with_(n=(nx, 36, 23), name=f"sphere3d_io_{nx}x36x23")
+    else:
+        case = small_case("wavy3d").with_(n=(nx, 36, 23), name=f"wavy3d_{nx}x36x23")
     if flow == "forced":
         case = case.with_(flow_mode=FLOW_FORCED, g=(0.3, 0.0, 0.0))
     o = OracleSolver(case)
@@ -326,18 +329,20 @@ def test_predictor_every_z_chunk_matches_oracle(flow, nx):
             assert _rel(o, ug[c], o.u[c], c) < TOL64, (kz, c)
         if first is None:
             first = ug
-        elif flow == "forced":
+        elif flow != "const_flux":
             for c in range(3):
                 assert np.array_equal(first[c], ug[c]), (kz, c, int((first[c] != ug[c]).sum()))
         g.close()
 
 
+@pytest.mark.parametrize("name", ["sphere3d", "sphere3d_io", "tubes3d_io"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_tma_and_register_momentum_forms_agree(precision):
-    """Both forms of the momentum predictor on a ragged grid with x a multiple of 16
-    (48 x 30 x 26: a half-empty x tile, a partial y tile, free-slip ghosts), over full
-    steps: FP64 to 1e-12 of each other, FP32 to 1e-5."""
-    case = small_case("sphere3d", precision=precision)
+def test_tma_and_register_momentum_forms_agree(precision, name):
+    """Both forms of the momentum predictor on grids with x a multiple of 16 (48 x 30 x 26:
+    a half-empty x tile, a partial y tile, free-slip ghosts; with inflow / outflow x the
+    ghost columns and the outflow face; the tube union), over full steps: FP64 to 1e-12
+    of each other, FP32 to 1e-5."""
+    case = small_case(name, precision=precision)
     f = initial_field(case)
     runs = []
     for tma in (True, False):
