@@ -26,6 +26,7 @@ from .weights import build_weights, B_of_x, RK3_A, RK3_B, RK3_C
 from .momentum import (rhs, stage_update, pressure_gradient, masked, inflow_face, outflow_update,
                        outflow_balance)
 from .poisson import divergence, gradient, solve_spectral, solve_direct
+from .forces import body_terms, stage_impulse
 
 FLOW_FORCED, FLOW_CONST_FLUX = 0, 1
 
@@ -52,6 +53,12 @@ class OracleSolver:
         self.Nprev = [z.copy(), z.copy(), z.copy()]
         self.step_count = 0
         self.last_pi = 0.0
+        # force of the fluid on the body (forces.py): per step, and summed since the last read
+        self.BN_prev = np.zeros(3)
+        self.step_impulse = np.zeros(3)
+        self.last_force = np.zeros(3)
+        self.force_sum = np.zeros(3)
+        self.force_steps = 0
 
     # ---- state --------------------------------------------------------------
     def set_state(self, u, v, w, p):
@@ -70,6 +77,11 @@ class OracleSolver:
         um = masked(g, cls, self.u)
         ustar = stage_update(g, cls, um, N, self.Nprev, gp, self.w.lam, k, self.dt,
                              self.bmode, RK3_A, RK3_B, RK3_C, B_of_x)
+        # the body's share of the stage: the IBM division's part I of u* - u (what the
+        # explicit R does not explain) and the right-hand side's faces toward the solid
+        R = [self.dt * (RK3_A[k] * N[c] + RK3_B[k] * self.Nprev[c]) - RK3_C[k] * self.dt * gp[c] for c in range(3)]
+        I = [np.where(cls.internal[c], ustar[c] - um[c] - R[c], 0.0) for c in range(3)]
+        BN = body_terms(g, cls, self.u, self.w.src, self.nu)
         if g.xflow:
             # the outflow face: convective condition, then the flux balance
             ub, Nb = outflow_update(g, cls, self.u, self.Nprev[0][..., -1:], k, self.dt, RK3_A, RK3_B)
@@ -91,6 +103,9 @@ class OracleSolver:
             self.u = ustar
             return
         self._project(ustar, RK3_C[k] * self.dt, update_p=True)
+        self.step_impulse = self.step_impulse + stage_impulse(g, cls, I, BN, self.BN_prev, self.p, k, self.dt,
+                                                              RK3_A, RK3_B, RK3_C)
+        self.BN_prev = BN
 
     def _project(self, ustar, ckdt: float, update_p: bool):
         g = self.grid
@@ -105,9 +120,21 @@ class OracleSolver:
     # ---- public -------------------------------------------------------------
     def step(self, nsteps: int = 1):
         for _ in range(nsteps):
+            self.step_impulse = np.zeros(3)
             for k in range(3):
                 self.substage(k)
             self.step_count += 1
+            self.last_force = -self.step_impulse / self.dt
+            self.force_sum = self.force_sum + self.last_force
+            self.force_steps += 1
+
+    def mean_force(self, reset: bool = True):
+        """Mean force of the fluid on the body over the steps since the last reset."""
+        f = self.force_sum / self.force_steps if self.force_steps else np.full(3, np.nan)
+        if reset:
+            self.force_sum = np.zeros(3)
+            self.force_steps = 0
+        return f
 
     def project(self):
         """Initial-condition projection: zero the unreadable velocities, balance the outflow

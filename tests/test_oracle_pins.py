@@ -597,3 +597,60 @@ def test_tube_union_trunk_crosses_the_x_faces_and_the_other_faces_are_solid():
             assert (np.asarray(ls.phi(a, np.full_like(a, y), 0.5 * b)) > 0).all()
         for z in (0.0, 0.5):
             assert (np.asarray(ls.phi(a, 0.75 * b, np.full_like(a, z))) > 0).all()
+
+
+# ---- force of the fluid on the body ---------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["sphere3d", "cylinder2d"])
+def test_body_force_closes_the_momentum_budget(name):
+    """In a box periodic in x (and z) with free-slip y walls the box faces exchange no x (z)
+    momentum, so over a step the fluid momentum changes by the body force g V dt minus the
+    force on the body times dt.  The force is computed from the body's terms alone (IBM
+    division, faces toward solid points, pressure at the ends of internal runs), the change
+    from the fields: a dropped term, a wrong sign or a wrong face breaks the balance."""
+    from inputs import FLOW_FORCED
+    case = small_case(name).with_(flow_mode=FLOW_FORCED, g=(0.7, 0.0, 0.0))
+    o = OracleSolver(case)
+    f = initial_field(case)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    o.project()
+    dV = o.grid.cell_volume()
+    comps = (0, 2) if case.ndim == 3 else (0,)
+    for _ in range(2):
+        M0 = [np.sum(np.where(o.cls.internal[c], o.u[c], 0.0)) * dV for c in range(3)]
+        o.step(1)
+        for c in comps:
+            M1 = np.sum(np.where(o.cls.internal[c], o.u[c], 0.0)) * dV
+            V = np.count_nonzero(o.cls.internal[c]) * dV
+            expect = case.g[c] * V * case.dt - o.last_force[c] * case.dt
+            scale = np.sum(np.abs(np.where(o.cls.internal[c], o.u[c], 0.0))) * dV + abs(o.last_force[c]) * case.dt
+            assert abs((M1 - M0[c]) - expect) < 1e-12 * scale, (c, M1 - M0[c], expect)
+            # the body's term is far above the tolerance: the balance tests it
+            assert abs(o.last_force[c]) * case.dt > 1e-7 * scale or c != 0
+
+
+def test_centred_cylinder_has_no_lift():
+    """A cylinder on the axis of a mirror-symmetric inflow/outflow channel feels no lift:
+    the y terms of the force cancel between the two halves to round-off."""
+    case = small_case("cylinder2d_io").with_(geom_params=(0.0, 0.0, 0.5, -1.0), init={"kind": "uniform", "U": 1.0})
+    o = OracleSolver(case)
+    f = initial_field(case)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    o.project()
+    for _ in range(12):      # past the start-up swings of the pressure
+        o.step(1)
+        assert abs(o.last_force[1]) < 1e-11 * abs(o.last_force[0])
+    assert o.last_force[0] > 0.0
+
+
+def test_couette_walls_take_equal_and_opposite_shear():
+    """In steady Couette flow the moving wall drags the fluid as much as the wall at rest holds
+    it back: the force on the body (both walls) is zero to round-off against one wall's shear
+    nu U / (b - a) per unit length.  Without the moving wall's source term it would not be."""
+    case = couette_case()
+    o = OracleSolver(case)
+    f = initial_field(case)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    o.step(2)
+    shear = case.nu * case.wall_u[0] / (0.871 - 0.113) * case.L[0]
+    assert abs(o.last_force[0]) < 1e-11 * shear
