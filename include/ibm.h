@@ -135,6 +135,9 @@ typedef struct {
     double target_flux; /* IBM_FLOW_CONST_FLUX: target volume integral of u over internal u points */
     double wall_u[3];   /* velocity of the moving surface (see the geometry kinds) */
     int no_ibm;         /* 1: lambda := 0, no wall source (the staircase baseline) */
+    int body_force;     /* 1: every full step adds the force of the fluid on the body to the
+                         * sums ibm_diagnostics reports (two small launches per substage over the
+                         * IBM points); 0: not computed */
 } ibm_physics;
 
 typedef struct {
@@ -146,6 +149,14 @@ typedef struct {
     double pi;          /* forcing of the last constant-flow-rate substage */
     long long step;     /* completed full steps */
     int status;         /* IBM_OK or IBM_E_DIVERGED */
+    double force[3];    /* ibm_physics.body_force = 1: mean over the full steps since the previous
+                         * ibm_diagnostics call (or ibm_build_weights) of the force of the fluid on
+                         * the body, from the discrete momentum budget: the momentum the IBM
+                         * division, the right-hand side's faces toward solid points and the
+                         * pressure at the ends of the runs of internal points exchange with the
+                         * fluid (the paper reports drag and lift, Sec. 4.1, without a method;
+                         * this is the reading taken).  NaN when no step was counted. */
+    long long force_steps; /* full steps in that mean; the call resets the sums */
 } ibm_diag;
 
 typedef struct {

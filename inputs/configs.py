@@ -102,6 +102,22 @@ def cylinder_c2_io(re: float = 40.0, precision: str = "fp64", steps: int = 10, s
                 seed=seed)
 
 
+def cylinder_paper(re: float = 30.0, precision: str = "fp32", h: float = 0.02, steps: int = 0) -> Case:
+    """The cylinder flow of the paper's first example (Sec. 4.1): D = 1 at the origin, domain
+    x in [-9, 40], y in [-17, 17], here on a uniform grid of step h (the paper's step near the
+    body).  Uniform inflow U = 1, convective outflow; the lateral faces are free-slip walls
+    (not stated in the paper).  dt is 80% of the explicit viscous limit of RK3 (2.51 / (8 nu / h^2))
+    or 0.4 h / U, whichever is smaller."""
+    nx, ny = int(round(49.0 / h)), int(round(34.0 / h))
+    nu = 1.0 / re
+    dt = min(0.8 * 2.51 / (8.0 * nu / (h * h)), 0.4 * h)
+    return Case(name=f"cylinder_paper_re{int(re)}_{nx}x{ny}", ndim=2, n=(nx, ny, 1), L=(49.0, 34.0, 1.0),
+                origin=(-9.0, -17.0, 0.0), bc_lo=(BC_INFLOW, BC_FREESLIP, BC_PERIODIC),
+                bc_hi=(BC_OUTFLOW, BC_FREESLIP, BC_PERIODIC), geom_kind=GEOM_CYLINDER,
+                geom_params=(0.0, 0.0, 0.5, -1.0), nu=nu, dt=dt, inflow=(1.0, 0.0, 0.0),
+                precision=precision, steps=steps, init={"kind": "uniform", "U": 1.0})
+
+
 def cylinder_c2(re: float = 40.0, precision: str = "fp64", steps: int = 10, seed: int = 0,
                 n=(1536, 768)) -> Case:
     """2D cylinder D=1 in a 30D x 15D box; centre offset by a seeded fraction of a cell.

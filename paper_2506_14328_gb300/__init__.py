@@ -51,12 +51,13 @@ class ibm_buffers(C.Structure):
 class ibm_physics(C.Structure):
     _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("g", C.c_double * 3), ("bmode", C.c_int),
                 ("flow_mode", C.c_int), ("target_flux", C.c_double), ("wall_u", C.c_double * 3),
-                ("no_ibm", C.c_int)]
+                ("no_ibm", C.c_int), ("body_force", C.c_int)]
 
 
 class ibm_diag(C.Structure):
     _fields_ = [("div_l2", C.c_double), ("div_linf", C.c_double), ("cfl", C.c_double), ("flux", C.c_double * 3),
-                ("ke", C.c_double), ("pi", C.c_double), ("step", C.c_longlong), ("status", C.c_int)]
+                ("ke", C.c_double), ("pi", C.c_double), ("step", C.c_longlong), ("status", C.c_int),
+                ("force", C.c_double * 3), ("force_steps", C.c_longlong)]
 
 
 class ibm_kernel_time(C.Structure):

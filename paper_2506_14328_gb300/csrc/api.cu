@@ -181,7 +181,7 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
     if (npart < DIAG_PART) npart = DIAG_PART;
     if (npart < 120 * 4) npart = 120 * 4;
     char* partials = take((size_t)npart * sizeof(double));
-    char* scal = take(16 * sizeof(double));
+    char* scal = take(SCAL_N * sizeof(double));
     if (h && base) {
         h->mask = (uint8_t*)mask;
         h->velbits = (uint8_t*)velbits;
@@ -388,7 +388,7 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     if (st == IBM_OK) st = geom_pivots(h);
     if (st == IBM_OK) st = poisson_prepare(h);
     if (st == IBM_OK) {
-        cudaError_t e = cudaMemsetAsync(h->scal, 0, 16 * sizeof(double), h->stream);
+        cudaError_t e = cudaMemsetAsync(h->scal, 0, SCAL_N * sizeof(double), h->stream);
         if (e != cudaSuccess) st = ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e));
     }
     if (st != IBM_OK) {
@@ -422,8 +422,13 @@ ibm_status ibm_build_weights(ibm_solver* h, const ibm_physics* phys, void* weigh
     size_t need = weights_layout(h, nullptr);
     if (weights_bytes < need) return ibm_set_error(IBM_E_NOMEM, "weights buffer too small: need " + std::to_string(need));
     drop_graph(h);
+    if (phys->body_force != 0 && phys->body_force != 1) return ibm_set_error(IBM_E_INVALID, "body_force is 0 or 1");
     h->phys = *phys;
     weights_layout(h, (char*)weights);
+    {   // new physics: the force sums start again
+        cudaError_t e = cudaMemsetAsync(h->scal + SCAL_FORCE, 0, (SCAL_N - SCAL_FORCE) * sizeof(double), h->stream);
+        if (e != cudaSuccess) return ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e));
+    }
     st = geom_build_lists_and_weights(h);
     if (st == IBM_OK) st = geom_stage_coefficients(h);
     if (st != IBM_OK) return st;
@@ -494,9 +499,17 @@ ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
     ibm_status st = check_handle(h);
     if (st != IBM_OK) return st;
     if (!out) return ibm_set_error(IBM_E_INVALID, "out is NULL");
-    double r[16];
+    double r[SCAL_N];
     st = run_diagnostics(h, r);
     if (st != IBM_OK) return st;
+    {   // the force sums restart with the next step
+        cudaError_t e = cudaMemsetAsync(h->scal + SCAL_FORCE, 0, 3 * sizeof(double), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->scal + SCAL_FSTEPS, 0, sizeof(double), h->stream);
+        if (e != cudaSuccess) {
+            h->failed = true;
+            return ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e));
+        }
+    }
     const GridP& g = h->gp;
     double dV = g.dx * g.dy * (g.ndim == 3 ? g.dz : 1.0);
     const double* s = r + 4;
@@ -513,6 +526,9 @@ ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
     out->cfl = cfl * h->phys.dt;
     out->pi = r[0];
     out->step = h->steps;
+    out->force_steps = (long long)r[SCAL_FSTEPS];
+    for (int c = 0; c < 3; ++c)
+        out->force[c] = out->force_steps > 0 ? r[SCAL_FORCE + c] / r[SCAL_FSTEPS] : std::nan("");
     if (r[3] != 0.0) {
         // a TMA momentum block gave up waiting for its plane loads (a bounded wait ran out)
         out->status = IBM_E_TIMEOUT;

@@ -122,6 +122,22 @@ __device__ __forceinline__ double warp_max(double v) {
 constexpr int DIAG_FOLD = 8;
 constexpr int DIAG_BLOCKS = 4 * 304;   // blocks of the diagnostics kernel (12 partials each)
 
+// Device scalars (h->scal): [0] Pi of the substage, [2] its typed copy, [3] momentum timeout flag,
+// [4..15] diagnostics sums, then the body-force sums.
+constexpr int SCAL_N = 32;
+constexpr int SCAL_FORCE = 16;    // 3: force on the body summed over the counted steps
+constexpr int SCAL_BNPREV = 19;   // 3: the right-hand side's body share of the previous substage
+constexpr int SCAL_FSTEPS = 22;   // counted steps
+constexpr int SCAL_IMP = 24;      // 3: impulse of the current step so far
+
+// B of the implicit update (Eq. Bexpr and the Taylor options): B = x / (e^x - 1), 1 at x = 0.
+__device__ __forceinline__ double ibm_B_of_x(double x, int mode) {
+    if (mode == IBM_B_EULER) return 1.0;
+    if (mode == IBM_B_TAYLOR2) return 1.0 / (1.0 + x / 2.0);
+    if (!(x > 0.0)) return 1.0;
+    return x / expm1(x);
+}
+
 struct FF { float hi, lo; };   // value hi + lo, |lo| <= ulp(hi) / 2
 
 // Each rounding whose error is kept is an explicit _rn operation, so no
@@ -378,7 +394,7 @@ void momentum_release(ibm_solver* h);
 bool momentum_uses_tma(const ibm_solver* h);
 ibm_status run_project(ibm_solver* h);
 ibm_status run_poisson(ibm_solver* h, void* rhs_inout);
-ibm_status run_diagnostics(ibm_solver* h, double* out11);
+ibm_status run_diagnostics(ibm_solver* h, double* out);   // SCAL_N doubles
 ibm_status poisson_prepare(ibm_solver* h);   // Neumann x: the DCT twiddle table
 
 // timing hooks used by both

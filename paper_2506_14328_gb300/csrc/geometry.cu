@@ -396,12 +396,7 @@ __global__ void k_weights(GridP g, GeomP geo, WeightArgs a, const uint8_t* __res
 // ---------------------------------------------------------------------------
 // Per-stage implicit coefficients (Eq. Bexpr / expint / rk3-rai)
 // ---------------------------------------------------------------------------
-__device__ double B_of_x(double x, int mode) {
-    if (mode == IBM_B_EULER) return 1.0;
-    if (mode == IBM_B_TAYLOR2) return 1.0 / (1.0 + x / 2.0);
-    if (!(x > 0.0)) return 1.0;
-    return x / expm1(x);
-}
+__device__ double B_of_x(double x, int mode) { return ibm_B_of_x(x, mode); }
 
 template <typename T>
 struct CoefArgs {

@@ -185,6 +185,8 @@ extern "C" ibm_status ibm_diagnostics_noalloc(const ibm_grid_desc* grid, const v
     }
     out->cfl = cfl * dt;
     out->step = -1;
+    for (int c = 0; c < 3; ++c) out->force[c] = std::nan("");   // needs a solver's IBM points
+    out->force_steps = 0;
     const bool finite = s[11] == 0.0 && std::isfinite(out->div_l2) && std::isfinite(out->ke);
     out->status = finite ? IBM_OK : IBM_E_DIVERGED;
     if (!finite) return ibm_set_error(IBM_E_DIVERGED, "non-finite values in the fields");

@@ -956,6 +956,193 @@ ibm_status launch_correct(ibm_solver* h, T* const us[3], T inv_ckdt, int update_
 }
 
 
+// ---------------------------------------------------------------------------
+// Force of the fluid on the body (diagnostic, per substage): the body's share
+// of the discrete momentum budget of the internal points.  Per IBM point P of
+// component c:
+//   I  = -x u* + (1 - B)(u* - u)   what the implicit division adds to u* - u
+//        beyond the explicit R (from (B + x) u* = B u + R)
+//   BN = wall source + over the arms toward external points: -s F / D_d
+//        + nu (0 - u) / D_d^2, F the face's convective flux as the right-hand
+//        side forms it (the external value reads 0)
+//   PQ = over the arms along c: +q(cell P + e_c) (s = +1), -q(cell P) (s = -1),
+//        q = p + psi / (c_k dt) the new pressure (the solve returns psi = c_k dt phi),
+//        the pressure at the end of a run of internal points
+// A final single block turns the sums into the stage's impulse
+//   dV (sum I - c_k dt PQ / D_c + dt (a_k BN + b_k BN_prev))
+// and, after the third stage, adds -impulse / dt to the force sums.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct BodyArgs {
+    GridP g;
+    const T* u[3];
+    const T* us[3];
+    const T* p;
+    const T* psi;            // c_k dt phi
+    const uint8_t* mask;
+    const int* idx[3];
+    const double* lam[3];
+    const double* src[3];
+    int cnt[3];
+    double ckdt, inv_ckdt, nu;
+    int bmode;
+    double* part;
+};
+
+// value of component d at (i, j, k) as the right-hand side reads it (0 unless
+// internal or the fluid outflow face of u); i may be nx or -1 only in a periodic x
+template <typename T>
+__device__ __forceinline__ double body_rd(const BodyArgs<T>& a, int d, int i, int j, int k) {
+    const GridP& g = a.g;
+    if (g.xper) i = (i + g.nx) % g.nx;
+    if (g.ndim == 3) k = (k + g.nz) % g.nz;
+    const long long l = i + (long long)g.nx * (j + (long long)g.ny * k);
+    const uint32_t m = a.mask[l];
+    bool rd = (m >> d) & 1u;
+    if (d == 0 && !g.xper && i == g.nx - 1) rd = (m & IBM_MASK_FACE) != 0;
+    return rd ? (double)a.u[d][l] : 0.0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_body_force(BodyArgs<T> a) {
+    const GridP& g = a.g;
+    const int c = blockIdx.y;
+    double sI = 0.0, sBN = 0.0, sPQ = 0.0;
+    const int nd = g.ndim;
+    const double D[3] = {g.dx, g.dy, g.dz};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < a.cnt[c]; m += gridDim.x * blockDim.x) {
+        const long long lin = a.idx[c][m];
+        const int pi = (int)(lin % g.nx);
+        const int pj = (int)((lin / g.nx) % g.ny);
+        const int pk = (int)(lin / ((long long)g.nx * g.ny));
+        const double u0 = (double)a.u[c][lin];
+        const double us = (double)a.us[c][lin];
+        const double x = a.lam[c][m] * a.ckdt;
+        const double B = ibm_B_of_x(x, a.bmode);
+        sI += -x * us + (1.0 - B) * (us - u0);
+        sBN += a.src[c][m];
+        const int P[3] = {pi, pj, pk};
+        for (int d = 0; d < nd; ++d) {
+            const bool per = d == 2 || (d == 0 && g.xper);
+            for (int s = 1; s >= -1; s -= 2) {
+                int Q[3] = {P[0], P[1], P[2]};
+                Q[d] += s;
+                if (per) Q[d] = (Q[d] + n[d]) % n[d];
+                else if (Q[d] < 0 || Q[d] >= n[d]) continue;
+                // box-boundary points (v on the +y wall, u on the outflow face) are not arms
+                if ((c == 1 && Q[1] == g.ny - 1) || (c == 0 && !g.xper && Q[0] == g.nx - 1)) continue;
+                const long long lq = Q[0] + (long long)g.nx * (Q[1] + (long long)g.ny * Q[2]);
+                if ((a.mask[lq] >> c) & 1u) continue;          // internal: its flux cancels
+                const double h = (u0 + 0.0) / 2.0;
+                double F;
+                if (d == c) {
+                    F = h * h;
+                } else {
+                    int e[3] = {0, 0, 0};
+                    e[c] = 1;
+                    const int o = s > 0 ? 0 : -1;   // the face's advecting points: P (+ e_c), shifted by -e_d for s = -1
+                    int A[3] = {P[0], P[1], P[2]};
+                    A[d] += o;
+                    const double adv = (body_rd(a, d, A[0], A[1], A[2]) +
+                                        body_rd(a, d, A[0] + e[0], A[1] + e[1], A[2] + e[2])) / 2.0;
+                    F = adv * h;
+                }
+                sBN += -s * F / D[d] + a.nu * (0.0 - u0) / (D[d] * D[d]);
+                if (d == c) {
+                    if (s > 0) {
+                        const long long lc = Q[0] + (long long)g.nx * (Q[1] + (long long)g.ny * Q[2]);
+                        sPQ += (double)a.p[lc] + (double)a.psi[lc] * a.inv_ckdt;
+                    } else {
+                        sPQ -= (double)a.p[lin] + (double)a.psi[lin] * a.inv_ckdt;
+                    }
+                }
+            }
+        }
+    }
+    __shared__ double sh[3][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double v[3] = {sI, sBN, sPQ};
+    for (int q = 0; q < 3; ++q) {
+        double t = v[q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[q][wid] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sh[threadIdx.x][w];
+        a.part[((long long)c * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_body_force_final(const double* __restrict__ part, int nbx, double* __restrict__ scal,
+                                   double dV, double dt, double ak, double bk, double ckdt, double dx, double dy,
+                                   double dz, int last) {
+    // warp c sums component c's block partials in a fixed order
+    __shared__ double tot[3][3];
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (c < 3) {
+        for (int q = 0; q < 3; ++q) {
+            double t = 0.0;
+            for (int b = lane; b < nbx; b += 32) t += part[((long long)c * nbx + b) * 3 + q];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) tot[c][q] = t;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double D[3] = {dx, dy, dz};
+        for (int q = 0; q < 3; ++q) {
+            const double BN = tot[q][1];
+            const double imp = dV * (tot[q][0] - ckdt * tot[q][2] / D[q] + dt * (ak * BN + bk * scal[SCAL_BNPREV + q]));
+            scal[SCAL_IMP + q] += imp;
+            scal[SCAL_BNPREV + q] = BN;
+        }
+        if (last) {
+            for (int q = 0; q < 3; ++q) {
+                scal[SCAL_FORCE + q] += -scal[SCAL_IMP + q] / dt;
+                scal[SCAL_IMP + q] = 0.0;
+            }
+            scal[SCAL_FSTEPS] += 1.0;
+        }
+    }
+}
+
+template <typename T>
+ibm_status body_force_t(ibm_solver* h, int k) {
+    const GridP& g = h->gp;
+    BodyArgs<T> a;
+    a.g = g;
+    int mx = 0;
+    for (int c = 0; c < 3; ++c) {
+        const bool on = c < g.ncomp;
+        a.u[c] = (const T*)h->buf.u[on ? c : 0];
+        a.us[c] = (const T*)h->ustar[on ? c : 0];
+        a.idx[c] = h->idx[c];
+        a.lam[c] = h->lam[c];
+        a.src[c] = h->src[c];
+        a.cnt[c] = on ? h->counts[c] : 0;
+        mx = std::max(mx, a.cnt[c]);
+    }
+    a.p = (const T*)h->buf.p;
+    a.psi = (const T*)h->rhs;
+    a.mask = h->mask;
+    a.ckdt = h->phys.dt * RK_C[k];
+    a.inv_ckdt = 1.0 / a.ckdt;
+    a.nu = h->phys.nu;
+    a.bmode = h->phys.bmode;
+    a.part = h->partials;
+    int nbx = std::max(1, std::min((mx + 255) / 256, std::min(256, h->npartials / 9)));
+    k_body_force<T><<<dim3(nbx, 3), 256, 0, h->stream>>>(a);
+    IBM_LAUNCH_CHECK();
+    const double dV = g.dx * g.dy * (g.ndim == 3 ? g.dz : 1.0);
+    k_body_force_final<<<1, 96, 0, h->stream>>>(h->partials, nbx, h->scal, dV, h->phys.dt, RK_A[k], RK_B[k],
+                                                h->phys.dt * RK_C[k], g.dx, g.dy, g.dz, k == 2 ? 1 : 0);
+    IBM_LAUNCH_CHECK();
+    return IBM_OK;
+}
+
 // Outflow face of stage k (update) or, for the initial projection, only the flux balance.
 template <typename T>
 ibm_status outflow_t(ibm_solver* h, int k, bool update) {
@@ -1015,6 +1202,12 @@ ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
     const FluxCorr<T> fc = flux_corr<T>(h, k);
     ibm_status st = divergence_and_solve<T>(h, us, cflux, fc);
     if (st != IBM_OK) return st;
+    if (h->phys.body_force) {
+        timer_begin(h, "body_force", &t);
+        st = body_force_t<T>(h, k);
+        if (st != IBM_OK) return st;
+        timer_end(h, t, "body_force");
+    }
     timer_begin(h, "correct", &t);
     st = launch_correct<T>(h, us, (T)(1.0 / (dt * RK_C[k])), 1, cflux, fc);
     if (st != IBM_OK) return st;
@@ -1050,7 +1243,7 @@ ibm_status diag_t(ibm_solver* h, double* out) {
     IBM_LAUNCH_CHECK();
     k_diag_final<<<1, 12 * 32, 0, h->stream>>>(h->partials, DIAG_BLOCKS, h->scal + 4);
     IBM_LAUNCH_CHECK();
-    IBM_CUDA_TRY(cudaMemcpyAsync(out, h->scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    IBM_CUDA_TRY(cudaMemcpyAsync(out, h->scal, SCAL_N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return IBM_OK;
 }
@@ -1146,6 +1339,6 @@ ibm_status run_poisson(ibm_solver* h, void* rhs_inout) {
 }
 
 // out: [0] Pi, [4..15] the 12 diagnostics sums
-ibm_status run_diagnostics(ibm_solver* h, double* out16) {
-    return h->prec == IBM_FP64 ? diag_t<double>(h, out16) : diag_t<float>(h, out16);
+ibm_status run_diagnostics(ibm_solver* h, double* out) {
+    return h->prec == IBM_FP64 ? diag_t<double>(h, out) : diag_t<float>(h, out);
 }

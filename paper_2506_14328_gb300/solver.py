@@ -24,11 +24,11 @@ class Solver:
 
     Parameters mirror the C structs: ndim, n=(nx,ny,nz), L, origin, bc_lo,
     bc_hi, precision ('fp64'|'fp32'), geom_kind, geom_params, and physics
-    nu, dt, g, bmode, flow_mode, target_flux, wall_u, no_ibm; inflow (x inflow/outflow)."""
+    nu, dt, g, bmode, flow_mode, target_flux, wall_u, no_ibm, body_force; inflow (x inflow/outflow)."""
 
     def __init__(self, *, ndim, n, L, origin, bc_lo, bc_hi, precision, geom_kind, geom_params, nu, dt,
                  g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0, wall_u=(0.0, 0.0, 0.0), no_ibm=False,
-                 inflow=(0.0, 0.0, 0.0), device="cuda", stream=None):
+                 body_force=False, inflow=(0.0, 0.0, 0.0), device="cuda", stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("the IBM solver needs a CUDA device")
         self.device = torch.device(device)
@@ -84,7 +84,7 @@ class Solver:
             self.h = ibm_setup_geometry(gd, geo, bufs, self.stream.cuda_stream)
             self.weights = None
             self.set_physics(nu=nu, dt=dt, g=g, bmode=bmode, flow_mode=flow_mode, target_flux=target_flux,
-                             wall_u=wall_u, no_ibm=no_ibm)
+                             wall_u=wall_u, no_ibm=no_ibm, body_force=body_force)
 
     @classmethod
     def from_case(cls, case, precision=None, no_ibm=False, **kw):
@@ -96,7 +96,7 @@ class Solver:
                    inflow=getattr(case, "inflow", (0.0, 0.0, 0.0)), **kw)
 
     def set_physics(self, *, nu, dt, g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0,
-                    wall_u=(0.0, 0.0, 0.0), no_ibm=False):
+                    wall_u=(0.0, 0.0, 0.0), no_ibm=False, body_force=False):
         ph = ibm_physics()
         ph.nu = float(nu)
         ph.dt = float(dt)
@@ -107,6 +107,7 @@ class Solver:
         ph.flow_mode = int(flow_mode)
         ph.target_flux = float(target_flux)
         ph.no_ibm = 1 if no_ibm else 0
+        ph.body_force = 1 if body_force else 0
         self.phys = ph
         wb = ibm_weights_bytes(self.h)
         if self.weights is None or self.weights.numel() < wb:
@@ -131,7 +132,8 @@ class Solver:
     def diagnostics(self, raise_on_diverged=True) -> dict:
         d = ibm_diagnostics(self.h, raise_on_diverged)
         return {"div_l2": d.div_l2, "div_linf": d.div_linf, "cfl": d.cfl, "flux": list(d.flux), "ke": d.ke,
-                "pi": d.pi, "step": d.step, "status": d.status}
+                "pi": d.pi, "step": d.step, "status": d.status, "force": list(d.force),
+                "force_steps": d.force_steps}
 
     def classification(self):
         counts = ibm_get_classification(self.h, None, None)

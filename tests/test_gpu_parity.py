@@ -381,3 +381,56 @@ def test_inflow_outflow_faces_and_balance_match_oracle(name):
     assert abs(got[fl].sum() - q_in) < 1e-12 * q_in
     d = g.diagnostics()
     assert d["div_linf"] < 1e-11 * case.inflow[0] / min(o.grid.d[:o.grid.ndim])
+
+
+@pytest.mark.parametrize("name", CASES + ["couette"])
+def test_body_force_matches_oracle(name):
+    """The force of the fluid on the body (IBM division, faces toward solid points, pressure
+    at run ends) per step and as the mean over several steps, FP64 against the oracle.  It is
+    a sum of terms that cancel in part, so the tolerance is 1e-10 of the larger of the force
+    and the wall shear scale."""
+    case = couette_case() if name == "couette" else small_case(name)
+    f = initial_field(case)
+    g = _gpu(case, body_force=True)
+    g.set_state(f["u"], f["v"], f["w"], f["p"])
+    o = OracleSolver(case)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    nc = o.grid.ncomp
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        d = g.diagnostics()
+        assert d["force_steps"] == 1
+        ref = o.last_force[:nc]
+        scale = max(np.abs(ref).max(), case.nu * 1.0)
+        assert np.abs(np.array(d["force"][:nc]) - ref).max() < 1e-10 * scale, (d["force"], ref)
+    o.mean_force(reset=True)
+    g.step(3)
+    o.step(3)
+    d = g.diagnostics()
+    ref = o.mean_force()[:nc]
+    assert d["force_steps"] == 3
+    assert np.abs(np.array(d["force"][:nc]) - ref).max() < 1e-10 * max(np.abs(ref).max(), case.nu)
+    assert g.diagnostics()["force_steps"] == 0     # the read resets the sums
+    g.close()
+
+
+def test_body_force_off_reports_nan_and_fp32_is_close():
+    case = small_case("sphere3d_io")
+    f = initial_field(case)
+    g = _gpu(case)
+    g.set_state(f["u"], f["v"], f["w"], f["p"])
+    g.step(1)
+    d = g.diagnostics()
+    assert d["force_steps"] == 0 and all(math.isnan(v) for v in d["force"])
+    g.close()
+    g32 = _gpu(case, precision="fp32", body_force=True)
+    g32.set_state(f["u"], f["v"], f["w"], f["p"])
+    o = OracleSolver(case)
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    g32.step(2)
+    o.step(2)
+    F32 = np.array(g32.diagnostics()["force"])
+    F64 = o.mean_force()
+    assert np.abs(F32 - F64).max() < 1e-3 * np.abs(F64).max()
+    g32.close()
