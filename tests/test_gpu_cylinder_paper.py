@@ -1,5 +1,6 @@
 """The paper's first example on the GPU: the cylinder in a uniform stream (Sec. 4.1), with the
-drag from the solver's force diagnostic against the value the paper prints (Table re30).
+drag and lift from the solver's force diagnostic against the values the paper prints
+(Tables re30 and re185).
 
 Set-up as the paper states it: D = 1 at the origin, domain [-9D, 40D] x [-17D, 17D], grid
 step 0.02D (uniform here, the paper's step near the body), uniform inflow, Re = U D / nu = 30.
@@ -49,3 +50,42 @@ def test_cylinder_drag_at_re30_matches_the_paper():
     assert abs(cd - cd_a) < 0.005 * cd       # steady
     assert abs(lift) < 1e-3 * cd             # symmetric wake
     assert abs(cd - ref) < 0.02 * ref
+
+
+def test_cylinder_shedding_at_re185_matches_the_paper():
+    """Re = 185: periodic shedding.  A 1% seeded perturbation of the start breaks the mirror
+    symmetry; after t = 100 the force is sampled every 10 steps over t in [100, 150] (about ten
+    periods).  Pins: mean C_d within 4% of 1.382, r.m.s. C_l within 10% of 0.470, Strouhal
+    number (from the zero crossings of C_l) within 3% of 0.198 (Table re185; the literature
+    there spans C_d 1.28-1.43, C_l' 0.42-0.47, St 0.193-0.199)."""
+    from paper_2506_14328_gb300.solver import Solver
+    case = cylinder_paper(re=185.0).with_(init={"kind": "uniform_noise", "U": 1.0, "noise": 0.01})
+    g = Solver.from_case(case, body_force=True)
+    f = initial_field(case)
+    g.set_state(f["u"], f["v"], f["w"], f["p"])
+    g.project()
+    g.step(int(round(100.0 / case.dt)))
+    g.diagnostics()
+    every = 10
+    nsamp = int(round(50.0 / case.dt)) // every
+    cd, cl = np.zeros(nsamp), np.zeros(nsamp)
+    for q in range(nsamp):
+        g.step(every)
+        d = g.diagnostics()
+        cd[q] = 2.0 * d["force"][0]
+        cl[q] = 2.0 * d["force"][1]
+    g.close()
+    t = (np.arange(nsamp) + 0.5) * every * case.dt
+    up = np.flatnonzero((cl[:-1] < 0.0) & (cl[1:] >= 0.0))
+    # linear interpolation of the upward zero crossings
+    tz = t[up] - cl[up] * (t[up + 1] - t[up]) / (cl[up + 1] - cl[up])
+    period = (tz[-1] - tz[0]) / (len(tz) - 1)
+    st = 1.0 / period                  # f D / U
+    ref = GOLDEN["cylinder_re185"]
+    cd_mean, cl_rms = cd.mean(), np.sqrt(np.mean((cl - cl.mean()) ** 2))
+    print(f"C_d = {cd_mean:.4f} (paper {ref['Cd']}), C_l' = {cl_rms:.4f} ({ref['Cl_rms']}), "
+          f"St = {st:.4f} ({ref['St']}), {len(tz)} crossings")
+    assert len(tz) >= 6
+    assert abs(cd_mean - ref["Cd"]) < 0.04 * ref["Cd"]
+    assert abs(cl_rms - ref["Cl_rms"]) < 0.10 * ref["Cl_rms"]
+    assert abs(st - ref["St"]) < 0.03 * ref["St"]
