@@ -654,3 +654,28 @@ def test_couette_walls_take_equal_and_opposite_shear():
     o.step(2)
     shear = case.nu * case.wall_u[0] / (0.871 - 0.113) * case.L[0]
     assert abs(o.last_force[0]) < 1e-11 * shear
+
+
+# ---- sampled level set ----------------------------------------------------------------------
+
+def test_sampled_plane_walls_equal_the_closed_form():
+    """phi sampled from two plane walls is linear along every crossing arm, so the straight-line
+    root of the samples is the exact wall distance: the same masks and lists as PLANES, and
+    lambda within 1e-9 (a wrong interpolation formula, e.g. phi_Q / (phi_P - phi_Q), fails)."""
+    from inputs import GEOM_SAMPLED
+    case = channel_c1()
+    g = Grid(case)
+    ls = LevelSet(case.geom_kind, case.geom_params)
+    samples = [ls.phi_points(g, c) for c in range(3)]
+    sc = case.with_(geom_kind=GEOM_SAMPLED, geom_params=())
+    ls_s = LevelSet(GEOM_SAMPLED, (), samples)
+    ca = classify(g, ls)
+    cb = classify(g, ls_s)
+    wa = build_weights(g, ls, ca, case.nu)
+    wb = build_weights(g, ls_s, cb, sc.nu)
+    for c in range(2):
+        assert np.array_equal(ca.mask, cb.mask)
+        assert np.array_equal(ca.lists[c], cb.lists[c])
+        if len(wa.lam_list[c]):
+            assert np.abs(wa.lam_list[c] - wb.lam_list[c]).max() <= 1e-9 * np.abs(wa.lam_list[c]).max()
+    assert len(ca.lists[0]) > 0
