@@ -79,7 +79,10 @@ enum {
                              * phi = min over tubes and segments of |X - C| - r(t), with C the
                              * projection of X on the segment, t in [0,1] its position and r
                              * interpolated linearly between the segment's end radii        */
-    IBM_GEOM_SAMPLED = 6    /* reserved (IBM_E_UNSUPPORTED)                                   */
+    IBM_GEOM_SAMPLED = 6    /* phi sampled at the velocity points: sdf[c] of ibm_geom_desc.
+                             * Fluid where phi < 0; delta = Delta phi_P / (phi_P - phi_Q)
+                             * (linear interpolation, Sec. 2.2 leaves the root-finding open).
+                             * Needs a periodic x (the inflow face is not a sample point).   */
 };
 /* B(x) of Eq. (Bexpr), x = lambda c_k dt */
 enum { IBM_B_EXACT = 0, IBM_B_EULER = 1, IBM_B_TAYLOR2 = 2 };
@@ -116,6 +119,11 @@ typedef struct {
     const double* data; /* IBM_GEOM_TUBES: host array of ndata doubles (see the enum), read at
                          * setup; NULL for the other kinds */
     int ndata;
+    const double* sdf[3]; /* IBM_GEOM_SAMPLED: DEVICE arrays, FP64, layout (nz, ny, nx) x fastest,
+                           * phi of component c at its own points (u on +x faces, v on +y, w on +z);
+                           * sdf[2] unused in 2D.  Caller-owned: read by ibm_setup_geometry and by
+                           * every ibm_build_weights call, so they must stay valid and unchanged
+                           * while weights may be rebuilt.  NULL for the other kinds. */
 } ibm_geom_desc;
 
 typedef struct {

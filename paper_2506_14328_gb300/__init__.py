@@ -41,7 +41,7 @@ class ibm_grid_desc(C.Structure):
 
 class ibm_geom_desc(C.Structure):
     _fields_ = [("kind", C.c_int), ("nparam", C.c_int), ("param", C.c_double * 32),
-                ("data", C.POINTER(C.c_double)), ("ndata", C.c_int)]
+                ("data", C.POINTER(C.c_double)), ("ndata", C.c_int), ("sdf", C.c_void_p * 3)]
 
 
 class ibm_buffers(C.Structure):

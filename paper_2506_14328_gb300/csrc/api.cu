@@ -316,7 +316,14 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     int kind = geom->kind;
     int need = kind == IBM_GEOM_PLANES ? 2 : kind == IBM_GEOM_CYLINDER ? 4 : kind == IBM_GEOM_SPHERE ? 5
              : kind == IBM_GEOM_SINE_WALL ? 4 : 0;
-    if (kind == IBM_GEOM_SAMPLED) return ibm_set_error(IBM_E_UNSUPPORTED, "geometry kind not built");
+    if (kind == IBM_GEOM_SAMPLED) {
+        const int nc = grid->ndim == 3 ? 3 : 2;
+        for (int c = 0; c < nc; ++c)
+            if (!geom->sdf[c] || ((uintptr_t)geom->sdf[c] & 7u))
+                return ibm_set_error(IBM_E_INVALID, "sampled geometry: sdf[c] must be 8-byte aligned device arrays");
+        if (grid->bc_lo[0] != IBM_BC_PERIODIC)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "sampled geometry needs a periodic x (the inflow face is not sampled)");
+    }
     if (kind == IBM_GEOM_TUBES) {
         if (!geom->data || geom->ndata < 2) return ibm_set_error(IBM_E_INVALID, "tubes: data is missing");
         const double nt = geom->data[0], np = geom->data[1];
@@ -355,6 +362,8 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
         h->geo.npts = (int)geom->data[1];
         std::memcpy(h->geo.tube, geom->data + 2, (size_t)h->geo.ntubes * h->geo.npts * 4 * sizeof(double));
     }
+    for (int c = 0; c < 3; ++c)
+        h->geo.sdf[c] = (kind == IBM_GEOM_SAMPLED && c < g.ncomp) ? geom->sdf[c] : nullptr;
     h->geom.data = nullptr;   // the caller's array is not kept
     h->geom.ndata = 0;
     h->prec = grid->precision;

@@ -40,6 +40,7 @@ struct GeomP {
     double p[8];
     int ntubes, npts;
     double tube[TUBE_MAX * TUBE_PTS * 4];
+    const double* sdf[3];   // IBM_GEOM_SAMPLED: phi of each component at its points (device)
 };
 
 // The IBM coefficients of one stage for one component: indexed by list

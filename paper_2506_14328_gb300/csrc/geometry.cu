@@ -95,8 +95,14 @@ __global__ void k_classify_vel(GridP g, GeomP geo, uint8_t* __restrict__ velbits
     uint8_t b = 0;
     for (int c = 0; c < g.ncomp; ++c) {
         if (bface(g, c, i, j)) continue;
-        double x = coord(g, 0, i, c), y = coord(g, 1, j, c), z = coord(g, 2, k, c);
-        if (phi_at(geo, x, y, z) < 0.0) b |= (uint8_t)(1u << c);
+        double phi;
+        if (geo.kind == IBM_GEOM_SAMPLED) {
+            phi = geo.sdf[c][id];
+        } else {
+            double x = coord(g, 0, i, c), y = coord(g, 1, j, c), z = coord(g, 2, k, c);
+            phi = phi_at(geo, x, y, z);
+        }
+        if (phi < 0.0) b |= (uint8_t)(1u << c);
     }
     if (!g.xper) {
         // bit 7: the inflow face (u at i = -1, i.e. x = origin) of row (j, k) is fluid at i = 0,
@@ -364,8 +370,9 @@ __global__ void k_weights(GridP g, GeomP geo, WeightArgs a, const uint8_t* __res
     int k = lin / (g.nx * g.ny);
     double lam = 0.0, src = 0.0;
     if (!a.no_ibm) {
+        const bool sampled = geo.kind == IBM_GEOM_SAMPLED;
         double P[3] = {coord(g, 0, i, c), coord(g, 1, j, c), coord(g, 2, k, c)};
-        double phiP = phi_at(geo, P[0], P[1], P[2]);
+        double phiP = sampled ? geo.sdf[c][lin] : phi_at(geo, P[0], P[1], P[2]);
         for (int d = 0; d < g.ndim; ++d) {
             double D = d == 0 ? g.dx : (d == 1 ? g.dy : g.dz);
             for (int s = 1; s >= -1; s -= 2) {
@@ -374,16 +381,19 @@ __global__ void k_weights(GridP g, GeomP geo, WeightArgs a, const uint8_t* __res
                 if (bface(g, c, ii, jj)) continue;
                 long long q = ii + (long long)g.nx * (jj + (long long)g.ny * kk);
                 if ((mask[q] >> c) & 1u) continue;       // internal neighbour
-                double phiQ = phi_at(geo, coord(g, 0, ii, c), coord(g, 1, jj, c), coord(g, 2, kk, c));
+                double phiQ = sampled ? geo.sdf[c][q]
+                                      : phi_at(geo, coord(g, 0, ii, c), coord(g, 1, jj, c), coord(g, 2, kk, c));
                 double dl;
                 if (phiQ == 0.0) {
                     dl = D;
+                } else if (sampled) {
+                    // the root of the straight line through the two samples
+                    dl = __dmul_rn(D, __ddiv_rn(phiP, __dsub_rn(phiP, phiQ)));
                 } else {
                     dl = delta_closed(geo, P, d, s, D);
                     if (dl < 0.0) dl = delta_bisect(geo, P, d, s, D);
                 }
                 dl = fmin(fmax(dl, 1e-12 * D), D);
-                (void)phiP;
                 lam = lam + a.nu * (D - dl) / (dl * D * D);
                 src = src + a.nu * (a.wall_u[c] * wall_factor(geo.kind, d, s)) / (dl * D);
             }

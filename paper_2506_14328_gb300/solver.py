@@ -28,7 +28,7 @@ class Solver:
 
     def __init__(self, *, ndim, n, L, origin, bc_lo, bc_hi, precision, geom_kind, geom_params, nu, dt,
                  g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0, wall_u=(0.0, 0.0, 0.0), no_ibm=False,
-                 body_force=False, inflow=(0.0, 0.0, 0.0), device="cuda", stream=None):
+                 body_force=False, inflow=(0.0, 0.0, 0.0), samples=None, device="cuda", stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("the IBM solver needs a CUDA device")
         self.device = torch.device(device)
@@ -60,6 +60,14 @@ class Solver:
             geo.data = C.cast(self._geom_data, C.POINTER(C.c_double))
             geo.ndata = len(geom_params)
             geo.nparam = 0
+        elif geo.kind == 6:    # IBM_GEOM_SAMPLED: phi of each component at its points, on the device
+            if samples is None:
+                raise ValueError("a sampled geometry needs samples: phi of u, v (and w) at their points")
+            self._sdf = [torch.as_tensor(np.ascontiguousarray(samples[c], dtype=np.float64).reshape(self.shape),
+                                         device=self.device) for c in range(3 if self.ndim == 3 else 2)]
+            for c, t in enumerate(self._sdf):
+                geo.sdf[c] = t.data_ptr()
+            torch.cuda.synchronize(self.device)
         else:
             geo.nparam = len(geom_params)
             for q, v in enumerate(geom_params):
@@ -88,6 +96,7 @@ class Solver:
 
     @classmethod
     def from_case(cls, case, precision=None, no_ibm=False, **kw):
+        # a sampled geometry takes its samples through kw (samples=[phi_u, phi_v, phi_w])
         """Build from any object with the attributes of a workload description."""
         return cls(ndim=case.ndim, n=case.n, L=case.L, origin=case.origin, bc_lo=case.bc_lo, bc_hi=case.bc_hi,
                    precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,

@@ -434,3 +434,46 @@ def test_body_force_off_reports_nan_and_fp32_is_close():
     F64 = o.mean_force()
     assert np.abs(F32 - F64).max() < 1e-3 * np.abs(F64).max()
     g32.close()
+
+
+def _sphere_samples(case):
+    """phi of the sphere (exact signed distance |X - C| - R) at the u, v, w points."""
+    nx, ny, nz = case.n
+    d = [case.L[a] / case.n[a] for a in range(3)]
+    cx, cy, cz, R, sgn = case.geom_params
+    out = []
+    for c in range(3):
+        ax = [case.origin[a] + (np.arange(case.n[a]) + (1.0 if a == c else 0.5)) * d[a] for a in range(3)]
+        z, y, x = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        out.append(-sgn * (np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) - R))
+    return out
+
+
+def test_sampled_geometry_matches_oracle():
+    """A sampled level set (the sphere's distance at the velocity points) through the device
+    path: classification bit-exact, weights (straight-line root of the samples) and two full
+    steps to 1e-12."""
+    from inputs import GEOM_SAMPLED
+    base = small_case("sphere3d")
+    samples = _sphere_samples(base)
+    case = base.with_(geom_kind=GEOM_SAMPLED, geom_params=())
+    f = initial_field(case)
+    g = _gpu(case, samples=samples)
+    o = OracleSolver(case, samples=samples)
+    mask, lists = g.classification()
+    assert np.array_equal(mask, o.cls.mask)
+    for c in range(3):
+        assert np.array_equal(lists[c], o.cls.lists[c])
+    lam, _ = g.weights_lists()
+    for c in range(3):
+        ref = o.w.lam_list[c]
+        assert np.abs(lam[c] - ref).max() <= TOL64 * np.abs(ref).max()
+    g.set_state(f["u"], f["v"], f["w"], f["p"])
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        ug, _ = g.state()
+        for c in range(3):
+            assert _rel(o, ug[c], o.u[c], c) < TOL64, c
+    g.close()
