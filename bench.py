@@ -50,11 +50,13 @@ TRIDIAG_BYTES_PER_SPECTRAL_POINT = 64.0
 # keyed by kernel, with the hash of the source file it was taken on; a changed
 # source makes the figure stale and it is reported as null.
 NCU_TRAFFIC = {
-    # profiles/c3_wavy_384x256x256_momentum_tma_ncu.md: the three stages of one step on the
-    # 384x256x256 grid read+wrote 1025.2, 1325.6 and 1041.6 MB; their mean per launch
-    "momentum": ((1025.195264e6 + 1325.607680e6 + 1041.563136e6) / 3.0, "9d17244a60fed4d0"),
+    # (kernel, workload): (DRAM bytes per launch, mean of the three RK3 stages of one step, and
+    # the sha256[:16] of the kernel's source file the capture ran on)
+    # profiles/c3_wavy_384x256x256_momentum_tma_ncu.md: 1025.2, 1324.3 and 1040.7 MB
+    ("momentum", "c3"): ((1025.162496e6 + 1324.251648e6 + 1040.737792e6) / 3.0, "6e256579b35afb2d"),
+    # profiles/c4_airway_512x384x256_momentum_tma_traffic.md: 2269.7, 2894.1 and 2300.9 MB
+    ("momentum", "c4"): ((2269.658624e6 + 2894.148096e6 + 2300.914176e6) / 3.0, "6e256579b35afb2d"),
 }
-
 
 KERNEL_FILE = {"momentum": "momentum.cu"}   # other kernels of this library live in step.cu
 
@@ -341,7 +343,7 @@ def run_gpu(args):
                 alg += nibm * 16.0
         achieved = alg / avg_s / 1e9 if avg_s > 0 else None
         traffic = None
-        rec = NCU_TRAFFIC.get(dom)
+        rec = NCU_TRAFFIC.get((dom, args.workload))
         if rec and rec[1] == src_hash(KERNEL_FILE.get(dom, "step.cu")):
             traffic = rec[0]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
