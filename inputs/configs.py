@@ -45,6 +45,7 @@ class Case:
     target_flux: float = 0.0   # volume integral of u over the fluid (FLOW_CONST_FLUX)
     wall_u: tuple = (0.0, 0.0, 0.0)
     inflow: tuple = (0.0, 0.0, 0.0)   # velocity entering through the -x face (x inflow / outflow boxes)
+    projection: str = "fullbox"       # "fullbox" (the unmodified projection) or "masked" (internal faces only)
     precision: str = "fp64"    # "fp64" or "fp32" (FP32 momentum, FP64 tridiagonal/reductions)
     steps: int = 1
     init: dict = field(default_factory=lambda: {"kind": "zero"})

@@ -204,3 +204,64 @@ def solve_direct(grid, rhs):
     b = np.concatenate([rhs.ravel(), [0.0]])
     x = spla.spsolve(M, b)
     return x[:N].reshape(grid.shape)
+
+
+# ---- reading B of the projection: the masked (consistent) operator ---------------------------
+#
+# Sec. 3.3 says that only the internal pressure points are updated.  Read literally, the
+# correction acts only on internal velocity points (the faces between two internal cells)
+# and the Poisson operator is D M G, M zeroing G on every other face.  Summed over the
+# internal faces f between cells a and b (b = a + e_d):
+#     (D M G phi)_a += (phi_b - phi_a) / Delta_d^2,   (D M G phi)_b -= (phi_b - phi_a) / Delta_d^2.
+# The unknowns are the internal (pressure) cells; the operator is singular with one constant
+# per connected group of them, and the gauge is a zero mean over each group.
+
+def masked_operator_matrix(grid, cls):
+    """Sparse D M G over all cells: the 2 x 2 stencil of every internal velocity point."""
+    N = grid.shape[0] * grid.shape[1] * grid.shape[2]
+    idx = np.arange(N).reshape(grid.shape)
+    rows, cols, vals = [], [], []
+    for d in range(grid.ncomp):
+        inv = 1.0 / grid.d[d] ** 2
+        face = cls.internal[d]                     # internal velocity point = face between a and a + e_d
+        b_idx = np.roll(idx, -1, axis=AX[d])       # never wraps at an internal face of a wall direction
+        a = idx[face]
+        b = b_idx[face]
+        rows += [a, a, b, b]
+        cols += [b, a, a, b]
+        vals += [np.full(a.size, inv), np.full(a.size, -inv), np.full(a.size, inv), np.full(a.size, -inv)]
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+
+
+def solve_masked(grid, cls, rhs):
+    """phi on the internal cells with D M G phi = rhs there (zero mean over each connected
+    group of internal cells), zero on every other cell.  The operator is singular with one
+    constant per group: phi is fixed to 0 at the first cell of each group, the rest is a
+    sparse solve (conjugate gradients of scipy on the symmetric positive definite negative of
+    the reduced operator, to a relative residual of 1e-14: a sparse LU fills in too much on
+    3D grids), and each group is then shifted to zero mean (the right-hand side sums to zero
+    over a group, so the fixed cell's equation holds as well)."""
+    from scipy.sparse.csgraph import connected_components
+    A = masked_operator_matrix(grid, cls)
+    inside = np.flatnonzero(cls.p_internal.ravel())
+    Ai = A[inside][:, inside].tocsr()
+    ngroups, label = connected_components(Ai != 0, directed=False)
+    n = inside.size
+    first = np.array([np.flatnonzero(label == q)[0] for q in range(ngroups)])
+    keep = np.setdiff1d(np.arange(n), first)
+    x = np.zeros(n)
+    K = -Ai[keep][:, keep].tocsr()
+    b = -rhs.ravel()[inside][keep]
+    y, info = spla.cg(K, b, rtol=1e-14, atol=0.0, maxiter=50 * keep.size)
+    if info != 0 or not np.abs(K @ y - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300):
+        raise RuntimeError("masked Poisson solve did not converge")
+    x[keep] = y
+    for q in range(ngroups):
+        sel = label == q
+        x[sel] -= x[sel].mean()
+    out = np.zeros(grid.shape[0] * grid.shape[1] * grid.shape[2])
+    out[inside] = x
+    return out.reshape(grid.shape)

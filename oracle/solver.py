@@ -7,6 +7,10 @@ Order per substage k (paper Sec. 2.1 and Eq. rk3-rai):
   4. phi: D G phi = D u* / (c_k Delta t)                   (poisson.solve_*)
   5. u^k = u* - c_k Delta t G phi,  p^k = p^{k-1} + phi
 
+Projection: "fullbox" (the default) solves D G phi on the whole box and corrects every face
+whose velocity is not prescribed; "masked" (poisson.solve_masked) solves D M G phi over the
+internal cells and corrects only the internal faces, so the external faces keep u* = 0.
+
 Constant flow rate is not described in the paper (its nose case imposes a
 pressure drop, its channel keeps the flow rate).  Reading taken: a uniform
 forcing Pi enters R as + c_k Delta t Pi on every internal u point, so it
@@ -25,14 +29,14 @@ from .classify import classify
 from .weights import build_weights, B_of_x, RK3_A, RK3_B, RK3_C
 from .momentum import (rhs, stage_update, pressure_gradient, masked, inflow_face, outflow_update,
                        outflow_balance)
-from .poisson import divergence, gradient, solve_spectral, solve_direct
+from .poisson import divergence, gradient, solve_spectral, solve_direct, solve_masked
 from .forces import body_terms, stage_impulse
 
 FLOW_FORCED, FLOW_CONST_FLUX = 0, 1
 
 
 class OracleSolver:
-    def __init__(self, case, samples=None, no_ibm: bool = False, poisson: str = "spectral"):
+    def __init__(self, case, samples=None, no_ibm: bool = False, poisson: str = "spectral", projection=None):
         self.case = case
         self.grid = Grid(case)
         self.levelset = LevelSet(case.geom_kind, case.geom_params, samples)
@@ -47,6 +51,11 @@ class OracleSolver:
         if self.grid.xflow and self.flow_mode == FLOW_CONST_FLUX:
             raise ValueError("a constant flow rate needs a periodic x direction")
         self.poisson = solve_spectral if poisson == "spectral" else solve_direct
+        # "fullbox": the unmodified projection (D G of the whole box, every non-prescribed face
+        # corrected); "masked": D M G over the internal cells, only internal faces corrected
+        self.projection = projection or getattr(case, "projection", "fullbox")
+        if self.projection not in ("fullbox", "masked"):
+            raise ValueError("projection is 'fullbox' or 'masked'")
         z = np.zeros(self.grid.shape)
         self.u = [z.copy(), z.copy(), z.copy()]
         self.p = z.copy()
@@ -110,9 +119,14 @@ class OracleSolver:
     def _project(self, ustar, ckdt: float, update_p: bool):
         g = self.grid
         r = divergence(g, ustar, inflow_face(g, self.cls) if g.xflow else None) / ckdt
-        phi = self.poisson(g, r)
-        G = gradient(g, phi)
-        self.u = [ustar[c] - ckdt * G[c] for c in range(3)]
+        if self.projection == "masked":
+            phi = solve_masked(g, self.cls, r)
+            G = gradient(g, phi)
+            self.u = [np.where(self.cls.internal[c], ustar[c] - ckdt * G[c], ustar[c]) for c in range(3)]
+        else:
+            phi = self.poisson(g, r)
+            G = gradient(g, phi)
+            self.u = [ustar[c] - ckdt * G[c] for c in range(3)]
         if update_p:
             self.p = self.p + phi
         self.last_phi = phi
