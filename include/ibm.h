@@ -165,6 +165,8 @@ typedef struct {
                          * fluid (the paper reports drag and lift, Sec. 4.1, without a method;
                          * this is the reading taken).  NaN when no step was counted. */
     long long force_steps; /* full steps in that mean; the call resets the sums */
+    int proj_iters;     /* IBM_PROJ_MASKED: iterations of the last projection solve (0 otherwise) */
+    double proj_resid;  /* its final residual over the right-hand side (2-norms) */
 } ibm_diag;
 
 typedef struct {
@@ -218,6 +220,26 @@ ibm_status ibm_project(ibm_solver* h);
  * y), zero box mean; `rhs_inout` is a device array of N grid-precision values
  * overwritten by phi.  The rhs must sum to zero.  Asynchronous. */
 ibm_status ibm_poisson(ibm_solver* h, void* rhs_inout);
+
+/* Projection operators.  IBM_PROJ_FULLBOX (the default): the unmodified projection, D G of the
+ * whole box, every face whose velocity is not prescribed corrected.  IBM_PROJ_MASKED: the
+ * literal reading of Sec. 3.3 ("only the internal pressure points are updated"): D M G phi =
+ * D u* over the internal cells, M keeping only internal faces, and only internal faces
+ * corrected, so external faces keep u* = 0 and every internal cell of the field the operators
+ * read is divergence-free.  Solved by conjugate gradients in FP64 preconditioned with the
+ * full-box solve; each iteration reads back its inner products (no graph capture). */
+enum { IBM_PROJ_FULLBOX = 0, IBM_PROJ_MASKED = 1 };
+
+/* Device bytes IBM_PROJ_MASKED needs: five FP64 fields of N values. */
+ibm_status ibm_projection_bytes(const ibm_solver* h, size_t* bytes);
+
+/* Select the projection.  IBM_PROJ_MASKED: `buffer` is a caller-owned device buffer of at
+ * least ibm_projection_bytes (256-byte aligned, kept until the mode changes or the solver is
+ * destroyed); the iteration stops at a residual of tol times the right-hand side (2-norm) or
+ * after maxit iterations (the last count and residual are in ibm_diag).  IBM_PROJ_FULLBOX:
+ * buffer, tol and maxit are ignored.  IBM_STEP_GRAPH and batches refuse IBM_PROJ_MASKED
+ * (IBM_E_UNSUPPORTED).  Blocking only in that it drops a captured graph. */
+ibm_status ibm_set_projection(ibm_solver* h, int mode, double tol, int maxit, void* buffer, size_t bytes);
 
 /* Norms, CFL, flux, kinetic energy of the current fields.  Blocking; returns
  * IBM_E_DIVERGED (and fills out->status) if a field is not finite. */

@@ -20,13 +20,15 @@ IBM_OK, IBM_E_INVALID, IBM_E_CUDA, IBM_E_NOMEM, IBM_E_UNSUPPORTED, IBM_E_DIVERGE
 IBM_BC_PERIODIC, IBM_BC_NOSLIP, IBM_BC_FREESLIP, IBM_BC_INFLOW, IBM_BC_OUTFLOW = 0, 1, 2, 3, 4
 IBM_FP64, IBM_FP32 = 0, 1
 IBM_STEP_PREDICTOR_ONLY, IBM_STEP_GRAPH = 1, 2
+IBM_PROJ_FULLBOX, IBM_PROJ_MASKED = 0, 1
 
 STATUS_NAMES = {0: "IBM_OK", -1: "IBM_E_INVALID", -2: "IBM_E_CUDA", -3: "IBM_E_NOMEM", -4: "IBM_E_UNSUPPORTED",
                 -5: "IBM_E_DIVERGED", -6: "IBM_E_TIMEOUT", -7: "IBM_E_STATE"}
 
 # every symbol the header declares
 EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_geometry", "ibm_weights_bytes",
-            "ibm_build_weights", "ibm_step", "ibm_project", "ibm_poisson", "ibm_diagnostics",
+            "ibm_build_weights", "ibm_step", "ibm_project", "ibm_poisson", "ibm_projection_bytes",
+            "ibm_set_projection", "ibm_diagnostics",
             "ibm_get_classification", "ibm_get_weights", "ibm_state_bytes", "ibm_export_state",
             "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_diagnostics_noalloc",
             "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
@@ -57,7 +59,8 @@ class ibm_physics(C.Structure):
 class ibm_diag(C.Structure):
     _fields_ = [("div_l2", C.c_double), ("div_linf", C.c_double), ("cfl", C.c_double), ("flux", C.c_double * 3),
                 ("ke", C.c_double), ("pi", C.c_double), ("step", C.c_longlong), ("status", C.c_int),
-                ("force", C.c_double * 3), ("force_steps", C.c_longlong)]
+                ("force", C.c_double * 3), ("force_steps", C.c_longlong), ("proj_iters", C.c_int),
+                ("proj_resid", C.c_double)]
 
 
 class ibm_kernel_time(C.Structure):
@@ -85,6 +88,8 @@ def _load() -> C.CDLL:
         "ibm_step": ([C.c_void_p, C.c_int, C.c_uint], C.c_int),
         "ibm_project": ([C.c_void_p], C.c_int),
         "ibm_poisson": ([C.c_void_p, C.c_void_p], C.c_int),
+        "ibm_projection_bytes": ([C.c_void_p, P(C.c_size_t)], C.c_int),
+        "ibm_set_projection": ([C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_size_t], C.c_int),
         "ibm_diagnostics": ([C.c_void_p, P(ibm_diag)], C.c_int),
         "ibm_get_classification": ([C.c_void_p, C.c_void_p, P(C.c_void_p), P(C.c_int)], C.c_int),
         "ibm_get_weights": ([C.c_void_p, P(C.c_void_p), P(C.c_void_p)], C.c_int),
@@ -162,6 +167,17 @@ def ibm_project(h: int):
 
 def ibm_poisson(h: int, rhs_ptr: int):
     _check(lib.ibm_poisson(C.c_void_p(h), C.c_void_p(rhs_ptr)), "ibm_poisson")
+
+
+def ibm_projection_bytes(h: int) -> int:
+    b = C.c_size_t(0)
+    _check(lib.ibm_projection_bytes(C.c_void_p(h), C.byref(b)), "ibm_projection_bytes")
+    return b.value
+
+
+def ibm_set_projection(h: int, mode: int, tol: float, maxit: int, buf_ptr: int, nbytes: int):
+    _check(lib.ibm_set_projection(C.c_void_p(h), int(mode), float(tol), int(maxit), C.c_void_p(buf_ptr),
+                                  C.c_size_t(nbytes)), "ibm_set_projection")
 
 
 def ibm_diagnostics(h: int, raise_on_diverged: bool = True) -> ibm_diag:

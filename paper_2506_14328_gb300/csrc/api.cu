@@ -459,6 +459,8 @@ ibm_status ibm_step(ibm_solver* h, int nsteps, unsigned flags) {
     }
     if (flags & IBM_STEP_GRAPH) {
         if (h->timing) return ibm_set_error(IBM_E_STATE, "timing is not available in graph mode");
+        if (h->proj_mode == IBM_PROJ_MASKED)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "the masked projection reads back its inner products: no graph mode");
         if (!h->graph_ready) {
             cudaGraph_t graph;
             IBM_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -536,6 +538,8 @@ ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
     out->pi = r[0];
     out->step = h->steps;
     out->force_steps = (long long)r[SCAL_FSTEPS];
+    out->proj_iters = h->proj_mode == IBM_PROJ_MASKED ? h->proj_iters : 0;
+    out->proj_resid = h->proj_mode == IBM_PROJ_MASKED ? h->proj_resid : 0.0;
     for (int c = 0; c < 3; ++c)
         out->force[c] = out->force_steps > 0 ? r[SCAL_FORCE + c] / r[SCAL_FSTEPS] : std::nan("");
     if (r[3] != 0.0) {
@@ -547,6 +551,39 @@ ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
     bool finite = s[11] == 0.0 && std::isfinite(out->div_l2) && std::isfinite(out->ke);
     out->status = finite ? IBM_OK : IBM_E_DIVERGED;
     if (!finite) return ibm_set_error(IBM_E_DIVERGED, "non-finite values in the fields");
+    return IBM_OK;
+}
+
+ibm_status ibm_projection_bytes(const ibm_solver* h, size_t* bytes) {
+    if (!h) return ibm_set_error(IBM_E_INVALID, "NULL handle");
+    if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");
+    const size_t one = ((size_t)h->N * sizeof(double) + ALIGN - 1) / ALIGN * ALIGN;
+    *bytes = 5 * one;
+    return IBM_OK;
+}
+
+ibm_status ibm_set_projection(ibm_solver* h, int mode, double tol, int maxit, void* buffer, size_t bytes) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (mode != IBM_PROJ_FULLBOX && mode != IBM_PROJ_MASKED) return ibm_set_error(IBM_E_INVALID, "bad projection mode");
+    drop_graph(h);
+    if (mode == IBM_PROJ_FULLBOX) {
+        h->proj_mode = mode;
+        for (double*& v : h->pcg) v = nullptr;
+        return IBM_OK;
+    }
+    if (!(tol > 0.0) || !std::isfinite(tol) || maxit < 1) return ibm_set_error(IBM_E_INVALID, "need tol > 0 and maxit >= 1");
+    size_t need = 0;
+    ibm_projection_bytes(h, &need);
+    if (!buffer || (uintptr_t)buffer % ALIGN) return ibm_set_error(IBM_E_INVALID, "buffer must be 256-byte aligned");
+    if (bytes < need) return ibm_set_error(IBM_E_NOMEM, "projection buffer too small: need " + std::to_string(need));
+    const size_t one = need / 5;
+    for (int q = 0; q < 5; ++q) h->pcg[q] = (double*)((char*)buffer + q * one);
+    h->proj_mode = mode;
+    h->proj_tol = tol;
+    h->proj_maxit = maxit;
+    h->proj_iters = 0;
+    h->proj_resid = 0.0;
     return IBM_OK;
 }
 
@@ -751,6 +788,8 @@ ibm_status ibm_batch_set(ibm_batch* b, ibm_solver* const* members, const int* st
         if (st != IBM_OK) return st;
         if (!members[q]->weights_ready) return ibm_set_error(IBM_E_STATE, "a member has no weights");
         if (members[q]->timing) return ibm_set_error(IBM_E_STATE, "disable member timing before batching");
+        if (members[q]->proj_mode == IBM_PROJ_MASKED)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "a member uses the masked projection (no graph capture)");
         if (steps[q] < 0) return ibm_set_error(IBM_E_INVALID, "negative step count");
     }
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }

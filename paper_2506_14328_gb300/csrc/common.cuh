@@ -356,6 +356,14 @@ struct ibm_solver {
     cudaGraphExec_t graph = nullptr;
     bool graph_ready = false;
     long long graph_launches = 0;   // kernels of this library in one captured step
+
+    // masked projection (IBM_PROJ_MASKED): conjugate-gradient vectors x, r, z, p, A p (FP64)
+    int proj_mode = IBM_PROJ_FULLBOX;
+    double proj_tol = 1e-10;
+    int proj_maxit = 500;
+    double* pcg[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int proj_iters = 0;
+    double proj_resid = 0.0;
 };
 
 // The IBM coefficient lists of RK stage k (list position -> {alpha, beta, s}).

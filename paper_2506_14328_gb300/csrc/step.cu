@@ -902,6 +902,270 @@ FluxCorr<T> flux_corr(ibm_solver* h, int k) {
     return fc;
 }
 
+// ---------------------------------------------------------------------------
+// Masked projection (IBM_PROJ_MASKED): conjugate gradients on A' = -D M G over the
+// internal cells, preconditioned with the full-box solve (z = -(D G)^{-1} r), FP64
+// vectors that are zero outside the internal cells.  Block partial sums of the inner
+// products go to h->partials; the host adds them in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int PCG_BLOCKS = 4 * 152;
+
+__device__ __forceinline__ double block_sum256(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 8; ++w) t += sh[w];
+    return t;
+}
+
+// b = -(D u*) on the internal cells; x = 0; r = b; partial sums of r.r
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_init(long long N, const uint8_t* __restrict__ mask,
+                                                  const T* __restrict__ rhs, double* __restrict__ x,
+                                                  double* __restrict__ r, double* __restrict__ part) {
+    __shared__ double sh[8];
+    double s = 0.0;
+    for (long long id = blockIdx.x * 256LL + threadIdx.x; id < N; id += (long long)gridDim.x * 256) {
+        const double b = (mask[id] & IBM_MASK_P) ? -(double)rhs[id] : 0.0;
+        x[id] = 0.0;
+        r[id] = b;
+        s += b * b;
+    }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// y = -(D M G x) on the internal cells (zero elsewhere); partial sums of x.y
+__global__ void __launch_bounds__(256) k_pcg_matvec(GridP g, const uint8_t* __restrict__ mask,
+                                                    const double* __restrict__ x, double* __restrict__ y,
+                                                    double* __restrict__ part) {
+    __shared__ double sh[8];
+    double s = 0.0;
+    const double inv2[3] = {1.0 / (g.dx * g.dx), 1.0 / (g.dy * g.dy), 1.0 / (g.dz * g.dz)};
+    for (long long id = blockIdx.x * 256LL + threadIdx.x; id < g.N; id += (long long)gridDim.x * 256) {
+        const uint32_t m = mask[id];
+        double out = 0.0;
+        if (m & IBM_MASK_P) {
+            const int i = (int)(id % g.nx);
+            const int j = (int)((id / g.nx) % g.ny);
+            const int k = (int)(id / ((long long)g.nx * g.ny));
+            const double xc = x[id];
+            double acc = 0.0;
+            for (int d = 0; d < g.ndim; ++d) {
+                const int n = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+                const int q = d == 0 ? i : (d == 1 ? j : k);
+                const long long st = d == 0 ? 1 : (d == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
+                const bool per = d == 2 || (d == 0 && g.xper);
+                // +d face: the velocity point of this cell
+                if ((m >> d) & 1u) {
+                    const long long ip = q + 1 < n ? id + st : id - (long long)(n - 1) * st;
+                    acc += (x[ip] - xc) * inv2[d];
+                }
+                // -d face: the velocity point of the cell below
+                if (q > 0 || per) {
+                    const long long im = q > 0 ? id - st : id + (long long)(n - 1) * st;
+                    if ((mask[im] >> d) & 1u) acc -= (xc - x[im]) * inv2[d];
+                }
+            }
+            out = -acc;
+        }
+        y[id] = out;
+        s += x[id] * out;
+    }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// x += alpha p; r -= alpha Ap; partial sums of r.r
+__global__ void __launch_bounds__(256) k_pcg_update(long long N, double alpha, double* __restrict__ x,
+                                                    double* __restrict__ r, const double* __restrict__ p,
+                                                    const double* __restrict__ Ap, double* __restrict__ part) {
+    __shared__ double sh[8];
+    double s = 0.0;
+    for (long long id = blockIdx.x * 256LL + threadIdx.x; id < N; id += (long long)gridDim.x * 256) {
+        x[id] += alpha * p[id];
+        const double rn = r[id] - alpha * Ap[id];
+        r[id] = rn;
+        s += rn * rn;
+    }
+    s = block_sum256(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// the preconditioner's input: -r in the grid precision
+template <typename T>
+__global__ void k_pcg_to_field(long long N, const double* __restrict__ r, T* __restrict__ f) {
+    for (long long id = blockIdx.x * 256LL + threadIdx.x; id < N; id += (long long)gridDim.x * 256)
+        f[id] = (T)(-r[id]);
+}
+
+// z = the full-box solution on the internal cells (0 elsewhere); partial sums of z.r and z.Ap
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_from_field(long long N, const uint8_t* __restrict__ mask,
+                                                        const T* __restrict__ f, double* __restrict__ z,
+                                                        const double* __restrict__ r, const double* __restrict__ Ap,
+                                                        double* __restrict__ part, int nb) {
+    __shared__ double sh[8];
+    double s1 = 0.0, s2 = 0.0;
+    for (long long id = blockIdx.x * 256LL + threadIdx.x; id < N; id += (long long)gridDim.x * 256) {
+        const double v = (mask[id] & IBM_MASK_P) ? (double)f[id] : 0.0;
+        z[id] = v;
+        s1 += v * r[id];
+        s2 += v * Ap[id];
+    }
+    s1 = block_sum256(s1, sh);
+    __syncthreads();
+    s2 = block_sum256(s2, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s1;
+        part[nb + blockIdx.x] = s2;
+    }
+}
+
+__global__ void k_pcg_direction(long long N, double beta, const double* __restrict__ z, double* __restrict__ p) {
+    for (long long id = blockIdx.x * 256LL + threadIdx.x; id < N; id += (long long)gridDim.x * 256)
+        p[id] = z[id] + beta * p[id];
+}
+
+template <typename T>
+__global__ void k_pcg_out(long long N, const double* __restrict__ x, T* __restrict__ f) {
+    for (long long id = blockIdx.x * 256LL + threadIdx.x; id < N; id += (long long)gridDim.x * 256)
+        f[id] = (T)x[id];
+}
+
+// reads back nsum groups of nb block partials and adds each group in order
+ibm_status pcg_sums(ibm_solver* h, int nb, int nsum, double* out) {
+    std::vector<double> buf((size_t)nb * nsum);
+    IBM_CUDA_TRY(cudaMemcpyAsync(buf.data(), h->partials, buf.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int q = 0; q < nsum; ++q) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += buf[(size_t)q * nb + b];
+        out[q] = s;
+    }
+    return IBM_OK;
+}
+
+// D M G psi = rhs over the internal cells; rhs (the divergence, grid precision) in h->rhs is
+// replaced by psi.  Host-driven: one read-back of inner products per iteration.
+template <typename T>
+ibm_status masked_solve_t(ibm_solver* h) {
+    const GridP& g = h->gp;
+    const int nb = std::min(PCG_BLOCKS, h->npartials / 2);
+    double* x = h->pcg[0];
+    double* r = h->pcg[1];
+    double* z = h->pcg[2];
+    double* p = h->pcg[3];
+    double* Ap = h->pcg[4];
+    T* f = (T*)h->rhs;
+    double sums[2];
+    k_pcg_init<T><<<nb, 256, 0, h->stream>>>(g.N, h->mask, f, x, r, h->partials);
+    IBM_LAUNCH_CHECK();
+    ibm_status st = pcg_sums(h, nb, 1, sums);
+    if (st != IBM_OK) return st;
+    const double bnorm = std::sqrt(sums[0]);
+    int it = 0;
+    double rr = sums[0];
+    auto precondition = [&](bool with_ap) -> ibm_status {
+        k_pcg_to_field<T><<<nb, 256, 0, h->stream>>>(g.N, r, f);
+        IBM_LAUNCH_CHECK();
+        ibm_status s2 = poisson_t<T>(h, f);
+        if (s2 != IBM_OK) return s2;
+        k_pcg_from_field<T><<<nb, 256, 0, h->stream>>>(g.N, h->mask, f, z, r, with_ap ? Ap : r, h->partials, nb);
+        IBM_LAUNCH_CHECK();
+        return pcg_sums(h, nb, 2, sums);
+    };
+    if (bnorm > 0.0 && std::isfinite(bnorm)) {
+        st = precondition(false);
+        if (st != IBM_OK) return st;
+        double rz = sums[0];
+        k_pcg_direction<<<nb, 256, 0, h->stream>>>(g.N, 0.0, z, p);
+        IBM_LAUNCH_CHECK();
+        double best = rr;
+        int best_it = 0;
+        for (it = 1; it <= h->proj_maxit; ++it) {
+            k_pcg_matvec<<<nb, 256, 0, h->stream>>>(g, h->mask, p, Ap, h->partials);
+            IBM_LAUNCH_CHECK();
+            if ((st = pcg_sums(h, nb, 1, sums)) != IBM_OK) return st;
+            const double pAp = sums[0];
+            if (!(pAp > 0.0)) break;                      // the search direction vanished
+            const double alpha = rz / pAp;
+            k_pcg_update<<<nb, 256, 0, h->stream>>>(g.N, alpha, x, r, p, Ap, h->partials);
+            IBM_LAUNCH_CHECK();
+            if ((st = pcg_sums(h, nb, 1, sums)) != IBM_OK) return st;
+            rr = sums[0];
+            if (!std::isfinite(rr) || std::sqrt(rr) <= h->proj_tol * bnorm) break;
+            // stagnation at the round-off floor (the right-hand side sums to zero over each
+            // group of internal cells only to round-off): stop after 25 iterations without gain
+            if (rr < best) {
+                best = rr;
+                best_it = it;
+            } else if (it - best_it > 25) {
+                break;
+            }
+            if ((st = precondition(true)) != IBM_OK) return st;
+            // Polak-Ribiere: z_new.(r_new - r_old) / rz_old = -alpha z_new.Ap / rz_old
+            const double beta = -alpha * sums[1] / rz;
+            rz = sums[0];
+            k_pcg_direction<<<nb, 256, 0, h->stream>>>(g.N, beta, z, p);
+            IBM_LAUNCH_CHECK();
+        }
+    } else {
+        rr = 0.0;
+    }
+    h->proj_iters = std::min(it, h->proj_maxit);
+    h->proj_resid = bnorm > 0.0 ? std::sqrt(rr) / bnorm : 0.0;
+    k_pcg_out<T><<<nb, 256, 0, h->stream>>>(g.N, x, f);
+    IBM_LAUNCH_CHECK();
+    return IBM_OK;
+}
+
+// u = u* - G psi on the internal faces only (+ the constant-flow-rate increment at internal
+// u points), u = u* on every other face; p += psi / (c_k dt)
+template <typename T, bool FLUX>
+__global__ void k_correct_masked(GridP g, const T* __restrict__ us0, const T* __restrict__ us1,
+                                 const T* __restrict__ us2, const T* __restrict__ psi, const uint8_t* __restrict__ mask,
+                                 T* __restrict__ u0, T* __restrict__ u1, T* __restrict__ u2, T* __restrict__ p, T idx,
+                                 T idy, T idz, T inv_ckdt, int update_p, FluxCorr<T> fc) {
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * 32 + lane;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z;
+    if (j >= g.ny) return;                                   // whole warp
+    const bool live = i < g.nx;
+    const long long id = live ? i + (long long)g.nx * (j + (long long)g.ny * k) : 0;
+    const uint32_t m = live ? mask[id] : 0u;
+    T uc = T(0);
+    if (FLUX) {
+        const T pic = *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt;
+        const unsigned b = __ballot_sync(0xffffffffu, (m & IBM_MASK_IBM_U) != 0);
+        if (live) uc = flux_increment(fc, pic, (uint8_t)m, b, (j + g.ny * k) * g.nsegx + (int)blockIdx.x, lane);
+    }
+    if (!live) return;
+    const T pc = psi[id];
+    if (m & IBM_MASK_U) {
+        const long long ie = i + 1 < g.nx ? id + 1 : id - (g.nx - 1);
+        u0[id] = us0[id] + uc - (psi[ie] - pc) * idx;
+    } else {
+        u0[id] = us0[id];
+    }
+    if (m & IBM_MASK_V) u1[id] = us1[id] - (psi[id + g.nx] - pc) * idy;   // internal v: j + 1 < ny
+    else u1[id] = us1[id];
+    if (g.ndim == 3) {
+        const long long plane = (long long)g.nx * g.ny;
+        if (m & IBM_MASK_W) {
+            const long long it = k + 1 < g.nz ? id + plane : id - (long long)(g.nz - 1) * plane;
+            u2[id] = us2[id] - (psi[it] - pc) * idz;
+        } else {
+            u2[id] = us2[id];
+        }
+    }
+    if (update_p) p[id] = p[id] + pc * inv_ckdt;
+}
+
 template <typename T>
 ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const FluxCorr<T>& fc) {
     const GridP& g = h->gp;
@@ -923,6 +1187,13 @@ ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const 
     }
     IBM_LAUNCH_CHECK();
     timer_end(h, t, "divergence");
+    if (h->proj_mode == IBM_PROJ_MASKED) {
+        timer_begin(h, "masked_solve", &t);
+        ibm_status st = masked_solve_t<T>(h);
+        if (st != IBM_OK) return st;
+        timer_end(h, t, "masked_solve");
+        return IBM_OK;
+    }
     return poisson_t<T>(h, h->rhs);
 }
 
@@ -937,6 +1208,17 @@ ibm_status launch_correct(ibm_solver* h, T* const us[3], T inv_ckdt, int update_
     T* u2 = g.ndim == 3 ? (T*)h->buf.u[2] : u0;
     T* us2 = g.ndim == 3 ? us[2] : us[0];
     T* p = (T*)h->buf.p;
+    if (h->proj_mode == IBM_PROJ_MASKED) {
+        const dim3 cg = cell_grid(g);
+        if (flux)
+            k_correct_masked<T, true><<<cg, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix, iy,
+                                                                 iz, inv_ckdt, update_p, fc);
+        else
+            k_correct_masked<T, false><<<cg, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, ix,
+                                                                  iy, iz, inv_ckdt, update_p, fc);
+        IBM_LAUNCH_CHECK();
+        return IBM_OK;
+    }
 #define IBM_CORRECT(THREE_, FLUX_, XF_)                                                                        \
     k_correct<T, THREE_, FLUX_, XF_><<<grd, blk, 0, h->stream>>>(g, us[0], us[1], us2, psi, h->mask, u0, u1, u2, p, \
                                                                  ix, iy, iz, inv_ckdt, update_p, fc)

@@ -16,7 +16,7 @@ from . import (ibm_grid_desc, ibm_geom_desc, ibm_buffers, ibm_physics, IBM_FP64,
                ibm_project, ibm_poisson, ibm_diagnostics, ibm_get_classification, ibm_get_weights,
                ibm_state_bytes, ibm_export_state, ibm_import_state, ibm_timing, ibm_get_timing,
                ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_get_tiles, ibm_set_momentum_tma,
-               ibm_destroy)
+               ibm_destroy, ibm_projection_bytes, ibm_set_projection, IBM_PROJ_FULLBOX, IBM_PROJ_MASKED)
 
 
 class Solver:
@@ -96,13 +96,17 @@ class Solver:
 
     @classmethod
     def from_case(cls, case, precision=None, no_ibm=False, **kw):
-        # a sampled geometry takes its samples through kw (samples=[phi_u, phi_v, phi_w])
-        """Build from any object with the attributes of a workload description."""
-        return cls(ndim=case.ndim, n=case.n, L=case.L, origin=case.origin, bc_lo=case.bc_lo, bc_hi=case.bc_hi,
-                   precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,
-                   nu=case.nu, dt=case.dt, g=case.g, bmode=case.bmode, flow_mode=case.flow_mode,
-                   target_flux=case.target_flux, wall_u=case.wall_u, no_ibm=no_ibm,
-                   inflow=getattr(case, "inflow", (0.0, 0.0, 0.0)), **kw)
+        """Build from any object with the attributes of a workload description.  A sampled
+        geometry takes its samples through kw (samples=[phi_u, phi_v, phi_w]); a workload
+        with projection 'masked' gets the masked projection."""
+        s = cls(ndim=case.ndim, n=case.n, L=case.L, origin=case.origin, bc_lo=case.bc_lo, bc_hi=case.bc_hi,
+                precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,
+                nu=case.nu, dt=case.dt, g=case.g, bmode=case.bmode, flow_mode=case.flow_mode,
+                target_flux=case.target_flux, wall_u=case.wall_u, no_ibm=no_ibm,
+                inflow=getattr(case, "inflow", (0.0, 0.0, 0.0)), **kw)
+        if getattr(case, "projection", "fullbox") == "masked":
+            s.set_projection("masked")
+        return s
 
     def set_physics(self, *, nu, dt, g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0,
                     wall_u=(0.0, 0.0, 0.0), no_ibm=False, body_force=False):
@@ -125,6 +129,21 @@ class Solver:
             self.stream.synchronize()
         ibm_build_weights(self.h, ph, self.weights.data_ptr(), self.weights.numel())
 
+    def set_projection(self, mode="masked", tol=1e-10, maxit=500):
+        """'fullbox' (the unmodified projection) or 'masked' (D M G over the internal cells,
+        conjugate gradients in FP64 with a buffer of five fields held by this object)."""
+        if mode == "fullbox":
+            ibm_set_projection(self.h, IBM_PROJ_FULLBOX, 1.0, 1, 0, 0)
+            self._proj_buf = None
+            return
+        if mode != "masked":
+            raise ValueError("mode is 'fullbox' or 'masked'")
+        nbytes = ibm_projection_bytes(self.h)
+        with torch.cuda.stream(self.stream):
+            self._proj_buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream.synchronize()
+        ibm_set_projection(self.h, IBM_PROJ_MASKED, tol, maxit, self._proj_buf.data_ptr(), nbytes)
+
     # ---- calls -------------------------------------------------------------
     def step(self, nsteps=1, flags=0):
         ibm_step(self.h, nsteps, flags)
@@ -142,7 +161,7 @@ class Solver:
         d = ibm_diagnostics(self.h, raise_on_diverged)
         return {"div_l2": d.div_l2, "div_linf": d.div_linf, "cfl": d.cfl, "flux": list(d.flux), "ke": d.ke,
                 "pi": d.pi, "step": d.step, "status": d.status, "force": list(d.force),
-                "force_steps": d.force_steps}
+                "force_steps": d.force_steps, "proj_iters": d.proj_iters, "proj_resid": d.proj_resid}
 
     def classification(self):
         counts = ibm_get_classification(self.h, None, None)
