@@ -22,7 +22,7 @@ import math
 
 BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW, BC_OUTFLOW = 0, 1, 2, 3, 4
 GEOM_NONE, GEOM_PLANES, GEOM_CYLINDER, GEOM_SPHERE, GEOM_SINE_WALL, GEOM_TUBES, GEOM_SAMPLED = range(7)
-B_EXACT, B_EULER, B_TAYLOR2 = 0, 1, 2
+B_EXACT, B_EULER, B_TAYLOR2, B_EXPLICIT = 0, 1, 2, 3
 FLOW_FORCED, FLOW_CONST_FLUX = 0, 1
 
 
@@ -46,6 +46,8 @@ class Case:
     wall_u: tuple = (0.0, 0.0, 0.0)
     inflow: tuple = (0.0, 0.0, 0.0)   # velocity entering through the -x face (x inflow / outflow boxes)
     projection: str = "fullbox"       # "fullbox" (the unmodified projection) or "masked" (internal faces only)
+    g_amp: tuple = (0.0, 0.0, 0.0)    # time-periodic forcing g + g_amp sin(2 pi g_freq t)
+    g_freq: float = 0.0
     precision: str = "fp64"    # "fp64" or "fp32" (FP32 momentum, FP64 tridiagonal/reductions)
     steps: int = 1
     init: dict = field(default_factory=lambda: {"kind": "zero"})

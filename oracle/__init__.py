@@ -24,7 +24,7 @@ solve (tests/test_oracle_*.py).  No function is "parity unpinned".
 from .grid import Grid
 from .geometry import LevelSet
 from .classify import Classification, classify
-from .weights import Weights, build_weights, stage_coefficients, B_of_x, RK3_A, RK3_B, RK3_C
+from .weights import Weights, build_weights, stage_coefficients, B_of_x, RK3_A, RK3_B, RK3_C, RK3_T
 from .momentum import rhs, stage_update
 from .poisson import divergence, gradient, solve_spectral, solve_direct
 from .solver import OracleSolver

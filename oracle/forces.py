@@ -59,9 +59,10 @@ def _shift_cells(q, grid, d: int, s: int):
     return out
 
 
-def body_terms(grid, cls, u_prev, src, nu: float):
+def body_terms(grid, cls, u_prev, src, nu: float, lam_explicit=None):
     """BN_k per component (the body's share of sum_P N_P over internal points), from the
-    stage's starting velocity u_prev (the fields the right-hand side reads)."""
+    stage's starting velocity u_prev (the fields the right-hand side reads).  With the
+    explicit IBM treatment the right-hand side also holds -lambda u (lam_explicit)."""
     U = masked(grid, cls, u_prev)
     uin = None
     if grid.xflow:
@@ -71,6 +72,8 @@ def body_terms(grid, cls, u_prev, src, nu: float):
     for c in range(grid.ncomp):
         inside = cls.internal[c]
         total = float(np.sum(np.where(inside, src[c], 0.0)))
+        if lam_explicit is not None:
+            total -= float(np.sum(np.where(inside, lam_explicit[c] * U[c], 0.0)))
         for d in range(grid.ndim):
             Dd = grid.d[d]
             for s in (+1, -1):

@@ -26,7 +26,7 @@ import numpy as np
 from .grid import Grid
 from .geometry import LevelSet
 from .classify import classify
-from .weights import build_weights, B_of_x, RK3_A, RK3_B, RK3_C
+from .weights import build_weights, B_of_x, RK3_A, RK3_B, RK3_C, RK3_T, B_EXPLICIT
 from .momentum import (rhs, stage_update, pressure_gradient, masked, inflow_face, outflow_update,
                        outflow_balance)
 from .poisson import divergence, gradient, solve_spectral, solve_direct, solve_masked
@@ -44,6 +44,10 @@ class OracleSolver:
         self.nu = float(case.nu)
         self.dt = float(case.dt)
         self.g = tuple(float(v) for v in case.g)
+        # time-periodic forcing (Sec. 2.5): g(t) = g + g_amp sin(2 pi g_freq t), evaluated at the
+        # time of the stage's explicit right-hand side
+        self.g_amp = tuple(float(v) for v in getattr(case, "g_amp", (0.0, 0.0, 0.0)))
+        self.g_freq = float(getattr(case, "g_freq", 0.0))
         self.bmode = int(case.bmode)
         self.flow_mode = int(case.flow_mode)
         self.target_flux = float(case.target_flux)
@@ -81,16 +85,24 @@ class OracleSolver:
     # ---- one substage -------------------------------------------------------
     def substage(self, k: int, predictor_only: bool = False):
         g, cls = self.grid, self.cls
-        N = rhs(g, cls, self.u, self.nu, self.g, self.w.src)
+        t = (self.step_count + RK3_T[k]) * self.dt
+        gk = tuple(self.g[c] + self.g_amp[c] * np.sin(2.0 * np.pi * self.g_freq * t) for c in range(3))
+        N = rhs(g, cls, self.u, self.nu, gk, self.w.src)
         gp = pressure_gradient(g, self.p)
         um = masked(g, cls, self.u)
-        ustar = stage_update(g, cls, um, N, self.Nprev, gp, self.w.lam, k, self.dt,
+        lam = self.w.lam
+        if self.bmode == B_EXPLICIT:
+            # the classic explicit treatment: -lambda w in the right-hand side, no division
+            N = [N[c] - np.where(cls.internal[c], lam[c] * um[c], 0.0) for c in range(3)]
+            lam = [np.zeros(g.shape) for _ in range(3)]
+        ustar = stage_update(g, cls, um, N, self.Nprev, gp, lam, k, self.dt,
                              self.bmode, RK3_A, RK3_B, RK3_C, B_of_x)
         # the body's share of the stage: the IBM division's part I of u* - u (what the
         # explicit R does not explain) and the right-hand side's faces toward the solid
         R = [self.dt * (RK3_A[k] * N[c] + RK3_B[k] * self.Nprev[c]) - RK3_C[k] * self.dt * gp[c] for c in range(3)]
         I = [np.where(cls.internal[c], ustar[c] - um[c] - R[c], 0.0) for c in range(3)]
-        BN = body_terms(g, cls, self.u, self.w.src, self.nu)
+        BN = body_terms(g, cls, self.u, self.w.src, self.nu,
+                        self.w.lam if self.bmode == B_EXPLICIT else None)
         if g.xflow:
             # the outflow face: convective condition, then the flux balance
             ub, Nb = outflow_update(g, cls, self.u, self.Nprev[0][..., -1:], k, self.dt, RK3_A, RK3_B)
@@ -100,7 +112,7 @@ class OracleSolver:
         self.Nprev = N
         if self.flow_mode == FLOW_CONST_FLUX:
             ckdt = RK3_C[k] * self.dt
-            x = self.w.lam[0] * ckdt
+            x = self.w.lam[0] * ckdt if self.bmode != B_EXPLICIT else np.zeros(g.shape)
             beta = np.where(cls.internal[0], 1.0 / (B_of_x(x, self.bmode) + x), 0.0)
             dV = g.cell_volume()
             Q0 = np.sum(np.where(cls.internal[0], ustar[0], 0.0)) * dV

@@ -24,7 +24,9 @@ Rai-Moin RK3 (Eq. rk3-rai) the stage-k value of x is lambda c_k Delta t.
 B(0) is 0/0; reading taken: B := 1 when x == 0, so the plain scheme is
 recovered exactly.  EULER mode is B = 1 (Eq. time-adv-impl); TAYLOR2 is the
 reciprocal of the 2-term Taylor expansion of (e^x - 1)/x, B = 1/(1 + x/2)
-(the option mentioned after Eq. Bexpr).
+(the option mentioned after Eq. Bexpr).  EXPLICIT is the classic explicit treatment
+the paper compares against (end of Sec. 2.5): -lambda w joins the explicit right-hand
+side and there is no division (B = 1, x = 0 in the stage update).
 """
 from __future__ import annotations
 
@@ -36,12 +38,16 @@ RK3_A = (64.0 / 120.0, 50.0 / 120.0, 90.0 / 120.0)
 RK3_B = (0.0, -34.0 / 120.0, -50.0 / 120.0)
 RK3_C = tuple(a + b for a, b in zip(RK3_A, RK3_B))
 
-B_EXACT, B_EULER, B_TAYLOR2 = 0, 1, 2
+B_EXACT, B_EULER, B_TAYLOR2, B_EXPLICIT = 0, 1, 2, 3
+
+# stage times of the Rai-Moin RK3 as fractions of the step: stage k evaluates its explicit
+# right-hand side at t_n + RK3_T[k] dt (RK3_T[k] = sum of the c of the earlier stages)
+RK3_T = (0.0, RK3_C[0], RK3_C[0] + RK3_C[1])
 
 
 def B_of_x(x, mode: int):
     x = np.asarray(x, dtype=np.float64)
-    if mode == B_EULER:
+    if mode in (B_EULER, B_EXPLICIT):
         return np.ones_like(x)
     if mode == B_TAYLOR2:
         return 1.0 / (1.0 + x / 2.0)

@@ -742,3 +742,50 @@ def test_masked_projection_removes_internal_gradients():
     o._project(us, 1.0, update_p=False)
     for c in range(3):
         assert np.abs(o.u[c]).max() < 1e-11 * np.abs(us[c]).max()
+
+
+# ---- time-periodic forcing and the explicit IBM (Sec. 2.5) ----------------------------------
+
+def _uniform_forced(dt, T=0.37, f=2.0):
+    """u(T) of a uniform stream in an empty box driven by g(t) = sin(2 pi f t) from rest."""
+    case = _channel(8, 0.0, 1.0, nx=8, bc=BC_FREESLIP).with_(geom_kind=GEOM_NONE, geom_params=(), dt=dt,
+                                                             g_amp=(1.0, 0.0, 0.0), g_freq=f)
+    s = OracleSolver(case)
+    s.step(int(round(T / dt)))
+    return s.u[0][0, 4, 4], (1.0 - math.cos(2.0 * math.pi * f * T)) / (2.0 * math.pi * f)
+
+
+def test_periodic_forcing_is_third_order_in_time():
+    """A uniform stream has no convection or diffusion, so u' = sin(2 pi f t) exactly; with the
+    forcing taken at each stage's own time the Rai-Moin RK3 is third order (the error drops 8x
+    per halving of dt).  Taking it at the start of the step for every stage would be first order."""
+    errs = []
+    for dt in (0.037, 0.0185, 0.00925):
+        u, exact = _uniform_forced(dt)
+        errs.append(abs(u - exact))
+    p1 = math.log2(errs[0] / errs[1])
+    p2 = math.log2(errs[1] / errs[2])
+    assert 2.7 < p1 < 3.3 and 2.7 < p2 < 3.3, (errs, p1, p2)
+
+
+def test_explicit_ibm_matches_exact_b_without_crossing_arms_and_blows_up_when_stiff():
+    """With the walls on grid lines every delta equals Delta, lambda is 0 and the explicit
+    treatment is the exact-B scheme bit for bit.  With a wall close to a grid point, lambda
+    c_k dt far above the RK3 stability bound makes the explicit treatment grow without bound
+    while the implicit division stays bounded (end of Sec. 2.5)."""
+    from inputs import B_EXPLICIT
+    on = _channel(16, 3.5 / 16, 12.5 / 16, nx=4).with_(g=(1.0, 0.0, 0.0), dt=1e-4)   # walls through u points
+    a = OracleSolver(on.with_(bmode=B_EXACT))
+    b = OracleSolver(on.with_(bmode=B_EXPLICIT))
+    a.step(3)
+    b.step(3)
+    assert np.all(a.w.lam_list[0] == 0.0) and np.array_equal(a.u[0], b.u[0])
+    near = _channel(16, 2.5 / 16 - 1e-5, 13.5 / 16 + 1e-5, nx=4).with_(g=(1.0, 0.0, 0.0), dt=1e-3)
+    imp = OracleSolver(near.with_(bmode=B_EXACT))
+    exp_ = OracleSolver(near.with_(bmode=B_EXPLICIT))
+    assert np.max(imp.w.lam_list[0]) * RK3_C[0] * near.dt > 100.0
+    imp.step(20)
+    with np.errstate(all="ignore"):
+        exp_.step(20)
+    assert np.abs(imp.u[0]).max() < 1.0
+    assert not np.all(np.isfinite(exp_.u[0])) or np.abs(exp_.u[0]).max() > 1e6
