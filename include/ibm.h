@@ -85,7 +85,9 @@ enum {
                              * Needs a periodic x (the inflow face is not a sample point).   */
 };
 /* B(x) of Eq. (Bexpr), x = lambda c_k dt */
-enum { IBM_B_EXACT = 0, IBM_B_EULER = 1, IBM_B_TAYLOR2 = 2 };
+enum { IBM_B_EXACT = 0, IBM_B_EULER = 1, IBM_B_TAYLOR2 = 2,
+       IBM_B_EXPLICIT = 3 /* the classic explicit treatment the paper compares against (end of
+                           * Sec. 2.5): -lambda w in the explicit right-hand side, no division */ };
 /* forcing */
 enum { IBM_FLOW_FORCED = 0, IBM_FLOW_CONST_FLUX = 1 };
 /* ibm_step flags */
@@ -146,6 +148,11 @@ typedef struct {
     int body_force;     /* 1: every full step adds the force of the fluid on the body to the
                          * sums ibm_diagnostics reports (two small launches per substage over the
                          * IBM points); 0: not computed */
+    double g_amp[3];    /* time-periodic forcing (Sec. 2.5): the body force is g + g_amp sin(2 pi
+                         * g_freq t), t taken at each RK3 stage's own time (t_n, t_n + 8/15 dt,
+                         * t_n + 2/3 dt) with t_n = completed steps * dt.  Nonzero g_amp refuses
+                         * IBM_STEP_GRAPH and batches (the stage values change every step). */
+    double g_freq;
 } ibm_physics;
 
 typedef struct {

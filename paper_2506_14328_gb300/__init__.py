@@ -53,7 +53,7 @@ class ibm_buffers(C.Structure):
 class ibm_physics(C.Structure):
     _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("g", C.c_double * 3), ("bmode", C.c_int),
                 ("flow_mode", C.c_int), ("target_flux", C.c_double), ("wall_u", C.c_double * 3),
-                ("no_ibm", C.c_int), ("body_force", C.c_int)]
+                ("no_ibm", C.c_int), ("body_force", C.c_int), ("g_amp", C.c_double * 3), ("g_freq", C.c_double)]
 
 
 class ibm_diag(C.Structure):

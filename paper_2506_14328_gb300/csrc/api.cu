@@ -422,7 +422,10 @@ ibm_status ibm_build_weights(ibm_solver* h, const ibm_physics* phys, void* weigh
     if (!phys || !weights) return ibm_set_error(IBM_E_INVALID, "NULL argument");
     if (!(phys->dt > 0.0) || !(phys->nu >= 0.0) || !std::isfinite(phys->dt) || !std::isfinite(phys->nu))
         return ibm_set_error(IBM_E_INVALID, "need dt > 0 and nu >= 0");
-    if (phys->bmode < IBM_B_EXACT || phys->bmode > IBM_B_TAYLOR2) return ibm_set_error(IBM_E_INVALID, "bad bmode");
+    if (phys->bmode < IBM_B_EXACT || phys->bmode > IBM_B_EXPLICIT) return ibm_set_error(IBM_E_INVALID, "bad bmode");
+    if (!std::isfinite(phys->g_freq) || !std::isfinite(phys->g_amp[0]) || !std::isfinite(phys->g_amp[1]) ||
+        !std::isfinite(phys->g_amp[2]))
+        return ibm_set_error(IBM_E_INVALID, "g_amp and g_freq must be finite");
     if (phys->flow_mode != IBM_FLOW_FORCED && phys->flow_mode != IBM_FLOW_CONST_FLUX)
         return ibm_set_error(IBM_E_INVALID, "bad flow_mode");
     if (phys->flow_mode == IBM_FLOW_CONST_FLUX && !h->gp.xper)
@@ -461,6 +464,8 @@ ibm_status ibm_step(ibm_solver* h, int nsteps, unsigned flags) {
         if (h->timing) return ibm_set_error(IBM_E_STATE, "timing is not available in graph mode");
         if (h->proj_mode == IBM_PROJ_MASKED)
             return ibm_set_error(IBM_E_UNSUPPORTED, "the masked projection reads back its inner products: no graph mode");
+        if (h->phys.g_amp[0] != 0.0 || h->phys.g_amp[1] != 0.0 || h->phys.g_amp[2] != 0.0)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "a time-periodic forcing changes every step: no graph mode");
         if (!h->graph_ready) {
             cudaGraph_t graph;
             IBM_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -790,6 +795,8 @@ ibm_status ibm_batch_set(ibm_batch* b, ibm_solver* const* members, const int* st
         if (members[q]->timing) return ibm_set_error(IBM_E_STATE, "disable member timing before batching");
         if (members[q]->proj_mode == IBM_PROJ_MASKED)
             return ibm_set_error(IBM_E_UNSUPPORTED, "a member uses the masked projection (no graph capture)");
+        if (members[q]->phys.g_amp[0] != 0.0 || members[q]->phys.g_amp[1] != 0.0 || members[q]->phys.g_amp[2] != 0.0)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "a member has a time-periodic forcing (no graph capture)");
         if (steps[q] < 0) return ibm_set_error(IBM_E_INVALID, "negative step count");
     }
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }

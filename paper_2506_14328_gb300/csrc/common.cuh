@@ -74,6 +74,8 @@ template <typename T> struct StageP {
 inline constexpr double RK_A[3] = {64.0 / 120.0, 50.0 / 120.0, 90.0 / 120.0};
 inline constexpr double RK_B[3] = {0.0, -34.0 / 120.0, -50.0 / 120.0};
 inline constexpr double RK_C[3] = {64.0 / 120.0, 16.0 / 120.0, 40.0 / 120.0};
+// stage times as fractions of the step: the sums of the c of the earlier stages
+inline constexpr double RK_T[3] = {0.0, 64.0 / 120.0, 80.0 / 120.0};
 
 // Momentum tiling: blocks of 32 x 8 threads own 32 x 16 cells in (x, y) and
 // march g.kzm planes in z.  The autotuner picks kzm from KZM_CHOICES; the flux
@@ -133,7 +135,7 @@ constexpr int SCAL_IMP = 24;      // 3: impulse of the current step so far
 
 // B of the implicit update (Eq. Bexpr and the Taylor options): B = x / (e^x - 1), 1 at x = 0.
 __device__ __forceinline__ double ibm_B_of_x(double x, int mode) {
-    if (mode == IBM_B_EULER) return 1.0;
+    if (mode == IBM_B_EULER || mode == IBM_B_EXPLICIT) return 1.0;
     if (mode == IBM_B_TAYLOR2) return 1.0 / (1.0 + x / 2.0);
     if (!(x > 0.0)) return 1.0;
     return x / expm1(x);

@@ -415,6 +415,7 @@ struct CoefArgs {
     Coef4<T>* coef[3];   // [3 stages][count]
     int count[3];
     double ckdt[3];
+    double dta[3];      // dt a_k
     int bmode;
 };
 
@@ -426,13 +427,20 @@ __global__ void k_coefs(CoefArgs<T> a) {
     double lam = a.lam[c][m];
     double s = a.src[c][m];
     for (int st = 0; st < 3; ++st) {
-        double x = lam * a.ckdt[st];
-        double B = B_of_x(x, a.bmode);
         Coef4<T> q;
-        q.a = (T)(B / (B + x));
-        q.b = (T)(1.0 / (B + x));
         q.s = (T)s;
-        q.pad = (T)0;
+        if (a.bmode == IBM_B_EXPLICIT) {
+            // -lambda u joins N (through pad) and u* = u + R: alpha = 1 - dt a_k lambda, beta = 1
+            q.a = (T)(1.0 - a.dta[st] * lam);
+            q.b = (T)1;
+            q.pad = (T)lam;
+        } else {
+            double x = lam * a.ckdt[st];
+            double B = B_of_x(x, a.bmode);
+            q.a = (T)(B / (B + x));
+            q.b = (T)(1.0 / (B + x));
+            q.pad = (T)0;
+        }
         a.coef[c][(long long)st * a.count[c] + m] = q;
     }
 }
@@ -450,7 +458,7 @@ __global__ void k_flux_response(GridP g, const uint8_t* __restrict__ mask, const
         double l = lam_u[m];
         double ck[3] = {ck0, ck1, ck2};
         for (int st = 0; st < 3; ++st) {
-            double x = l * ck[st];
+            double x = bmode == IBM_B_EXPLICIT ? 0.0 : l * ck[st];
             double B = B_of_x(x, bmode);
             acc[1 + st] += 1.0 - 1.0 / (B + x);
         }
@@ -581,6 +589,7 @@ ibm_status geom_build_lists_and_weights(ibm_solver* h) {
 
 ibm_status geom_stage_coefficients(ibm_solver* h) {
     const double rkc[3] = {64.0 / 120.0, 16.0 / 120.0, 40.0 / 120.0};
+    const double rka[3] = {64.0 / 120.0, 50.0 / 120.0, 90.0 / 120.0};
     int maxc = 1;
     for (int c = 0; c < 3; ++c) maxc = h->counts[c] > maxc ? h->counts[c] : maxc;
     dim3 grid((maxc + 127) / 128, 3);
@@ -589,6 +598,7 @@ ibm_status geom_stage_coefficients(ibm_solver* h) {
         for (int c = 0; c < 3; ++c) {
             a.lam[c] = h->lam[c]; a.src[c] = h->src[c]; a.count[c] = h->counts[c];
             a.coef[c] = (Coef4<double>*)h->coef[c]; a.ckdt[c] = rkc[c] * h->phys.dt;
+            a.dta[c] = rka[c] * h->phys.dt;
         }
         a.bmode = h->phys.bmode;
         k_coefs<double><<<grid, 128, 0, h->stream>>>(a);
@@ -597,6 +607,7 @@ ibm_status geom_stage_coefficients(ibm_solver* h) {
         for (int c = 0; c < 3; ++c) {
             a.lam[c] = h->lam[c]; a.src[c] = h->src[c]; a.count[c] = h->counts[c];
             a.coef[c] = (Coef4<float>*)h->coef[c]; a.ckdt[c] = rkc[c] * h->phys.dt;
+            a.dta[c] = rka[c] * h->phys.dt;
         }
         a.bmode = h->phys.bmode;
         k_coefs<float><<<grid, 128, 0, h->stream>>>(a);

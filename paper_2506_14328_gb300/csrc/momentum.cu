@@ -240,10 +240,11 @@ __device__ __forceinline__ void mom_update(const StageP<T>& sp, T uP, T N, T dp,
 }
 
 // the implicit IBM division of one IBM point (Eq. rk3-rai): the wall source s
-// joins N, and u* = alpha u + beta R
+// joins N, and u* = alpha u + beta R.  The explicit treatment stores lambda in pad
+// (0 otherwise), so that -lambda u joins N as well.
 template <typename T>
 __device__ __forceinline__ void mom_ibm(const StageP<T>& sp, const Coef4<T>& q, T uP, T R, T& out, T& N) {
-    N += q.s;
+    N += q.s - q.pad * uP;
     out = q.a * uP + q.b * (R + sp.dta * q.s);
 }
 
@@ -1033,7 +1034,11 @@ ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib,
     sp.dtb = (T)(dt * RK_B[k]);
     sp.ckdt = (T)(dt * RK_C[k]);
     sp.nu = (T)h->phys.nu;
-    for (int c = 0; c < 3; ++c) sp.g[c] = (T)h->phys.g[c];
+    {   // the body force at the stage's own time (time-periodic forcing, Sec. 2.5)
+        const double tk = ((double)h->steps + RK_T[k]) * dt;
+        const double sk = h->phys.g_freq != 0.0 ? std::sin(2.0 * M_PI * h->phys.g_freq * tk) : 0.0;
+        for (int c = 0; c < 3; ++c) sp.g[c] = (T)(h->phys.g[c] + h->phys.g_amp[c] * sk);
+    }
     sp.idx = (T)(1.0 / g.dx); sp.idy = (T)(1.0 / g.dy); sp.idz = (T)(1.0 / g.dz);
     sp.nx2 = (T)(h->phys.nu / (g.dx * g.dx)); sp.ny2 = (T)(h->phys.nu / (g.dy * g.dy));
     sp.nz2 = (T)(h->phys.nu / (g.dz * g.dz));

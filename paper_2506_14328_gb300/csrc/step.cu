@@ -1300,10 +1300,15 @@ __global__ void __launch_bounds__(256) k_body_force(BodyArgs<T> a) {
         const int pk = (int)(lin / ((long long)g.nx * g.ny));
         const double u0 = (double)a.u[c][lin];
         const double us = (double)a.us[c][lin];
-        const double x = a.lam[c][m] * a.ckdt;
-        const double B = ibm_B_of_x(x, a.bmode);
-        sI += -x * us + (1.0 - B) * (us - u0);
-        sBN += a.src[c][m];
+        if (a.bmode == IBM_B_EXPLICIT) {
+            // -lambda u is part of N; the update has no division (I = 0)
+            sBN += a.src[c][m] - a.lam[c][m] * u0;
+        } else {
+            const double x = a.lam[c][m] * a.ckdt;
+            const double B = ibm_B_of_x(x, a.bmode);
+            sI += -x * us + (1.0 - B) * (us - u0);
+            sBN += a.src[c][m];
+        }
         const int P[3] = {pi, pj, pk};
         for (int d = 0; d < nd; ++d) {
             const bool per = d == 2 || (d == 0 && g.xper);

@@ -28,7 +28,8 @@ class Solver:
 
     def __init__(self, *, ndim, n, L, origin, bc_lo, bc_hi, precision, geom_kind, geom_params, nu, dt,
                  g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0, wall_u=(0.0, 0.0, 0.0), no_ibm=False,
-                 body_force=False, inflow=(0.0, 0.0, 0.0), samples=None, device="cuda", stream=None):
+                 body_force=False, g_amp=(0.0, 0.0, 0.0), g_freq=0.0, inflow=(0.0, 0.0, 0.0), samples=None,
+                 device="cuda", stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("the IBM solver needs a CUDA device")
         self.device = torch.device(device)
@@ -92,7 +93,7 @@ class Solver:
             self.h = ibm_setup_geometry(gd, geo, bufs, self.stream.cuda_stream)
             self.weights = None
             self.set_physics(nu=nu, dt=dt, g=g, bmode=bmode, flow_mode=flow_mode, target_flux=target_flux,
-                             wall_u=wall_u, no_ibm=no_ibm, body_force=body_force)
+                             wall_u=wall_u, no_ibm=no_ibm, body_force=body_force, g_amp=g_amp, g_freq=g_freq)
 
     @classmethod
     def from_case(cls, case, precision=None, no_ibm=False, **kw):
@@ -103,13 +104,14 @@ class Solver:
                 precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,
                 nu=case.nu, dt=case.dt, g=case.g, bmode=case.bmode, flow_mode=case.flow_mode,
                 target_flux=case.target_flux, wall_u=case.wall_u, no_ibm=no_ibm,
-                inflow=getattr(case, "inflow", (0.0, 0.0, 0.0)), **kw)
+                inflow=getattr(case, "inflow", (0.0, 0.0, 0.0)), g_amp=getattr(case, "g_amp", (0.0, 0.0, 0.0)),
+                g_freq=getattr(case, "g_freq", 0.0), **kw)
         if getattr(case, "projection", "fullbox") == "masked":
             s.set_projection("masked")
         return s
 
     def set_physics(self, *, nu, dt, g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0,
-                    wall_u=(0.0, 0.0, 0.0), no_ibm=False, body_force=False):
+                    wall_u=(0.0, 0.0, 0.0), no_ibm=False, body_force=False, g_amp=(0.0, 0.0, 0.0), g_freq=0.0):
         ph = ibm_physics()
         ph.nu = float(nu)
         ph.dt = float(dt)
@@ -121,6 +123,9 @@ class Solver:
         ph.target_flux = float(target_flux)
         ph.no_ibm = 1 if no_ibm else 0
         ph.body_force = 1 if body_force else 0
+        for c in range(3):
+            ph.g_amp[c] = float(g_amp[c])
+        ph.g_freq = float(g_freq)
         self.phys = ph
         wb = ibm_weights_bytes(self.h)
         if self.weights is None or self.weights.numel() < wb:

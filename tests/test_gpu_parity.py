@@ -504,3 +504,22 @@ def test_masked_projection_matches_oracle(name):
     d = g.diagnostics()
     assert 0 < d["proj_iters"] < 1000 and d["proj_resid"] <= 1e-11
     g.close()
+
+
+@pytest.mark.parametrize("variant", ["periodic_forcing", "explicit_ibm"])
+def test_forcing_and_explicit_ibm_match_oracle(variant):
+    """Time-periodic forcing at each stage's own time, and the explicit IBM treatment, over
+    full steps against the oracle (1e-12)."""
+    from inputs import B_EXPLICIT
+    if variant == "periodic_forcing":
+        case = small_case("sphere3d").with_(g_amp=(0.5, -0.2, 0.1), g_freq=3.0)
+    else:
+        case = small_case("channel2d").with_(bmode=B_EXPLICIT)
+    g, o = _pair(case)
+    for s in range(case.steps):
+        g.step(1)
+        o.step(1)
+        assert all(np.all(np.isfinite(o.u[c])) for c in range(3))
+        ug, _ = g.state()
+        for c in range(o.grid.ncomp):
+            assert _rel(o, ug[c], o.u[c], c) < TOL64, (s, c)
