@@ -52,10 +52,10 @@ TRIDIAG_BYTES_PER_SPECTRAL_POINT = 64.0
 NCU_TRAFFIC = {
     # (kernel, workload): (DRAM bytes per launch, mean of the three RK3 stages of one step, and
     # the sha256[:16] of the kernel's source file the capture ran on)
-    # profiles/c3_wavy_384x256x256_momentum_tma_ncu.md: 1025.2, 1324.3 and 1040.7 MB
-    ("momentum", "c3"): ((1025.162496e6 + 1324.251648e6 + 1040.737792e6) / 3.0, "6e256579b35afb2d"),
-    # profiles/c4_airway_512x384x256_momentum_tma_traffic.md: 2269.7, 2894.1 and 2300.9 MB
-    ("momentum", "c4"): ((2269.658624e6 + 2894.148096e6 + 2300.914176e6) / 3.0, "6e256579b35afb2d"),
+    # profiles/c3_wavy_384x256x256_momentum_tma_ncu.md
+    ("momentum", "c3"): ((1025.940736e6 + 1330.600704e6 + 1047.626752e6) / 3.0, "689c1e4d1b26425a"),
+    # profiles/c4_airway_512x384x256_momentum_tma_traffic.md
+    ("momentum", "c4"): ((2164.721664e6 + 2774.362624e6 + 2182.648576e6) / 3.0, "689c1e4d1b26425a"),
 }
 
 KERNEL_FILE = {"momentum": "momentum.cu"}   # other kernels of this library live in step.cu

@@ -292,8 +292,8 @@ ibm_status ibm_get_tiles(ibm_solver* h, int* kz_momentum, int* kz_march, int* tm
  * compute the same update (a tuning and testing aid, not in the paper). */
 ibm_status ibm_set_momentum_tma(ibm_solver* h, int enable);
 
-/* Batched stepping of many resident solves (continuous batching, SURVEY's
- * serving pattern; the paper has no counterpart).  A batch owns a
+/* Batched stepping of many resident solves (continuous batching for serving
+ * many small solves; the paper has no counterpart).  A batch owns a
  * non-default stream.  ibm_batch_set captures ONE CUDA graph that forks onto
  * every member's own stream, runs steps[i] full steps of member i there and
  * joins back, so the members' kernels overlap on the device; call it again
