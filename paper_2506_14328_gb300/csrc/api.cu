@@ -83,7 +83,9 @@ int momentum_blocks(const GridP& g) {
 }
 
 // Creates the transform plans with auto-allocation off; returns the largest work size.
-// Periodic x: one 2D (z, x) R2C / C2R pair (1D in x for 2D grids), *pfz = *piz = 0.
+// Periodic x: an R2C / C2R pair along the contiguous x rows and, in 3D, one in-place C2C
+// plan along z over the half spectrum (*pfz; *piz = 0); the same passes a 2D (z, x) plan
+// makes, with the same spectrum layout.
 // Neumann x: an R2C / C2R pair along x (the FFT inside the DCT) and, in 3D, a strided
 // R2C / C2R pair along z over the real DCT coefficients.
 ibm_status make_plans(const GridP& g, int prec, cufftHandle* pf, cufftHandle* pi, cufftHandle* pfz,
@@ -98,20 +100,22 @@ ibm_status make_plans(const GridP& g, int prec, cufftHandle* pf, cufftHandle* pi
     cufftSetAutoAllocation(*pf, 0);
     cufftSetAutoAllocation(*pi, 0);
     cufftResult r1 = CUFFT_SUCCESS, r2 = CUFFT_SUCCESS, r3 = CUFFT_SUCCESS, r4 = CUFFT_SUCCESS;
-    if (g.xper && g.nz > 1) {
-        long long nxh = g.nxh;
-        long long n[2] = {nz, nx};
-        long long ie[2] = {nz, ny * nx};
-        long long oe[2] = {nz, ny * nxh};
-        r1 = cufftMakePlanMany64(*pf, 2, n, ie, 1, nx, oe, 1, nxh, tf, ny, &wf);
-        r2 = cufftMakePlanMany64(*pi, 2, n, oe, 1, nxh, ie, 1, nx, ti, ny, &wi);
-    } else {
+    {
         long long nxr = nx / 2 + 1;   // half spectrum of a real row
         long long n[1] = {nx};
         long long ie[1] = {nx};
         long long oe[1] = {nxr};
         r1 = cufftMakePlanMany64(*pf, 1, n, ie, 1, nx, oe, 1, nxr, tf, ny * nz, &wf);
         r2 = cufftMakePlanMany64(*pi, 1, n, oe, 1, nxr, ie, 1, nx, ti, ny * nz, &wi);
+        if (g.xper && g.nz > 1) {
+            if (cufftCreate(pfz) != CUFFT_SUCCESS) return ibm_set_error(IBM_E_CUDA, "cufftCreate failed");
+            cufftSetAutoAllocation(*pfz, 0);
+            const long long nxh = g.nxh;
+            long long nzn[1] = {nz};
+            long long ze[1] = {nz};
+            r3 = cufftMakePlanMany64(*pfz, 1, nzn, ze, ny * nxh, 1, ze, ny * nxh, 1,
+                                     prec == IBM_FP64 ? CUFFT_Z2Z : CUFFT_C2C, ny * nxh, &wfz);
+        }
         if (!g.xper && g.nz > 1) {
             if (cufftCreate(pfz) != CUFFT_SUCCESS || cufftCreate(piz) != CUFFT_SUCCESS)
                 return ibm_set_error(IBM_E_CUDA, "cufftCreate failed");

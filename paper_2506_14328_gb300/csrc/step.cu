@@ -815,10 +815,17 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
         return h->prec == IBM_FP64 ? cufftExecZ2D(p, (cufftDoubleComplex*)in, (cufftDoubleReal*)out)
                                    : cufftExecC2R(p, (cufftComplex*)in, (cufftReal*)out);
     };
+    // in-place C2C along z over the half spectrum (periodic x, 3D)
+    auto zc2c = [&](int dir) {
+        return h->prec == IBM_FP64
+                   ? cufftExecZ2Z(h->plan_fz, (cufftDoubleComplex*)h->spec, (cufftDoubleComplex*)h->spec, dir)
+                   : cufftExecC2C(h->plan_fz, (cufftComplex*)h->spec, (cufftComplex*)h->spec, dir);
+    };
     timer_begin(h, "fft_forward", &t);
     cufftResult r = CUFFT_SUCCESS;
     if (g.xper) {
         r = fwd(h->plan_f, rhs_inout, h->spec);
+        if (r == CUFFT_SUCCESS && g.nz > 1) r = zc2c(CUFFT_FORWARD);
     } else {
         // DCT of the x rows into rhs, then (3D) the real FFT along z into the spectrum
         T* x = (T*)rhs_inout;
@@ -863,7 +870,8 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
     timer_end(h, t, "tridiag");
     timer_begin(h, "fft_inverse", &t);
     if (g.xper) {
-        r = inv(h->plan_i, h->spec, rhs_inout);
+        if (g.nz > 1) r = zc2c(CUFFT_INVERSE);
+        if (r == CUFFT_SUCCESS) r = inv(h->plan_i, h->spec, rhs_inout);
     } else {
         T* x = (T*)rhs_inout;
         if (g.nz > 1) {
