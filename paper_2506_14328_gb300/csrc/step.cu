@@ -421,6 +421,130 @@ __device__ __forceinline__ void tridiag_warp64(const GridP& g, C* spec, const do
         }
 }
 
+// The same warp sweep for FP32 storage in float-float arithmetic (a value is an
+// unevaluated sum hi + lo of two floats, about 2^-44 relative): the near-singular
+// systems need more than FP32 but not FP64, and the FP32 pipes are 58x faster than
+// the FP64 ones on this GPU.  Inputs and outputs are FP32; the pivots are split
+// from their FP64 values.
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, -b.hi, -b.lo); }
+__device__ __forceinline__ FF ff_mulf(FF a, FF b) { return ff_mul(a, b.hi, b.lo); }
+__device__ __forceinline__ FF ff_shfl_up(FF a, int off) {
+    return FF{__shfl_up_sync(0xffffffffu, a.hi, off), __shfl_up_sync(0xffffffffu, a.lo, off)};
+}
+__device__ __forceinline__ FF ff_shfl_down(FF a, int off) {
+    return FF{__shfl_down_sync(0xffffffffu, a.hi, off), __shfl_down_sync(0xffffffffu, a.lo, off)};
+}
+
+template <int TW_ROWS>
+__device__ __forceinline__ void tridiag_warp_ff(const GridP& g, float2* spec, const double* __restrict__ piv,
+                                                long long base, double scale, bool zero_mode) {
+    const int lane = threadIdx.x & 31;
+    const int ny = g.ny;
+    const int E = (ny + 31) / 32;
+    const int j0 = lane * E;
+    const long long st = g.nxh;
+    const float sf = (float)scale;
+    FF dr[TW_ROWS], di[TW_ROWS], w[TW_ROWS];
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t) {
+        dr[t] = di[t] = w[t] = FF{0.f, 0.f};
+        if (t < E && j0 + t < ny) {
+            const long long o = base + (long long)(j0 + t) * st;
+            const float2 r = spec[o];
+            dr[t] = FF{r.x * sf, 0.f};          // the scale applied in FP32, as the FP64 sweep does
+            di[t] = FF{r.y * sf, 0.f};
+            const double wd = piv[o];
+            const float wh = (float)wd;
+            w[t] = FF{wh, (float)(wd - (double)wh)};
+        }
+    }
+    const FF one{1.f, 0.f};
+    // forward: this lane's map e_out = A + B e_in
+    FF Ar{0.f, 0.f}, Ai{0.f, 0.f}, B = one;
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t)
+        if (t < E && j0 + t < ny) {
+            Ar = ff_mulf(w[t], ff_sub(dr[t], Ar));
+            Ai = ff_mulf(w[t], ff_sub(di[t], Ai));
+            B = ff_mulf(FF{-w[t].hi, -w[t].lo}, B);
+        }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const FF pr = ff_shfl_up(Ar, off), pi = ff_shfl_up(Ai, off), pb = ff_shfl_up(B, off);
+        if (lane >= off) {
+            const FF br = ff_mulf(B, pr), bi = ff_mulf(B, pi);
+            Ar = ff_add(Ar, br.hi, br.lo);
+            Ai = ff_add(Ai, bi.hi, bi.lo);
+            B = ff_mulf(B, pb);
+        }
+    }
+    FF er = ff_shfl_up(Ar, 1), ei = ff_shfl_up(Ai, 1);
+    if (lane == 0) er = ei = FF{0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t)
+        if (t < E && j0 + t < ny) {
+            er = ff_mulf(w[t], ff_sub(dr[t], er));
+            ei = ff_mulf(w[t], ff_sub(di[t], ei));
+            dr[t] = er;
+            di[t] = ei;
+        }
+    // backward: this lane's map x_first = Cm + D x_in
+    FF Cr{0.f, 0.f}, Ci{0.f, 0.f}, D = one;
+#pragma unroll
+    for (int t = TW_ROWS - 1; t >= 0; --t)
+        if (t < E && j0 + t < ny) {
+            Cr = ff_sub(dr[t], ff_mulf(w[t], Cr));
+            Ci = ff_sub(di[t], ff_mulf(w[t], Ci));
+            D = ff_mulf(FF{-w[t].hi, -w[t].lo}, D);
+        }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const FF pr = ff_shfl_down(Cr, off), pi = ff_shfl_down(Ci, off), pd = ff_shfl_down(D, off);
+        if (lane + off < 32) {
+            const FF dr2 = ff_mulf(D, pr), di2 = ff_mulf(D, pi);
+            Cr = ff_add(Cr, dr2.hi, dr2.lo);
+            Ci = ff_add(Ci, di2.hi, di2.lo);
+            D = ff_mulf(D, pd);
+        }
+    }
+    FF xr = ff_shfl_down(Cr, 1), xi = ff_shfl_down(Ci, 1);
+    if (lane == 31) xr = xi = FF{0.f, 0.f};
+    double sr = 0.0, si = 0.0;
+#pragma unroll
+    for (int t = TW_ROWS - 1; t >= 0; --t)
+        if (t < E && j0 + t < ny) {
+            xr = ff_sub(dr[t], ff_mulf(w[t], xr));
+            xi = ff_sub(di[t], ff_mulf(w[t], xi));
+            dr[t] = xr;
+            di[t] = xi;
+            if (zero_mode) {
+                sr += (double)xr.hi + (double)xr.lo;
+                si += (double)xi.hi + (double)xi.lo;
+            }
+        }
+    double mr = 0.0, mi = 0.0;
+    if (zero_mode) {                                   // box-mean gauge
+        sr = warp_sum(sr);
+        si = warp_sum(si);
+        mr = __shfl_sync(0xffffffffu, sr, 0) / ny;
+        mi = __shfl_sync(0xffffffffu, si, 0) / ny;
+    }
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t)
+        if (t < E && j0 + t < ny) {
+            const long long o = base + (long long)(j0 + t) * st;
+            float2 r;
+            if (zero_mode) {
+                r.x = (float)((double)dr[t].hi + (double)dr[t].lo - mr);
+                r.y = (float)((double)di[t].hi + (double)di[t].lo - mi);
+            } else {
+                r.x = __fadd_rn(dr[t].hi, dr[t].lo);
+                r.y = __fadd_rn(di[t].hi, di[t].lo);
+            }
+            spec[o] = r;
+        }
+}
+
 // One warp per block; `order` lists the systems (kz * nxh + kx) with every
 // FP64 system first, so the scarce FP64 pipes of all SMs share the low modes.
 // FP64 systems take two threads (real and imaginary part), FP32 systems one.
@@ -435,7 +559,10 @@ __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, 
             const int sys = order[blockIdx.x];
             const int kx = sys % g.nxh, kz = sys / g.nxh;
             const long long base = (long long)kz * g.ny * g.nxh + kx;
-            tridiag_warp64<C, R>(g, spec, piv, base, scale, kx == 0 && kz == 0);
+            if constexpr (sizeof(C) == sizeof(float2))
+                tridiag_warp_ff<R>(g, reinterpret_cast<float2*>(spec), piv, base, scale, kx == 0 && kz == 0);
+            else
+                tridiag_warp64<C, R>(g, spec, piv, base, scale, kx == 0 && kz == 0);
             return;
         }
     }
