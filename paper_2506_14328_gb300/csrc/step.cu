@@ -546,6 +546,89 @@ __device__ __forceinline__ void tridiag_warp_ff(const GridP& g, float2* spec, co
         }
 }
 
+// The warp sweep of one strongly dominant FP32 system in FP32 (FP32 pivots, the
+// scale applied on the way out as the thread-per-system sweep does).  Used when
+// there are too few systems for one thread each to fill the GPU (the 2D cylinder:
+// 1024 such systems of 768 rows, one dependent chain per thread).
+template <int TW_ROWS>
+__device__ __forceinline__ void tridiag_warp_f32(const GridP& g, float2* spec, const float* __restrict__ piv,
+                                                 long long base, float scale) {
+    const int lane = threadIdx.x & 31;
+    const int ny = g.ny;
+    const int E = (ny + 31) / 32;
+    const int j0 = lane * E;
+    const long long st = g.nxh;
+    float dr[TW_ROWS], di[TW_ROWS], w[TW_ROWS];
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t) {
+        dr[t] = di[t] = w[t] = 0.f;
+        if (t < E && j0 + t < ny) {
+            const long long o = base + (long long)(j0 + t) * st;
+            const float2 r = spec[o];
+            dr[t] = r.x;
+            di[t] = r.y;
+            w[t] = piv[o];
+        }
+    }
+    float Ar = 0.f, Ai = 0.f, B = 1.f;
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t)
+        if (t < E && j0 + t < ny) {
+            Ar = (dr[t] - Ar) * w[t];
+            Ai = (di[t] - Ai) * w[t];
+            B = -w[t] * B;
+        }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float pr = __shfl_up_sync(0xffffffffu, Ar, off);
+        const float pi = __shfl_up_sync(0xffffffffu, Ai, off);
+        const float pb = __shfl_up_sync(0xffffffffu, B, off);
+        if (lane >= off) {
+            Ar += B * pr;
+            Ai += B * pi;
+            B *= pb;
+        }
+    }
+    float er = __shfl_up_sync(0xffffffffu, Ar, 1), ei = __shfl_up_sync(0xffffffffu, Ai, 1);
+    if (lane == 0) er = ei = 0.f;
+#pragma unroll
+    for (int t = 0; t < TW_ROWS; ++t)
+        if (t < E && j0 + t < ny) {
+            er = (dr[t] - er) * w[t];
+            ei = (di[t] - ei) * w[t];
+            dr[t] = er;
+            di[t] = ei;
+        }
+    float Cr = 0.f, Ci = 0.f, D = 1.f;
+#pragma unroll
+    for (int t = TW_ROWS - 1; t >= 0; --t)
+        if (t < E && j0 + t < ny) {
+            Cr = dr[t] - w[t] * Cr;
+            Ci = di[t] - w[t] * Ci;
+            D = -w[t] * D;
+        }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float pr = __shfl_down_sync(0xffffffffu, Cr, off);
+        const float pi = __shfl_down_sync(0xffffffffu, Ci, off);
+        const float pd = __shfl_down_sync(0xffffffffu, D, off);
+        if (lane + off < 32) {
+            Cr += D * pr;
+            Ci += D * pi;
+            D *= pd;
+        }
+    }
+    float xr = __shfl_down_sync(0xffffffffu, Cr, 1), xi = __shfl_down_sync(0xffffffffu, Ci, 1);
+    if (lane == 31) xr = xi = 0.f;
+#pragma unroll
+    for (int t = TW_ROWS - 1; t >= 0; --t)
+        if (t < E && j0 + t < ny) {
+            xr = dr[t] - w[t] * xr;
+            xi = di[t] - w[t] * xi;
+            spec[base + (long long)(j0 + t) * st] = make_float2(xr * scale, xi * scale);
+        }
+}
+
 // One warp per block; `order` lists the systems (kz * nxh + kx) with every
 // FP64 system first, so the scarce FP64 pipes of all SMs share the low modes.
 // FP64 systems take two threads (real and imaginary part), FP32 systems one.
@@ -553,7 +636,7 @@ __device__ __forceinline__ void tridiag_warp_ff(const GridP& g, float2* spec, co
 template <typename C, int R>
 __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, const double* __restrict__ piv,
                                                 const float* __restrict__ piv32, const int* __restrict__ order,
-                                                int n64, int nsys, double scale) {
+                                                int n64, int nsys, double scale, int warp32) {
     if constexpr (R > 0) {
         // one warp (block) per FP64 system
         if ((int)blockIdx.x < n64) {
@@ -578,6 +661,15 @@ __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, 
         return;
     }
     if constexpr (sizeof(C) == sizeof(float2)) {
+        if constexpr (R > 0) {
+            if (warp32) {                          // one warp per FP32 system
+                const int sys = order[n64 + (blockIdx.x - nb64)];
+                const int kx = sys % g.nxh, kz = sys / g.nxh;
+                tridiag_warp_f32<R>(g, reinterpret_cast<float2*>(spec), piv32,
+                                    (long long)kz * g.ny * g.nxh + kx, (float)scale);
+                return;
+            }
+        }
         const int q = n64 + (blockIdx.x - nb64) * 32 + threadIdx.x;
         if (q >= nsys) return;
         const int sys = order[q];
@@ -976,17 +1068,19 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout) {
     double scale = g.dy * g.dy / ((double)g.nx * (double)g.nz);
     const int nsys = g.nzs * g.nxh;
     const int nb64 = g.ny <= 32 * TW_ROWS ? h->n64 : (2 * h->n64 + 31) / 32;
-    const int nblk = nb64 + (nsys - h->n64 + 31) / 32;
+    // FP32 systems: one warp each when one thread each would leave the GPU nearly idle
+    const int warp32 = (h->prec == IBM_FP32 && g.ny <= 32 * TW_ROWS && nsys - h->n64 < 16384) ? 1 : 0;
+    const int nblk = nb64 + (warp32 ? nsys - h->n64 : (nsys - h->n64 + 31) / 32);
     timer_begin(h, "tridiag", &t);
     // rows per lane of the warp path, rounded up to a compiled size
 #define IBM_TRIDIAG(RR)                                                                                          \
     do {                                                                                                         \
         if (h->prec == IBM_FP64)                                                                                 \
             k_tridiag<double2, RR><<<nblk, 32, 0, h->stream>>>(g, (double2*)h->spec, (double2*)h->spec, h->pivots, \
-                                                               h->pivots32, h->sys_order, h->n64, nsys, scale);  \
+                                                               h->pivots32, h->sys_order, h->n64, nsys, scale, warp32); \
         else                                                                                                     \
             k_tridiag<float2, RR><<<nblk, 32, 0, h->stream>>>(g, (float2*)h->spec, (double2*)h->dtemp, h->pivots,  \
-                                                              h->pivots32, h->sys_order, h->n64, nsys, scale);   \
+                                                              h->pivots32, h->sys_order, h->n64, nsys, scale, warp32); \
     } while (0)
     if (g.ny <= 32 * 8) IBM_TRIDIAG(8);
     else if (g.ny <= 32 * 16) IBM_TRIDIAG(16);
