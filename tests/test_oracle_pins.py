@@ -789,3 +789,43 @@ def test_explicit_ibm_matches_exact_b_without_crossing_arms_and_blows_up_when_st
         exp_.step(20)
     assert np.abs(imp.u[0]).max() < 1.0
     assert not np.all(np.isfinite(exp_.u[0])) or np.abs(exp_.u[0]).max() > 1e6
+
+
+# ---- wall-shear stress and its Fourier components (Sec. 4.2) --------------------------------
+
+def test_wall_shear_of_a_parabola_is_exact_on_flat_walls():
+    """u = U (1 - ((y - y_c)/h)^2) between plane walls: the quadratic through the wall, P and Q is
+    the profile itself, so tau = 2 nu U / h in every column (1e-12) and both Fourier components
+    vanish."""
+    from oracle.forces import wall_shear
+    case = channel_c1()
+    a, b = case.geom_params
+    g, ls, cls, _ = _setup(case)
+    h, yc, U = (b - a) / 2, (a + b) / 2, 1.3
+    _, y, _ = g.coords(0)
+    u = np.broadcast_to(U * (1.0 - ((y - yc) / h) ** 2), g.shape)
+    tau, t1c, t1s = wall_shear(g, cls, ls, u, case.nu, g.L[0])
+    exact = 2.0 * case.nu * U / h
+    assert np.all(np.isfinite(tau)) and np.abs(tau - exact).max() < 1e-12 * exact
+    assert abs(t1c) < 1e-12 * exact and abs(t1s) < 1e-12 * exact
+
+
+def test_wall_shear_fourier_components_over_a_sine_wall():
+    """u = c(x) (y - y_w(x)) with c = 1 + 0.3 cos(2 pi x / lambda) is linear along every vertical
+    line, so tau(x) = nu c(x) exactly (the arm's distance comes from the wall's closed form) and
+    tau_1c = 0.3 nu, tau_1s = 0 over whole periods; a phase shift moves it to tau_1s."""
+    from oracle.forces import wall_shear
+    base = small_case("wavy3d")          # the wall raised so that every column crosses it
+    case = base.with_(geom_params=(0.05,) + tuple(base.geom_params[1:]))
+    g, ls, cls, _ = _setup(case)
+    y0, A, lam = case.geom_params[0], case.geom_params[1], case.geom_params[2]
+    x, y, _ = g.coords(0)
+    yw = y0 + A * np.sin(2.0 * np.pi * x / lam)
+    for phase, (e1c, e1s) in ((0.0, (0.3, 0.0)), (np.pi / 2, (0.0, -0.3))):
+        c = 1.0 + 0.3 * np.cos(2.0 * np.pi * x / lam + phase)
+        u = np.broadcast_to(c * (y - yw), g.shape)
+        tau, t1c, t1s = wall_shear(g, cls, ls, u, case.nu, lam)
+        xi = g.axis_coords(0, 1.0)
+        expect = case.nu * (1.0 + 0.3 * np.cos(2.0 * np.pi * xi / lam + phase))
+        assert np.abs(tau - expect).max() < 1e-12 * case.nu
+        assert abs(t1c - e1c * case.nu) < 1e-12 * case.nu and abs(t1s - e1s * case.nu) < 1e-12 * case.nu
