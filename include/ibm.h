@@ -228,6 +228,16 @@ ibm_status ibm_project(ibm_solver* h);
  * overwritten by phi.  The rhs must sum to zero.  Asynchronous. */
 ibm_status ibm_poisson(ibm_solver* h, void* rhs_inout);
 
+/* Wall-shear stress of the current velocity along a lower wall (Sec. 4.2 reports the Fourier
+ * components tau_1c, tau_1s of the time-averaged tau(x) over the wavy wall).  Per column of u
+ * points, the lowest internal point P whose -y arm crosses the wall (distance delta, found as for
+ * the weights) and the internal point Q above it: tau = nu u'(0) of the quadratic through 0 at the
+ * wall, u_P and u_Q (u_P / delta when Q is not internal), averaged over z.  tau_x: host array of nx
+ * values (NaN in columns without such a point) or NULL; tau1: host [2] = {tau_1c, tau_1s} =
+ * (2/nx) sum_i tau(x_i) {cos, sin}(2 pi x_i / wavelength), x_i the u points' x, or NULL.
+ * Uses the divergence scratch (call between steps).  Blocking. */
+ibm_status ibm_wall_shear(ibm_solver* h, double wavelength, double* tau_x, double* tau1);
+
 /* Projection operators.  IBM_PROJ_FULLBOX (the default): the unmodified projection, D G of the
  * whole box, every face whose velocity is not prescribed corrected.  IBM_PROJ_MASKED: the
  * literal reading of Sec. 3.3 ("only the internal pressure points are updated"): D M G phi =

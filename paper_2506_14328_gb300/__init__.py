@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "IBM_OK", -1: "IBM_E_INVALID", -2: "IBM_E_CUDA", -3: "IBM_E_N
 # every symbol the header declares
 EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_geometry", "ibm_weights_bytes",
             "ibm_build_weights", "ibm_step", "ibm_project", "ibm_poisson", "ibm_projection_bytes",
-            "ibm_set_projection", "ibm_diagnostics",
+            "ibm_set_projection", "ibm_wall_shear", "ibm_diagnostics",
             "ibm_get_classification", "ibm_get_weights", "ibm_state_bytes", "ibm_export_state",
             "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_diagnostics_noalloc",
             "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
@@ -89,6 +89,7 @@ def _load() -> C.CDLL:
         "ibm_project": ([C.c_void_p], C.c_int),
         "ibm_poisson": ([C.c_void_p, C.c_void_p], C.c_int),
         "ibm_projection_bytes": ([C.c_void_p, P(C.c_size_t)], C.c_int),
+        "ibm_wall_shear": ([C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
         "ibm_set_projection": ([C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_size_t], C.c_int),
         "ibm_diagnostics": ([C.c_void_p, P(ibm_diag)], C.c_int),
         "ibm_get_classification": ([C.c_void_p, C.c_void_p, P(C.c_void_p), P(C.c_int)], C.c_int),
@@ -167,6 +168,11 @@ def ibm_project(h: int):
 
 def ibm_poisson(h: int, rhs_ptr: int):
     _check(lib.ibm_poisson(C.c_void_p(h), C.c_void_p(rhs_ptr)), "ibm_poisson")
+
+
+def ibm_wall_shear(h: int, wavelength: float, tau_ptr: int, tau1_ptr: int):
+    _check(lib.ibm_wall_shear(C.c_void_p(h), float(wavelength), C.c_void_p(tau_ptr), C.c_void_p(tau1_ptr)),
+           "ibm_wall_shear")
 
 
 def ibm_projection_bytes(h: int) -> int:

@@ -563,6 +563,16 @@ ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
     return IBM_OK;
 }
 
+ibm_status ibm_wall_shear(ibm_solver* h, double wavelength, double* tau_x, double* tau1) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!h->weights_ready) return ibm_set_error(IBM_E_STATE, "ibm_build_weights has not run");
+    if (!(wavelength > 0.0) || !std::isfinite(wavelength)) return ibm_set_error(IBM_E_INVALID, "wavelength must be > 0");
+    if ((size_t)h->N * h->esz < 2 * (size_t)h->gp.nx * sizeof(double))
+        return ibm_set_error(IBM_E_UNSUPPORTED, "grid too small for the wall-shear scratch");
+    return geom_wall_shear(h, wavelength, tau_x, tau1);
+}
+
 ibm_status ibm_projection_bytes(const ibm_solver* h, size_t* bytes) {
     if (!h) return ibm_set_error(IBM_E_INVALID, "NULL handle");
     if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");

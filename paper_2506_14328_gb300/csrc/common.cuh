@@ -389,6 +389,7 @@ ibm_status geom_classify(ibm_solver* h);
 ibm_status geom_build_lists_and_weights(ibm_solver* h);
 ibm_status geom_stage_coefficients(ibm_solver* h);
 ibm_status geom_pivots(ibm_solver* h);
+ibm_status geom_wall_shear(ibm_solver* h, double wavelength, double* tau_x, double* tau1);
 
 // step.cu
 ibm_status run_substage(ibm_solver* h, int k, bool predictor_only);

@@ -520,7 +520,88 @@ __global__ void k_pivots(GridP g, double* __restrict__ piv, float* __restrict__ 
     }
 }
 
+// Wall-shear stress along a lower wall: per u IBM point whose -y arm crosses the wall,
+// nu times the slope at the wall of the quadratic through 0 (wall), u_P (delta) and u_Q
+// (delta + dy, the point above; u_P / delta when Q is not internal), summed per x column
+// with a count, into acc[0..nx) and acc[nx..2nx).
+template <typename T>
+__global__ void k_wall_shear(GridP g, GeomP geo, const int* __restrict__ idx, int count,
+                             const uint8_t* __restrict__ mask, const T* __restrict__ u, double nu,
+                             double* __restrict__ acc) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    const int lin = idx[m];
+    const int i = lin % g.nx;
+    const int j = (lin / g.nx) % g.ny;
+    const int k = lin / (g.nx * g.ny);
+    if (j == 0) return;
+    const int below = lin - g.nx;
+    if (mask[below] & IBM_MASK_U) return;             // no wall below this point
+    const double D = g.dy;
+    const double P[3] = {coord(g, 0, i, 0), coord(g, 1, j, 0), coord(g, 2, k, 0)};
+    const bool sampled = geo.kind == IBM_GEOM_SAMPLED;
+    const double phiP = sampled ? geo.sdf[0][lin] : phi_at(geo, P[0], P[1], P[2]);
+    const double phiQ = sampled ? geo.sdf[0][below] : phi_at(geo, P[0], coord(g, 1, j - 1, 0), P[2]);
+    double dl;
+    if (phiQ == 0.0) {
+        dl = D;
+    } else if (sampled) {
+        dl = __dmul_rn(D, __ddiv_rn(phiP, __dsub_rn(phiP, phiQ)));
+    } else {
+        dl = delta_closed(geo, P, 1, -1, D);
+        if (dl < 0.0) dl = delta_bisect(geo, P, 1, -1, D);
+    }
+    dl = fmin(fmax(dl, 1e-12 * D), D);
+    const double uP = (double)u[lin];
+    double slope;
+    if (j + 1 < g.ny && (mask[lin + g.nx] & IBM_MASK_U)) {
+        const double uQ = (double)u[lin + g.nx];
+        const double a = dl + D;
+        slope = (uP * (a * a) - uQ * (dl * dl)) / (dl * D * a);
+    } else {
+        slope = uP / dl;
+    }
+    atomicAdd(acc + i, nu * slope);
+    atomicAdd(acc + g.nx + i, 1.0);
+}
+
 }  // namespace
+
+ibm_status geom_wall_shear(ibm_solver* h, double wavelength, double* tau_x, double* tau1) {
+    const GridP& g = h->gp;
+    double* acc = (double*)h->rhs;                     // scratch between steps
+    IBM_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * (size_t)g.nx * sizeof(double), h->stream));
+    const int cnt = h->counts[0];
+    if (cnt > 0) {
+        const int nb = (cnt + 127) / 128;
+        if (h->prec == IBM_FP64)
+            k_wall_shear<double><<<nb, 128, 0, h->stream>>>(g, h->geo, h->idx[0], cnt, h->mask,
+                                                           (const double*)h->buf.u[0], h->phys.nu, acc);
+        else
+            k_wall_shear<float><<<nb, 128, 0, h->stream>>>(g, h->geo, h->idx[0], cnt, h->mask,
+                                                          (const float*)h->buf.u[0], h->phys.nu, acc);
+        IBM_LAUNCH_CHECK();
+    }
+    std::vector<double> v(2 * (size_t)g.nx);
+    IBM_CUDA_TRY(cudaMemcpyAsync(v.data(), acc, v.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    double c1 = 0.0, s1 = 0.0;
+    const double two_pi = 6.283185307179586;
+    for (int i = 0; i < g.nx; ++i) {
+        const double t = v[g.nx + i] > 0.0 ? v[i] / v[g.nx + i] : std::nan("");
+        if (tau_x) tau_x[i] = t;
+        if (v[g.nx + i] > 0.0) {
+            const double xi = g.ox + (i + 1.0) * g.dx;
+            c1 += t * std::cos(two_pi * xi / wavelength);
+            s1 += t * std::sin(two_pi * xi / wavelength);
+        }
+    }
+    if (tau1) {
+        tau1[0] = 2.0 / g.nx * c1;
+        tau1[1] = 2.0 / g.nx * s1;
+    }
+    return IBM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Host side

@@ -16,7 +16,8 @@ from . import (ibm_grid_desc, ibm_geom_desc, ibm_buffers, ibm_physics, IBM_FP64,
                ibm_project, ibm_poisson, ibm_diagnostics, ibm_get_classification, ibm_get_weights,
                ibm_state_bytes, ibm_export_state, ibm_import_state, ibm_timing, ibm_get_timing,
                ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_get_tiles, ibm_set_momentum_tma,
-               ibm_destroy, ibm_projection_bytes, ibm_set_projection, IBM_PROJ_FULLBOX, IBM_PROJ_MASKED)
+               ibm_destroy, ibm_projection_bytes, ibm_set_projection, IBM_PROJ_FULLBOX, IBM_PROJ_MASKED,
+               ibm_wall_shear)
 
 
 class Solver:
@@ -133,6 +134,14 @@ class Solver:
                 self.weights = torch.empty(max(wb, 256), dtype=torch.uint8, device=self.device)
             self.stream.synchronize()
         ibm_build_weights(self.h, ph, self.weights.data_ptr(), self.weights.numel())
+
+    def wall_shear(self, wavelength):
+        """(tau(x) per u column, tau_1c, tau_1s) of the current velocity along the lower wall."""
+        self.stream.synchronize()
+        tau = np.empty(self.n[0])
+        t1 = np.empty(2)
+        ibm_wall_shear(self.h, wavelength, tau.ctypes.data, t1.ctypes.data)
+        return tau, float(t1[0]), float(t1[1])
 
     def set_projection(self, mode="masked", tol=1e-10, maxit=500):
         """'fullbox' (the unmodified projection) or 'masked' (D M G over the internal cells,

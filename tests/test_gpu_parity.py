@@ -523,3 +523,25 @@ def test_forcing_and_explicit_ibm_match_oracle(variant):
         ug, _ = g.state()
         for c in range(o.grid.ncomp):
             assert _rel(o, ug[c], o.u[c], c) < TOL64, (s, c)
+
+
+@pytest.mark.parametrize("name", ["wavy3d", "channel2d", "cylinder2d", "sphere3d"])
+def test_wall_shear_matches_oracle(name):
+    """tau(x) along the lower wall and its Fourier components after a full step, FP64, against
+    the oracle (the same columns undefined, values to 1e-10 of the largest)."""
+    from inputs import GEOM_SINE_WALL
+    from oracle.forces import wall_shear
+    case = small_case(name)
+    g, o = _pair(case)
+    g.step(1)
+    o.step(1)
+    lam = case.geom_params[2] if case.geom_kind == GEOM_SINE_WALL else case.L[0]
+    tg, cg, sg = g.wall_shear(lam)
+    to, co, so = wall_shear(o.grid, o.cls, o.levelset, o.u[0], case.nu, lam)
+    assert np.array_equal(np.isnan(tg), np.isnan(to))
+    ok = np.isfinite(to)
+    assert ok.any()
+    scale = np.abs(to[ok]).max()
+    assert np.abs(tg[ok] - to[ok]).max() <= 1e-10 * scale
+    assert abs(cg - co) <= 1e-10 * scale and abs(sg - so) <= 1e-10 * scale
+    g.close()
