@@ -31,7 +31,7 @@ EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_g
             "ibm_set_projection", "ibm_wall_shear", "ibm_diagnostics",
             "ibm_get_classification", "ibm_get_weights", "ibm_state_bytes", "ibm_export_state",
             "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_diagnostics_noalloc",
-            "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
+            "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_set_own_fft", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
             "ibm_batch_destroy", "ibm_destroy")
 
 
@@ -106,6 +106,7 @@ def _load() -> C.CDLL:
         "ibm_set_tiles": ([C.c_void_p, C.c_int, C.c_int], C.c_int),
         "ibm_get_tiles": ([C.c_void_p, P(C.c_int), P(C.c_int), P(C.c_int)], C.c_int),
         "ibm_set_momentum_tma": ([C.c_void_p, C.c_int], C.c_int),
+        "ibm_set_own_fft": ([C.c_void_p, C.c_int, P(C.c_int)], C.c_int),
         "ibm_batch_create": ([C.c_void_p, P(C.c_void_p)], C.c_int),
         "ibm_batch_set": ([C.c_void_p, P(C.c_void_p), P(C.c_int), C.c_int], C.c_int),
         "ibm_batch_run": ([C.c_void_p], C.c_int),
@@ -270,6 +271,12 @@ def ibm_get_tiles(h: int) -> tuple:
 
 def ibm_set_momentum_tma(h: int, enable: bool):
     _check(lib.ibm_set_momentum_tma(C.c_void_p(h), 1 if enable else 0), "ibm_set_momentum_tma")
+
+
+def ibm_set_own_fft(h: int, mode: int) -> bool:
+    own = C.c_int(0)
+    _check(lib.ibm_set_own_fft(C.c_void_p(h), int(mode), C.byref(own)), "ibm_set_own_fft")
+    return bool(own.value)
 
 
 def ibm_batch_create(stream: int) -> int:

@@ -179,6 +179,7 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
     char* order = take((size_t)g.nzs * g.nxh * sizeof(int));
     char* rtmp = g.xper ? nullptr : take(g.N * esz);            // reordered rows of the DCT
     char* twid = g.xper ? nullptr : take((size_t)g.nx * 2 * esz);   // cos, sin of pi k / 2nx
+    char* fftab = take(((size_t)g.nx + 2) * 2 * esz);                 // own row-FFT twiddles
     char* dtemp = prec == IBM_FP32 ? take(nspec * 2 * sizeof(double)) : nullptr;
     char* fftw = take(fft_work);
     int npart = momentum_blocks(g);
@@ -206,6 +207,7 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
         h->dtemp = dtemp;
         h->rtmp = rtmp;
         h->twid = twid;
+        h->fftab = fftab;
         h->fft_work = fftw;
         h->partials = (double*)partials;
         h->npartials = npart;
@@ -765,6 +767,17 @@ ibm_status ibm_set_momentum_tma(ibm_solver* h, int enable) {
     drop_graph(h);
     h->mom_tma = enable != 0;
     return IBM_OK;
+}
+
+ibm_status ibm_set_own_fft(ibm_solver* h, int mode, int* own) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (mode < 0 || mode > 2) return ibm_set_error(IBM_E_INVALID, "mode is 0, 1 or 2");
+    drop_graph(h);
+    h->own_fft_mode = mode;
+    st = poisson_prepare(h);
+    if (own) *own = h->own_fft ? 1 : 0;
+    return st;
 }
 
 ibm_status ibm_launch_count(const ibm_solver* h, long long* count) {

@@ -343,6 +343,13 @@ struct ibm_solver {
     cufftHandle plan_fz = 0, plan_iz = 0;   // Neumann x, 3D: transforms along z
     void* rtmp = nullptr;                    // Neumann x: reordered rows of the DCT (N reals)
     void* twid = nullptr;                    // Neumann x: cos, sin of pi k / 2nx (field precision)
+    // own real FFT of the x rows (field precision): radices of nx/2, the table
+    // exp(-2 pi i t / (nx/2)), t < nx/2, then exp(-2 pi i k / nx), k <= nx/2
+    bool own_fft = false;                    // the rows run the own kernels (nx supported)
+    int own_fft_mode = 2;                    // ibm_set_own_fft: 0 never, 1 where supported, 2 automatic
+    int fft_nrad = 0;
+    int fft_rad[16] = {0};
+    void* fftab = nullptr;
     bool plans = false;
 
     bool failed = false;
@@ -407,7 +414,7 @@ bool momentum_uses_tma(const ibm_solver* h);
 ibm_status run_project(ibm_solver* h);
 ibm_status run_poisson(ibm_solver* h, void* rhs_inout);
 ibm_status run_diagnostics(ibm_solver* h, double* out);   // SCAL_N doubles
-ibm_status poisson_prepare(ibm_solver* h);   // Neumann x: the DCT twiddle table
+ibm_status poisson_prepare(ibm_solver* h);   // the own row-FFT plan and tables; Neumann x: the DCT twiddles
 
 // timing hooks used by both
 void timer_begin(ibm_solver* h, const char* name, cudaEvent_t* ev);

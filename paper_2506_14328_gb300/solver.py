@@ -15,7 +15,7 @@ from . import (ibm_grid_desc, ibm_geom_desc, ibm_buffers, ibm_physics, IBM_FP64,
                ibm_workspace_bytes, ibm_setup_geometry, ibm_weights_bytes, ibm_build_weights, ibm_step,
                ibm_project, ibm_poisson, ibm_diagnostics, ibm_get_classification, ibm_get_weights,
                ibm_state_bytes, ibm_export_state, ibm_import_state, ibm_timing, ibm_get_timing,
-               ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_get_tiles, ibm_set_momentum_tma,
+               ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_get_tiles, ibm_set_momentum_tma, ibm_set_own_fft,
                ibm_destroy, ibm_projection_bytes, ibm_set_projection, IBM_PROJ_FULLBOX, IBM_PROJ_MASKED,
                ibm_wall_shear)
 
@@ -232,6 +232,12 @@ class Solver:
 
     def use_tma(self, enable=True):
         ibm_set_momentum_tma(self.h, enable)
+
+    def use_own_fft(self, enable=True) -> bool:
+        """The own x-row FFT: True (wherever it can run), False (never) or "auto" (the
+        default choice); returns whether it runs on this grid."""
+        mode = 2 if enable == "auto" else (1 if enable else 0)
+        return ibm_set_own_fft(self.h, mode)
 
     def footprint_bytes(self) -> int:
         return (sum(t.numel() * t.element_size() for t in self.u + [self.p]) + self.work.numel() +
