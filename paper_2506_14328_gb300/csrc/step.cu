@@ -968,6 +968,28 @@ __device__ __forceinline__ void dft_small(C* v, int R) {
     }
 }
 
+// DFT of 8 points: two DFTs of 4 (even and odd points) joined by exp(SIGN 2 pi i p / 8)
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft8(C* v) {
+    using T = typename CT<C>::T;
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    dft_small<SIGN>(e, 4);
+    dft_small<SIGN>(o, 4);
+    const T r = (T)0.70710678118654752440;
+    const C w1 = C{r * (o[1].x - SIGN * o[1].y), r * (o[1].y + SIGN * o[1].x)};     // (1 + SIGN i)/sqrt2 o1
+    const C w2 = cmuli<SIGN>(o[2]);                                                   // SIGN i o2
+    const C w3 = C{r * (-o[3].x - SIGN * o[3].y), r * (-o[3].y + SIGN * o[3].x)};   // (-1 + SIGN i)/sqrt2 o3
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], w1);
+    v[5] = csub(e[1], w1);
+    v[2] = cadd(e[2], w2);
+    v[6] = csub(e[2], w2);
+    v[3] = cadd(e[3], w3);
+    v[7] = csub(e[3], w3);
+}
+
 struct FftPlan {
     int M, nrad;
     int rad[16];
@@ -1016,7 +1038,7 @@ __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ 
 }
 
 // The same FFT with the length known at compile time: the stage loop unrolled, the
-// index arithmetic by constants (radices chosen in the same order: 4, 2, 3, 5).
+// index arithmetic by constants, radix 8 where it divides (then 4, 2, 3, 5).
 template <int SIGN, int M, int R, int NS, typename C>
 __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict__ y, const C* __restrict__ tw) {
     constexpr int MR = M / R;
@@ -1036,10 +1058,11 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict
             }
             v[q] = a;
         }
-        C vv[5];
+        C vv[8];
 #pragma unroll
         for (int q = 0; q < R; ++q) vv[q] = v[q];
-        dft_small<SIGN>(vv, R);
+        if (R == 8) dft8<SIGN>(vv);
+        else dft_small<SIGN>(vv, R);
         const int base = (j / NS) * NS * R + k;
 #pragma unroll
         for (int q = 0; q < R; ++q) y[base + q * NS] = vv[q];
@@ -1048,7 +1071,7 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict
 
 template <int SIGN, int M, int NS, int REM>
 struct FftRun {
-    static constexpr int R = REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : (REM % 3 == 0 ? 3 : 5));
+    static constexpr int R = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : (REM % 3 == 0 ? 3 : 5)));
     template <typename C>
     static __device__ __forceinline__ const C* run(const C* x, C* b0, C* b1, const C* tw) {
         fft_stage<SIGN, M, R, NS>(x, b0, tw);
