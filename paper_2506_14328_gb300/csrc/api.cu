@@ -680,11 +680,21 @@ ibm_status ibm_import_state(ibm_solver* h, const void* host, size_t bytes) {
         return ibm_set_error(IBM_E_INVALID, "state snapshot does not match this solver");
     const char* p = (const char*)host + 64;
     size_t fb = h->N * h->esz;
-    for (int c = 0; c < h->gp.ncomp; ++c, p += fb)
-        IBM_CUDA_TRY(cudaMemcpyAsync(h->buf.u[c], p, fb, cudaMemcpyHostToDevice, h->stream));
-    IBM_CUDA_TRY(cudaMemcpyAsync(h->buf.p, p, fb, cudaMemcpyHostToDevice, h->stream));
+    // one stream per field, after everything already queued on the solver's stream
+    if (!h->copy_fork) {
+        IBM_CUDA_TRY(cudaEventCreateWithFlags(&h->copy_fork, cudaEventDisableTiming));
+        for (cudaStream_t& s : h->copy_streams) IBM_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    }
+    IBM_CUDA_TRY(cudaEventRecord(h->copy_fork, h->stream));
+    void* dst[4] = {h->buf.u[0], h->buf.u[1], h->gp.ncomp == 3 ? h->buf.u[2] : nullptr, h->buf.p};
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q]) continue;
+        IBM_CUDA_TRY(cudaStreamWaitEvent(h->copy_streams[q], h->copy_fork, 0));
+        IBM_CUDA_TRY(cudaMemcpyAsync(dst[q], p, fb, cudaMemcpyHostToDevice, h->copy_streams[q]));
+        p += fb;
+    }
     h->steps = (long long)hdr[4];
-    IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (cudaStream_t s : h->copy_streams) IBM_CUDA_TRY(cudaStreamSynchronize(s));
     return IBM_OK;
 }
 
@@ -895,6 +905,9 @@ void ibm_destroy(ibm_solver* h) {
         cudaEventDestroy(t.b);
     }
     drop_graph(h);
+    for (cudaStream_t s : h->copy_streams)
+        if (s) cudaStreamDestroy(s);
+    if (h->copy_fork) cudaEventDestroy(h->copy_fork);
     if (h->plans) {
         cufftDestroy(h->plan_f);
         cufftDestroy(h->plan_i);

@@ -295,6 +295,10 @@ struct ibm_solver {
     ibm_geom_desc geom;
     ibm_buffers buf;
     cudaStream_t stream = nullptr;
+    // state import / export: the field copies go out on their own streams (several copy
+    // engines), ordered after the solver's stream by an event; created on first use
+    cudaStream_t copy_streams[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t copy_fork = nullptr;
     GridP gp;
     GeomP geo;
     int prec = IBM_FP64;
