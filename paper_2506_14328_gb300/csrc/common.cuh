@@ -350,6 +350,7 @@ struct ibm_solver {
     // own real FFT of the x rows (field precision): radices of nx/2, the table
     // exp(-2 pi i t / (nx/2)), t < nx/2, then exp(-2 pi i k / nx), k <= nx/2
     bool own_fft = false;                    // the rows run the own kernels (nx supported)
+    bool dct_rows = false;                   // inflow/outflow x: the DCT rows in one pass each way
     int own_fft_mode = 2;                    // ibm_set_own_fft: 0 never, 1 where supported, 2 automatic
     int fft_nrad = 0;
     int fft_rad[16] = {0};

@@ -1245,6 +1245,86 @@ __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restr
     rfft_post<C>(M, Z, out + row * (M + 1), tab + M);
 }
 
+// The type-II DCT of whole x rows in one pass (inflow/outflow x): the row is read, placed in
+// the Makhoul order v[n/2] = x[n] (n even), v[N-1-(n-1)/2] = x[n] (n odd) in shared memory,
+// transformed there as M complex pairs, and X_k = cos(pi k/2N) Re V_k + sin(pi k/2N) Im V_k,
+// with V_k = conj V_{N-k} above N/2, is written back over the row.  Replaces the reorder
+// pass, cuFFT's R2C and the twiddle pass (three trips through HBM).
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) k_dct_rows(FftPlan pl, long long rows, T* __restrict__ x,
+                                                  const C* __restrict__ tab, const T* __restrict__ tw) {
+    extern __shared__ unsigned char fft_smem[];
+    const int M = pl.M, N = 2 * pl.M;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + wq;
+    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * (3 * M + 2);
+    C* b1 = b0 + M;
+    C* b2 = b1 + M;                                       // M + 2 values
+    if (row >= rows) return;
+    T* xr = x + row * N;
+    T* v = reinterpret_cast<T*>(b2);
+    for (int n = lane; n < N; n += 32) v[(n & 1) ? N - 1 - (n >> 1) : (n >> 1)] = xr[n];
+    __syncwarp();
+    const C* Z = warp_fft_any<-1, C>(pl, reinterpret_cast<const C*>(v), b0, b1, tab);
+    // V_k, k = 0..M, into the other buffer (the one Z is not in), then the twiddle
+    C* V = (Z == b0) ? b1 : b0;
+    const C* twN = tab + M;
+    for (int k = lane; k <= M && k < M; k += 32) {
+        const C zk = Z[k];
+        const C zc = cconj(Z[k == 0 ? 0 : M - k]);
+        const C e = C{(zk.x + zc.x) * (T)0.5, (zk.y + zc.y) * (T)0.5};
+        const C d = C{(zk.x - zc.x) * (T)0.5, (zk.y - zc.y) * (T)0.5};
+        V[k] = cadd(e, cmul(twN[k], C{d.y, -d.x}));
+    }
+    const C z0 = Z[0];                                    // V_M = Re Z_0 - Im Z_0 (real)
+    __syncwarp();
+    for (int k = lane; k < N; k += 32) {
+        C vk;
+        if (k < M) vk = V[k];
+        else if (k == M) vk = C{z0.x - z0.y, (T)0};
+        else { vk = V[N - k]; vk.y = -vk.y; }
+        xr[k] = tw[2 * k] * vk.x + tw[2 * k + 1] * vk.y;
+    }
+}
+
+// The inverse: V_k = (c a + s b, s a - c b) from a = X_k, b = X_{N-k} (0 at k = 0), the
+// unnormalised inverse real transform of V, and x[n] = v[pos(n)] written back over the row.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) k_idct_rows(FftPlan pl, long long rows, T* __restrict__ x,
+                                                   const C* __restrict__ tab, const T* __restrict__ tw) {
+    extern __shared__ unsigned char fft_smem[];
+    const int M = pl.M, N = 2 * pl.M;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + wq;
+    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * (3 * M + 2);
+    C* b1 = b0 + M;
+    C* b2 = b1 + M;                                       // V_0..V_M
+    if (row >= rows) return;
+    T* xr = x + row * N;
+    for (int k = lane; k <= M; k += 32) {
+        const T a = xr[k];
+        const T b = k == 0 ? T(0) : xr[N - k];
+        const T c = tw[2 * k], sn = tw[2 * k + 1];
+        b2[k] = C{c * a + sn * b, sn * a - c * b};
+    }
+    __syncwarp();
+    // the pre-processing of the inverse real transform, into b0
+    const C* twN = tab + M;
+    for (int k = lane; k < M; k += 32) {
+        const C xk = b2[k];
+        const C xc = cconj(b2[M - k]);
+        const C e = cadd(xk, xc);
+        const C d = cmul(csub(xk, xc), cconj(twN[k]));
+        b0[k] = cadd(e, C{-d.y, d.x});
+    }
+    __syncwarp();
+    // the transform reads b0 and alternates between b1 and b2 (V is no longer needed)
+    const C* z = warp_fft_any<+1, C>(pl, b0, b1, b2, tab);
+    const T* v = reinterpret_cast<const T*>(z);
+    __syncwarp();
+    for (int n = lane; n < N; n += 32) xr[n] = v[(n & 1) ? N - 1 - (n >> 1) : (n >> 1)];
+}
+
 template <typename T>
 __global__ void k_fft_tables(int M, T* __restrict__ tab) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1269,6 +1349,9 @@ inline int fft_rows_per_block(int M, size_t csz) {
     return r < 1 ? 1 : (r > 8 ? 8 : r);
 }
 
+template <typename T, typename C>
+void dct_rows(ibm_solver* h, T* x, bool inverse);
+
 template <typename C>
 ibm_status own_rfft(ibm_solver* h, const void* in, void* out, bool inverse) {
     const GridP& g = h->gp;
@@ -1287,6 +1370,24 @@ ibm_status own_rfft(ibm_solver* h, const void* in, void* out, bool inverse) {
     IBM_LAUNCH_CHECK();
     return IBM_OK;
 }
+
+template <typename T, typename C>
+void dct_rows(ibm_solver* h, T* x, bool inverse) {
+    const GridP& g = h->gp;
+    FftPlan pl;
+    pl.M = g.nx / 2;
+    pl.nrad = h->fft_nrad;
+    for (int q = 0; q < 16; ++q) pl.rad[q] = h->fft_rad[q];
+    const long long rows = (long long)g.ny * g.nz;
+    const int rpb = fft_rows_per_block(pl.M + 1, sizeof(C));
+    const size_t smem = (3 * (size_t)pl.M + 2) * sizeof(C) * rpb;
+    const int nb = (int)((rows + rpb - 1) / rpb);
+    if (inverse)
+        k_idct_rows<T, C><<<nb, 32 * rpb, smem, h->stream>>>(pl, rows, x, (const C*)h->fftab, (const T*)h->twid);
+    else
+        k_dct_rows<T, C><<<nb, 32 * rpb, smem, h->stream>>>(pl, rows, x, (const C*)h->fftab, (const T*)h->twid);
+}
+
 
 template <typename T, typename C>
 __global__ void k_dct_post(GridP g, const C* __restrict__ V, T* __restrict__ X, const T* __restrict__ tw) {
@@ -1444,12 +1545,18 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout, bool x_done = false) {
     } else {
         // DCT of the x rows into rhs, then (3D) the real FFT along z into the spectrum
         T* x = (T*)rhs_inout;
-        k_dct_reorder<T><<<nbN, 256, 0, h->stream>>>(g, x, (T*)h->rtmp, 0);
-        IBM_LAUNCH_CHECK();
-        r = xfwd(h->rtmp, h->spec);
-        if (r == CUFFT_SUCCESS) {
-            k_dct_post<T, C><<<nbN, 256, 0, h->stream>>>(g, (const C*)h->spec, x, (const T*)h->twid);
+        if (h->dct_rows) {
+            dct_rows<T, C>(h, x, false);                  // reorder, row FFT and twiddle in one pass
+        } else {
+            k_dct_reorder<T><<<nbN, 256, 0, h->stream>>>(g, x, (T*)h->rtmp, 0);
             IBM_LAUNCH_CHECK();
+            r = xfwd(h->rtmp, h->spec);
+            if (r == CUFFT_SUCCESS) {
+                k_dct_post<T, C><<<nbN, 256, 0, h->stream>>>(g, (const C*)h->spec, x, (const T*)h->twid);
+                IBM_LAUNCH_CHECK();
+            }
+        }
+        if (r == CUFFT_SUCCESS) {
             if (g.nz > 1) {
                 r = fwd(h->plan_fz, x, h->spec);
             } else {
@@ -1497,7 +1604,9 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout, bool x_done = false) {
             k_unpack_real<T, C><<<nbN, 256, 0, h->stream>>>(g.N, (const C*)h->spec, x);
             IBM_LAUNCH_CHECK();
         }
-        if (r == CUFFT_SUCCESS) {
+        if (r == CUFFT_SUCCESS && h->dct_rows) {
+            dct_rows<T, C>(h, x, true);
+        } else if (r == CUFFT_SUCCESS) {
             const long long nh = (long long)g.ny * g.nz * (g.nx / 2 + 1);
             k_idct_pre<T, C><<<(int)((nh + 255) / 256), 256, 0, h->stream>>>(g, x, (C*)h->spec, (const T*)h->twid);
             IBM_LAUNCH_CHECK();
@@ -2274,6 +2383,10 @@ ibm_status poisson_prepare(ibm_solver* h) {
         // per pass on 384 x 256 x 256); cuFFT is faster on power-of-two rows (512: 0.56 against 0.53)
         const bool pow2 = (M & (M - 1)) == 0;
         h->own_fft = ok && (h->own_fft_mode == 1 || (h->own_fft_mode == 2 && !pow2));
+        // the DCT rows of an inflow/outflow x: fused whenever the own FFT can run (the fusion saves
+        // two passes over the field, which outweighs cuFFT's edge on power-of-two rows)
+        h->dct_rows = ok && !h->gp.xper && h->own_fft_mode != 0 &&
+                      (3 * (size_t)M + 2) * csz <= 48 * 1024;
         h->fft_nrad = ok ? nr : 0;
         for (int q = 0; q < 16; ++q) h->fft_rad[q] = (ok && q < nr) ? rad[q] : 0;
         if (ok) {
