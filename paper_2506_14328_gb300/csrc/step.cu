@@ -1163,20 +1163,25 @@ __global__ void __launch_bounds__(256) k_irfft_rows(FftPlan pl, long long rows, 
 // increment of the internal u points as in k_divergence, u*(x-1) from the lane below or
 // carried from the previous pass) into shared memory and transforms it there, so the
 // divergence never goes through HBM.
-template <typename T, typename C, bool THREE, bool FLUX>
+// XF: an inflow/outflow x instead: the inflow face value is the left neighbour of x = 0,
+// the row goes into the DCT order, and the twiddled DCT coefficients are written over the
+// row of xout (as k_dct_rows) instead of a half spectrum.
+template <typename T, typename C, bool THREE, bool FLUX, bool XF>
 __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restrict__ u, const T* __restrict__ v,
                                                        const T* __restrict__ w, const uint8_t* __restrict__ mask,
                                                        FluxCorr<T> fc, T idx, T idy, T idz, FftPlan pl,
-                                                       C* __restrict__ out, const C* __restrict__ tab) {
+                                                       C* __restrict__ out, const C* __restrict__ tab,
+                                                       T* __restrict__ xout, const T* __restrict__ tw) {
     extern __shared__ unsigned char fft_smem[];
     const int M = pl.M;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const long long rows = (long long)g.ny * g.nz;
     const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + wq;
-    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * 3 * M;
+    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * (3 * M + 2);
     C* b1 = b0 + M;
     C* b2 = b1 + M;
     if (row >= rows) return;                              // whole warp
+    const int N = 2 * M;
     const int j = (int)(row % g.ny), k = (int)(row / g.ny);
     const long long rowb = row * g.nx;
     const long long rowm = THREE ? (long long)(k > 0 ? k - 1 : g.nz - 1) * g.ny * g.nx + (long long)j * g.nx : 0;
@@ -1184,9 +1189,12 @@ __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restr
     const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
     const int nseg = g.nsegx;
     const int rowseg = (j + g.ny * k) * nseg;
-    // u* at x = nx - 1 (with its increment): the left neighbour of x = 0
+    // u* at x = nx - 1 (with its increment): the left neighbour of x = 0; the inflow face
+    // value for an inflow/outflow x
     T carry;
-    {
+    if (XF) {
+        carry = (mask[rowb] & IBM_MASK_FACE) ? (T)g.uin : T(0);
+    } else {
         const int s = nseg - 1;
         const int x = s * 32 + lane;
         const bool live = x < g.nx;
@@ -1236,13 +1244,36 @@ __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restr
                 T dv = (ucc - ul) * idx;
                 dv += (vc[t] - vm[t]) * idy;
                 if (THREE) dv += (wc[t] - wm[t]) * idz;
-                d[x] = dv;
+                d[XF ? ((x & 1) ? N - 1 - (x >> 1) : (x >> 1)) : x] = dv;
             }
         }
     }
     __syncwarp();
     const C* Z = warp_fft_any<-1, C>(pl, reinterpret_cast<const C*>(d), b0, b1, tab);
-    rfft_post<C>(M, Z, out + row * (M + 1), tab + M);
+    if (!XF) {
+        rfft_post<C>(M, Z, out + row * (M + 1), tab + M);
+        return;
+    }
+    // DCT twiddle as in k_dct_rows
+    C* V = (Z == b0) ? b1 : b0;
+    const C* twN = tab + M;
+    for (int kk = lane; kk < M; kk += 32) {
+        const C zk = Z[kk];
+        const C zc = cconj(Z[kk == 0 ? 0 : M - kk]);
+        const C e = C{(zk.x + zc.x) * (T)0.5, (zk.y + zc.y) * (T)0.5};
+        const C dd = C{(zk.x - zc.x) * (T)0.5, (zk.y - zc.y) * (T)0.5};
+        V[kk] = cadd(e, cmul(twN[kk], C{dd.y, -dd.x}));
+    }
+    const C z0 = Z[0];
+    __syncwarp();
+    T* xr = xout + row * N;
+    for (int kk = lane; kk < N; kk += 32) {
+        C vk;
+        if (kk < M) vk = V[kk];
+        else if (kk == M) vk = C{z0.x - z0.y, (T)0};
+        else { vk = V[N - kk]; vk.y = -vk.y; }
+        xr[kk] = tw[2 * kk] * vk.x + tw[2 * kk + 1] * vk.y;
+    }
 }
 
 // The type-II DCT of whole x rows in one pass (inflow/outflow x): the row is read, placed in
@@ -1545,7 +1576,9 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout, bool x_done = false) {
     } else {
         // DCT of the x rows into rhs, then (3D) the real FFT along z into the spectrum
         T* x = (T*)rhs_inout;
-        if (h->dct_rows) {
+        if (x_done) {
+            // the divergence kernel wrote the DCT coefficients of the rows
+        } else if (h->dct_rows) {
             dct_rows<T, C>(h, x, false);                  // reorder, row FFT and twiddle in one pass
         } else {
             k_dct_reorder<T><<<nbN, 256, 0, h->stream>>>(g, x, (T*)h->rtmp, 0);
@@ -1904,7 +1937,8 @@ template <typename T>
 ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const FluxCorr<T>& fc) {
     const GridP& g = h->gp;
     cudaEvent_t t;
-    if (g.xper && h->own_fft && h->proj_mode != IBM_PROJ_MASKED) {
+    const bool fuse_x = g.xper ? h->own_fft : h->dct_rows;
+    if (fuse_x && h->proj_mode != IBM_PROJ_MASKED) {
         // the divergence fused with the transform of the x rows (own FFT, periodic x)
         using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
         timer_begin(h, "div_fft_x", &t);
@@ -1915,20 +1949,25 @@ ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const 
         pl.nrad = h->fft_nrad;
         for (int q = 0; q < 16; ++q) pl.rad[q] = h->fft_rad[q];
         const long long rows = (long long)g.ny * g.nz;
-        const int rpb = fft_rows_per_block(pl.M, sizeof(C));
-        const size_t smem = 3 * (size_t)pl.M * sizeof(C) * rpb;
+        const int rpb = fft_rows_per_block(pl.M + 1, sizeof(C));
+        const size_t smem = (3 * (size_t)pl.M + 2) * sizeof(C) * rpb;
         const int nb = (int)((rows + rpb - 1) / rpb);
         C* out = (C*)h->spec;
         const C* tab = (const C*)h->fftab;
-#define IBM_DIVFFT(THREE_, FLUX_)                                                                                 \
-    k_div_rfft_rows<T, C, THREE_, FLUX_><<<nb, 32 * rpb, smem, h->stream>>>(g, us[0], us[1], w, h->mask, fc, ix, iy, iz, \
-                                                                             pl, out, tab)
-        if (g.ndim == 3) {
-            if (flux) IBM_DIVFFT(true, true);
-            else IBM_DIVFFT(true, false);
+        T* xo = (T*)h->rhs;
+        const T* twd = (const T*)h->twid;
+#define IBM_DIVFFT(THREE_, FLUX_, XF_)                                                                            \
+    k_div_rfft_rows<T, C, THREE_, FLUX_, XF_><<<nb, 32 * rpb, smem, h->stream>>>(g, us[0], us[1], w, h->mask, fc, ix, iy, \
+                                                                                  iz, pl, out, tab, xo, twd)
+        if (!g.xper) {   // inflow/outflow x (no constant flow rate)
+            if (g.ndim == 3) IBM_DIVFFT(true, false, true);
+            else IBM_DIVFFT(false, false, true);
+        } else if (g.ndim == 3) {
+            if (flux) IBM_DIVFFT(true, true, false);
+            else IBM_DIVFFT(true, false, false);
         } else {
-            if (flux) IBM_DIVFFT(false, true);
-            else IBM_DIVFFT(false, false);
+            if (flux) IBM_DIVFFT(false, true, false);
+            else IBM_DIVFFT(false, false, false);
         }
 #undef IBM_DIVFFT
         IBM_LAUNCH_CHECK();

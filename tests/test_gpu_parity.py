@@ -582,17 +582,23 @@ def test_own_row_fft_matches_cufft_and_oracle(n, precision):
     g.close()
 
 
-@pytest.mark.parametrize("variant", ["wavy3d_flux", "cylinder2d_flux", "sphere3d_forced", "channel2d_forced"])
+@pytest.mark.parametrize("variant", ["wavy3d_flux", "cylinder2d_flux", "sphere3d_forced", "channel2d_forced",
+                                     "cylinder2d_io", "sphere3d_io", "tubes3d_io"])
 def test_fused_divergence_and_row_transform_match_oracle(variant):
     """The divergence fused with the own transform of the x rows (periodic x, rows whose half
     length has a factor 3): 3D and 2D, with and without the constant-flow-rate increment, over
-    full steps against the oracle (1e-12); the unfused path (cuFFT rows) agrees as well."""
+    full steps against the oracle (1e-12); the unfused path (cuFFT rows) agrees as well.  The
+    inflow/outflow boxes fuse it with the DCT of the rows instead (inflow face as the left
+    neighbour of the first cell)."""
     from inputs import FLOW_FORCED
     case = {
         "wavy3d_flux": small_case("wavy3d").with_(n=(96, 36, 20), name="wavy3d_96x36x20"),
         "cylinder2d_flux": small_case("cylinder2d"),
         "sphere3d_forced": small_case("sphere3d"),
         "channel2d_forced": small_case("channel2d").with_(n=(96, 32, 1), flow_mode=FLOW_FORCED, g=(0.5, 0.0, 0.0)),
+        "cylinder2d_io": small_case("cylinder2d_io"),
+        "sphere3d_io": small_case("sphere3d_io"),
+        "tubes3d_io": small_case("tubes3d_io"),
     }[variant]
     f = initial_field(case)
     o = OracleSolver(case)
