@@ -291,7 +291,9 @@ ibm_status ibm_get_timing(ibm_solver* h, ibm_kernel_time* out, int max, int* cou
  * between full steps, outside stream capture.  Blocking.  2D grids keep the
  * defaults. */
 ibm_status ibm_autotune(ibm_solver* h, int* kz_momentum, int* kz_march);
-/* Set the z-chunks directly (values from a cached autotune). */
+/* Set the z-chunks directly (values from a cached autotune).  kz_momentum:
+ * the planes one momentum block marches, 8 to 86 (the last chunk takes the
+ * rest); kz_march one of {4, 8, 16, 32}.  IBM_E_INVALID otherwise. */
 ibm_status ibm_set_tiles(ibm_solver* h, int kz_momentum, int kz_march);
 /* The z-chunks in use, and whether the momentum predictor runs its TMA form
  * (*tma = 1: plane tiles arrive by tensor copies into a shared-memory ring;

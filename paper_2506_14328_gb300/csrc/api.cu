@@ -752,8 +752,8 @@ ibm_status ibm_autotune(ibm_solver* h, int* kz_momentum, int* kz_march) {
 ibm_status ibm_set_tiles(ibm_solver* h, int kz_momentum, int kz_march) {
     ibm_status st = check_handle(h);
     if (st != IBM_OK) return st;
-    bool okm = false, okd = false;
-    for (int v : KZM_CHOICES) okm |= v == kz_momentum;
+    const bool okm = kz_momentum >= MOM_KZ_MIN && kz_momentum <= KZM_CHOICES[7];
+    bool okd = false;
     for (int v : KZD_CHOICES) okd |= v == kz_march;
     if (!okm || !okd) return ibm_set_error(IBM_E_INVALID, "z-chunk not among the supported choices");
     drop_graph(h);

@@ -301,8 +301,9 @@ def test_full_size_wavy_channel_launch_configuration():
 @pytest.mark.parametrize("nx", [70, 64])
 @pytest.mark.parametrize("flow", ["forced", "const_flux", "inflow"])
 def test_predictor_every_z_chunk_matches_oracle(flow, nx):
-    """The momentum predictor at every z-chunk the autotuner may pick, on a grid whose
-    z extent (23) leaves odd and short chunks, against the oracle to 1e-12.  nx = 64 runs
+    """The momentum predictor at every z-chunk the autotuner may pick and at lengths
+    between them, on a grid whose z extent (23) leaves odd and short chunks, against the
+    oracle to 1e-12.  nx = 64 runs
     the TMA form (x a multiple of 16), nx = 70 the register form.  With a forced flow or an
     inflow/outflow x, u* is also the same bit for bit at every chunk; under the constant
     flow rate the forcing sums per-block partials, whose grouping follows the chunking."""
@@ -318,7 +319,7 @@ def test_predictor_every_z_chunk_matches_oracle(flow, nx):
     o.set_state(f["u"], f["v"], f["w"], f["p"])
     o.substage(0, predictor_only=True)
     first = None
-    for kz in (8, 12, 16, 24, 32, 48, 64, 86):
+    for kz in (8, 9, 11, 12, 13, 14, 16, 24, 32, 48, 64, 86):
         g = _gpu(case)
         g.set_state(f["u"], f["v"], f["w"], f["p"])
         g.set_tiles(kz, 16)
