@@ -995,9 +995,22 @@ struct FftPlan {
     int rad[16];
 };
 
+// Shared-memory place of complex value i of a row buffer: one pad slot after every 16,
+// so that the stride-R and stride-NS stores of the early stages spread over the banks
+// (unpadded, the first radix-8 stage's stores hit the same two banks 16 times).
+// PAD = false keeps the plain layout (the flow-rate divergence kernel, whose integer
+// pipe is the busy one: the pads' index arithmetic cost it more than they saved).
+template <bool PAD = true>
+__device__ __forceinline__ int pz(int i) { return PAD ? i + (i >> 4) : i; }
+// ... and of real value r of a row buffer viewed as reals
+template <bool PAD = true>
+__device__ __forceinline__ int pzr(int r) { return 2 * pz<PAD>(r >> 1) + (r & 1); }
+// complex slots of one row buffer (values 0 .. M + 2 with their pads)
+__host__ __device__ inline int fft_ps(int M) { return M + (M >> 4) + 4; }
+
 // The warp's FFT of length M from src (shared or global) to a shared buffer; returns the
 // buffer holding the result.  tw[t] = exp(-2 pi i t / M).
-template <int SIGN, typename C>
+template <int SIGN, bool GS, bool PAD, typename C>
 __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ src, C* b0, C* b1,
                                        const C* __restrict__ tw) {
     const int lane = threadIdx.x & 31;
@@ -1015,7 +1028,7 @@ __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ 
 #pragma unroll
             for (int q = 0; q < 5; ++q)
                 if (q < R) {
-                    C a = x[j + q * MR];
+                    C a = (GS && s == 0) ? x[j + q * MR] : x[pz<PAD>(j + q * MR)];
                     if (q > 0 && k > 0) {
                         C w = tw[q * k * step];
                         if (SIGN > 0) w = cconj(w);
@@ -1027,7 +1040,7 @@ __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ 
             const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
             for (int q = 0; q < 5; ++q)
-                if (q < R) y[base + q * Ns] = v[q];
+                if (q < R) y[pz<PAD>(base + q * Ns)] = v[q];
         }
         __syncwarp();
         x = y;
@@ -1039,7 +1052,7 @@ __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ 
 
 // The same FFT with the length known at compile time: the stage loop unrolled, the
 // index arithmetic by constants, radix 8 where it divides (then 4, 2, 3, 5).
-template <int SIGN, int M, int R, int NS, typename C>
+template <int SIGN, int M, int R, int NS, bool GS, bool PAD, typename C>
 __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict__ y, const C* __restrict__ tw) {
     constexpr int MR = M / R;
     constexpr int STEP = M / (NS * R);
@@ -1050,7 +1063,7 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict
         C v[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            C a = x[j + q * MR];
+            C a = GS ? x[j + q * MR] : x[pz<PAD>(j + q * MR)];
             if (q > 0 && NS > 1) {
                 C w = tw[q * k * STEP];
                 if (SIGN > 0) w = cconj(w);
@@ -1065,45 +1078,46 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict
         else dft_small<SIGN>(vv, R);
         const int base = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int q = 0; q < R; ++q) y[base + q * NS] = vv[q];
+        for (int q = 0; q < R; ++q) y[pz<PAD>(base + q * NS)] = vv[q];
     }
 }
 
-template <int SIGN, int M, int NS, int REM>
+template <int SIGN, int M, int NS, int REM, bool GS, bool PAD>
 struct FftRun {
     static constexpr int R = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : (REM % 3 == 0 ? 3 : 5)));
     template <typename C>
     static __device__ __forceinline__ const C* run(const C* x, C* b0, C* b1, const C* tw) {
-        fft_stage<SIGN, M, R, NS>(x, b0, tw);
+        fft_stage<SIGN, M, R, NS, GS, PAD>(x, b0, tw);
         __syncwarp();
-        return FftRun<SIGN, M, NS * R, REM / R>::run(b0, b1, b0, tw);
+        return FftRun<SIGN, M, NS * R, REM / R, false, PAD>::run(b0, b1, b0, tw);
     }
 };
-template <int SIGN, int M, int NS>
-struct FftRun<SIGN, M, NS, 1> {
+template <int SIGN, int M, int NS, bool GS, bool PAD>
+struct FftRun<SIGN, M, NS, 1, GS, PAD> {
     template <typename C>
     static __device__ __forceinline__ const C* run(const C* x, C*, C*, const C*) { return x; }
 };
 
 // lengths with a compiled form (the workloads' rows: 384, 512 and 1536 reals)
-template <int SIGN, typename C>
+// GS: src is the row in global memory (unpadded); else a padded shared row buffer.
+template <int SIGN, typename C, bool GS = false, bool PAD = true>
 __device__ __forceinline__ const C* warp_fft_any(const FftPlan& pl, const C* src, C* b0, C* b1, const C* tw) {
     switch (pl.M) {
-        case 192: return FftRun<SIGN, 192, 1, 192>::run(src, b0, b1, tw);
-        case 256: return FftRun<SIGN, 256, 1, 256>::run(src, b0, b1, tw);
-        case 768: return FftRun<SIGN, 768, 1, 768>::run(src, b0, b1, tw);
-        default: return warp_fft<SIGN, C>(pl, src, b0, b1, tw);
+        case 192: return FftRun<SIGN, 192, 1, 192, GS, PAD>::run(src, b0, b1, tw);
+        case 256: return FftRun<SIGN, 256, 1, 256, GS, PAD>::run(src, b0, b1, tw);
+        case 768: return FftRun<SIGN, 768, 1, 768, GS, PAD>::run(src, b0, b1, tw);
+        default: return warp_fft<SIGN, GS, PAD, C>(pl, src, b0, b1, tw);
     }
 }
 
 // The split of the two interleaved real transforms: X_k, k = 0..M, from Z = FFT(z).
-template <typename C>
+template <typename C, bool PAD = true>
 __device__ __forceinline__ void rfft_post(int M, const C* Z, C* __restrict__ o, const C* __restrict__ twN) {
     using T = typename CT<C>::T;
     const int lane = threadIdx.x & 31;
     for (int k = lane; k <= M; k += 32) {
-        const C zk = Z[k == M ? 0 : k];
-        const C zc = cconj(Z[k == 0 ? 0 : M - k]);
+        const C zk = Z[pz<PAD>(k == M ? 0 : k)];
+        const C zc = cconj(Z[pz<PAD>(k == 0 ? 0 : M - k)]);
         const C e = C{(zk.x + zc.x) * (T)0.5, (zk.y + zc.y) * (T)0.5};        // (Z_k + conj Z_{M-k}) / 2
         const C d = C{(zk.x - zc.x) * (T)0.5, (zk.y - zc.y) * (T)0.5};
         const C od = C{d.y, -d.x};                                              // d / i
@@ -1120,12 +1134,12 @@ __global__ void __launch_bounds__(256) k_rfft_rows(FftPlan pl, long long rows, c
     const int M = pl.M;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + w;
-    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)w * 2 * M;
-    C* b1 = b0 + M;
+    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)w * 3 * fft_ps(M);
+    C* b1 = b0 + fft_ps(M);
     if (row >= rows) return;                              // whole warp
     const C* twM = tab;                                   // exp(-2 pi i t / M)
     const C* twN = tab + M;                               // exp(-2 pi i k / 2M)
-    const C* Z = warp_fft_any<-1, C>(pl, in + row * M, b0, b1, twM);
+    const C* Z = warp_fft_any<-1, C, true>(pl, in + row * M, b0, b1, twM);
     rfft_post<C>(M, Z, out + row * (M + 1), twN);
 }
 
@@ -1138,9 +1152,9 @@ __global__ void __launch_bounds__(256) k_irfft_rows(FftPlan pl, long long rows, 
     const int M = pl.M;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + w;
-    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)w * 3 * M;
-    C* b1 = b0 + M;
-    C* b2 = b1 + M;
+    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)w * 3 * fft_ps(M);
+    C* b1 = b0 + fft_ps(M);
+    C* b2 = b1 + fft_ps(M);
     if (row >= rows) return;
     const C* twM = tab;
     const C* twN = tab + M;
@@ -1150,12 +1164,12 @@ __global__ void __launch_bounds__(256) k_irfft_rows(FftPlan pl, long long rows, 
         const C xc = cconj(X[M - k]);
         const C e = cadd(xk, xc);
         const C d = cmul(csub(xk, xc), cconj(twN[k]));        // (X_k - conj X_{M-k}) exp(+2 pi i k / 2M)
-        b2[k] = cadd(e, C{-d.y, d.x});                        // e + i d
+        b2[pz(k)] = cadd(e, C{-d.y, d.x});                    // e + i d
     }
     __syncwarp();
     const C* z = warp_fft_any<+1, C>(pl, b2, b0, b1, twM);
     C* o = out + row * M;
-    for (int n = lane; n < M; n += 32) o[n] = z[n];
+    for (int n = lane; n < M; n += 32) o[n] = z[pz(n)];
 }
 
 // The divergence of u* fused with the forward transform of its x rows (periodic x):
@@ -1173,13 +1187,14 @@ __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restr
                                                        C* __restrict__ out, const C* __restrict__ tab,
                                                        T* __restrict__ xout, const T* __restrict__ tw) {
     extern __shared__ unsigned char fft_smem[];
+    constexpr bool PAD = !FLUX;
     const int M = pl.M;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const long long rows = (long long)g.ny * g.nz;
     const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + wq;
-    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * (3 * M + 2);
-    C* b1 = b0 + M;
-    C* b2 = b1 + M;
+    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * 3 * fft_ps(M);
+    C* b1 = b0 + fft_ps(M);
+    C* b2 = b1 + fft_ps(M);
     if (row >= rows) return;                              // whole warp
     const int N = 2 * M;
     const int j = (int)(row % g.ny), k = (int)(row / g.ny);
@@ -1244,34 +1259,34 @@ __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restr
                 T dv = (ucc - ul) * idx;
                 dv += (vc[t] - vm[t]) * idy;
                 if (THREE) dv += (wc[t] - wm[t]) * idz;
-                d[XF ? ((x & 1) ? N - 1 - (x >> 1) : (x >> 1)) : x] = dv;
+                d[pzr<PAD>(XF ? ((x & 1) ? N - 1 - (x >> 1) : (x >> 1)) : x)] = dv;
             }
         }
     }
     __syncwarp();
-    const C* Z = warp_fft_any<-1, C>(pl, reinterpret_cast<const C*>(d), b0, b1, tab);
+    const C* Z = warp_fft_any<-1, C, false, PAD>(pl, reinterpret_cast<const C*>(d), b0, b1, tab);
     if (!XF) {
-        rfft_post<C>(M, Z, out + row * (M + 1), tab + M);
+        rfft_post<C, PAD>(M, Z, out + row * (M + 1), tab + M);
         return;
     }
     // DCT twiddle as in k_dct_rows
     C* V = (Z == b0) ? b1 : b0;
     const C* twN = tab + M;
     for (int kk = lane; kk < M; kk += 32) {
-        const C zk = Z[kk];
-        const C zc = cconj(Z[kk == 0 ? 0 : M - kk]);
+        const C zk = Z[pz<PAD>(kk)];
+        const C zc = cconj(Z[pz<PAD>(kk == 0 ? 0 : M - kk)]);
         const C e = C{(zk.x + zc.x) * (T)0.5, (zk.y + zc.y) * (T)0.5};
         const C dd = C{(zk.x - zc.x) * (T)0.5, (zk.y - zc.y) * (T)0.5};
-        V[kk] = cadd(e, cmul(twN[kk], C{dd.y, -dd.x}));
+        V[pz<PAD>(kk)] = cadd(e, cmul(twN[kk], C{dd.y, -dd.x}));
     }
     const C z0 = Z[0];
     __syncwarp();
     T* xr = xout + row * N;
     for (int kk = lane; kk < N; kk += 32) {
         C vk;
-        if (kk < M) vk = V[kk];
+        if (kk < M) vk = V[pz<PAD>(kk)];
         else if (kk == M) vk = C{z0.x - z0.y, (T)0};
-        else { vk = V[N - kk]; vk.y = -vk.y; }
+        else { vk = V[pz<PAD>(N - kk)]; vk.y = -vk.y; }
         xr[kk] = tw[2 * kk] * vk.x + tw[2 * kk + 1] * vk.y;
     }
 }
@@ -1288,32 +1303,32 @@ __global__ void __launch_bounds__(256) k_dct_rows(FftPlan pl, long long rows, T*
     const int M = pl.M, N = 2 * pl.M;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + wq;
-    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * (3 * M + 2);
-    C* b1 = b0 + M;
-    C* b2 = b1 + M;                                       // M + 2 values
+    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * 3 * fft_ps(M);
+    C* b1 = b0 + fft_ps(M);
+    C* b2 = b1 + fft_ps(M);                               // M + 2 values
     if (row >= rows) return;
     T* xr = x + row * N;
     T* v = reinterpret_cast<T*>(b2);
-    for (int n = lane; n < N; n += 32) v[(n & 1) ? N - 1 - (n >> 1) : (n >> 1)] = xr[n];
+    for (int n = lane; n < N; n += 32) v[pzr((n & 1) ? N - 1 - (n >> 1) : (n >> 1))] = xr[n];
     __syncwarp();
     const C* Z = warp_fft_any<-1, C>(pl, reinterpret_cast<const C*>(v), b0, b1, tab);
     // V_k, k = 0..M, into the other buffer (the one Z is not in), then the twiddle
     C* V = (Z == b0) ? b1 : b0;
     const C* twN = tab + M;
-    for (int k = lane; k <= M && k < M; k += 32) {
-        const C zk = Z[k];
-        const C zc = cconj(Z[k == 0 ? 0 : M - k]);
+    for (int k = lane; k < M; k += 32) {
+        const C zk = Z[pz(k)];
+        const C zc = cconj(Z[pz(k == 0 ? 0 : M - k)]);
         const C e = C{(zk.x + zc.x) * (T)0.5, (zk.y + zc.y) * (T)0.5};
         const C d = C{(zk.x - zc.x) * (T)0.5, (zk.y - zc.y) * (T)0.5};
-        V[k] = cadd(e, cmul(twN[k], C{d.y, -d.x}));
+        V[pz(k)] = cadd(e, cmul(twN[k], C{d.y, -d.x}));
     }
     const C z0 = Z[0];                                    // V_M = Re Z_0 - Im Z_0 (real)
     __syncwarp();
     for (int k = lane; k < N; k += 32) {
         C vk;
-        if (k < M) vk = V[k];
+        if (k < M) vk = V[pz(k)];
         else if (k == M) vk = C{z0.x - z0.y, (T)0};
-        else { vk = V[N - k]; vk.y = -vk.y; }
+        else { vk = V[pz(N - k)]; vk.y = -vk.y; }
         xr[k] = tw[2 * k] * vk.x + tw[2 * k + 1] * vk.y;
     }
 }
@@ -1327,33 +1342,33 @@ __global__ void __launch_bounds__(256) k_idct_rows(FftPlan pl, long long rows, T
     const int M = pl.M, N = 2 * pl.M;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + wq;
-    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * (3 * M + 2);
-    C* b1 = b0 + M;
-    C* b2 = b1 + M;                                       // V_0..V_M
+    C* b0 = reinterpret_cast<C*>(fft_smem) + (size_t)wq * 3 * fft_ps(M);
+    C* b1 = b0 + fft_ps(M);
+    C* b2 = b1 + fft_ps(M);                               // V_0..V_M
     if (row >= rows) return;
     T* xr = x + row * N;
     for (int k = lane; k <= M; k += 32) {
         const T a = xr[k];
         const T b = k == 0 ? T(0) : xr[N - k];
         const T c = tw[2 * k], sn = tw[2 * k + 1];
-        b2[k] = C{c * a + sn * b, sn * a - c * b};
+        b2[pz(k)] = C{c * a + sn * b, sn * a - c * b};
     }
     __syncwarp();
     // the pre-processing of the inverse real transform, into b0
     const C* twN = tab + M;
     for (int k = lane; k < M; k += 32) {
-        const C xk = b2[k];
-        const C xc = cconj(b2[M - k]);
+        const C xk = b2[pz(k)];
+        const C xc = cconj(b2[pz(M - k)]);
         const C e = cadd(xk, xc);
         const C d = cmul(csub(xk, xc), cconj(twN[k]));
-        b0[k] = cadd(e, C{-d.y, d.x});
+        b0[pz(k)] = cadd(e, C{-d.y, d.x});
     }
     __syncwarp();
     // the transform reads b0 and alternates between b1 and b2 (V is no longer needed)
     const C* z = warp_fft_any<+1, C>(pl, b0, b1, b2, tab);
     const T* v = reinterpret_cast<const T*>(z);
     __syncwarp();
-    for (int n = lane; n < N; n += 32) xr[n] = v[(n & 1) ? N - 1 - (n >> 1) : (n >> 1)];
+    for (int n = lane; n < N; n += 32) xr[n] = v[pzr((n & 1) ? N - 1 - (n >> 1) : (n >> 1))];
 }
 
 template <typename T>
@@ -1373,9 +1388,9 @@ __global__ void k_fft_tables(int M, T* __restrict__ tab) {
     }
 }
 
-// rows per block and shared bytes of the row kernels (three buffers of M per warp)
+// rows per block of the row kernels (three padded row buffers per warp)
 inline int fft_rows_per_block(int M, size_t csz) {
-    const size_t per = 3 * (size_t)M * csz;
+    const size_t per = 3 * (size_t)fft_ps(M) * csz;
     int r = (int)(48 * 1024 / per);
     return r < 1 ? 1 : (r > 8 ? 8 : r);
 }
@@ -1392,7 +1407,7 @@ ibm_status own_rfft(ibm_solver* h, const void* in, void* out, bool inverse) {
     for (int s = 0; s < 16; ++s) pl.rad[s] = h->fft_rad[s];
     const long long rows = (long long)g.ny * g.nz;
     const int rpb = fft_rows_per_block(pl.M, sizeof(C));
-    const size_t smem = 3 * (size_t)pl.M * sizeof(C) * rpb;
+    const size_t smem = 3 * (size_t)fft_ps(pl.M) * sizeof(C) * rpb;
     const int nb = (int)((rows + rpb - 1) / rpb);
     if (inverse)
         k_irfft_rows<C><<<nb, 32 * rpb, smem, h->stream>>>(pl, rows, (const C*)in, (C*)out, (const C*)h->fftab);
@@ -1410,8 +1425,8 @@ void dct_rows(ibm_solver* h, T* x, bool inverse) {
     pl.nrad = h->fft_nrad;
     for (int q = 0; q < 16; ++q) pl.rad[q] = h->fft_rad[q];
     const long long rows = (long long)g.ny * g.nz;
-    const int rpb = fft_rows_per_block(pl.M + 1, sizeof(C));
-    const size_t smem = (3 * (size_t)pl.M + 2) * sizeof(C) * rpb;
+    const int rpb = fft_rows_per_block(pl.M, sizeof(C));
+    const size_t smem = 3 * (size_t)fft_ps(pl.M) * sizeof(C) * rpb;
     const int nb = (int)((rows + rpb - 1) / rpb);
     if (inverse)
         k_idct_rows<T, C><<<nb, 32 * rpb, smem, h->stream>>>(pl, rows, x, (const C*)h->fftab, (const T*)h->twid);
@@ -1952,8 +1967,8 @@ ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const 
         pl.nrad = h->fft_nrad;
         for (int q = 0; q < 16; ++q) pl.rad[q] = h->fft_rad[q];
         const long long rows = (long long)g.ny * g.nz;
-        const int rpb = fft_rows_per_block(pl.M + 1, sizeof(C));
-        const size_t smem = (3 * (size_t)pl.M + 2) * sizeof(C) * rpb;
+        const int rpb = fft_rows_per_block(pl.M, sizeof(C));
+        const size_t smem = 3 * (size_t)fft_ps(pl.M) * sizeof(C) * rpb;
         const int nb = (int)((rows + rpb - 1) / rpb);
         C* out = (C*)h->spec;
         const C* tab = (const C*)h->fftab;
@@ -2420,7 +2435,7 @@ ibm_status poisson_prepare(ibm_solver* h) {
         while (m % 3 == 0 && nr < 16) { rad[nr++] = 3; m /= 3; }
         while (m % 5 == 0 && nr < 16) { rad[nr++] = 5; m /= 5; }
         const size_t csz = 2 * h->esz;
-        const bool ok = h->gp.nx % 2 == 0 && M >= 2 && m == 1 && 3 * (size_t)M * csz <= 48 * 1024;
+        const bool ok = h->gp.nx % 2 == 0 && M >= 2 && m == 1 && 3 * (size_t)fft_ps(M) * csz <= 48 * 1024;
         // automatic: where the rows have a factor 3 or 5 (384 reals: 0.073 against cuFFT's 0.101 ms
         // per pass on 384 x 256 x 256); cuFFT is faster on power-of-two rows (512: 0.56 against 0.53)
         const bool pow2 = (M & (M - 1)) == 0;
