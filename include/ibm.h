@@ -305,9 +305,12 @@ ibm_status ibm_get_tiles(ibm_solver* h, int* kz_momentum, int* kz_march, int* tm
 ibm_status ibm_set_momentum_tma(ibm_solver* h, int enable);
 /* The library's own real FFT of the x rows (a warp per row, self-sorting mixed-radix FFT in
  * shared memory) against cuFFT's R2C / C2R.  It can run where nx = 2M with M a product of 2, 3
- * and 5 (M <= 2048 in FP32, 1024 in FP64).  mode 0: never; 1: wherever it can; 2 (the default):
- * where M has a factor 3 or 5 (measured faster than cuFFT there, slower on powers of two).
- * *own reports whether it runs (may be NULL).  Both compute the same transform. */
+ * and 5 (M <= 1920 in FP32, 960 in FP64).  mode 0: never; 1: wherever it can; 2 (the default):
+ * on a periodic x where M has a factor 3 or 5 (measured faster than cuFFT there, slower on
+ * powers of two), on an inflow/outflow x wherever it can (the DCT of a row in one pass).  Where
+ * it runs, the divergence is computed inside the forward row transform (except under the masked
+ * projection).  *own reports whether it runs on this grid (may be NULL).  Both paths compute
+ * the same transform. */
 ibm_status ibm_set_own_fft(ibm_solver* h, int mode, int* own);
 
 /* Batched stepping of many resident solves (continuous batching for serving

@@ -786,7 +786,7 @@ ibm_status ibm_set_own_fft(ibm_solver* h, int mode, int* own) {
     drop_graph(h);
     h->own_fft_mode = mode;
     st = poisson_prepare(h);
-    if (own) *own = h->own_fft ? 1 : 0;
+    if (own) *own = (h->own_fft || h->dct_rows) ? 1 : 0;
     return st;
 }
 

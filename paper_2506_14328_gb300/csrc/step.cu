@@ -2442,8 +2442,7 @@ ibm_status poisson_prepare(ibm_solver* h) {
         h->own_fft = ok && (h->own_fft_mode == 1 || (h->own_fft_mode == 2 && !pow2));
         // the DCT rows of an inflow/outflow x: fused whenever the own FFT can run (the fusion saves
         // two passes over the field, which outweighs cuFFT's edge on power-of-two rows)
-        h->dct_rows = ok && !h->gp.xper && h->own_fft_mode != 0 &&
-                      (3 * (size_t)M + 2) * csz <= 48 * 1024;
+        h->dct_rows = ok && !h->gp.xper && h->own_fft_mode != 0;
         h->fft_nrad = ok ? nr : 0;
         for (int q = 0; q < 16; ++q) h->fft_rad[q] = (ok && q < nr) ? rad[q] : 0;
         if (ok) {
