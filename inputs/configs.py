@@ -19,6 +19,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field, replace
 import math
+import numpy as np
 
 BC_PERIODIC, BC_NOSLIP, BC_FREESLIP, BC_INFLOW, BC_OUTFLOW = 0, 1, 2, 3, 4
 GEOM_NONE, GEOM_PLANES, GEOM_CYLINDER, GEOM_SPHERE, GEOM_SINE_WALL, GEOM_TUBES, GEOM_SAMPLED = range(7)
@@ -48,6 +49,7 @@ class Case:
     projection: str = "fullbox"       # "fullbox" (the unmodified projection) or "masked" (internal faces only)
     g_amp: tuple = (0.0, 0.0, 0.0)    # time-periodic forcing g + g_amp sin(2 pi g_freq t)
     g_freq: float = 0.0
+    y_faces: tuple = ()        # stretched wall-normal grid: the ny + 1 face heights (empty: uniform)
     precision: str = "fp64"    # "fp64" or "fp32" (FP32 momentum, FP64 tridiagonal/reductions)
     steps: int = 1
     init: dict = field(default_factory=lambda: {"kind": "zero"})
@@ -75,6 +77,15 @@ def channel_c1(precision: str = "fp64", steps: int = 2000) -> Case:
                 bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), geom_kind=GEOM_PLANES,
                 geom_params=(0.137, 0.861), nu=nu, dt=0.008, g=(2.0 * nu / h ** 2, 0.0, 0.0),
                 precision=precision, steps=steps, init={"kind": "zero"})
+
+
+def tanh_faces(ny: int, y0: float, L: float, beta: float) -> tuple:
+    """ny + 1 face heights on [y0, y0 + L] clustered toward both ends by a tanh map of
+    strength beta (the usual wall-normal stretching of channel simulations)."""
+    eta = np.arange(ny + 1) / ny
+    y = y0 + 0.5 * L * (1.0 + np.tanh(beta * (2.0 * eta - 1.0)) / np.tanh(beta))
+    y[0], y[-1] = y0, y0 + L
+    return tuple(float(v) for v in y)
 
 
 def couette_case(nx: int = 16, ny: int = 24, a: float = 0.113, b: float = 0.871,

@@ -17,6 +17,10 @@ Every floating-point computation is FP64 numpy, in the order the formulas are
 written, with no blocking or fusion.  Where the paper is silent the reading
 taken is stated next to the code and listed in the design notes.
 
+A stretched wall-normal grid (face heights given) is supported by the grid, the operators,
+the projection, the weights and the steady solver (readings in the design notes, pins in
+tests/test_oracle_stretched.py); the force accounting stays uniform-grid only.
+
 Parity status: every function here is pinned by a `-m "not gpu"` test against
 a closed form, a value printed in the paper, an invariant or a brute-force
 solve (tests/test_oracle_*.py).  No function is "parity unpinned".

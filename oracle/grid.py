@@ -52,13 +52,56 @@ class Grid:
             raise NotImplementedError("y box faces must be no-slip or free-slip walls")
         if self.n[1] < 2:
             raise ValueError("ny >= 2")
+        # stretched wall-normal grid (y): the ny + 1 face heights; cell centres midway
+        # between faces, v on the faces (its index j on face j + 1)
+        yf = tuple(getattr(case, "y_faces", ()))
+        self.stretched = len(yf) > 0
+        if self.stretched:
+            yf = np.asarray(yf, dtype=np.float64)
+            ny = self.n[1]
+            if yf.shape != (ny + 1,) or np.any(np.diff(yf) <= 0.0):
+                raise ValueError("y_faces: ny + 1 increasing heights")
+            if abs(yf[0] - self.origin[1]) > 1e-12 * self.L[1] or \
+                    abs(yf[-1] - self.origin[1] - self.L[1]) > 1e-12 * self.L[1]:
+                raise ValueError("y_faces must span the box")
+            self.yf = yf
+            self.dyc = np.diff(yf)                       # cell heights
+            self.yc = 0.5 * (yf[:-1] + yf[1:])           # cell centres
+            # distance from centre j to centre j + 1; past the walls the mirror ghost of the
+            # first / last centre, at its own height from the wall on the other side
+            yc_ext = np.concatenate(([2 * yf[0] - self.yc[0]], self.yc, [2 * yf[-1] - self.yc[-1]]))
+            self.hc = np.diff(yc_ext)                    # ny + 1 values: hc[j] spans centres j-1 .. j
 
     def periodic(self, d: int) -> bool:
         return self.bc_lo[d] == BC_PERIODIC
 
     def axis_coords(self, d: int, offset: float) -> np.ndarray:
-        """origin_d + (index + offset) * Delta_d for every index along d."""
+        """origin_d + (index + offset) * Delta_d for every index along d (offset 0.5: cell
+        centres, 1.0: the +d faces); on a stretched y the centres and faces given."""
+        if d == 1 and self.stretched:
+            return self.yc.copy() if offset == 0.5 else self.yf[1:].copy()
         return self.origin[d] + (np.arange(self.n[d]) + offset) * self.d[d]
+
+    # ---- stretched y: spacings at every point, shaped (1, ny, 1) -------------------------
+    def ycol(self, a) -> np.ndarray:
+        return np.asarray(a, dtype=np.float64).reshape(1, self.n[1], 1)
+
+    def y_spacing(self, c: int):
+        """(h_minus, h_plus): distances from each point of component c to its y neighbours
+        below and above (centres for u, w, p; faces for v).  Past a wall the mirror ghost of a
+        centre; v's last index is the wall face itself (never solved, given its cell height)."""
+        if c == 1:
+            up = np.concatenate((self.dyc[1:], self.dyc[-1:]))
+            return self.ycol(self.dyc), self.ycol(up)
+        return self.ycol(self.hc[:-1]), self.ycol(self.hc[1:])
+
+    def cell_heights(self) -> np.ndarray:
+        return self.ycol(self.dyc)
+
+    def face_heights(self) -> np.ndarray:
+        """Distance between the centres on either side of each v face (the v control height);
+        the last entry (the wall face) repeats the last cell height."""
+        return self.ycol(np.concatenate((self.hc[1:-1], self.dyc[-1:])))
 
     def coords(self, c: int):
         """Broadcastable (x, y, z) coordinates of the points of component c.
@@ -82,7 +125,16 @@ class Grid:
             m[tuple(idx)] = True
         return m
 
+    def cell_volumes(self) -> np.ndarray:
+        """Volume (area in 2D) of every cell, broadcastable to the field shape."""
+        if not self.stretched:
+            return np.full((1, 1, 1), self.cell_volume())
+        v = self.d[0] * self.cell_heights()
+        return v * self.d[2] if self.ndim == 3 else v
+
     def cell_volume(self) -> float:
+        if self.stretched:
+            raise ValueError("a stretched grid has no single cell volume (cell_volumes)")
         v = self.d[0] * self.d[1]
         if self.ndim == 3:
             v *= self.d[2]

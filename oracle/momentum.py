@@ -95,6 +95,8 @@ def nb(q, grid, c: int, d: int, s: int, lo_normal=None):
 
 def rhs(grid, cls, fields, nu: float, g, src):
     """N_c at every point (meaningful at internal points), FP64."""
+    if grid.stretched:
+        return rhs_stretched(grid, cls, fields, nu, g, src)
     U, V, W = masked(grid, cls, fields)
     dx, dy, dz = grid.d
     three = grid.ndim == 3
@@ -154,6 +156,96 @@ def rhs(grid, cls, fields, nu: float, g, src):
     return out
 
 
+def d2_y(q, qn, qs, hm, hp):
+    """The three-point second difference along y on unevenly spaced points: with hm, hp the
+    distances to the neighbours below and above, d(+1) = 2/(hp (hm + hp)),
+    d(-1) = 2/(hm (hm + hp)), d(0) = -2/(hm hp) (exact on quadratics)."""
+    return 2.0 * qn / (hp * (hm + hp)) + 2.0 * qs / (hm * (hm + hp)) - 2.0 * q / (hm * hp)
+
+
+def y_face_value(q, qn, dyc, dyc_up):
+    """A cell-centred quantity (q at this centre, qn at the centre above) linearly
+    interpolated to the face between them, which lies dyc/2 above this centre and
+    dyc_up/2 below the other."""
+    return (dyc_up * q + dyc * qn) / (dyc + dyc_up)
+
+
+def rhs_stretched(grid, cls, fields, nu: float, g, src):
+    """N_c on a stretched y (readings of the paper's stretched wall-normal grids, Sec. 4.2,
+    which it does not write out): x and z as on the uniform grid; along y
+      * the Laplacian is the three-point second difference on the uneven points (d2_y);
+      * the convective fluxes stay in flux form: a cell-centred quantity (u, w) is carried
+        to a v face by linear interpolation (y_face_value) and the flux difference is
+        divided by the height of the point's own control volume (the cell height for u and
+        w, the distance between the centres on either side for v); v is carried to a
+        centre by the plain average (the centre lies midway between its faces)."""
+    U, V, W = masked(grid, cls, fields)
+    dx, _, dz = grid.d
+    three = grid.ndim == 3
+    uin = inflow_face(grid, cls) if grid.xflow else None
+    dyc = grid.cell_heights()
+    dyc_up = grid.ycol(np.concatenate((grid.dyc[1:], grid.dyc[-1:])))    # the cell above (mirror)
+    dyc_dn = grid.ycol(np.concatenate((grid.dyc[:1], grid.dyc[:-1])))    # the cell below (mirror)
+    hv = grid.face_heights()
+    hm_c, hp_c = grid.y_spacing(0)
+    hm_v, hp_v = grid.y_spacing(1)
+    out = []
+
+    # ---- u ----
+    uE, uW = nb(U, grid, 0, 0, +1), nb(U, grid, 0, 0, -1, uin)
+    uN, uS = nb(U, grid, 0, 1, +1), nb(U, grid, 0, 1, -1)
+    cx = (((U + uE) / 2) ** 2 - ((uW + U) / 2) ** 2) / dx
+    vN = (V + nb(V, grid, 1, 0, +1)) / 2                       # v on the top face at the u point's x
+    vS = (nb(V, grid, 1, 1, -1) + nb(nb(V, grid, 1, 0, +1), grid, 1, 1, -1)) / 2
+    cy = (vN * y_face_value(U, uN, dyc, dyc_up) - vS * y_face_value(uS, U, dyc_dn, dyc)) / dyc
+    lap = (uE - 2 * U + uW) / dx ** 2 + d2_y(U, uN, uS, hm_c, hp_c)
+    cz = 0.0
+    if three:
+        uT, uB = nb(U, grid, 0, 2, +1), nb(U, grid, 0, 2, -1)
+        wT = (W + nb(W, grid, 2, 0, +1)) / 2
+        wB = (nb(W, grid, 2, 2, -1) + nb(nb(W, grid, 2, 0, +1), grid, 2, 2, -1)) / 2
+        cz = (wT * ((U + uT) / 2) - wB * ((uB + U) / 2)) / dz
+        lap = lap + (uT - 2 * U + uB) / dz ** 2
+    out.append(-(cx + cy + cz) + nu * lap + g[0] + src[0])
+
+    # ---- v (on the face above its cell: between centres j and j + 1) ----
+    vE, vW = nb(V, grid, 1, 0, +1), nb(V, grid, 1, 0, -1)
+    vNn, vSs = nb(V, grid, 1, 1, +1), nb(V, grid, 1, 1, -1)
+    uEe = y_face_value(U, nb(U, grid, 0, 1, +1), dyc, dyc_up)            # u at this face, x = i + 1
+    uWl = nb(U, grid, 0, 0, -1, uin)
+    uWe = y_face_value(uWl, nb(uWl, grid, 0, 1, +1), dyc, dyc_up)
+    cx = (uEe * ((V + vE) / 2) - uWe * ((vW + V) / 2)) / dx
+    cy = (((V + vNn) / 2) ** 2 - ((vSs + V) / 2) ** 2) / hv
+    lap = (vE - 2 * V + vW) / dx ** 2 + d2_y(V, vNn, vSs, hm_v, hp_v)
+    cz = 0.0
+    if three:
+        vT, vB = nb(V, grid, 1, 2, +1), nb(V, grid, 1, 2, -1)
+        wTe = y_face_value(W, nb(W, grid, 2, 1, +1), dyc, dyc_up)
+        wBl = nb(W, grid, 2, 2, -1)
+        wBe = y_face_value(wBl, nb(wBl, grid, 2, 1, +1), dyc, dyc_up)
+        cz = (wTe * ((V + vT) / 2) - wBe * ((vB + V) / 2)) / dz
+        lap = lap + (vT - 2 * V + vB) / dz ** 2
+    out.append(-(cx + cy + cz) + nu * lap + g[1] + src[1])
+
+    # ---- w ----
+    if three:
+        wE, wW = nb(W, grid, 2, 0, +1), nb(W, grid, 2, 0, -1)
+        wN, wS = nb(W, grid, 2, 1, +1), nb(W, grid, 2, 1, -1)
+        wT, wB = nb(W, grid, 2, 2, +1), nb(W, grid, 2, 2, -1)
+        uEe = (U + nb(U, grid, 0, 2, +1)) / 2
+        uWe = (nb(U, grid, 0, 0, -1, uin) + nb(nb(U, grid, 0, 0, -1, uin), grid, 0, 2, +1)) / 2
+        cx = (uEe * ((W + wE) / 2) - uWe * ((wW + W) / 2)) / dx
+        vNe = (V + nb(V, grid, 1, 2, +1)) / 2
+        vSe = (nb(V, grid, 1, 1, -1) + nb(nb(V, grid, 1, 1, -1), grid, 1, 2, +1)) / 2
+        cy = (vNe * y_face_value(W, wN, dyc, dyc_up) - vSe * y_face_value(wS, W, dyc_dn, dyc)) / dyc
+        cz = (((W + wT) / 2) ** 2 - ((wB + W) / 2) ** 2) / dz
+        lap = (wE - 2 * W + wW) / dx ** 2 + d2_y(W, wN, wS, hm_c, hp_c) + (wT - 2 * W + wB) / dz ** 2
+        out.append(-(cx + cy + cz) + nu * lap + g[2] + src[2])
+    else:
+        out.append(np.zeros(grid.shape))
+    return out
+
+
 def pressure_gradient(grid, p):
     """(G p)_c on the faces; zero on wall faces (Gp is not used there)."""
     out = []
@@ -172,7 +264,10 @@ def pressure_gradient(grid, p):
             a[AX[c]] = slice(1, n)
             b[AX[c]] = slice(0, n - 1)
             o[AX[c]] = slice(0, n - 1)
-            gph[tuple(o)] = (p[tuple(a)] - p[tuple(b)]) / grid.d[c]
+            if c == 1 and grid.stretched:
+                gph[tuple(o)] = (p[tuple(a)] - p[tuple(b)]) / grid.face_heights()[:, :-1, :]
+            else:
+                gph[tuple(o)] = (p[tuple(a)] - p[tuple(b)]) / grid.d[c]
             out.append(gph)
     return out
 

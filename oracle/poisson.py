@@ -55,7 +55,7 @@ def divergence(grid, vel, inflow_face=None):
             a[AX[d]] = slice(1, n)
             b[AX[d]] = slice(0, n - 1)
             qm[tuple(a)] = q[tuple(b)]
-        out = out + (q - qm) / grid.d[d]
+        out = out + (q - qm) / (grid.cell_heights() if (d == 1 and grid.stretched) else grid.d[d])
     return out
 
 
@@ -75,7 +75,10 @@ def gradient(grid, phi):
             b = [slice(None)] * 3
             a[AX[c]] = slice(1, n)
             b[AX[c]] = slice(0, n - 1)
-            g[tuple(b)] = (phi[tuple(a)] - phi[tuple(b)]) / grid.d[c]
+            if c == 1 and grid.stretched:     # between the centres on either side of each face
+                g[tuple(b)] = (phi[tuple(a)] - phi[tuple(b)]) / grid.face_heights()[:, :-1, :]
+            else:
+                g[tuple(b)] = (phi[tuple(a)] - phi[tuple(b)]) / grid.d[c]
             out.append(g)
     return out
 
@@ -133,14 +136,23 @@ def solve_spectral(grid, rhs):
         K = K + np.zeros((nz, 1))
     # y-systems: (phi_{j-1} - 2 phi_j + phi_{j+1})/dy^2 - K phi_j = r_j, Neumann ends
     d = np.moveaxis(rh, 1, 0)                          # (y, kz, kx)
-    inv = 1.0 / dy ** 2
-    a = np.full(ny, inv)
-    c = np.full(ny, inv)
-    a[0] = 0.0
-    c[-1] = 0.0
-    diag = np.full(ny, -2.0 * inv)
-    diag[0] = -inv
-    diag[-1] = -inv
+    if grid.stretched:
+        # D G along y: (phi_{j+1} - phi_j)/h_{j+1/2} - (phi_j - phi_{j-1})/h_{j-1/2}, over the
+        # cell height; h the distance between the centres on either side of a face
+        a = 1.0 / (grid.dyc * grid.hc[:-1])
+        c = 1.0 / (grid.dyc * grid.hc[1:])
+        a[0] = 0.0
+        c[-1] = 0.0
+        diag = -(a + c)
+    else:
+        inv = 1.0 / dy ** 2
+        a = np.full(ny, inv)
+        c = np.full(ny, inv)
+        a[0] = 0.0
+        c[-1] = 0.0
+        diag = np.full(ny, -2.0 * inv)
+        diag[0] = -inv
+        diag[-1] = -inv
     b = diag[:, None, None] - K[None, :, :]
     zero = (K == 0.0)
     b_safe = np.where(zero[None], -1.0, b)            # placeholder; the zero mode is solved below
@@ -175,6 +187,9 @@ def operator_matrix(grid):
         ax = AX[d]
         n = grid.n[d]
         for s in (+1, -1):
+            if d == 1 and grid.stretched:     # per cell: 1 / (cell height x centre distance)
+                h = grid.hc[1:] if s > 0 else grid.hc[:-1]
+                inv = np.broadcast_to(grid.ycol(1.0 / (grid.dyc * h)), grid.shape)
             nbr = np.roll(idx, -s, axis=ax)
             valid = np.ones(grid.shape, dtype=bool)
             if not grid.periodic(d):
@@ -187,9 +202,10 @@ def operator_matrix(grid):
                 continue
             r = idx[valid]
             q = nbr[valid]
+            w = inv[valid] if isinstance(inv, np.ndarray) else np.full(r.size, inv)
             rows += [r, r]
             cols += [q, r]
-            vals += [np.full(r.size, inv), np.full(r.size, -inv)]
+            vals += [w, -w]
     rows = np.concatenate(rows)
     cols = np.concatenate(cols)
     vals = np.concatenate(vals)
@@ -245,6 +261,8 @@ def solve_masked(grid, cls, rhs):
     3D grids), and each group is then shifted to zero mean (the right-hand side sums to zero
     over a group, so the fixed cell's equation holds as well)."""
     from scipy.sparse.csgraph import connected_components
+    if grid.stretched:
+        raise NotImplementedError("the masked projection on a stretched grid")
     A = masked_operator_matrix(grid, cls)
     inside = np.flatnonzero(cls.p_internal.ravel())
     Ai = A[inside][:, inside].tocsr()

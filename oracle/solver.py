@@ -101,8 +101,9 @@ class OracleSolver:
         # explicit R does not explain) and the right-hand side's faces toward the solid
         R = [self.dt * (RK3_A[k] * N[c] + RK3_B[k] * self.Nprev[c]) - RK3_C[k] * self.dt * gp[c] for c in range(3)]
         I = [np.where(cls.internal[c], ustar[c] - um[c] - R[c], 0.0) for c in range(3)]
-        BN = body_terms(g, cls, self.u, self.w.src, self.nu,
-                        self.w.lam if self.bmode == B_EXPLICIT else None)
+        # (the force accounting is written for the uniform grid; a stretched one reports NaN)
+        BN = None if g.stretched else body_terms(g, cls, self.u, self.w.src, self.nu,
+                                                 self.w.lam if self.bmode == B_EXPLICIT else None)
         if g.xflow:
             # the outflow face: convective condition, then the flux balance
             ub, Nb = outflow_update(g, cls, self.u, self.Nprev[0][..., -1:], k, self.dt, RK3_A, RK3_B)
@@ -114,9 +115,14 @@ class OracleSolver:
             ckdt = RK3_C[k] * self.dt
             x = self.w.lam[0] * ckdt if self.bmode != B_EXPLICIT else np.zeros(g.shape)
             beta = np.where(cls.internal[0], 1.0 / (B_of_x(x, self.bmode) + x), 0.0)
-            dV = g.cell_volume()
-            Q0 = np.sum(np.where(cls.internal[0], ustar[0], 0.0)) * dV
-            S = np.sum(ckdt * beta) * dV
+            if g.stretched:
+                dV = g.cell_volumes()
+                Q0 = np.sum(np.where(cls.internal[0], ustar[0], 0.0) * dV)
+                S = np.sum(ckdt * beta * dV)
+            else:
+                dV = g.cell_volume()
+                Q0 = np.sum(np.where(cls.internal[0], ustar[0], 0.0)) * dV
+                S = np.sum(ckdt * beta) * dV
             Pi = (self.target_flux - Q0) / S
             ustar[0] = ustar[0] + Pi * ckdt * beta
             self.last_pi = Pi
@@ -124,6 +130,9 @@ class OracleSolver:
             self.u = ustar
             return
         self._project(ustar, RK3_C[k] * self.dt, update_p=True)
+        if g.stretched:
+            self.step_impulse = np.full(3, np.nan)
+            return
         self.step_impulse = self.step_impulse + stage_impulse(g, cls, I, BN, self.BN_prev, self.p, k, self.dt,
                                                               RK3_A, RK3_B, RK3_C)
         self.BN_prev = BN
@@ -174,16 +183,24 @@ class OracleSolver:
     def diagnostics(self) -> dict:
         g, cls = self.grid, self.cls
         div = divergence(g, self.u, inflow_face(g, cls) if g.xflow else None)
-        dV = g.cell_volume()
+        dV = g.cell_volumes() if g.stretched else g.cell_volume()
         out = {"div_l2": float(np.sqrt(np.mean(div ** 2))), "div_linf": float(np.max(np.abs(div)))}
         cfl = 0.0
         flux = [0.0, 0.0, 0.0]
         ke = 0.0
         for c in range(g.ncomp):
             ui = np.where(cls.internal[c], self.u[c], 0.0)
-            cfl += float(np.max(np.abs(ui))) / g.d[c]
-            flux[c] = float(np.sum(ui)) * dV
-            ke += 0.5 * float(np.sum(ui * ui)) * dV
+            if g.stretched:
+                # v moves between the cells on either side of its face: the smaller of the two
+                sp_c = np.minimum(g.cell_heights(), g.ycol(np.concatenate((g.dyc[1:], g.dyc[-1:])))) \
+                    if c == 1 else g.d[c]
+                cfl += float(np.max(np.abs(ui) / sp_c))
+                flux[c] = float(np.sum(ui * dV))
+                ke += 0.5 * float(np.sum(ui * ui * dV))
+            else:
+                cfl += float(np.max(np.abs(ui))) / g.d[c]
+                flux[c] = float(np.sum(ui)) * dV
+                ke += 0.5 * float(np.sum(ui * ui)) * dV
         out["cfl"] = cfl * self.dt
         out["flux"] = flux
         out["ke"] = ke

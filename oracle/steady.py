@@ -39,10 +39,15 @@ def laplacian_matrix(grid, cls, c: int):
         n = grid.n[d]
         pos = np.arange(n).reshape([n if a == ax else 1 for a in range(3)])
         for s in (+1, -1):
+            if d == 1 and grid.stretched:
+                # uneven three-point second difference: arm s weighs 2 / (Delta_s (Delta_- + Delta_+))
+                hm, hp = grid.y_spacing(c)
+                inv = np.broadcast_to(2.0 / ((hp if s > 0 else hm) * (hm + hp)), grid.shape)
+            w = (lambda sel: inv[sel]) if isinstance(inv, np.ndarray) else (lambda sel: np.full(int(sel.sum()), inv))
             r = ids[internal]
             rows.append(r)
             cols.append(r)
-            vals.append(np.full(r.size, -inv))
+            vals.append(-w(internal))
             q_ids = np.roll(ids, -s, axis=ax)
             q_int = np.roll(internal, -s, axis=ax)
             if grid.periodic(d):
@@ -52,13 +57,13 @@ def laplacian_matrix(grid, cls, c: int):
             take = internal & inbox & q_int
             rows.append(ids[take])
             cols.append(q_ids[take])
-            vals.append(np.full(int(take.sum()), inv))
+            vals.append(w(take))
             if not grid.periodic(d) and c != d:
                 out = internal & ~inbox
                 sign = grid.wall_sign("hi" if s > 0 else "lo")
                 rows.append(ids[out])
                 cols.append(ids[out])
-                vals.append(np.full(int(out.sum()), sign * inv))
+                vals.append(sign * w(out))
     A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
     sel = np.flatnonzero(internal.ravel())
     return A[sel][:, sel], sel

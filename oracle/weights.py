@@ -82,13 +82,18 @@ def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm
             ext = cls.external[c]
             phi = cls.phi[c]
             # pass 1: the crossed arms of every IBM point, in accumulation order
-            arms = []          # (m, P, d, s, Delta, phiP, phiQ)
+            arms = []          # (m, P, d, s, Delta, phiP, phiQ, Delta_- + Delta_+)
+            if grid.stretched:
+                ycs = grid.axis_coords(1, 1.0 if c == 1 else 0.5)
+                hm_y, hp_y = (a.ravel() for a in grid.y_spacing(c))
             for m, lin in enumerate(lst):
                 i = lin % nx
                 j = (lin // nx) % ny
                 k = lin // (nx * ny)
                 idx = [i, j, k]
                 P = [grid.origin[d] + (idx[d] + (1.0 if d == c else 0.5)) * grid.d[d] for d in range(3)]
+                if grid.stretched:
+                    P[1] = float(ycs[j])
                 for d in range(grid.ndim):
                     for s in (+1, -1):
                         q = list(idx)
@@ -100,7 +105,13 @@ def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm
                         qk = (q[2], q[1], q[0])
                         if not ext[qk]:
                             continue
-                        arms.append((m, P, d, s, grid.d[d], float(phi[k, j, i]), float(phi[qk])))
+                        if d == 1 and grid.stretched:
+                            Dd = float(hp_y[j] if s > 0 else hm_y[j])
+                            Dsum = float(hm_y[j] + hp_y[j])
+                        else:
+                            Dd = grid.d[d]
+                            Dsum = 2.0 * Dd
+                        arms.append((m, P, d, s, Dd, float(phi[k, j, i]), float(phi[qk]), Dsum))
             deltas = levelset.delta_many(np.array([a[1] for a in arms]).reshape(-1, 3),
                                          np.array([a[2] for a in arms], dtype=int),
                                          np.array([a[3] for a in arms], dtype=int),
@@ -110,10 +121,16 @@ def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm
             # pass 2: lambda and the source, summed arm by arm
             lam_p = np.zeros(len(lst))
             src_p = np.zeros(len(lst))
-            for (m, P, d, s, Dd, _, _), delta in zip(arms, deltas):
-                lam_p[m] += nu * (Dd - delta) / (delta * Dd * Dd)
+            for (m, P, d, s, Dd, _, _, Dsum), delta in zip(arms, deltas):
                 uw = wall_u[c] * levelset.wall_velocity_factor(d, s)
-                src_p[m] += nu * uw / (delta * Dd)
+                if d == 1 and grid.stretched:
+                    # d(s) = 2 / (Delta_s (Delta_- + Delta_+)) of the uneven three-point second
+                    # difference in place of 1 / Delta^2 (same extrapolation, same form)
+                    lam_p[m] += nu * 2.0 * (Dd - delta) / (delta * Dd * Dsum)
+                    src_p[m] += nu * uw * 2.0 / (delta * Dsum)
+                else:
+                    lam_p[m] += nu * (Dd - delta) / (delta * Dd * Dd)
+                    src_p[m] += nu * uw / (delta * Dd)
             for m, lin in enumerate(lst):
                 i = lin % nx
                 j = (lin // nx) % ny

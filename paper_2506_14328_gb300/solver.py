@@ -101,6 +101,8 @@ class Solver:
         """Build from any object with the attributes of a workload description.  A sampled
         geometry takes its samples through kw (samples=[phi_u, phi_v, phi_w]); a workload
         with projection 'masked' gets the masked projection."""
+        if len(getattr(case, "y_faces", ())):
+            raise NotImplementedError("stretched wall-normal grids are not in the CUDA library")
         s = cls(ndim=case.ndim, n=case.n, L=case.L, origin=case.origin, bc_lo=case.bc_lo, bc_hi=case.bc_hi,
                 precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,
                 nu=case.nu, dt=case.dt, g=case.g, bmode=case.bmode, flow_mode=case.flow_mode,
