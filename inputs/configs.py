@@ -50,6 +50,7 @@ class Case:
     g_amp: tuple = (0.0, 0.0, 0.0)    # time-periodic forcing g + g_amp sin(2 pi g_freq t)
     g_freq: float = 0.0
     y_faces: tuple = ()        # stretched wall-normal grid: the ny + 1 face heights (empty: uniform)
+    body_velocity: tuple = ()  # a translating cylinder or sphere: its velocity (empty: at rest)
     precision: str = "fp64"    # "fp64" or "fp32" (FP32 momentum, FP64 tridiagonal/reductions)
     steps: int = 1
     init: dict = field(default_factory=lambda: {"kind": "zero"})

@@ -19,7 +19,9 @@ taken is stated next to the code and listed in the design notes.
 
 A stretched wall-normal grid (face heights given) is supported by the grid, the operators,
 the projection, the weights and the steady solver (readings in the design notes, pins in
-tests/test_oracle_stretched.py); the force accounting stays uniform-grid only.
+tests/test_oracle_stretched.py); the force accounting stays uniform-grid only.  A translating
+cylinder or sphere (reading in solver.py, pins in tests/test_oracle_moving_body.py) is
+reclassified at every step.
 
 Parity status: every function here is pinned by a `-m "not gpu"` test against
 a closed form, a value printed in the paper, an invariant or a brute-force

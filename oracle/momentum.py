@@ -93,8 +93,12 @@ def nb(q, grid, c: int, d: int, s: int, lo_normal=None):
     return out
 
 
-def rhs(grid, cls, fields, nu: float, g, src):
-    """N_c at every point (meaningful at internal points), FP64."""
+def rhs(grid, cls, fields, nu: float, g, src, body_u=None):
+    """N_c at every point (meaningful at internal points), FP64.  body_u: the velocity of a
+    translating body, which the convective terms read at its (external) points; the
+    Laplacian still reads them as zero, its wall term being -lambda w + s (reading R24)."""
+    if body_u is not None:
+        return rhs_moving(grid, cls, fields, nu, g, src, body_u)
     if grid.stretched:
         return rhs_stretched(grid, cls, fields, nu, g, src)
     U, V, W = masked(grid, cls, fields)
@@ -154,6 +158,23 @@ def rhs(grid, cls, fields, nu: float, g, src):
     else:
         out.append(np.zeros(grid.shape))
     return out
+
+
+def rhs_moving(grid, cls, fields, nu: float, g, src, body_u):
+    """rhs with a translating body (uniform grid): convection of the field whose external
+    points hold the body velocity, plus nu times the Laplacian of the field whose external
+    points hold zero; each is the uniform rhs of its own field, so the split is
+    N = rhs(convection part, nu = 0) + (rhs(diffusion part) - its own convection)."""
+    from dataclasses import replace
+    conv_field = [np.where(cls.external[c], body_u[c], fields[c]) if c < grid.ncomp else fields[c]
+                  for c in range(3)]
+    # the body's points made readable for the convective call (they hold body_u now)
+    cls_b = replace(cls, internal=[cls.internal[c] | cls.external[c] for c in range(3)])
+    zero = [np.zeros(grid.shape)] * 3
+    Nc = rhs(grid, cls_b, conv_field, 0.0, (0.0, 0.0, 0.0), zero)    # -C(u with the body's velocity)
+    Nd = rhs(grid, cls, fields, nu, g, src)                          # -C(u masked) + nu L + g + s
+    Nd0 = rhs(grid, cls, fields, 0.0, (0.0, 0.0, 0.0), zero)         # -C(u masked)
+    return [Nc[c] + (Nd[c] - Nd0[c]) for c in range(3)]
 
 
 def d2_y(q, qn, qs, hm, hp):

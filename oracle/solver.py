@@ -18,13 +18,21 @@ raises u* there by Pi c_k Delta t / (B + x).  Pi is chosen so that the volume
 integral of u* over the internal u points equals the target:
   Pi = (Q_target - Q(u*_0)) / S_k,  S_k = sum_internal c_k Delta t / (B + x) Delta V.
 The projection keeps the box integral of u in a periodic x direction.
+
+A translating body (reading R24; the paper, Sec. 3.1 end: apply the IBM in the frame in which
+the body is at rest, i.e. subtract its velocity): a cylinder or sphere whose centre moves with
+the constant velocity U_b.  At the start of every step the level set is placed at the step's
+time, the points are classified again and the weights rebuilt with the wall velocity U_b (the
+source s of the moving-wall extrapolation); points that became fluid take U_b.  Within the step
+the body stays there.  The convective terms read the body's points as U_b, the Laplacian reads
+them as zero (its wall term is -lambda w + s), and u* on the body's points is U_b.
 """
 from __future__ import annotations
 
 import numpy as np
 
 from .grid import Grid
-from .geometry import LevelSet
+from .geometry import LevelSet, CYLINDER, SPHERE
 from .classify import classify
 from .weights import build_weights, B_of_x, RK3_A, RK3_B, RK3_C, RK3_T, B_EXPLICIT
 from .momentum import (rhs, stage_update, pressure_gradient, masked, inflow_face, outflow_update,
@@ -51,7 +59,15 @@ class OracleSolver:
         self.bmode = int(case.bmode)
         self.flow_mode = int(case.flow_mode)
         self.target_flux = float(case.target_flux)
-        self.w = build_weights(self.grid, self.levelset, self.cls, self.nu, case.wall_u, no_ibm=no_ibm)
+        self.body_u = tuple(float(v) for v in getattr(case, "body_velocity", ()))
+        self.moving = any(v != 0.0 for v in self.body_u)
+        self.no_ibm = no_ibm
+        if self.moving:
+            if case.geom_kind not in (CYLINDER, SPHERE) or self.grid.stretched:
+                raise NotImplementedError("a translating cylinder or sphere on a uniform grid")
+            self._place_body(0.0)
+        self.w = build_weights(self.grid, self.levelset, self.cls, self.nu,
+                               self.body_u if self.moving else case.wall_u, no_ibm=no_ibm)
         if self.grid.xflow and self.flow_mode == FLOW_CONST_FLUX:
             raise ValueError("a constant flow rate needs a periodic x direction")
         self.poisson = solve_spectral if poisson == "spectral" else solve_direct
@@ -74,6 +90,23 @@ class OracleSolver:
         self.force_steps = 0
 
     # ---- state --------------------------------------------------------------
+    def _place_body(self, t: float):
+        """Level set and classification with the body's centre moved by U_b t."""
+        p = list(self.case.geom_params)
+        for d in range(2 if self.case.geom_kind == CYLINDER else 3):
+            p[d] = p[d] + self.body_u[d] * t
+        self.levelset = LevelSet(self.case.geom_kind, tuple(p))
+        self.cls = classify(self.grid, self.levelset)
+
+    def _move_body(self):
+        """Start of a step: the body at t_n, weights again, fresh fluid points set to U_b."""
+        was = [a.copy() for a in self.cls.internal]
+        self._place_body(self.step_count * self.dt)
+        self.w = build_weights(self.grid, self.levelset, self.cls, self.nu, self.body_u, no_ibm=self.no_ibm)
+        for c in range(self.grid.ncomp):
+            fresh = self.cls.internal[c] & ~was[c]
+            self.u[c] = np.where(fresh, self.body_u[c], self.u[c])
+
     def set_state(self, u, v, w, p):
         self.u = [np.array(u, dtype=np.float64), np.array(v, dtype=np.float64),
                   np.array(w, dtype=np.float64)]
@@ -87,7 +120,7 @@ class OracleSolver:
         g, cls = self.grid, self.cls
         t = (self.step_count + RK3_T[k]) * self.dt
         gk = tuple(self.g[c] + self.g_amp[c] * np.sin(2.0 * np.pi * self.g_freq * t) for c in range(3))
-        N = rhs(g, cls, self.u, self.nu, gk, self.w.src)
+        N = rhs(g, cls, self.u, self.nu, gk, self.w.src, self.body_u if self.moving else None)
         gp = pressure_gradient(g, self.p)
         um = masked(g, cls, self.u)
         lam = self.w.lam
@@ -97,12 +130,15 @@ class OracleSolver:
             lam = [np.zeros(g.shape) for _ in range(3)]
         ustar = stage_update(g, cls, um, N, self.Nprev, gp, lam, k, self.dt,
                              self.bmode, RK3_A, RK3_B, RK3_C, B_of_x)
+        if self.moving:      # the body's points move with it
+            ustar = [np.where(cls.external[c], self.body_u[c], ustar[c]) if c < g.ncomp else ustar[c]
+                     for c in range(3)]
         # the body's share of the stage: the IBM division's part I of u* - u (what the
         # explicit R does not explain) and the right-hand side's faces toward the solid
         R = [self.dt * (RK3_A[k] * N[c] + RK3_B[k] * self.Nprev[c]) - RK3_C[k] * self.dt * gp[c] for c in range(3)]
         I = [np.where(cls.internal[c], ustar[c] - um[c] - R[c], 0.0) for c in range(3)]
         # (the force accounting is written for the uniform grid; a stretched one reports NaN)
-        BN = None if g.stretched else body_terms(g, cls, self.u, self.w.src, self.nu,
+        BN = None if (g.stretched or self.moving) else body_terms(g, cls, self.u, self.w.src, self.nu,
                                                  self.w.lam if self.bmode == B_EXPLICIT else None)
         if g.xflow:
             # the outflow face: convective condition, then the flux balance
@@ -130,7 +166,7 @@ class OracleSolver:
             self.u = ustar
             return
         self._project(ustar, RK3_C[k] * self.dt, update_p=True)
-        if g.stretched:
+        if g.stretched or self.moving:
             self.step_impulse = np.full(3, np.nan)
             return
         self.step_impulse = self.step_impulse + stage_impulse(g, cls, I, BN, self.BN_prev, self.p, k, self.dt,
@@ -155,6 +191,8 @@ class OracleSolver:
     # ---- public -------------------------------------------------------------
     def step(self, nsteps: int = 1):
         for _ in range(nsteps):
+            if self.moving:
+                self._move_body()
             self.step_impulse = np.zeros(3)
             for k in range(3):
                 self.substage(k)
@@ -175,6 +213,9 @@ class OracleSolver:
         """Initial-condition projection: zero the unreadable velocities, balance the outflow
         (inflow/outflow x), then project (p unchanged)."""
         um = masked(self.grid, self.cls, self.u)
+        if self.moving:      # a translating body's points hold its velocity
+            um = [np.where(self.cls.external[c], self.body_u[c], um[c]) if c < self.grid.ncomp else um[c]
+                  for c in range(3)]
         if self.grid.xflow:
             um[0] = um[0].copy()
             um[0][..., -1:] = outflow_balance(self.grid, self.cls, um[0][..., -1:])
