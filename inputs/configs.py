@@ -51,6 +51,7 @@ class Case:
     g_freq: float = 0.0
     y_faces: tuple = ()        # stretched wall-normal grid: the ny + 1 face heights (empty: uniform)
     body_velocity: tuple = ()  # a translating cylinder or sphere: its velocity (empty: at rest)
+    body_omega: float = 0.0    # a cylinder rotating about its own axis: the rate
     precision: str = "fp64"    # "fp64" or "fp32" (FP32 momentum, FP64 tridiagonal/reductions)
     steps: int = 1
     init: dict = field(default_factory=lambda: {"kind": "zero"})

@@ -26,6 +26,8 @@ time, the points are classified again and the weights rebuilt with the wall velo
 source s of the moving-wall extrapolation); points that became fluid take U_b.  Within the step
 the body stays there.  The convective terms read the body's points as U_b, the Laplacian reads
 them as zero (its wall term is -lambda w + s), and u* on the body's points is U_b.
+A cylinder rotating about its own axis with the rate omega (the same reading) keeps its place:
+its points hold omega x r, and each crossed arm's wall velocity is omega x r at the crossing.
 """
 from __future__ import annotations
 
@@ -61,13 +63,31 @@ class OracleSolver:
         self.target_flux = float(case.target_flux)
         self.body_u = tuple(float(v) for v in getattr(case, "body_velocity", ()))
         self.moving = any(v != 0.0 for v in self.body_u)
+        self.omega = float(getattr(case, "body_omega", 0.0))
+        self.rotating = self.omega != 0.0
         self.no_ibm = no_ibm
+        if (self.moving or self.rotating) and (case.geom_kind not in (CYLINDER, SPHERE) or self.grid.stretched):
+            raise NotImplementedError("a translating or rotating cylinder or sphere on a uniform grid")
+        if self.moving and self.rotating:
+            raise NotImplementedError("a body that translates and rotates")
+        if self.rotating and case.geom_kind != CYLINDER:
+            raise NotImplementedError("rotation: a cylinder about its own axis")
+        # the body's velocity at every point of each component (what its points hold)
+        self.body_field = None
+        wall_field = None
         if self.moving:
-            if case.geom_kind not in (CYLINDER, SPHERE) or self.grid.stretched:
-                raise NotImplementedError("a translating cylinder or sphere on a uniform grid")
             self._place_body(0.0)
+            self.body_field = list(self.body_u)
+        if self.rotating:
+            xc, yc = float(case.geom_params[0]), float(case.geom_params[1])
+            om = self.omega
+            x0, y0, _ = self.grid.coords(0)
+            x1, y1, _ = self.grid.coords(1)
+            self.body_field = [np.broadcast_to(-om * (y0 - yc), self.grid.shape).copy(),
+                               np.broadcast_to(om * (x1 - xc), self.grid.shape).copy(), 0.0]
+            wall_field = lambda X, c: (-om * (X[1] - yc), om * (X[0] - xc), 0.0)[c]   # omega x r at X
         self.w = build_weights(self.grid, self.levelset, self.cls, self.nu,
-                               self.body_u if self.moving else case.wall_u, no_ibm=no_ibm)
+                               self.body_u if self.moving else case.wall_u, no_ibm=no_ibm, wall_field=wall_field)
         if self.grid.xflow and self.flow_mode == FLOW_CONST_FLUX:
             raise ValueError("a constant flow rate needs a periodic x direction")
         self.poisson = solve_spectral if poisson == "spectral" else solve_direct
@@ -120,7 +140,7 @@ class OracleSolver:
         g, cls = self.grid, self.cls
         t = (self.step_count + RK3_T[k]) * self.dt
         gk = tuple(self.g[c] + self.g_amp[c] * np.sin(2.0 * np.pi * self.g_freq * t) for c in range(3))
-        N = rhs(g, cls, self.u, self.nu, gk, self.w.src, self.body_u if self.moving else None)
+        N = rhs(g, cls, self.u, self.nu, gk, self.w.src, self.body_field)
         gp = pressure_gradient(g, self.p)
         um = masked(g, cls, self.u)
         lam = self.w.lam
@@ -130,15 +150,15 @@ class OracleSolver:
             lam = [np.zeros(g.shape) for _ in range(3)]
         ustar = stage_update(g, cls, um, N, self.Nprev, gp, lam, k, self.dt,
                              self.bmode, RK3_A, RK3_B, RK3_C, B_of_x)
-        if self.moving:      # the body's points move with it
-            ustar = [np.where(cls.external[c], self.body_u[c], ustar[c]) if c < g.ncomp else ustar[c]
+        if self.body_field is not None:      # the body's points move with it
+            ustar = [np.where(cls.external[c], self.body_field[c], ustar[c]) if c < g.ncomp else ustar[c]
                      for c in range(3)]
         # the body's share of the stage: the IBM division's part I of u* - u (what the
         # explicit R does not explain) and the right-hand side's faces toward the solid
         R = [self.dt * (RK3_A[k] * N[c] + RK3_B[k] * self.Nprev[c]) - RK3_C[k] * self.dt * gp[c] for c in range(3)]
         I = [np.where(cls.internal[c], ustar[c] - um[c] - R[c], 0.0) for c in range(3)]
         # (the force accounting is written for the uniform grid; a stretched one reports NaN)
-        BN = None if (g.stretched or self.moving) else body_terms(g, cls, self.u, self.w.src, self.nu,
+        BN = None if (g.stretched or self.body_field is not None) else body_terms(g, cls, self.u, self.w.src, self.nu,
                                                  self.w.lam if self.bmode == B_EXPLICIT else None)
         if g.xflow:
             # the outflow face: convective condition, then the flux balance
@@ -166,7 +186,7 @@ class OracleSolver:
             self.u = ustar
             return
         self._project(ustar, RK3_C[k] * self.dt, update_p=True)
-        if g.stretched or self.moving:
+        if g.stretched or self.body_field is not None:
             self.step_impulse = np.full(3, np.nan)
             return
         self.step_impulse = self.step_impulse + stage_impulse(g, cls, I, BN, self.BN_prev, self.p, k, self.dt,
@@ -213,8 +233,8 @@ class OracleSolver:
         """Initial-condition projection: zero the unreadable velocities, balance the outflow
         (inflow/outflow x), then project (p unchanged)."""
         um = masked(self.grid, self.cls, self.u)
-        if self.moving:      # a translating body's points hold its velocity
-            um = [np.where(self.cls.external[c], self.body_u[c], um[c]) if c < self.grid.ncomp else um[c]
+        if self.body_field is not None:      # a moving body's points hold its velocity
+            um = [np.where(self.cls.external[c], self.body_field[c], um[c]) if c < self.grid.ncomp else um[c]
                   for c in range(3)]
         if self.grid.xflow:
             um[0] = um[0].copy()

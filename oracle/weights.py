@@ -66,10 +66,12 @@ class Weights:
     src_list: list
 
 
-def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm: bool = False) -> Weights:
+def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm: bool = False,
+                  wall_field=None) -> Weights:
     """lambda and the wall source at every IBM point, arms taken in the order d = x, y, z
     and s = +1, -1 (the distance of every crossed arm comes from levelset.delta_many,
-    which gives each arm the same value as levelset.delta)."""
+    which gives each arm the same value as levelset.delta).  wall_field(X, c): the wall's
+    velocity component c at the crossing point X (a rotating body), in place of wall_u."""
     lam, src, lam_list, src_list = [], [], [], []
     nx, ny, nz = grid.n
     for c in range(3):
@@ -122,7 +124,12 @@ def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm
             lam_p = np.zeros(len(lst))
             src_p = np.zeros(len(lst))
             for (m, P, d, s, Dd, _, _, Dsum), delta in zip(arms, deltas):
-                uw = wall_u[c] * levelset.wall_velocity_factor(d, s)
+                if wall_field is not None:
+                    X = list(P)
+                    X[d] = X[d] + s * delta
+                    uw = wall_field(X, c) * levelset.wall_velocity_factor(d, s)
+                else:
+                    uw = wall_u[c] * levelset.wall_velocity_factor(d, s)
                 if d == 1 and grid.stretched:
                     # d(s) = 2 / (Delta_s (Delta_- + Delta_+)) of the uneven three-point second
                     # difference in place of 1 / Delta^2 (same extrapolation, same form)

@@ -103,8 +103,8 @@ class Solver:
         with projection 'masked' gets the masked projection."""
         if len(getattr(case, "y_faces", ())):
             raise NotImplementedError("stretched wall-normal grids are not in the CUDA library")
-        if any(v != 0.0 for v in getattr(case, "body_velocity", ())):
-            raise NotImplementedError("translating bodies are not in the CUDA library")
+        if any(v != 0.0 for v in getattr(case, "body_velocity", ())) or getattr(case, "body_omega", 0.0):
+            raise NotImplementedError("translating and rotating bodies are not in the CUDA library")
         s = cls(ndim=case.ndim, n=case.n, L=case.L, origin=case.origin, bc_lo=case.bc_lo, bc_hi=case.bc_hi,
                 precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,
                 nu=case.nu, dt=case.dt, g=case.g, bmode=case.bmode, flow_mode=case.flow_mode,
