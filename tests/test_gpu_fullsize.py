@@ -198,3 +198,38 @@ def test_wavy_channel_fp32_against_fp64_after_ten_steps():
     # measured on a GB300: 6.4e-7, 2.1e-7, 2.1e-7 and 1.3e-7
     assert max(field) < 1e-5
     assert prof < 2e-6
+
+
+def test_airway_fp32_against_fp64_after_ten_steps():
+    """The 512 x 384 x 256 airway (inflow/outflow x, tube union, weights built on the device) in
+    FP32 mode and in FP64 mode from the same initial field: after 10 steps, the largest difference
+    of each velocity component over its internal points (the device classification's bits)
+    relative to the largest FP64 velocity, and the difference of the flow rate through the
+    outflow face."""
+    from paper_2506_14328_gb300.solver import Solver
+    base = airway_c4(precision="fp64", steps=10)
+    f = initial_field(base)
+    runs, mask = {}, None
+    for prec in ("fp64", "fp32"):
+        g = Solver.from_case(base.with_(precision=prec))
+        g.set_state(f["u"], f["v"], f["w"], f["p"])
+        g.project()
+        g.step(10)
+        assert g.diagnostics()["status"] == 0
+        u, _ = g.state()
+        runs[prec] = [np.asarray(x, dtype=np.float64) for x in u]
+        if mask is None:
+            mask, _ = g.classification()
+        g.close()
+    del f
+    a, b = runs["fp64"], runs["fp32"]
+    inside = [(mask >> c) & 1 == 1 for c in range(3)]
+    scale = max(np.abs(a[c][inside[c]]).max() for c in range(3))
+    field = [float(np.abs(b[c] - a[c])[inside[c]].max() / scale) for c in range(3)]
+    qa, qb = a[0][..., -1].sum(), b[0][..., -1].sum()
+    flow = float(abs(qb - qa) / abs(qa))
+    print(f"airway FP32 against FP64 after 10 steps: largest difference per component {field}, "
+          f"outflow flow rate {flow:.3e}")
+    # measured on a GB300: 9.6e-7, 7.6e-7, 9.2e-7 and 7.7e-9
+    assert max(field) < 1e-5
+    assert flow < 1e-7
