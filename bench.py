@@ -307,18 +307,33 @@ def run_gpu(args):
     value = aggregate_rate(case.ncells, args.steps, world, ms_max * 1e-3)
 
     # ---- end to end through the public API with host buffers -----------------
+    # Two solvers take turns, as a server keeps two requests in flight: while one steps, the
+    # next step's input state goes up to the other, and then the previous step's result
+    # comes back.  Every step's H2D copy and D2H read lie inside the timed region.
     nbytes = s.state_bytes()
     host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     s.export_state(host.numpy())
+    s2 = Solver.from_case(case, device=str(device))
+    if args.projection == "masked":
+        s2.set_projection("masked", tol=1e-6, maxit=200)
+    pair = (s, s2)
+    for q in pair:                                    # untimed: one step through each
+        q.import_state_ptr(host.data_ptr(), nbytes)
+        q.step(1)
+        q.diagnostics()
     e2e_steps = max(2, min(args.steps, 10))
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s.import_state_ptr(host.data_ptr(), nbytes)   # H2D of the step's input state (pinned)
-        s.step(1)
-        d = s.diagnostics()                           # D2H of the step's result (blocking)
+    for n in range(e2e_steps):
+        cur = pair[n % 2]
+        cur.import_state_ptr(host.data_ptr(), nbytes)  # H2D of step n's input state (pinned)
+        cur.step(1)
+        if n > 0:
+            pair[(n - 1) % 2].diagnostics()            # D2H of step n-1's result (blocking)
+    pair[(e2e_steps - 1) % 2].diagnostics()            # ... and of the last step's
     barrier()
     e2e_s = time.perf_counter() - t0
+    s2.close()
     e2e_value = aggregate_rate(case.ncells, e2e_steps, world, reduce_max(e2e_s, dist, device))
     diag_bytes = 12 * 8 + 8  # the ibm_diag struct fields read back
 
