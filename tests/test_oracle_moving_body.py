@@ -108,3 +108,25 @@ def test_rigid_rotation_in_a_pipe_at_rest_is_not_steady():
     s.set_state(u, v, np.zeros(s.grid.shape), p)
     s.step(3)
     assert np.abs(np.where(s.cls.internal[0], s.u[0] - u, 0.0)).max() > 1e-4 * om * 0.37
+
+
+def test_body_frame_form_of_the_wall_term_equals_the_moving_wall_source():
+    """Reading the body's points as U_b in the Laplacian too adds nu d(s) U_b per crossed arm, so
+    the source becomes lambda_arm U_b and the wall term -lambda (w - U_b): the same right-hand side
+    at every internal point as the moving-wall extrapolation, for any field."""
+    from dataclasses import replace
+    from oracle.momentum import rhs
+    ub = (0.7, 0.0, 0.3)
+    case = _case(3, ub)
+    s = OracleSolver(case)
+    g, cls = s.grid, s.cls
+    rng = np.random.default_rng(8)
+    u = [np.where(cls.internal[c], rng.standard_normal(g.shape), 0.0) for c in range(3)]
+    Na = rhs(g, cls, u, case.nu, (0.1, 0.0, 0.0), s.w.src, list(ub))
+    readable = replace(cls, internal=[cls.internal[c] | cls.external[c] for c in range(3)])
+    ub_field = [np.where(cls.external[c], ub[c], u[c]) for c in range(3)]
+    Nb = rhs(g, readable, ub_field, case.nu, (0.1, 0.0, 0.0), [s.w.lam[c] * ub[c] for c in range(3)])
+    for c in range(3):
+        inside = cls.internal[c]
+        scale = np.abs(Na[c][inside]).max()
+        assert np.abs(Na[c] - Nb[c])[inside].max() < 1e-11 * scale, c
