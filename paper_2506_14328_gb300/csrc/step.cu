@@ -1172,7 +1172,7 @@ __global__ void __launch_bounds__(256) k_irfft_rows(FftPlan pl, long long rows, 
     for (int n = lane; n < M; n += 32) o[n] = z[pz(n)];
 }
 
-// The divergence of u* fused with the forward transform of its x rows (periodic x):
+// The divergence of u* fused with the forward transform of its x rows (periodic x; XF below):
 // one warp computes the divergence of a whole row (32 cells per pass, the constant-flow-rate
 // increment of the internal u points as in k_divergence, u*(x-1) from the lane below or
 // carried from the previous pass) into shared memory and transforms it there, so the
@@ -1957,7 +1957,8 @@ ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const 
     cudaEvent_t t;
     const bool fuse_x = g.xper ? h->own_fft : h->dct_rows;
     if (fuse_x && h->proj_mode != IBM_PROJ_MASKED) {
-        // the divergence fused with the transform of the x rows (own FFT, periodic x)
+        // the divergence fused with the forward transform of the x rows (own real FFT on a periodic
+        // x, own DCT rows on an inflow/outflow x)
         using C = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
         timer_begin(h, "div_fft_x", &t);
         const T ix = (T)(1.0 / g.dx), iy = (T)(1.0 / g.dy), iz = (T)(1.0 / g.dz);
