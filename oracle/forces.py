@@ -137,9 +137,12 @@ def stage_impulse(grid, cls, I, BN_k, BN_prev, p_new, k: int, dt: float, a, b, c
 # u points' x and lambda the wall's wavelength (the box length for other walls).
 
 def wall_shear(grid, cls, levelset, u, nu: float, wavelength: float):
-    """(tau(x) per u column, tau_1c, tau_1s); columns without a lower-wall arm are NaN."""
+    """(tau(x) per u column, tau_1c, tau_1s); columns without a lower-wall arm are NaN.  On a
+    stretched y the arm below P and the step from P to Q are the row's own centre distances."""
     nx, ny, nz = grid.n
     Dy = grid.d[1]
+    if grid.stretched:
+        hm_y, hp_y = (a.ravel() for a in grid.y_spacing(0))
     x, y, z = [np.broadcast_to(a, grid.shape) for a in grid.coords(0)]
     phi = cls.phi[0]
     ext = cls.external[0]
@@ -152,11 +155,12 @@ def wall_shear(grid, cls, levelset, u, nu: float, wavelength: float):
                 if not (inside[k, j, i] and ext[k, j - 1, i]):
                     continue
                 P = [float(x[k, j, i]), float(y[k, j, i]), float(z[k, j, i])]
-                delta = levelset.delta(P, 1, -1, Dy, float(phi[k, j, i]), float(phi[k, j - 1, i]))
+                Dm, Dp = (float(hm_y[j]), float(hp_y[j])) if grid.stretched else (Dy, Dy)
+                delta = levelset.delta(P, 1, -1, Dm, float(phi[k, j, i]), float(phi[k, j - 1, i]))
                 uP = float(u[k, j, i])
                 if j + 1 < ny and inside[k, j + 1, i]:
                     uQ = float(u[k, j + 1, i])
-                    slope = (uP * (delta + Dy) ** 2 - uQ * delta ** 2) / (delta * Dy * (delta + Dy))
+                    slope = (uP * (delta + Dp) ** 2 - uQ * delta ** 2) / (delta * Dp * (delta + Dp))
                 else:
                     slope = uP / delta
                 tau_sum[i] += nu * slope

@@ -251,3 +251,20 @@ def test_hydrostatic_pressure_balances_the_body_force_on_a_stretched_grid():
     s.substage(0, predictor_only=True)
     assert np.abs(s.u[1]).max() < 1e-13 * abs(gy) * case.dt
     assert np.abs(s.u[0]).max() < 1e-15
+
+
+def test_wall_shear_of_a_parabola_is_exact_on_a_stretched_grid():
+    """The quadratic through the wall, P and Q is exact for a parabola whatever the spacing: with
+    the rows' own distances tau = 2 nu U / h in every column (1e-12)."""
+    from oracle.forces import wall_shear
+    case = couette_case(ny=28).with_(wall_u=(0.0, 0.0, 0.0))
+    case = case.with_(y_faces=_faces(case, 1.9))
+    s = OracleSolver(case)
+    g = s.grid
+    a, b = case.geom_params
+    h, yc, U = (b - a) / 2, (a + b) / 2, 1.3
+    y = np.broadcast_to(g.coords(0)[1], g.shape)
+    u = U * (1.0 - ((y - yc) / h) ** 2)
+    tau, t1c, t1s = wall_shear(g, s.cls, s.levelset, u, case.nu, g.L[0])
+    exact = 2.0 * case.nu * U / h
+    assert np.all(np.isfinite(tau)) and np.abs(tau - exact).max() < 1e-12 * exact
