@@ -313,6 +313,11 @@ def stage_update(grid, cls, u_prev, N_cur, N_prev, gradp, lam, k: int, dt: float
 def outflow_speed(grid, cls) -> float:
     """U_c: the inflow flux divided by the fluid outflow area (reading: the mean speed
     through the outflow face, fixed by the geometry)."""
+    if grid.stretched:                    # face areas differ from row to row: weigh by them
+        A = grid.cell_heights()[..., :1]
+        a_in = float(np.sum(np.where(cls.inflow_fluid, A, 0.0)))
+        a_out = float(np.sum(np.where(cls.outflow_fluid, A, 0.0)))
+        return grid.inflow[0] * a_in / a_out if a_out else 0.0
     n_in = int(np.count_nonzero(cls.inflow_fluid))
     n_out = int(np.count_nonzero(cls.outflow_fluid))
     return grid.inflow[0] * n_in / n_out if n_out else 0.0
@@ -335,6 +340,14 @@ def outflow_balance(grid, cls, ub):
     """Shift the fluid outflow face velocities by one constant so that the outflow flux
     equals the inflow flux (reading; the Poisson problem with prescribed normal velocity
     on every box face is solvable only then)."""
+    if grid.stretched:                    # the fluxes through faces of unequal area
+        A = grid.cell_heights()[..., :1]
+        a_in = float(np.sum(np.where(cls.inflow_fluid, A, 0.0)))
+        a_out = float(np.sum(np.where(cls.outflow_fluid, A, 0.0)))
+        if a_out == 0.0:
+            return ub
+        shift = (grid.inflow[0] * a_in - np.sum(np.where(cls.outflow_fluid, ub * A, 0.0))) / a_out
+        return np.where(cls.outflow_fluid, ub + shift, 0.0)
     n_in = int(np.count_nonzero(cls.inflow_fluid))
     n_out = int(np.count_nonzero(cls.outflow_fluid))
     if n_out == 0:
