@@ -289,3 +289,18 @@ def test_stretched_inflow_outflow_box_projects_to_round_off(name):
     inflow = np.sum(np.where(s.cls.inflow_fluid, case.inflow[0], 0.0) * g.cell_heights()[..., :1])
     outflow = np.sum(np.where(s.cls.outflow_fluid, s.u[0][..., -1:], 0.0) * g.cell_heights()[..., :1])
     assert abs(outflow - inflow) < 1e-10 * abs(inflow)
+
+
+def test_stretched_constant_flow_rate_holds_the_volume_integral():
+    """The constant-flow-rate forcing on a stretched grid: after the predictor the volume integral
+    of u over the internal u points, with each row's own cell height, equals the target."""
+    case = small_case("wavy3d").with_(n=(24, 36, 8), name="wavy3d_st")
+    case = case.with_(y_faces=_faces(case, 1.5))
+    s = OracleSolver(case)
+    f = initial_field(case)
+    s.set_state(f["u"], f["v"], f["w"], f["p"])
+    s.substage(0, predictor_only=True)
+    yf = np.asarray(case.y_faces)
+    dV = (case.L[0] / case.n[0]) * np.diff(yf)[None, :, None] * (case.L[2] / case.n[2])
+    Q = float(np.sum(np.where(s.cls.internal[0], s.u[0], 0.0) * dV))
+    assert abs(Q - case.target_flux) < 1e-12 * abs(case.target_flux)
