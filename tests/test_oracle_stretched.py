@@ -186,7 +186,7 @@ def test_stretched_y_convection_is_second_order():
         assert min(slopes) > 1.8, (c, e, slopes)
 
 
-def _steady_error(ny, beta, use_ibm):
+def _steady_error(ny, beta, use_ibm, c=0):
     a, b = 0.137, 0.861
     case = Case(name="ch", ndim=2, n=(4, ny, 1), L=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
                 bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
@@ -194,10 +194,10 @@ def _steady_error(ny, beta, use_ibm):
     case = case.with_(y_faces=tanh_faces(ny, 0.0, 1.0, beta))
     s = OracleSolver(case)
     g, cls = s.grid, s.cls
-    q = steady.solve_component(g, cls, s.w, 0, 1.0, 2.0, use_ibm=use_ibm)   # nu u'' = -2: u = (y-a)(b-y)
-    y = np.broadcast_to(g.coords(0)[1], g.shape)
+    q = steady.solve_component(g, cls, s.w, c, 1.0, 2.0, use_ibm=use_ibm)   # nu q'' = -2: q = (y-a)(b-y)
+    y = np.broadcast_to(g.coords(c)[1], g.shape)
     exact = (y - a) * (b - y)
-    return np.abs(q - exact)[cls.internal[0]].max()
+    return np.abs(q - exact)[cls.internal[c]].max()
 
 
 def test_stretched_steady_channel_converges_at_second_order():
@@ -304,3 +304,23 @@ def test_stretched_constant_flow_rate_holds_the_volume_integral():
     dV = (case.L[0] / case.n[0]) * np.diff(yf)[None, :, None] * (case.L[2] / case.n[2])
     Q = float(np.sum(np.where(s.cls.internal[0], s.u[0], 0.0) * dV))
     assert abs(Q - case.target_flux) < 1e-12 * abs(case.target_flux)
+
+
+def test_stretched_wall_normal_ibm_is_exact_on_a_line_through_the_wall():
+    """v = y - a vanishes on the lower off-grid wall: the linear extrapolation through the wall
+    returns the line itself, so with the stretched IBM weights of v (arms of face spacing) the
+    discrete Laplacian nu L v - lambda v is zero at every v point of the lower half (1e-12)."""
+    a, b = 0.137, 0.861
+    case = Case(name="ch", ndim=2, n=(4, 30, 1), L=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
+                bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
+                geom_kind=GEOM_PLANES, geom_params=(a, b), nu=1.0, dt=1e-3)
+    case = case.with_(y_faces=tanh_faces(30, 0.0, 1.0, 1.7))
+    s = OracleSolver(case)
+    g, cls = s.grid, s.cls
+    A, sel = steady.laplacian_matrix(g, cls, 1)
+    y = np.broadcast_to(g.coords(1)[1], g.shape).ravel()[sel]
+    v = y - a
+    res = A @ v - s.w.lam[1].ravel()[sel] * v
+    lower = y < 0.5 * (a + b) - 0.1
+    assert np.count_nonzero(s.w.lam[1].ravel()[sel][lower]) > 0
+    assert np.abs(res[lower]).max() < 1e-12 * np.abs(A).max()
