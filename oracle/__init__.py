@@ -30,12 +30,12 @@ solve (tests/test_oracle_*.py).  No function is "parity unpinned".
 from .grid import Grid
 from .geometry import LevelSet
 from .classify import Classification, classify
-from .weights import Weights, build_weights, stage_coefficients, B_of_x, RK3_A, RK3_B, RK3_C, RK3_T
+from .weights import Weights, build_weights, B_of_x, RK3_A, RK3_B, RK3_C, RK3_T
 from .momentum import rhs, stage_update
 from .poisson import divergence, gradient, solve_spectral, solve_direct
 from .solver import OracleSolver
 from . import steady
 
 __all__ = ["Grid", "LevelSet", "Classification", "classify", "Weights", "build_weights",
-           "stage_coefficients", "B_of_x", "RK3_A", "RK3_B", "RK3_C", "rhs", "stage_update",
+           "B_of_x", "RK3_A", "RK3_B", "RK3_C", "rhs", "stage_update",
            "divergence", "gradient", "solve_spectral", "solve_direct", "OracleSolver", "steady"]

@@ -152,13 +152,3 @@ def build_weights(grid, levelset, cls, nu: float, wall_u=(0.0, 0.0, 0.0), no_ibm
         src_list.append(sl)
     return Weights(lam, src, lam_list, src_list)
 
-
-def stage_coefficients(lam_list: np.ndarray, dt: float, mode: int):
-    """(alpha_k, beta_k) for k = 1..3 with u* = alpha u + beta R, alpha = B/(B+x), beta = 1/(B+x)."""
-    out = []
-    for k in range(3):
-        x = lam_list * RK3_C[k] * dt
-        B = B_of_x(x, mode)
-        out.append((B / (B + x), 1.0 / (B + x)))
-    return out
-

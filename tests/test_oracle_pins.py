@@ -441,18 +441,76 @@ def _startup_flux(dt, mode, T=0.05):
     return s.diagnostics()["flux"][0]
 
 
+def _temporal_slope(mode, T=0.0496):
+    ref = _startup_flux(1.25e-5, B_EXACT, T=T)
+    dts = [2e-4, 1e-4, 5e-5]
+    e = [abs(_startup_flux(dt, mode, T=T) - ref) for dt in dts]
+    return math.log2(e[1] / e[2])
+
+
 def test_temporal_order_exact_B_vs_euler():
     """Sec. 2.5: second order in time with the exponential B, first order with B = 1.
 
     Errors are taken against a run with the exponential B at dt/16 of the
     coarsest step; the slope is read from the two finest pairs."""
-    T = 0.0496
+    for mode, lo, hi in ((B_EXACT, 1.8, 2.6), (B_EULER, 0.85, 1.15)):
+        p = _temporal_slope(mode)
+        assert lo < p < hi, (mode, p)
+
+
+def test_taylor2_B_agrees_with_the_exponential_B_to_second_order_in_x():
+    """Sec. 2.4, the remark after Eq. (Bexpr): B may be the reciprocal of a Taylor expansion
+    of (e^x - 1)/x = 1 + x/2 + x^2/6 + ...  Cut after the linear term, its reciprocal differs
+    from x/(e^x - 1) = 1 - x/2 + x^2/12 - ... by -x^2/6 + O(x^3): the series of both sides
+    agree through the linear term, and the leading gap is fixed by the x^2 coefficients."""
+    x = np.logspace(-5, -2, 7)
+    exact = x / np.expm1(x)
+    gap = (exact - B_of_x(x, B_TAYLOR2)) / x ** 2
+    assert np.allclose(gap, -1.0 / 6.0, rtol=0, atol=0.02)
+    # a large x still respects 1 >= B >= 0 and decays like 2/x (the reciprocal of 1 + x/2)
+    big = np.array([1e3, 1e6])
+    assert np.allclose(B_of_x(big, B_TAYLOR2) * big, 2.0, rtol=2e-3)
+
+
+def _taylor2_orders(T=0.0496):
+    """(slope of the TAYLOR2 error against a fine exponential-B run, slope of the gap between
+    TAYLOR2 and the exponential B at equal steps), both from the finest pair of steps."""
     ref = _startup_flux(1.25e-5, B_EXACT, T=T)
     dts = [2e-4, 1e-4, 5e-5]
-    for mode, lo, hi in ((B_EXACT, 1.8, 2.6), (B_EULER, 0.85, 1.15)):
-        e = [abs(_startup_flux(dt, mode, T=T) - ref) for dt in dts]
-        p = math.log2(e[1] / e[2])
-        assert lo < p < hi, (mode, p)
+    t2 = [_startup_flux(dt, B_TAYLOR2, T=T) for dt in dts]
+    ex = [_startup_flux(dt, B_EXACT, T=T) for dt in dts[1:]]
+    err = [abs(a - ref) for a in t2]
+    gap = [abs(a - b) for a, b in zip(t2[1:], ex)]
+    return math.log2(err[1] / err[2]), math.log2(gap[0] / gap[1])
+
+
+def test_taylor2_B_is_second_order_in_time():
+    """Sec. 2.4-2.5: the order of the Taylor expansion under the reciprocal sets the order in
+    time (B = 1 is first order).  Cut after the linear term, the stage multiplier
+    B/(B + x) = 1/(1 + x + x^2/2) matches e^{-x} through x^2 and misses it by x^3/6, so
+    (a) the startup flux of the channel converges at least at second order, and (b) the gap
+    to the exponential B at the same step shrinks at exactly second order."""
+    p_err, p_gap = _taylor2_orders()
+    assert p_err > 1.8, p_err
+    assert 1.75 < p_gap < 2.3, p_gap
+
+
+def test_taylor2_pins_catch_a_wrong_expansion(monkeypatch):
+    """Planted mistake: B = 1/(1 + x), the reciprocal of a wrong linear term.  Both TAYLOR2
+    pins above must reject it (the O(x^2) gap in B, and the orders in time)."""
+    import oracle.solver as osolver
+
+    def wrong(x, mode):
+        if mode == B_TAYLOR2:
+            return 1.0 / (1.0 + np.asarray(x, dtype=np.float64))
+        return B_of_x(x, mode)
+
+    x = np.logspace(-5, -2, 7)
+    gap = (x / np.expm1(x) - wrong(x, B_TAYLOR2)) / x ** 2
+    assert not np.allclose(gap, -1.0 / 6.0, rtol=0, atol=0.02)
+    monkeypatch.setattr(osolver, "B_of_x", wrong)
+    p_err, p_gap = _taylor2_orders()
+    assert not (p_err > 1.8 and 1.75 < p_gap < 2.3), (p_err, p_gap)
 
 
 # ---- inflow / convective outflow in x, Neumann (DCT) Poisson direction --------------------
