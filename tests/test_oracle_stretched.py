@@ -210,6 +210,43 @@ def test_stretched_steady_channel_converges_at_second_order():
     assert max(s0[1:]) < 1.5, (e0, s0)
 
 
+def _tanh_map(eta, beta):
+    return 0.5 * (1.0 + np.tanh(beta * (2.0 * eta - 1.0)) / np.tanh(beta))
+
+
+def _fixed_fraction_error(ny, beta, c, use_ibm=True):
+    """Steady error of component c with both walls at a fixed sub-cell fraction of the mapped
+    coordinate (between faces ny/8 and ny/8 + 1 at 0.37, and symmetrically at 0.29 from the
+    top), so that refinement changes the spacing and not where the wall cuts its cell."""
+    m = ny // 8
+    a = float(_tanh_map((m + 0.37) / ny, beta))
+    b = float(_tanh_map(1.0 - (m + 0.29) / ny, beta))
+    case = Case(name="ch", ndim=2, n=(4, ny, 1), L=(1.0, 1.0, 1.0), origin=(0.0, 0.0, 0.0),
+                bc_lo=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC), bc_hi=(BC_PERIODIC, BC_NOSLIP, BC_PERIODIC),
+                geom_kind=GEOM_PLANES, geom_params=(a, b), nu=1.0, dt=1e-3)
+    case = case.with_(y_faces=tanh_faces(ny, 0.0, 1.0, beta))
+    s = OracleSolver(case)
+    g, cls = s.grid, s.cls
+    q = steady.solve_component(g, cls, s.w, c, 1.0, 2.0, use_ibm=use_ibm)   # nu q'' = -2: q = (y-a)(b-y)
+    y = np.broadcast_to(g.coords(c)[1], g.shape)
+    return np.abs(q - (y - a) * (b - y))[cls.internal[c]].max()
+
+
+@pytest.mark.parametrize("beta", [0.5, 1.5])
+def test_both_components_converge_at_second_order_with_the_wall_at_a_fixed_sub_cell_fraction(beta):
+    """Sec. 2.3 (second order of the implicit IBM) on the stretched grid, for the cell-centred
+    u and for v on the faces (arms of face spacing): slopes of 2 between ny = 32, 64, 128
+    once the wall keeps its place within its cell, 1 without the IBM correction."""
+    ns = (32, 64, 128)
+    for c in (0, 1):
+        e = [_fixed_fraction_error(n, beta, c) for n in ns]
+        slopes = [np.log2(e[i] / e[i + 1]) for i in range(len(e) - 1)]
+        assert all(1.9 < p < 2.2 for p in slopes), (c, e, slopes)
+    e0 = [_fixed_fraction_error(n, beta, 1, use_ibm=False) for n in ns]
+    s0 = [np.log2(e0[i] / e0[i + 1]) for i in range(len(e0) - 1)]
+    assert all(0.8 < p < 1.2 for p in s0), (e0, s0)
+
+
 def test_stretched_three_dimensional_run_keeps_the_divergence_at_round_off():
     case = small_case("wavy3d").with_(n=(24, 36, 8), name="wavy3d_st")
     case = case.with_(y_faces=_faces(case, 1.5))
