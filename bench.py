@@ -1,12 +1,13 @@
 """Throughput of the IBM time step on one GB300 (or N independent replicas).
 
-Default workload: the 3D channel over a sinusoidal wall, 384x256x256 cells,
-FP32 momentum/FFT with FP64 tridiagonal sweeps and reductions, constant flow
-rate (see inputs.configs.wavy_c3).  A "step" is one full RK3 time step: three
+Default workload: the tortuous airway-like duct, 512x384x256 cells (the largest
+single-GPU configuration): a seeded union of tubes, inflow and convective
+outflow in x, IBM weights built on the device, FP32 mode (see
+inputs.configs.airway_c4).  A "step" is one full RK3 time step: three
 substages, each a momentum predictor with the implicit IBM division followed
 by the projection.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c3s|c3_fp64|c1|c2|c2_fp64|c2_periodic|c4] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c4|c3|c3s|c3_fp64|c1|c2|c2_fp64|c2_periodic] [--impl reference]
 
 One JSON line on stdout (rank 0).  `value` is cells x steps / time over all
 ranks (replicas: every rank advances its own copy of the workload, no
@@ -43,8 +44,19 @@ ALG_BYTES_PER_CELL = {
     "divergence": 16.0,
     "correct": 36.0,
 }
-# tridiag: per spectral point read spec 8 + pivot 8 + write tmp 16, then tmp 16 + pivot 8 + spec 8
-TRIDIAG_BYTES_PER_SPECTRAL_POINT = 64.0
+# tridiag, per spectral point: one read of the right-hand side and of the pivot and one write of
+# the solution (the forward sweep's temporary is not counted): FP32 storage 8 + 4 + 8 B for a
+# system that sweeps in FP32 (FP32 pivot), 8 + 8 + 8 B for one that sweeps in FP64; FP64
+# storage 16 + 8 + 16 B
+TRIDIAG_BYTES_PER_SPECTRAL_POINT = {"fp32": 20.0, "fp32_fp64sweep": 24.0, "fp64": 40.0}
+
+PRECISION_DETAIL = {
+    "fp32": ("fp32 fields, momentum stencil, IBM division, per-cell divergence and FFTs; fp64 tridiagonal "
+             "sweeps of the near-singular spectral systems (K dy^2 < 1) and fp64 Thomas pivots of every system; "
+             "fp32 sweeps of the strongly dominant systems (K dy^2 >= 1, condition <= 5); fp64 sums in every "
+             "reduction (flow rate, outflow balance, diagnostics); IBM weights computed in fp64"),
+    "fp64": "fp64 throughout",
+}
 
 # DRAM traffic per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by kernel, with the hash of the source file it was taken on; a changed
@@ -95,6 +107,30 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def tridiag_alg_bytes(case) -> float:
+    """Algorithmic bytes of one tridiagonal launch: every spectral point once in and once out with
+    its pivot.  In FP32 mode the near-singular systems (K dy^2 < 1) sweep in FP64 with FP64
+    pivots, the others in FP32 with FP32 pivots (the same split the library makes)."""
+    import numpy as np
+    nx, ny, nz = case.n
+    xper = case.bc_lo[0] == 0
+    nxh = nx // 2 + 1 if xper else nx
+    dx, dy = case.L[0] / nx, case.L[1] / ny
+    kx = np.arange(nxh)
+    sx = np.sin(np.pi * kx / nx) if xper else np.sin(np.pi * kx / (2.0 * nx))
+    K = (4.0 * sx ** 2 / dx ** 2)[None, :]
+    if case.ndim == 3 and nz > 1:
+        dz = case.L[2] / nz
+        nzs = nz if xper else nz // 2 + 1     # a real transform in z on a Neumann x
+        K = K + (4.0 * np.sin(np.pi * np.arange(nzs) / nz) ** 2 / dz ** 2)[:, None]
+    nsys = K.size
+    if case.precision == "fp64":
+        return TRIDIAG_BYTES_PER_SPECTRAL_POINT["fp64"] * nsys * ny
+    n64 = int(np.count_nonzero(K * dy * dy < 1.0))
+    return ny * (TRIDIAG_BYTES_PER_SPECTRAL_POINT["fp32_fp64sweep"] * n64 +
+                 TRIDIAG_BYTES_PER_SPECTRAL_POINT["fp32"] * (nsys - n64))
+
+
 def reduce_max(x: float, dist=None, device="cpu") -> float:
     """Maximum of x over the ranks of the process group (x itself without one)."""
     import torch
@@ -109,22 +145,25 @@ def aggregate_rate(cells: int, steps: int, world: int, seconds: float) -> float:
     return world * cells * steps / seconds / 1e9
 
 
-def serving_sample(device, n_requests: int = 24, seed: int = 0, load: float = 0.8) -> dict:
-    """A bounded sample of the serving mix (C5): steps and linear sizes scaled
-    down, arrivals at `load` of an assumed 2 Gcell-updates/s capacity."""
+def serving_sample(device, n_requests: int = 16, seed: int = 0, load: float = 0.8,
+                   capacity: float = 3.0e9) -> dict:
+    """A bounded sample of the serving mix (C5) at its stated distributions (2D n^2 with n in
+    [128, 1024], 3D n^3 with n in [64, 192], 500-5000 steps), with Poisson arrivals at `load`
+    of an assumed aggregate capacity of `capacity` cell-updates/s."""
     from inputs import serving_mix, initial_field
     from paper_2506_14328_gb300.serving import Server, Request
-    probe = serving_mix(seed=seed, n_requests=n_requests, rate_hz=1.0, step_scale=0.1, size_scale=0.5)
+    probe = serving_mix(seed=seed, n_requests=n_requests, rate_hz=1.0)
     work = sum(c.ncells * s for _, c, s in probe) / len(probe)
-    rate = load * 2.0e9 / work
-    mix = serving_mix(seed=seed, n_requests=n_requests, rate_hz=rate, step_scale=0.1, size_scale=0.5)
+    rate = load * capacity / work
+    mix = serving_mix(seed=seed, n_requests=n_requests, rate_hz=rate)
     # each client sends its initial state with the request (prepared before arrival)
     reqs = [Request(q, t, c, s, init=initial_field(c)) for q, (t, c, s) in enumerate(mix)]
     srv = Server(device=str(device), max_resident=32, steps_per_tick=25)
     stats = srv.serve(reqs)
     srv.close()
-    stats.update({"arrival_rate_hz": rate, "mix": "C5 sample: 2D n^2 n in [64,512], 3D n^3 n in [32,96], "
-                  "steps 50-500, Re 10-2000, FP32, Poisson arrivals", "seed": seed})
+    stats.update({"arrival_rate_hz": rate, "assumed_capacity_gcell_s": capacity / 1e9,
+                  "mix": "C5 at its stated distributions: 2D n^2 n in [128,1024], 3D n^3 n in [64,192], "
+                         "steps 500-5000, Re 10-2000, FP32 mode, Poisson arrivals", "seed": seed})
     return stats
 
 
@@ -198,8 +237,9 @@ def oracle_slab(case, nz: int):
                       target_flux=case.target_flux * frac)
 
 
-def oracle_sample(case, steps: int = 2, nz: int = 32):
-    """Time the FP64 oracle, as it stands, on a bounded slab of the same workload."""
+def _oracle_run(args):
+    """One oracle process: `steps` full steps on the slab; returns (cells x steps, seconds)."""
+    case, steps, nz = args
     from oracle import OracleSolver
     from inputs import initial_field
     sample = oracle_slab(case, nz)
@@ -208,11 +248,38 @@ def oracle_sample(case, steps: int = 2, nz: int = 32):
     o.set_state(f["u"], f["v"], f["w"], f["p"])
     t = time.perf_counter()
     o.step(steps)
-    dt = time.perf_counter() - t
-    n = sample.n
-    return {"value": sample.ncells * steps / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full steps of the FP64 numpy oracle on a {n[0]}x{n[1]}x{n[2]} slab of the "
-                      f"same workload (same spacing and physics), {dt:.1f} s"}
+    return sample.ncells * steps, time.perf_counter() - t, sample.n
+
+
+def oracle_sample(case, steps: int = 2, nz: int = 32, procs: int = 1):
+    """Time the FP64 oracle, as it stands, on a bounded slab of the same workload: one process
+    (procs = 1), or `procs` independent processes at once, each stepping its own copy of the
+    slab (the host's cores used as replicas; throughput = all their cell updates / wall time)."""
+    if procs <= 1:
+        work, dt, n = _oracle_run((case, steps, nz))
+        desc = (f"{steps} full steps of the FP64 numpy oracle on a {n[0]}x{n[1]}x{n[2]} slab of the "
+                f"same workload (same spacing and physics), one process, {dt:.1f} s")
+        return {"value": work / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    import multiprocessing as mp
+    # numpy's own threads off in the workers, so that each process holds one core
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")        # never fork a process that has used the GPU
+    with ctx.Pool(procs) as pool:
+        pool.map(_ping, range(procs))   # the workers are up (imports done) before the clock starts
+        t = time.perf_counter()
+        res = pool.map(_oracle_run, [(case, steps, nz)] * procs)
+        wall = time.perf_counter() - t
+    work = sum(r[0] for r in res)
+    n = res[0][2]
+    desc = (f"{procs} oracle processes at once (spawned, one per host core), each {steps} full FP64 steps on "
+            f"its own {n[0]}x{n[1]}x{n[2]} slab of the same workload, {wall:.1f} s wall")
+    return {"value": work / wall / 1e9, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": desc}
+
+
+def _ping(_):
+    import oracle  # noqa: F401
+    return os.getpid()
 
 
 def run_reference(args):
@@ -307,35 +374,38 @@ def run_gpu(args):
     value = aggregate_rate(case.ncells, args.steps, world, ms_max * 1e-3)
 
     # ---- end to end through the public API with host buffers -----------------
-    # Two solvers take turns, as a server keeps two requests in flight: while one steps, the
-    # next step's input state goes up to the other, and then the previous step's result
-    # comes back.  Every step's H2D copy and D2H read lie inside the timed region.
+    # Two solvers take turns, as a server keeps two requests in flight: every step imports its
+    # input state (u, v, w, p) from pinned host memory, steps once, and exports the stepped
+    # state (u, v, w, p) back into pinned host memory.  While one solver steps, the other's
+    # copies run.  Every step's H2D copy and D2H copy of the whole field lie inside the timed
+    # region.
     nbytes = s.state_bytes()
-    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-    s.export_state(host.numpy())
+    host_in = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    host_out = [torch.empty(nbytes, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    s.export_state(host_in.numpy())
     s2 = Solver.from_case(case, device=str(device))
     if args.projection == "masked":
         s2.set_projection("masked", tol=1e-6, maxit=200)
     pair = (s, s2)
-    for q in pair:                                    # untimed: one step through each
-        q.import_state_ptr(host.data_ptr(), nbytes)
+    for q, out in zip(pair, host_out):                # untimed: one step through each
+        q.import_state_ptr(host_in.data_ptr(), nbytes)
         q.step(1)
-        q.diagnostics()
+        q.export_state(out.numpy())
     e2e_steps = max(2, min(args.steps, 10))
     barrier()
     t0 = time.perf_counter()
     for n in range(e2e_steps):
         cur = pair[n % 2]
-        cur.import_state_ptr(host.data_ptr(), nbytes)  # H2D of step n's input state (pinned)
+        cur.import_state_ptr(host_in.data_ptr(), nbytes)     # H2D of step n's input state
         cur.step(1)
         if n > 0:
-            pair[(n - 1) % 2].diagnostics()            # D2H of step n-1's result (blocking)
-    pair[(e2e_steps - 1) % 2].diagnostics()            # ... and of the last step's
+            pair[(n - 1) % 2].export_state(host_out[(n - 1) % 2].numpy())   # D2H of step n-1's state
+    pair[(e2e_steps - 1) % 2].export_state(host_out[(e2e_steps - 1) % 2].numpy())
     barrier()
     e2e_s = time.perf_counter() - t0
+    diag2 = s2.diagnostics()
     s2.close()
     e2e_value = aggregate_rate(case.ncells, e2e_steps, world, reduce_max(e2e_s, dist, device))
-    diag_bytes = 12 * 8 + 8  # the ibm_diag struct fields read back
 
     if rank == 0:
         peaks = measured_peaks()
@@ -352,8 +422,7 @@ def run_gpu(args):
         n_l, tot_ms = mine.get(dom, (1, float("nan")))
         avg_s = tot_ms / n_l * 1e-3
         if dom == "tridiag":
-            nspec = case.n[2] * case.n[1] * (case.n[0] // 2 + 1)
-            alg = TRIDIAG_BYTES_PER_SPECTRAL_POINT * nspec
+            alg = tridiag_alg_bytes(case)
         else:
             alg = ALG_BYTES_PER_CELL.get(dom, 0.0) * case.ncells
             if dom == "momentum":
@@ -367,13 +436,17 @@ def run_gpu(args):
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic, "kernel": dom,
                 "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3,
                 "peak_source": peaks["source"] + ", copy bandwidth; kernel timed inside a long step"}
-        cpu = oracle_sample(case) if world == 1 or rank == 0 else None
+        cpu = None
+        if world == 1:
+            ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+            cpu = oracle_sample(case, procs=ncores)
+            cpu["single_core"] = oracle_sample(case, procs=1)
+            cpu["nproc"] = os.cpu_count()
         cfg = describe(case)
         cfg.update({"model": "IBM RK3 step + projection", "parallelism": "replicas" if world > 1 else "single",
                     "l2": "inputs larger than L2 (working set ~%.1f GB)" % (
                         (s.work.numel() + 4 * s.N * (4 if case.precision == 'fp32' else 8)) / 1e9),
-                    "precision_detail": "fp32 momentum/divergence/FFT, fp64 tridiagonal + reductions"
-                    if case.precision == "fp32" else "fp64 throughout",
+                    "precision_detail": PRECISION_DETAIL[case.precision],
                     "ibm_points": nibm, "ibm_fraction_of_fluid_points": nibm / max(ninternal, 1),
                     "projection": args.projection,
                     "setup_s": setup_s, "final_div_linf": diag["div_linf"], "final_flux_u": diag["flux"][0]})
@@ -383,7 +456,10 @@ def run_gpu(args):
                 "dtype": "f32" if case.precision == "fp32" else "f64", "data": "synthetic", "config": cfg,
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                        "d2h_bytes_per_step": diag_bytes},
+                        "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
+                        "what": "two solvers in turn; per step: import u,v,w,p from pinned host memory, one "
+                                "full step, export u,v,w,p to pinned host memory",
+                        "final_div_linf": diag2["div_linf"]},
                 "clocks": clk, "gpu_launches": launches, "kernels": per_kernel}
         if args.serving > 0:
             line["serving"] = serving_sample(device, n_requests=args.serving)
@@ -399,9 +475,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="c3")
+    ap.add_argument("--workload", default="c4")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--serving", type=int, default=24, help="requests in the serving sample (0: skip)")
+    ap.add_argument("--serving", type=int, default=16, help="requests in the serving sample (0: skip)")
     ap.add_argument("--projection", default="fullbox", choices=["fullbox", "masked"],
                     help="masked: D M G over the internal cells by conjugate gradients (residual 1e-6)")
     args = ap.parse_args()

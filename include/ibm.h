@@ -36,9 +36,13 @@
  *     ABI.  ibm_last_error() gives a thread-local message.  After a CUDA
  *     error the handle is failed and later calls return IBM_E_STATE.
  *   - Precision: IBM_FP64 runs every step in FP64.  IBM_FP32 stores fields in
- *     FP32 and runs the momentum stencil, the IBM division, the divergence
- *     and the FFTs in FP32; the tridiagonal sweeps, all reductions and the
- *     IBM weights are FP64.
+ *     FP32 and runs the momentum stencil, the IBM division, the per-cell
+ *     divergence and the FFTs in FP32.  FP64 arithmetic is kept for the
+ *     tridiagonal sweeps of the near-singular spectral systems (K dy^2 < 1,
+ *     the low modes), the Thomas pivots of every system, the IBM weights,
+ *     and the sums of every reduction (flow rate, outflow balance,
+ *     diagnostics); the strongly dominant systems (K dy^2 >= 1, condition
+ *     number <= 5) sweep in FP32.
  */
 #ifndef IBM_H
 #define IBM_H
@@ -112,6 +116,13 @@ typedef struct {
     int precision;      /* IBM_FP64 or IBM_FP32 */
     double inflow[3];   /* x = IBM_BC_INFLOW / IBM_BC_OUTFLOW: velocity through the inflow face
                          * (inflow[0] used; uniform on the fluid part of the face) */
+    const double* y_faces; /* stretched wall-normal grid (Sec. 4.2 and Table wavy-parameters
+                         * stretch the wall-normal spacing): host array of the n[1] + 1 face
+                         * heights, strictly increasing from origin[1] to origin[1] + L[1]
+                         * (within 1e-12 L[1]), read once by ibm_setup_geometry; NULL for a
+                         * uniform y.  Cell centres lie midway between faces and v sits on
+                         * the faces.  Not with the masked projection, the body force or
+                         * ibm_diagnostics_noalloc (IBM_E_UNSUPPORTED). */
 } ibm_grid_desc;
 
 typedef struct {
@@ -153,6 +164,21 @@ typedef struct {
                          * t_n + 2/3 dt) with t_n = completed steps * dt.  Nonzero g_amp refuses
                          * IBM_STEP_GRAPH and batches (the stage values change every step). */
     double g_freq;
+    double body_u[3];   /* a translating body (Sec. 3.1, end: the IBM applies in the frame in which the
+                         * body is at rest; reading R24): a CYLINDER or SPHERE whose centre moves with
+                         * this constant velocity.  At the start of every full step the points are
+                         * classified again with the centre at its place at t_n = completed steps *
+                         * dt, the IBM weights rebuilt with the wall moving at body_u, and points
+                         * that became fluid take body_u; the body's own points read and hold
+                         * body_u.  Zero: at rest. */
+    double body_omega;  /* a CYLINDER rotating about its own axis at this rate (counter-clockwise):
+                         * its points hold omega x r and each crossed arm's wall velocity is
+                         * omega x r at the crossing.  Not with body_u.  A moving body needs a
+                         * periodic x, a uniform y, the forced flow (no constant flow rate) and
+                         * body_force = 0; a translating one refuses IBM_STEP_GRAPH and batches
+                         * (its weights change every step) and sizes the weights buffer with room
+                         * for 1.5 x its first IBM-point counts + 1024 per component
+                         * (IBM_E_NOMEM at a step that would exceed it). */
 } ibm_physics;
 
 typedef struct {
@@ -207,6 +233,10 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
 /* Device bytes the weights need (IBM-point lists, lambda, wall source and
  * per-stage coefficients), known after ibm_setup_geometry. */
 ibm_status ibm_weights_bytes(const ibm_solver* h, size_t* bytes);
+/* The weights buffer a translating body needs (ibm_physics.body_u, reading R24 of Sec. 3.1):
+ * room for 3/2 of the present IBM-point counts + 1024 per component, since the counts change
+ * as the body crosses the grid. */
+ibm_status ibm_weights_bytes_moving(const ibm_solver* h, size_t* bytes);
 
 /* Compute delta per crossed stencil arm, lambda (Sec. 2.2, Eq. lambda) and
  * the per-stage implicit coefficients (Eq. Bexpr, rk3-rai) into the caller's
@@ -312,6 +342,20 @@ ibm_status ibm_set_momentum_tma(ibm_solver* h, int enable);
  * projection).  *own reports whether it runs on this grid (may be NULL).  Both paths compute
  * the same transform. */
 ibm_status ibm_set_own_fft(ibm_solver* h, int mode, int* own);
+/* Form of the FP64 tridiagonal sweeps (the near-singular systems K dy^2 < 1 in FP32 mode,
+ * every system in FP64 mode).  form 0 (the default) and 1: one warp per system (affine-map
+ * scans over the lanes; all rows of a system in flight at once) where ny <= 1024, else one
+ * thread per system; 2: one thread per system (the least FP64 work, but a dependent chain
+ * of 2 ny steps that waits on memory).  Both compute the same Thomas solve in FP64
+ * arithmetic (a tuning and testing aid, not in the paper).  IBM_E_INVALID for other values. */
+ibm_status ibm_set_tridiag_form(ibm_solver* h, int form);
+/* Self-test (no counterpart in the paper): the FP64 tridiagonal sweeps of FP32 fields
+ * convert between FP32 and FP64 with integer instructions (exact widening; narrowing
+ * rounded to nearest, ties to even).  This runs n bit patterns (random doubles, exact
+ * rounding ties, random floats, doubles near the FP32 range ends) through both those
+ * conversions and the hardware's, on the current device's legacy default stream, and
+ * returns in *mismatches the count whose results differ in any bit.  Blocking. */
+ibm_status ibm_selftest_conversions(long long n, long long* mismatches);
 
 /* Batched stepping of many resident solves (continuous batching for serving
  * many small solves; the paper has no counterpart).  A batch owns a
@@ -344,8 +388,13 @@ ibm_status ibm_launch_count(const ibm_solver* h, long long* count);
  *   - Scratch: the per-block partial sums live in a fixed array of this
  *     library's own device memory (196,736 bytes, present on every GPU that
  *     loads the library until the process exits); nothing is allocated.
+ *   - Grids: the boundary conditions ibm_setup_geometry accepts (x periodic,
+ *     or inflow at -x with a convective outflow at +x, whose inflow face
+ *     value inflow[0] enters the divergence of the first cells as it does in
+ *     ibm_diagnostics; z periodic).
  *   - Limit: grids of at most 134,217,728 cells; larger ones return
- *     IBM_E_INVALID with a message.
+ *     IBM_E_INVALID with a message (checked factor by factor, so no size
+ *     overflows).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture on the device.

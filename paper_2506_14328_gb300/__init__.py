@@ -26,19 +26,19 @@ STATUS_NAMES = {0: "IBM_OK", -1: "IBM_E_INVALID", -2: "IBM_E_CUDA", -3: "IBM_E_N
                 -5: "IBM_E_DIVERGED", -6: "IBM_E_TIMEOUT", -7: "IBM_E_STATE"}
 
 # every symbol the header declares
-EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_geometry", "ibm_weights_bytes",
+EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_geometry", "ibm_weights_bytes", "ibm_weights_bytes_moving",
             "ibm_build_weights", "ibm_step", "ibm_project", "ibm_poisson", "ibm_projection_bytes",
             "ibm_set_projection", "ibm_wall_shear", "ibm_diagnostics",
             "ibm_get_classification", "ibm_get_weights", "ibm_state_bytes", "ibm_export_state",
             "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_diagnostics_noalloc",
-            "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_set_own_fft", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
+            "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_set_own_fft", "ibm_set_tridiag_form", "ibm_selftest_conversions", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
             "ibm_batch_destroy", "ibm_destroy")
 
 
 class ibm_grid_desc(C.Structure):
     _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3), ("origin", C.c_double * 3),
                 ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3), ("precision", C.c_int),
-                ("inflow", C.c_double * 3)]
+                ("inflow", C.c_double * 3), ("y_faces", C.POINTER(C.c_double))]
 
 
 class ibm_geom_desc(C.Structure):
@@ -53,7 +53,8 @@ class ibm_buffers(C.Structure):
 class ibm_physics(C.Structure):
     _fields_ = [("nu", C.c_double), ("dt", C.c_double), ("g", C.c_double * 3), ("bmode", C.c_int),
                 ("flow_mode", C.c_int), ("target_flux", C.c_double), ("wall_u", C.c_double * 3),
-                ("no_ibm", C.c_int), ("body_force", C.c_int), ("g_amp", C.c_double * 3), ("g_freq", C.c_double)]
+                ("no_ibm", C.c_int), ("body_force", C.c_int), ("g_amp", C.c_double * 3), ("g_freq", C.c_double),
+                ("body_u", C.c_double * 3), ("body_omega", C.c_double)]
 
 
 class ibm_diag(C.Structure):
@@ -84,6 +85,7 @@ def _load() -> C.CDLL:
         "ibm_workspace_bytes": ([P(ibm_grid_desc), P(C.c_size_t)], C.c_int),
         "ibm_setup_geometry": ([P(ibm_grid_desc), P(ibm_geom_desc), P(ibm_buffers), C.c_void_p, P(C.c_void_p)], C.c_int),
         "ibm_weights_bytes": ([C.c_void_p, P(C.c_size_t)], C.c_int),
+        "ibm_weights_bytes_moving": ([C.c_void_p, P(C.c_size_t)], C.c_int),
         "ibm_build_weights": ([C.c_void_p, P(ibm_physics), C.c_void_p, C.c_size_t], C.c_int),
         "ibm_step": ([C.c_void_p, C.c_int, C.c_uint], C.c_int),
         "ibm_project": ([C.c_void_p], C.c_int),
@@ -107,6 +109,8 @@ def _load() -> C.CDLL:
         "ibm_get_tiles": ([C.c_void_p, P(C.c_int), P(C.c_int), P(C.c_int)], C.c_int),
         "ibm_set_momentum_tma": ([C.c_void_p, C.c_int], C.c_int),
         "ibm_set_own_fft": ([C.c_void_p, C.c_int, P(C.c_int)], C.c_int),
+        "ibm_set_tridiag_form": ([C.c_void_p, C.c_int], C.c_int),
+        "ibm_selftest_conversions": ([C.c_longlong, P(C.c_longlong)], C.c_int),
         "ibm_batch_create": ([C.c_void_p, P(C.c_void_p)], C.c_int),
         "ibm_batch_set": ([C.c_void_p, P(C.c_void_p), P(C.c_int), C.c_int], C.c_int),
         "ibm_batch_run": ([C.c_void_p], C.c_int),
@@ -152,6 +156,12 @@ def ibm_setup_geometry(grid: ibm_grid_desc, geom: ibm_geom_desc, buffers: ibm_bu
 def ibm_weights_bytes(h: int) -> int:
     b = C.c_size_t(0)
     _check(lib.ibm_weights_bytes(C.c_void_p(h), C.byref(b)), "ibm_weights_bytes")
+    return b.value
+
+
+def ibm_weights_bytes_moving(h: int) -> int:
+    b = C.c_size_t(0)
+    _check(lib.ibm_weights_bytes_moving(C.c_void_p(h), C.byref(b)), "ibm_weights_bytes_moving")
     return b.value
 
 
@@ -277,6 +287,16 @@ def ibm_set_own_fft(h: int, mode: int) -> bool:
     own = C.c_int(0)
     _check(lib.ibm_set_own_fft(C.c_void_p(h), int(mode), C.byref(own)), "ibm_set_own_fft")
     return bool(own.value)
+
+
+def ibm_set_tridiag_form(h: int, form: int):
+    _check(lib.ibm_set_tridiag_form(C.c_void_p(h), int(form)), "ibm_set_tridiag_form")
+
+
+def ibm_selftest_conversions(n: int) -> int:
+    bad = C.c_longlong(0)
+    _check(lib.ibm_selftest_conversions(int(n), C.byref(bad)), "ibm_selftest_conversions")
+    return bad.value
 
 
 def ibm_batch_create(stream: int) -> int:

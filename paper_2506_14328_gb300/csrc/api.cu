@@ -45,7 +45,66 @@ ibm_status check_grid(const ibm_grid_desc* d) {
     for (int b : {d->bc_lo[1], d->bc_hi[1]})
         if (b != IBM_BC_NOSLIP && b != IBM_BC_FREESLIP)
             return ibm_set_error(IBM_E_UNSUPPORTED, "y faces must be no-slip or free-slip walls in this build");
+    if (d->y_faces) {
+        const double* yf = d->y_faces;
+        for (int j = 0; j <= d->n[1]; ++j)
+            if (!std::isfinite(yf[j]) || (j > 0 && !(yf[j] > yf[j - 1])))
+                return ibm_set_error(IBM_E_INVALID, "y_faces: n[1] + 1 finite, strictly increasing heights");
+        const double tol = 1e-12 * d->L[1];
+        if (std::fabs(yf[0] - d->origin[1]) > tol || std::fabs(yf[d->n[1]] - d->origin[1] - d->L[1]) > tol)
+            return ibm_set_error(IBM_E_INVALID, "y_faces must span the box from origin[1] to origin[1] + L[1]");
+    }
     return IBM_OK;
+}
+
+// The per-row tables of a stretched wall-normal grid (reading R23; layout YT_* in common.cuh).
+std::vector<double> y_tables(const ibm_grid_desc* d) {
+    const int ny = d->n[1];
+    const int S = ny + 1;
+    const double* yf = d->y_faces;
+    std::vector<double> t((size_t)YT_N * S, 0.0);
+    auto at = [&](int k, int j) -> double& { return t[(size_t)k * S + j]; };
+    std::vector<double> yc(ny), dyc(ny), dup(ny), hc(ny + 1);
+    for (int j = 0; j < ny; ++j) {
+        yc[j] = 0.5 * (yf[j] + yf[j + 1]);
+        dyc[j] = yf[j + 1] - yf[j];
+    }
+    for (int j = 0; j < ny; ++j) dup[j] = j + 1 < ny ? dyc[j + 1] : dyc[ny - 1];
+    // centres with the mirror ghosts past the walls
+    std::vector<double> ext(ny + 2);
+    ext[0] = 2.0 * yf[0] - yc[0];
+    for (int j = 0; j < ny; ++j) ext[j + 1] = yc[j];
+    ext[ny + 1] = 2.0 * yf[ny] - yc[ny - 1];
+    for (int j = 0; j <= ny; ++j) hc[j] = ext[j + 1] - ext[j];
+    // the symmetric, unit off-diagonal form of the Poisson rows: s_{j-1} s_j = hc_j
+    std::vector<double> sj(ny);
+    sj[0] = std::sqrt(hc[1]);
+    for (int j = 1; j < ny; ++j) sj[j] = hc[j] / sj[j - 1];
+    for (int j = 0; j < ny; ++j) {
+        at(YT_YC, j) = yc[j];
+        at(YT_YF, j) = yf[j + 1];
+        at(YT_DYC, j) = dyc[j];
+        at(YT_IDYC, j) = 1.0 / dyc[j];
+        at(YT_IHV, j) = 1.0 / (j + 1 < ny ? hc[j + 1] : dyc[ny - 1]);
+        at(YT_ALO, j) = dup[j] / (dyc[j] + dup[j]);
+        at(YT_AHI, j) = dyc[j] / (dyc[j] + dup[j]);
+        const double hm = hc[j], hp = hc[j + 1];
+        at(YT_DCM, j) = 2.0 / (hm * (hm + hp));
+        at(YT_DC0, j) = -2.0 / (hm * hp);
+        at(YT_DCP, j) = 2.0 / (hp * (hm + hp));
+        const double vm = dyc[j], vp = dup[j];
+        at(YT_DVM, j) = 2.0 / (vm * (vm + vp));
+        at(YT_DV0, j) = -2.0 / (vm * vp);
+        at(YT_DVP, j) = 2.0 / (vp * (vm + vp));
+        at(YT_IVSP, j) = 1.0 / std::min(dyc[j], dup[j]);
+        const double e_lo = j > 0 ? 1.0 / hc[j] : 0.0, e_hi = j + 1 < ny ? 1.0 / hc[j + 1] : 0.0;
+        at(YT_PIN, j) = sj[j] * dyc[j];
+        at(YT_POUT, j) = sj[j];
+        at(YT_PBE, j) = -sj[j] * sj[j] * (e_lo + e_hi);
+        at(YT_PBK, j) = sj[j] * sj[j] * dyc[j];
+    }
+    for (int j = 0; j <= ny; ++j) at(YT_HC, j) = hc[j];
+    return t;
 }
 
 GridP make_gridp(const ibm_grid_desc* d) {
@@ -73,6 +132,8 @@ GridP make_gridp(const ibm_grid_desc* d) {
     g.sig_hi = d->bc_hi[1] == IBM_BC_NOSLIP ? -1.0 : 1.0;
     g.kzm = 32;             // replaced by momentum_default_kzm at setup
     g.kzd = 16;
+    g.ystr = d->y_faces != nullptr;
+    g.yt = nullptr;         // set once the workspace is carved
     return g;
 }
 
@@ -187,7 +248,9 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
     if (npart < 120 * 4) npart = 120 * 4;
     char* partials = take((size_t)npart * sizeof(double));
     char* scal = take(SCAL_N * sizeof(double));
+    char* ytab = g.ystr ? take((size_t)YT_N * (g.ny + 1) * sizeof(double)) : nullptr;
     if (h && base) {
+        h->ytab = (double*)ytab;
         h->mask = (uint8_t*)mask;
         h->velbits = (uint8_t*)velbits;
         for (int c = 0; c < 3; ++c) {
@@ -216,7 +279,11 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
     return off;
 }
 
-size_t weights_layout(ibm_solver* h, char* base) {
+// IBM points per component a translating body's weights buffer holds
+int moving_capacity(int count) { return count + count / 2 + 1024; }
+
+// cap: IBM points per component to lay out (the counts, or a moving body's capacities)
+size_t weights_layout(ibm_solver* h, char* base, const int* cap) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -224,7 +291,7 @@ size_t weights_layout(ibm_solver* h, char* base) {
         return p;
     };
     for (int c = 0; c < 3; ++c) {
-        size_t n = (size_t)h->counts[c];
+        size_t n = (size_t)cap[c];
         char* idx = take(n * sizeof(int));
         char* lam = take(n * sizeof(double));
         char* src = take(n * sizeof(double));
@@ -249,6 +316,27 @@ void drop_graph(ibm_solver* h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
     h->graph_ready = false;
+}
+
+// A translating body at the start of a full step (reading R24): the level set with the centre at
+// its place at t_n, the points classified again (those that turn fluid take the body velocity),
+// the IBM lists, weights and stage coefficients rebuilt.  Blocking (reads the new counts back).
+ibm_status body_advance(ibm_solver* h) {
+    const double t = (double)h->steps * h->phys.dt;
+    const int nd = h->geo.kind == IBM_GEOM_CYLINDER ? 2 : 3;
+    for (int d = 0; d < nd; ++d) h->geo.p[d] = h->geo0[d] + h->body.ub[d] * t;
+    ibm_status st = geom_classify(h, true);
+    if (st != IBM_OK) return st;
+    for (int c = 0; c < 3; ++c)
+        if (h->counts[c] > h->cap[c]) {
+            h->failed = true;
+            return ibm_set_error(IBM_E_NOMEM, "the moving body's IBM points outgrew the weights buffer (component " +
+                                                  std::to_string(c) + ": " + std::to_string(h->counts[c]) + " > " +
+                                                  std::to_string(h->cap[c]) + ")");
+        }
+    st = geom_build_lists_and_weights(h);
+    if (st == IBM_OK) st = geom_stage_coefficients(h);
+    return st;
 }
 
 }  // namespace
@@ -361,6 +449,7 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     h->gp = g;
     h->geo.kind = kind;
     for (int q = 0; q < 8; ++q) h->geo.p[q] = q < geom->nparam ? geom->param[q] : 0.0;
+    for (int q = 0; q < 8; ++q) h->geo0[q] = h->geo.p[q];
     h->geo.ntubes = h->geo.npts = 0;
     std::memset(h->geo.tube, 0, sizeof(h->geo.tube));
     if (kind == IBM_GEOM_TUBES) {
@@ -389,6 +478,18 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
     }
     carve(h, g, h->prec, work, (char*)buffers->work);
     h->fft_work_bytes = work;
+    h->grid.y_faces = nullptr;   // the caller's array is not kept
+    if (g.ystr) {
+        h->ytab_host = y_tables(grid);
+        cudaError_t e = cudaMemcpyAsync(h->ytab, h->ytab_host.data(), h->ytab_host.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            ibm_destroy(h);
+            return ibm_set_error(IBM_E_CUDA, std::string("y tables: ") + cudaGetErrorString(e));
+        }
+        h->gp.yt = h->ytab;
+    }
     momentum_prepare(h);
     h->gp.kzm = momentum_default_kzm(h->gp, h->prec, momentum_uses_tma(h));
     bool plan_ok = true;
@@ -418,7 +519,17 @@ ibm_status ibm_weights_bytes(const ibm_solver* h, size_t* bytes) {
     ibm_status st = check_handle(h);
     if (st != IBM_OK) return st;
     if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");
-    *bytes = weights_layout(const_cast<ibm_solver*>(h), nullptr);
+    *bytes = weights_layout(const_cast<ibm_solver*>(h), nullptr, h->counts);
+    return IBM_OK;
+}
+
+ibm_status ibm_weights_bytes_moving(const ibm_solver* h, size_t* bytes) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (!bytes) return ibm_set_error(IBM_E_INVALID, "bytes is NULL");
+    int cap[3];
+    for (int c = 0; c < 3; ++c) cap[c] = moving_capacity(h->counts[c]);
+    *bytes = weights_layout(const_cast<ibm_solver*>(h), nullptr, cap);
     return IBM_OK;
 }
 
@@ -437,12 +548,39 @@ ibm_status ibm_build_weights(ibm_solver* h, const ibm_physics* phys, void* weigh
     if (phys->flow_mode == IBM_FLOW_CONST_FLUX && !h->gp.xper)
         return ibm_set_error(IBM_E_INVALID, "a constant flow rate needs a periodic x direction");
     if ((uintptr_t)weights % ALIGN) return ibm_set_error(IBM_E_INVALID, "weights must be 256-byte aligned");
-    size_t need = weights_layout(h, nullptr);
+    // a moving body (reading R24)
+    const bool translating = phys->body_u[0] != 0.0 || phys->body_u[1] != 0.0 || phys->body_u[2] != 0.0;
+    const bool rotating = phys->body_omega != 0.0;
+    for (double v : {phys->body_u[0], phys->body_u[1], phys->body_u[2], phys->body_omega})
+        if (!std::isfinite(v)) return ibm_set_error(IBM_E_INVALID, "body_u and body_omega must be finite");
+    if (translating || rotating) {
+        const int kind = h->geo.kind;
+        if (translating && rotating) return ibm_set_error(IBM_E_UNSUPPORTED, "a body that translates and rotates");
+        if (translating && kind != IBM_GEOM_CYLINDER && kind != IBM_GEOM_SPHERE)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "a translating body is a cylinder or a sphere");
+        if (rotating && kind != IBM_GEOM_CYLINDER)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "a rotating body is a cylinder about its own axis");
+        if (!h->gp.xper || h->gp.ystr || phys->flow_mode != IBM_FLOW_FORCED || phys->body_force)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "a moving body needs a periodic x, a uniform y, the forced flow "
+                                                    "and no body-force accounting");
+    }
+    int cap[3];
+    for (int c = 0; c < 3; ++c) cap[c] = translating ? moving_capacity(h->counts[c]) : h->counts[c];
+    size_t need = weights_layout(h, nullptr, cap);
     if (weights_bytes < need) return ibm_set_error(IBM_E_NOMEM, "weights buffer too small: need " + std::to_string(need));
     drop_graph(h);
     if (phys->body_force != 0 && phys->body_force != 1) return ibm_set_error(IBM_E_INVALID, "body_force is 0 or 1");
+    if (phys->body_force && h->gp.ystr)
+        return ibm_set_error(IBM_E_UNSUPPORTED, "the force accounting is written for a uniform y (a stretched "
+                                                "second difference does not conserve momentum)");
     h->phys = *phys;
-    weights_layout(h, (char*)weights);
+    for (int c = 0; c < 3; ++c) h->cap[c] = cap[c];
+    weights_layout(h, (char*)weights, cap);
+    h->body.kind = translating ? 1 : (rotating ? 2 : 0);
+    for (int c = 0; c < 3; ++c) h->body.ub[c] = phys->body_u[c];
+    h->body.om = phys->body_omega;
+    h->body.xc = h->geo0[0];
+    h->body.yc = h->geo0[1];
     {   // new physics: the force sums start again
         cudaError_t e = cudaMemsetAsync(h->scal + SCAL_FORCE, 0, (SCAL_N - SCAL_FORCE) * sizeof(double), h->stream);
         if (e != cudaSuccess) return ibm_set_error(IBM_E_CUDA, cudaGetErrorString(e));
@@ -468,6 +606,8 @@ ibm_status ibm_step(ibm_solver* h, int nsteps, unsigned flags) {
     }
     if (flags & IBM_STEP_GRAPH) {
         if (h->timing) return ibm_set_error(IBM_E_STATE, "timing is not available in graph mode");
+        if (h->body.kind == 1)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "a translating body is classified again every step: no graph mode");
         if (h->proj_mode == IBM_PROJ_MASKED)
             return ibm_set_error(IBM_E_UNSUPPORTED, "the masked projection reads back its inner products: no graph mode");
         if (h->phys.g_amp[0] != 0.0 || h->phys.g_amp[1] != 0.0 || h->phys.g_amp[2] != 0.0)
@@ -495,6 +635,10 @@ ibm_status ibm_step(ibm_solver* h, int nsteps, unsigned flags) {
         return IBM_OK;
     }
     for (int n = 0; n < nsteps; ++n) {
+        if (h->body.kind == 1) {
+            st = body_advance(h);
+            if (st != IBM_OK) return st;
+        }
         for (int k = 0; k < 3; ++k) {
             st = run_substage(h, k, false);
             if (st != IBM_OK) return st;
@@ -533,7 +677,9 @@ ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
         }
     }
     const GridP& g = h->gp;
-    double dV = g.dx * g.dy * (g.ndim == 3 ? g.dz : 1.0);
+    // a stretched y: the sums carry each row's cell height and the velocity maxima are
+    // already divided by their spacings (v's per row)
+    double dV = g.dx * (g.ystr ? 1.0 : g.dy) * (g.ndim == 3 ? g.dz : 1.0);
     const double* s = r + 4;
     std::memset(out, 0, sizeof(*out));
     out->div_l2 = std::sqrt(s[0] / (double)g.N);
@@ -541,7 +687,7 @@ ibm_status ibm_diagnostics(ibm_solver* h, ibm_diag* out) {
     double d[3] = {g.dx, g.dy, g.dz};
     double cfl = 0.0;
     for (int c = 0; c < g.ncomp; ++c) {
-        cfl += s[2 + c] / d[c];
+        cfl += g.ystr ? s[2 + c] : s[2 + c] / d[c];
         out->flux[c] = s[5 + c] * dV;
         out->ke += 0.5 * s[8 + c] * dV;
     }
@@ -594,6 +740,7 @@ ibm_status ibm_set_projection(ibm_solver* h, int mode, double tol, int maxit, vo
         return IBM_OK;
     }
     if (!(tol > 0.0) || !std::isfinite(tol) || maxit < 1) return ibm_set_error(IBM_E_INVALID, "need tol > 0 and maxit >= 1");
+    if (h->gp.ystr) return ibm_set_error(IBM_E_UNSUPPORTED, "the masked projection is written for a uniform y");
     size_t need = 0;
     ibm_projection_bytes(h, &need);
     if (!buffer || (uintptr_t)buffer % ALIGN) return ibm_set_error(IBM_E_INVALID, "buffer must be 256-byte aligned");
@@ -790,6 +937,20 @@ ibm_status ibm_set_own_fft(ibm_solver* h, int mode, int* own) {
     return st;
 }
 
+ibm_status ibm_set_tridiag_form(ibm_solver* h, int form) {
+    ibm_status st = check_handle(h);
+    if (st != IBM_OK) return st;
+    if (form < 0 || form > 2) return ibm_set_error(IBM_E_INVALID, "form is 0, 1 or 2");
+    drop_graph(h);
+    h->tri_form = form;
+    return IBM_OK;
+}
+
+ibm_status ibm_selftest_conversions(long long n, long long* mismatches) {
+    if (n < 0 || !mismatches) return ibm_set_error(IBM_E_INVALID, "n >= 0 and a mismatch counter");
+    return selftest_conversions(n, mismatches);
+}
+
 ibm_status ibm_launch_count(const ibm_solver* h, long long* count) {
     if (!h || !count) return ibm_set_error(IBM_E_INVALID, "NULL argument");
     *count = h->launches;
@@ -834,6 +995,8 @@ ibm_status ibm_batch_set(ibm_batch* b, ibm_solver* const* members, const int* st
             return ibm_set_error(IBM_E_UNSUPPORTED, "a member uses the masked projection (no graph capture)");
         if (members[q]->phys.g_amp[0] != 0.0 || members[q]->phys.g_amp[1] != 0.0 || members[q]->phys.g_amp[2] != 0.0)
             return ibm_set_error(IBM_E_UNSUPPORTED, "a member has a time-periodic forcing (no graph capture)");
+        if (members[q]->body.kind == 1)
+            return ibm_set_error(IBM_E_UNSUPPORTED, "a member has a translating body (no graph capture)");
         if (steps[q] < 0) return ibm_set_error(IBM_E_INVALID, "negative step count");
     }
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }

@@ -29,7 +29,38 @@ struct GridP {
     double sig_lo, sig_hi;  // tangential ghost factor at the y walls (-1 no-slip, +1 free-slip)
     int kzm;                // z planes one momentum block marches (autotuned)
     int kzd;                // z planes one divergence / correction block marches (autotuned)
+    int ystr;               // 1: stretched wall-normal grid, per-row tables at yt
+    const double* yt;       // device: YT_N tables of ny + 1 doubles (ytab(g, YT_*, j)), or NULL
 };
+
+// Per-row tables of a stretched wall-normal grid (reading R23), computed on the host in
+// FP64 from the ny + 1 face heights yf and stored one after another, ny + 1 doubles each.
+// hc[j] is the distance from centre j-1 to centre j (mirror ghosts of the first and last
+// centres past the walls), dyc the cell heights, dyc_up[j] the height of the cell above
+// (the last cell's own at the top).
+enum {
+    YT_YC = 0,     // cell-centre height (u, w, p rows)
+    YT_YF,         // v-face height yf[j + 1]
+    YT_DYC,        // cell height
+    YT_HC,         // hc[j], j = 0..ny
+    YT_IDYC,       // 1 / dyc
+    YT_IHV,        // 1 / (distance between the centres on either side of v face j; dyc at the top)
+    YT_ALO,        // face above row j: weight of row j in the linear interpolation of a
+    YT_AHI,        //   cell-centred value (dyc_up / (dyc + dyc_up)), and of row j + 1
+    YT_DCM,        // uneven second difference at centre rows: d(-1), d(0), d(+1)
+    YT_DC0,
+    YT_DCP,
+    YT_DVM,        // ... at v rows (face spacing)
+    YT_DV0,
+    YT_DVP,
+    YT_IVSP,       // 1 / min(dyc, dyc_up): v's CFL spacing
+    YT_PIN,        // Poisson: input factor s_j dyc_j of the symmetric, unit off-diagonal form
+    YT_POUT,       // Poisson: output factor s_j
+    YT_PBE,        // Poisson: diagonal -s_j^2 (1/hc_j + 1/hc_{j+1}) (wall ends: one term)
+    YT_PBK,        // Poisson: s_j^2 dyc_j, the factor of K on the diagonal
+    YT_N
+};
+__host__ __device__ __forceinline__ double ytab(const GridP& g, int t, int j) { return g.yt[(long long)t * (g.ny + 1) + j]; }
 
 // Union of tubes (IBM_GEOM_TUBES): polylines of (x, y, z, r) points, at most
 // TUBE_MAX tubes of TUBE_PTS points; passed by value with the other parameters.
@@ -42,6 +73,22 @@ struct GeomP {
     double tube[TUBE_MAX * TUBE_PTS * 4];
     const double* sdf[3];   // IBM_GEOM_SAMPLED: phi of each component at its points (device)
 };
+
+// A moving body (reading R24): kind 0 at rest, 1 translating with ub, 2 a cylinder rotating
+// about its axis (xc, yc) at the rate om.  Its points hold bodyvel(); the momentum operator
+// reads them as that velocity.
+struct BodyP {
+    int kind;
+    double ub[3];
+    double om, xc, yc;
+};
+
+// velocity of the body at the point of component c with coordinates (x, y)
+__host__ __device__ __forceinline__ double bodyvel(const BodyP& b, int c, double x, double y) {
+    if (b.kind == 1) return b.ub[c];
+    if (b.kind == 2) return c == 0 ? -b.om * (y - b.yc) : (c == 1 ? b.om * (x - b.xc) : 0.0);
+    return 0.0;
+}
 
 // The IBM coefficients of one stage for one component: indexed by list
 // position; segoff gives the list position of the first IBM point of every
@@ -323,6 +370,7 @@ struct ibm_solver {
     uint8_t* use32 = nullptr;      // per (kz, kx) system: 1 = FP32 sweep
     int* sys_order = nullptr;      // systems, FP64 ones first
     int n64 = 0;                   // number of FP64 systems
+    int tri_form = 0;              // ibm_set_tridiag_form: 0 automatic, 1 warp, 2 thread per FP64 system
     void* dtemp = nullptr;
     void* fft_work = nullptr;
     double* partials = nullptr;
@@ -331,7 +379,14 @@ struct ibm_solver {
     int npartials = 0;
 
     int counts[3] = {0, 0, 0};
+    int cap[3] = {0, 0, 0};    // IBM points the weights buffer holds per component (counts, or
+                               // 3 counts / 2 + 1024 for a translating body)
+    BodyP body = {0, {0.0, 0.0, 0.0}, 0.0, 0.0, 0.0};
+    double geo0[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // geometry parameters at t = 0 (a translating body)
     int nfaces[2] = {0, 0};    // inflow/outflow x: fluid inflow and outflow faces
+    double aface[2] = {0, 0};  // ... their areas over dx dz: counts, or the summed cell heights (stretched y)
+    std::vector<double> ytab_host;   // stretched y: the YT_N per-row tables (also in the workspace)
+    double* ytab = nullptr;
 
     // weights
     bool weights_ready = false;
@@ -397,7 +452,7 @@ inline IbmStage<T> stage_coefs(const ibm_solver* h, int k) {
 ibm_status ibm_set_error(ibm_status st, const std::string& msg);
 
 // geometry.cu
-ibm_status geom_classify(ibm_solver* h);
+ibm_status geom_classify(ibm_solver* h, bool fresh_fill = false);   // fresh_fill: points that turn fluid take the body velocity
 ibm_status geom_build_lists_and_weights(ibm_solver* h);
 ibm_status geom_stage_coefficients(ibm_solver* h);
 ibm_status geom_pivots(ibm_solver* h);
@@ -419,7 +474,8 @@ bool momentum_uses_tma(const ibm_solver* h);
 ibm_status run_project(ibm_solver* h);
 ibm_status run_poisson(ibm_solver* h, void* rhs_inout);
 ibm_status run_diagnostics(ibm_solver* h, double* out);   // SCAL_N doubles
-ibm_status poisson_prepare(ibm_solver* h);   // the own row-FFT plan and tables; Neumann x: the DCT twiddles
+ibm_status poisson_prepare(ibm_solver* h);
+ibm_status selftest_conversions(long long n, long long* bad);   // legacy default stream, blocking   // the own row-FFT plan and tables; Neumann x: the DCT twiddles
 
 // timing hooks used by both
 void timer_begin(ibm_solver* h, const char* name, cudaEvent_t* ev);

@@ -69,8 +69,10 @@ __device__ double phi_at(const GeomP& g, double x, double y, double z) {
     }
 }
 
-// coordinate of component c (0..2; 3 = cell centre) of index idx along direction d
+// coordinate of component c (0..2; 3 = cell centre) of index idx along direction d; on a
+// stretched y the tabulated centre or face height
 __device__ __forceinline__ double coord(const GridP& g, int d, int idx, int c) {
+    if (d == 1 && g.ystr) return ytab(g, c == 1 ? YT_YF : YT_YC, idx);
     double off = (d == c) ? 1.0 : 0.5;
     double o = d == 0 ? g.ox : (d == 1 ? g.oy : g.oz);
     double D = d == 0 ? g.dx : (d == 1 ? g.dy : g.dz);
@@ -112,6 +114,20 @@ __global__ void k_classify_vel(GridP g, GeomP geo, uint8_t* __restrict__ velbits
         if (i == g.nx - 1 && phi_at(geo, coord(g, 0, i, 0), yy, zz) < 0.0) b |= IBM_MASK_FACE;
     }
     velbits[id] = b;
+}
+
+// A translating body at the start of a step: velocity points that turn fluid (internal in the new
+// classification vb, not in the previous mask) take the body velocity.
+template <typename T>
+__global__ void k_fresh_fill(GridP g, const uint8_t* __restrict__ vb, const uint8_t* __restrict__ mask, BodyP body,
+                             T* __restrict__ u0, T* __restrict__ u1, T* __restrict__ u2) {
+    long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= g.N) return;
+    const uint8_t fresh = vb[id] & (uint8_t)~mask[id] & 7u;
+    if (!fresh) return;
+    T* u[3] = {u0, u1, u2};
+    for (int c = 0; c < g.ncomp; ++c)
+        if ((fresh >> c) & 1u) u[c][id] = (T)body.ub[c];
 }
 
 __device__ __forceinline__ bool vel_internal(const GridP& g, const uint8_t* vb, int c, int i, int j, int k) {
@@ -358,6 +374,7 @@ struct WeightArgs {
     double nu;
     double wall_u[3];
     int no_ibm;
+    BodyP body;      // a moving body: the body-frame source (below)
 };
 
 __global__ void k_weights(GridP g, GeomP geo, WeightArgs a, const uint8_t* __restrict__ mask) {
@@ -374,8 +391,18 @@ __global__ void k_weights(GridP g, GeomP geo, WeightArgs a, const uint8_t* __res
         double P[3] = {coord(g, 0, i, c), coord(g, 1, j, c), coord(g, 2, k, c)};
         double phiP = sampled ? geo.sdf[c][lin] : phi_at(geo, P[0], P[1], P[2]);
         for (int d = 0; d < g.ndim; ++d) {
-            double D = d == 0 ? g.dx : (d == 1 ? g.dy : g.dz);
             for (int s = 1; s >= -1; s -= 2) {
+                double D = d == 0 ? g.dx : (d == 1 ? g.dy : g.dz);
+                // a stretched y arm (reading R23): the distance to this neighbour on the
+                // component's own grid, and d(s) = 2 / (D (D_- + D_+)) in place of 1 / D^2
+                double Dsum = 2.0 * D;
+                if (d == 1 && g.ystr) {
+                    const double hm = ytab(g, c == 1 ? YT_DYC : YT_HC, j);
+                    const double hp = c == 1 ? (j + 1 < g.ny ? ytab(g, YT_DYC, j + 1) : ytab(g, YT_DYC, g.ny - 1))
+                                             : ytab(g, YT_HC, j + 1);
+                    D = s > 0 ? hp : hm;
+                    Dsum = hm + hp;
+                }
                 int ii = i, jj = j, kk = k;
                 if (!neighbour(g, d, s, ii, jj, kk)) continue;
                 if (bface(g, c, ii, jj)) continue;
@@ -394,8 +421,24 @@ __global__ void k_weights(GridP g, GeomP geo, WeightArgs a, const uint8_t* __res
                     if (dl < 0.0) dl = delta_bisect(geo, P, d, s, D);
                 }
                 dl = fmin(fmax(dl, 1e-12 * D), D);
-                lam = lam + a.nu * (D - dl) / (dl * D * D);
-                src = src + a.nu * (a.wall_u[c] * wall_factor(geo.kind, d, s)) / (dl * D);
+                if (d == 1 && g.ystr) {
+                    lam = lam + a.nu * 2.0 * (D - dl) / (dl * D * Dsum);
+                    src = src + a.nu * (a.wall_u[c] * wall_factor(geo.kind, d, s)) * 2.0 / (dl * Dsum);
+                } else if (a.body.kind != 0) {
+                    // a moving body: the wall velocity at the crossing X = P + s delta e_d, in the
+                    // body-frame form that pairs with the operator reading the body's point Q as
+                    // its own velocity: nu (U(X) / (delta D) - U(Q) / D^2) per crossed arm (for a
+                    // translating body lambda_arm U_b, so the wall term is -lambda (w - U_b))
+                    double X[3] = {P[0], P[1], P[2]};
+                    X[d] = X[d] + s * dl;
+                    const double uw = bodyvel(a.body, c, X[0], X[1]);
+                    const double uq = bodyvel(a.body, c, coord(g, 0, ii, c), coord(g, 1, jj, c));
+                    lam = lam + a.nu * (D - dl) / (dl * D * D);
+                    src = src + a.nu * (uw / (dl * D) - uq / (D * D));
+                } else {
+                    lam = lam + a.nu * (D - dl) / (dl * D * D);
+                    src = src + a.nu * (a.wall_u[c] * wall_factor(geo.kind, d, s)) / (dl * D);
+                }
             }
         }
     }
@@ -448,19 +491,21 @@ __global__ void k_coefs(CoefArgs<T> a) {
 // Flux control response: sum over the u IBM points of (1 - beta_k) and the
 // number of internal u points (the exact beta of non-IBM points is 1).
 __global__ void k_flux_response(GridP g, const uint8_t* __restrict__ mask, const double* __restrict__ lam_u,
-                                int count_u, double ck0, double ck1, double ck2, int bmode, double* out) {
+                                const int* __restrict__ idx_u, int count_u, double ck0, double ck1, double ck2, int bmode, double* out) {
     __shared__ double sh[4][32];
     double acc[4] = {0, 0, 0, 0};
     long long stride = (long long)gridDim.x * blockDim.x;
+    // a stretched y weighs each point by its cell height (the volumes differ by row)
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += stride)
-        acc[0] += (mask[id] & IBM_MASK_U) ? 1.0 : 0.0;
+        acc[0] += (mask[id] & IBM_MASK_U) ? (g.ystr ? ytab(g, YT_DYC, (int)((id / g.nx) % g.ny)) : 1.0) : 0.0;
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < count_u; m += stride) {
         double l = lam_u[m];
+        const double wy = g.ystr ? ytab(g, YT_DYC, (int)((idx_u[m] / g.nx) % g.ny)) : 1.0;
         double ck[3] = {ck0, ck1, ck2};
         for (int st = 0; st < 3; ++st) {
             double x = bmode == IBM_B_EXPLICIT ? 0.0 : l * ck[st];
             double B = B_of_x(x, bmode);
-            acc[1 + st] += 1.0 - 1.0 / (B + x);
+            acc[1 + st] += (1.0 - 1.0 / (B + x)) * wy;
         }
     }
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -487,6 +532,16 @@ __global__ void k_face_count(GridP g, const uint8_t* __restrict__ mask, int* __r
     if (mask[base + g.nx - 1] & IBM_MASK_FACE) atomicAdd(out + 1, 1);
 }
 
+// Stretched y: the summed cell heights of the fluid inflow (out[0]) and outflow (out[1]) faces
+__global__ void k_face_area(GridP g, const uint8_t* __restrict__ mask, double* __restrict__ out) {
+    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;   // row (j, k)
+    if (r >= (long long)g.ny * g.nz) return;
+    const long long base = r * g.nx;
+    const double A = ytab(g, YT_DYC, (int)(r % g.ny));
+    if (mask[base] & IBM_MASK_FACE) atomicAdd(out, A);
+    if (mask[base + g.nx - 1] & IBM_MASK_FACE) atomicAdd(out + 1, A);
+}
+
 // Thomas pivots of the y systems, one thread per (kz, kx)
 // ---------------------------------------------------------------------------
 __global__ void k_pivots(GridP g, double* __restrict__ piv, float* __restrict__ piv32, uint8_t* __restrict__ use32,
@@ -506,11 +561,16 @@ __global__ void k_pivots(GridP g, double* __restrict__ piv, float* __restrict__ 
     }
     double Kd = K * g.dy * g.dy;
     bool zero = (kx == 0 && kz == 0);
+    if (g.ystr) {     // the symmetric unit off-diagonal form: dominant when K s_j^2 dyc_j >= 1 in every row
+        double mn = 1e300;
+        for (int j = 0; j < g.ny; ++j) mn = fmin(mn, K * ytab(g, YT_PBK, j));
+        Kd = mn;
+    }
     use32[sys] = (!zero && Kd >= tau) ? 1 : 0;
     double wprev = 0.0;
     for (int j = 0; j < g.ny; ++j) {
         bool end = (j == 0 || j == g.ny - 1);
-        double b = (end ? -1.0 : -2.0) - Kd;
+        double b = g.ystr ? ytab(g, YT_PBE, j) - K * ytab(g, YT_PBK, j) : (end ? -1.0 : -2.0) - Kd;
         double w;
         if (j == 0) w = zero ? 0.0 : 1.0 / b;
         else w = 1.0 / (b - wprev);
@@ -537,7 +597,9 @@ __global__ void k_wall_shear(GridP g, GeomP geo, const int* __restrict__ idx, in
     if (j == 0) return;
     const int below = lin - g.nx;
     if (mask[below] & IBM_MASK_U) return;             // no wall below this point
-    const double D = g.dy;
+    // a stretched y: the arm below P and the step up to Q are the row's own centre distances
+    const double D = g.ystr ? ytab(g, YT_HC, j) : g.dy;
+    const double Dp = g.ystr ? ytab(g, YT_HC, j + 1) : g.dy;
     const double P[3] = {coord(g, 0, i, 0), coord(g, 1, j, 0), coord(g, 2, k, 0)};
     const bool sampled = geo.kind == IBM_GEOM_SAMPLED;
     const double phiP = sampled ? geo.sdf[0][lin] : phi_at(geo, P[0], P[1], P[2]);
@@ -556,8 +618,8 @@ __global__ void k_wall_shear(GridP g, GeomP geo, const int* __restrict__ idx, in
     double slope;
     if (j + 1 < g.ny && (mask[lin + g.nx] & IBM_MASK_U)) {
         const double uQ = (double)u[lin + g.nx];
-        const double a = dl + D;
-        slope = (uP * (a * a) - uQ * (dl * dl)) / (dl * D * a);
+        const double a = dl + Dp;
+        slope = (uP * (a * a) - uQ * (dl * dl)) / (dl * Dp * a);
     } else {
         slope = uP / dl;
     }
@@ -606,13 +668,24 @@ ibm_status geom_wall_shear(ibm_solver* h, double wavelength, double* tau_x, doub
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-ibm_status geom_classify(ibm_solver* h) {
+ibm_status geom_classify(ibm_solver* h, bool fresh_fill) {
     const GridP& g = h->gp;
     int nb = (int)((g.N + 255) / 256);
     cudaEvent_t t;
     timer_begin(h, "classify", &t);
     k_classify_vel<<<nb, 256, 0, h->stream>>>(g, h->geo, h->velbits);
     IBM_LAUNCH_CHECK();
+    if (fresh_fill) {     // before the new mask replaces the previous one
+        if (h->prec == IBM_FP64)
+            k_fresh_fill<double><<<nb, 256, 0, h->stream>>>(g, h->velbits, h->mask, h->body, (double*)h->buf.u[0],
+                                                            (double*)h->buf.u[1],
+                                                            (double*)h->buf.u[g.ncomp == 3 ? 2 : 0]);
+        else
+            k_fresh_fill<float><<<nb, 256, 0, h->stream>>>(g, h->velbits, h->mask, h->body, (float*)h->buf.u[0],
+                                                           (float*)h->buf.u[1],
+                                                           (float*)h->buf.u[g.ncomp == 3 ? 2 : 0]);
+        IBM_LAUNCH_CHECK();
+    }
     k_classify_final<<<nb, 256, 0, h->stream>>>(g, h->velbits, h->mask);
     IBM_LAUNCH_CHECK();
     timer_end(h, t, "classify");
@@ -641,6 +714,19 @@ ibm_status geom_classify(ibm_solver* h) {
     IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->nfaces[0] = faces[0];
     h->nfaces[1] = faces[1];
+    h->aface[0] = faces[0];
+    h->aface[1] = faces[1];
+    if (!g.xper && g.ystr) {           // faces of unequal height: their summed heights
+        double a[2] = {0.0, 0.0};
+        IBM_CUDA_TRY(cudaMemsetAsync(h->partials, 0, 2 * sizeof(double), h->stream));
+        const long long rows = (long long)g.ny * g.nz;
+        k_face_area<<<(int)((rows + 255) / 256), 256, 0, h->stream>>>(g, h->mask, h->partials);
+        IBM_LAUNCH_CHECK();
+        IBM_CUDA_TRY(cudaMemcpyAsync(a, h->partials, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        IBM_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        h->aface[0] = a[0];
+        h->aface[1] = a[1];
+    }
     return IBM_OK;
 }
 
@@ -663,6 +749,7 @@ ibm_status geom_build_lists_and_weights(ibm_solver* h) {
     }
     a.nu = h->phys.nu;
     a.no_ibm = h->phys.no_ibm;
+    a.body = h->body;
     k_weights<<<dim3((maxc + 127) / 128, 3), 128, 0, h->stream>>>(g, h->geo, a, h->mask);
     IBM_LAUNCH_CHECK();
     return IBM_OK;
@@ -697,7 +784,7 @@ ibm_status geom_stage_coefficients(ibm_solver* h) {
     // flux-control response S_k = c_k dt dV sum_internal beta_k
     const GridP& g = h->gp;
     int nb = 120;
-    k_flux_response<<<nb, 256, 0, h->stream>>>(g, h->mask, h->lam[0], h->counts[0], rkc[0] * h->phys.dt,
+    k_flux_response<<<nb, 256, 0, h->stream>>>(g, h->mask, h->lam[0], h->idx[0], h->counts[0], rkc[0] * h->phys.dt,
                                                rkc[1] * h->phys.dt, rkc[2] * h->phys.dt, h->phys.bmode, h->partials);
     IBM_LAUNCH_CHECK();
     std::vector<double> part(nb * 4);
@@ -707,7 +794,7 @@ ibm_status geom_stage_coefficients(ibm_solver* h) {
     double acc[4] = {0, 0, 0, 0};
     for (int b = 0; b < nb; ++b)
         for (int q = 0; q < 4; ++q) acc[q] += part[b * 4 + q];
-    double dV = g.dx * g.dy * (g.ndim == 3 ? g.dz : 1.0);
+    double dV = g.dx * (g.ystr ? 1.0 : g.dy) * (g.ndim == 3 ? g.dz : 1.0);   // stretched: dy in the sums
     for (int st = 0; st < 3; ++st) h->S[st] = rkc[st] * h->phys.dt * dV * (acc[0] - acc[1 + st]);
     return IBM_OK;
 }

@@ -555,6 +555,186 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
 }
 
 // ---------------------------------------------------------------------------
+// K3 in its general form: the update of k_momentum on a stretched wall-normal grid
+// (STR, reading R23) and/or with a moving body (BODY, reading R24).
+//   * STR: the y terms on uneven rows, from the per-row tables (ytab): the Laplacian's y
+//     part is the uneven three-point second difference of the point's own grid (centre rows
+//     for u and w, face rows for v); the convective y fluxes stay in flux form, u and w
+//     carried to a v face by linear interpolation between the centres on either side, v to a
+//     centre by the plain average, the flux difference divided by the point's own control
+//     height (the cell height for u and w, the centre distance across the face for v); v's
+//     pressure gradient is divided by the centre distance across its face.
+//   * BODY: the body's points (not internal, not a box face) are read as the body's velocity
+//     by the convective terms and the Laplacian alike, and hold it in u*; the wall source of
+//     the weights is then in its body-frame form (-lambda (w - U_b) for a translating body).
+// A 32 x 8 block covers the same 32 x 16 column and z chunk as k_momentum (so the flux
+// partials line up); each thread updates its two cells plane by plane, reading every
+// neighbour through the operator's rules straight from memory.
+// ---------------------------------------------------------------------------
+template <typename T, bool BODY>
+__device__ __forceinline__ T mom_op(const GridP& g, const T* __restrict__ f, const uint8_t* __restrict__ mask, int c,
+                                    int i, int j, int k, const StageP<T>& sp, const BodyP& body) {
+    int xk = 0, ii = i;
+    if (g.xper) ii = wrapi(i, g.nx);
+    else if (i < 0) { xk = 1; ii = 0; }
+    else if (i >= g.nx) { xk = 2; ii = g.nx - 1; }
+    T fct = T(1);
+    bool beyond = false;
+    int jj = j;
+    if (j < 0) { beyond = true; fct = sp.sig_lo; jj = 0; }
+    else if (j >= g.ny) { beyond = true; fct = sp.sig_hi; jj = g.ny - 1; }
+    const int kk = g.ndim == 3 ? wrapi(k, g.nz) : 0;
+    const long long id = ii + (long long)g.nx * (jj + (long long)g.ny * kk);
+    const uint32_t m = (uint32_t)__ldg(mask + id);
+    T x = __ldg(f + id);
+    if constexpr (BODY) {
+        // (a moving body needs a periodic x: the only box-face point is v on the +y wall)
+        if (!((m >> c) & 1u) && !(c == 1 && jj == g.ny - 1)) {
+            const double xc = g.ox + ((double)ii + (c == 0 ? 1.0 : 0.5)) * g.dx;
+            const double yc = g.oy + ((double)jj + (c == 1 ? 1.0 : 0.5)) * g.dy;
+            x = (T)bodyvel(body, c, xc, yc);
+            return beyond ? ((c == 1) ? T(0) : fct * x) : x;
+        }
+    }
+    const bool outc = !g.xper && xk == 0 && ii == g.nx - 1;
+    return mom_masked<T, true>(x, m, 0, c, beyond, fct, xk, outc, sp.uin);
+}
+
+template <typename T, bool THREE, bool STR, bool BODY>
+__global__ void __launch_bounds__(MX * MW) k_momentum_gen(GridP g, MomF<T> F, StageP<T> sp, IbmStage<T> ib,
+                                                          BodyP body, double* __restrict__ flux_part) {
+    __shared__ double shd[MW];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.x * MX + tx;
+    const bool livex = i < g.nx;
+    const int kbeg = THREE ? blockIdx.z * g.kzm : 0;
+    const int kend = THREE ? min(kbeg + g.kzm, g.nz) : 1;
+    const unsigned lt = lanemask_lt();
+    double fsum = 0.0;
+    for (int r = 0; r < 2; ++r) {
+        const int j = blockIdx.y * MY + 2 * ty + r;
+        if (j >= g.ny) break;                                    // whole warp
+        // per-row constants: the tables of a stretched y, else the uniform spacing
+        const T half = T(0.5);
+        const T dyc = STR ? (T)ytab(g, YT_DYC, j) : (T)g.dy;
+        const T idyc = STR ? (T)ytab(g, YT_IDYC, j) : sp.idy;
+        const T ihv = STR ? (T)ytab(g, YT_IHV, j) : sp.idy;
+        const T alo = STR ? (T)ytab(g, YT_ALO, j) : half, ahi = STR ? (T)ytab(g, YT_AHI, j) : half;
+        const T blo = (STR && j > 0) ? (T)ytab(g, YT_ALO, j - 1) : half;
+        const T bhi = (STR && j > 0) ? (T)ytab(g, YT_AHI, j - 1) : half;
+        const T cm = STR ? sp.nu * (T)ytab(g, YT_DCM, j) : sp.ny2;
+        const T c0 = STR ? sp.nu * (T)ytab(g, YT_DC0, j) : T(-2) * sp.ny2;
+        const T cp = STR ? sp.nu * (T)ytab(g, YT_DCP, j) : sp.ny2;
+        const T vm_ = STR ? sp.nu * (T)ytab(g, YT_DVM, j) : sp.ny2;
+        const T v0_ = STR ? sp.nu * (T)ytab(g, YT_DV0, j) : T(-2) * sp.ny2;
+        const T vp_ = STR ? sp.nu * (T)ytab(g, YT_DVP, j) : sp.ny2;
+        const T cgy = STR ? sp.ckdt * ihv : sp.cgy;
+        for (int k = kbeg; k < kend; ++k) {
+            auto U = [&](int di, int dj, int dk) { return mom_op<T, BODY>(g, F.u[0], F.mask, 0, i + di, j + dj, k + dk, sp, body); };
+            auto V = [&](int di, int dj, int dk) { return mom_op<T, BODY>(g, F.u[1], F.mask, 1, i + di, j + dj, k + dk, sp, body); };
+            auto W = [&](int di, int dj, int dk) { return mom_op<T, BODY>(g, F.u[2], F.mask, 2, i + di, j + dj, k + dk, sp, body); };
+            const long long id = (long long)i + (long long)g.nx * (j + (long long)g.ny * k);
+            const int ic = livex ? i : g.nx - 1;
+            const long long idc = (long long)ic + (long long)g.nx * (j + (long long)g.ny * k);
+            const uint32_t m = livex ? (uint32_t)__ldg(F.mask + idc) : 0u;
+            T Nv[3] = {T(0), T(0), T(0)}, Pv[3] = {T(0), T(0), T(0)};
+            T own[3] = {T(0), T(0), T(0)};
+            if (livex) {
+                const T pc = F.p[idc];
+                const T pE = F.p[(long long)(g.xper ? wrapi(i + 1, g.nx) : min(i + 1, g.nx - 1)) +
+                                 (long long)g.nx * (j + (long long)g.ny * k)];
+                const T pN = F.p[idc + (j + 1 < g.ny ? g.nx : 0)];
+                const T pT = THREE ? F.p[(long long)i + (long long)g.nx * (j + (long long)g.ny * wrapi(k + 1, g.nz))]
+                                   : T(0);
+                // ---- u
+                const T u0 = U(0, 0, 0), uE = U(1, 0, 0), uW = U(-1, 0, 0), uN = U(0, 1, 0), uS = U(0, -1, 0);
+                const T v0 = V(0, 0, 0), vE1 = V(1, 0, 0), vS0 = V(0, -1, 0), vSE = V(1, -1, 0);
+                T conv = ((u0 + uE) * (u0 + uE) - (uW + u0) * (uW + u0)) * sp.qx;
+                conv += ((v0 + vE1) * (alo * u0 + ahi * uN) - (vS0 + vSE) * (blo * uS + bhi * u0)) * half * idyc;
+                T lap = (uE - T(2) * u0 + uW) * sp.nx2 + cm * uS + c0 * u0 + cp * uN;
+                T wc = T(0), wT = T(0), wB = T(0), uT = T(0), uB = T(0), wE = T(0), wW = T(0), wN = T(0), wS = T(0);
+                if (THREE) {
+                    wc = W(0, 0, 0);
+                    uT = U(0, 0, 1);
+                    uB = U(0, 0, -1);
+                    const T wE1 = W(1, 0, 0), wB0 = W(0, 0, -1), wBE = W(1, 0, -1);
+                    conv += ((wc + wE1) * (u0 + uT) - (wB0 + wBE) * (uB + u0)) * sp.qz;
+                    lap += (uT - T(2) * u0 + uB) * sp.nz2;
+                    wE = wE1;
+                    wB = wB0;
+                }
+                Nv[0] = lap - conv + sp.g[0];
+                Pv[0] = pE - pc;
+                // ---- v
+                {
+                    const T vW = V(-1, 0, 0), vN = V(0, 1, 0);
+                    const T uWN = U(-1, 1, 0);
+                    T cv = ((alo * u0 + ahi * uN) * (v0 + vE1) - (alo * uW + ahi * uWN) * (vW + v0)) * half * sp.idx;
+                    cv += ((v0 + vN) * (v0 + vN) - (vS0 + v0) * (vS0 + v0)) * T(0.25) * ihv;
+                    T lv = (vE1 - T(2) * v0 + vW) * sp.nx2 + vm_ * vS0 + v0_ * v0 + vp_ * vN;
+                    if (THREE) {
+                        const T vT = V(0, 0, 1), vB = V(0, 0, -1);
+                        const T wN1 = W(0, 1, 0), wBN = W(0, 1, -1);
+                        cv += ((alo * wc + ahi * wN1) * (v0 + vT) - (alo * wB + ahi * wBN) * (vB + v0)) * half * sp.idz;
+                        lv += (vT - T(2) * v0 + vB) * sp.nz2;
+                        wN = wN1;
+                    }
+                    Nv[1] = lv - cv + sp.g[1];
+                    Pv[1] = pN - pc;
+                }
+                // ---- w
+                if (THREE) {
+                    wW = W(-1, 0, 0);
+                    wS = W(0, -1, 0);
+                    wT = W(0, 0, 1);
+                    const T uWT = U(-1, 0, 1), vT0 = V(0, 0, 1), vST = V(0, -1, 1);
+                    T cw = ((u0 + uT) * (wc + wE) - (uW + uWT) * (wW + wc)) * sp.qx;
+                    cw += ((v0 + vT0) * (alo * wc + ahi * wN) - (vS0 + vST) * (blo * wS + bhi * wc)) * half * idyc;
+                    cw += ((wc + wT) * (wc + wT) - (wB + wc) * (wB + wc)) * sp.qz;
+                    T lw = (wE - T(2) * wc + wW) * sp.nx2 + cm * wS + c0 * wc + cp * wN + (wT - T(2) * wc + wB) * sp.nz2;
+                    Nv[2] = lw - cw + sp.g[2];
+                    Pv[2] = pT - pc;
+                }
+                own[0] = u0;
+                own[1] = v0;
+                own[2] = wc;
+            }
+            // stage combination, the implicit IBM division at IBM points, stores
+            const T cg[3] = {sp.cgx, cgy, sp.cgz};
+            const int seg = (j + g.ny * k) * g.nsegx + (int)blockIdx.x;
+#pragma unroll
+            for (int c = 0; c < (THREE ? 3 : 2); ++c) {
+                T R = sp.dta * Nv[c] - cg[c] * Pv[c];
+                if (sp.read_prev && livex) R += sp.dtb * F.Nn[c][id];
+                T out = own[c] + R;
+                T Nc = Nv[c];
+                const bool ibmp = (m >> (4 + c)) & 1u;
+                const unsigned b = __ballot_sync(0xffffffffu, ibmp);
+                if (ibmp) mom_ibm(sp, ib.coef[c][ib.segoff[c][seg] + __popc(b & lt)], own[c], R, out, Nc);
+                if (!livex) continue;
+                if (c == 0 && !g.xper && i == g.nx - 1) continue;   // the outflow face: written by the outflow update
+                const bool in = (m >> c) & 1u;
+                // a moving body's points hold its velocity (own[c] is what the operator reads there)
+                const T rest = (BODY && !(c == 1 && j == g.ny - 1)) ? own[c] : T(0);
+                out = in ? out : rest;
+                Nc = in ? Nc : T(0);
+                F.us[c][id] = out;
+                if (sp.write_n) F.Nn[c][id] = Nc;
+                if (c == 0) fsum += (double)out * (double)dyc;
+            }
+        }
+    }
+    if (sp.flux_sum) {
+        const double ws = warp_sum(fsum);
+        if (tx == 0) shd[ty] = ws;
+        __syncthreads();
+        if (tx == 0 && ty == 0) {
+            double t = 0.0;
+            for (int w = 0; w < MW; ++w) t += shd[w];
+            flux_part[blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z)] = t;
+        }
+    }
+}
 
 // ---------------------------------------------------------------------------
 // K3 with TMA plane loads (3D, nx a multiple of 16).
@@ -1054,7 +1234,17 @@ ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib,
     ib = stage_coefs<T>(h, k);
     dim3 blk(MX, MW, 1);
     grd = momentum_grid(g);
-    if (g.ndim == 3 && h->mom_maps && h->mom_tma && tma_smem_ready<T>()) {
+    if (g.ystr || h->body.kind != 0) {
+        const BodyP& bd = h->body;
+        if (g.ystr) {   // (a moving body needs a uniform y)
+            if (g.ndim == 3) k_momentum_gen<T, true, true, false><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, bd, h->partials);
+            else k_momentum_gen<T, false, true, false><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, bd, h->partials);
+        } else {
+            if (g.ndim == 3) k_momentum_gen<T, true, false, true><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, bd, h->partials);
+            else k_momentum_gen<T, false, false, true><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, bd, h->partials);
+        }
+    }
+    else if (g.ndim == 3 && h->mom_maps && h->mom_tma && tma_smem_ready<T>()) {
         const MomMaps& maps = *static_cast<const MomMaps*>(h->mom_maps);
         if (g.xper)
             k_momentum_tma<T, true><<<grd, blk, TmaLay<T>::SMEM, h->stream>>>(g, F, sp, ib, h->partials, h->scal, maps);
@@ -1077,8 +1267,8 @@ void momentum_release(ibm_solver* h) {
 
 void momentum_prepare(ibm_solver* h) {
     momentum_release(h);
-    // the TMA form covers 3D grids whose x extent is a multiple of 16
-    if (h->gp.ndim != 3 || h->gp.nx % 16 != 0) return;
+    // the TMA form covers 3D grids whose x extent is a multiple of 16 (a uniform y)
+    if (h->gp.ndim != 3 || h->gp.nx % 16 != 0 || h->gp.ystr) return;
     h->mom_maps = h->prec == IBM_FP64 ? static_cast<void*>(build_maps<double>(h))
                                       : static_cast<void*>(build_maps<float>(h));
 }

@@ -140,13 +140,20 @@ extern "C" ibm_status ibm_diagnostics_noalloc(const ibm_grid_desc* grid, const v
         return ibm_set_error(IBM_E_INVALID, "need ny >= 2, and nz == 1 in 2D");
     if (grid->precision != IBM_FP64 && grid->precision != IBM_FP32)
         return ibm_set_error(IBM_E_INVALID, "bad precision");
-    for (int d : {0, 2})
-        if (grid->bc_lo[d] != IBM_BC_PERIODIC || grid->bc_hi[d] != IBM_BC_PERIODIC)
-            return ibm_set_error(IBM_E_UNSUPPORTED, "x and z must be periodic");
-    const long long N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
-    if (N > NA_MAX_CELLS)
-        return ibm_set_error(IBM_E_INVALID, "grid of " + std::to_string(N) +
+    if (grid->bc_lo[2] != IBM_BC_PERIODIC || grid->bc_hi[2] != IBM_BC_PERIODIC)
+        return ibm_set_error(IBM_E_UNSUPPORTED, "z must be periodic");
+    if (grid->y_faces) return ibm_set_error(IBM_E_UNSUPPORTED, "a stretched y needs its per-row tables: use ibm_diagnostics");
+    const bool xper = grid->bc_lo[0] == IBM_BC_PERIODIC && grid->bc_hi[0] == IBM_BC_PERIODIC;
+    const bool xio = grid->bc_lo[0] == IBM_BC_INFLOW && grid->bc_hi[0] == IBM_BC_OUTFLOW;
+    if (!xper && !xio)
+        return ibm_set_error(IBM_E_UNSUPPORTED, "x must be periodic, or an inflow at -x with an outflow at +x");
+    // the cell count is checked factor by factor, so that the product cannot overflow
+    const long long n0 = grid->n[0], n1 = grid->n[1], n2 = grid->n[2];
+    if (n0 > NA_MAX_CELLS || n1 > NA_MAX_CELLS / n0 || n2 > NA_MAX_CELLS / (n0 * n1))
+        return ibm_set_error(IBM_E_INVALID, "grid of " + std::to_string(n0) + " x " + std::to_string(n1) + " x " +
+                                                std::to_string(n2) +
                                                 " cells exceeds the 134217728-cell limit of ibm_diagnostics_noalloc");
+    const long long N = n0 * n1 * n2;
     if (!u || !v || !p || !mask || (grid->ndim == 3 && !w))
         return ibm_set_error(IBM_E_INVALID, "field or mask pointer is NULL");
 
@@ -165,8 +172,8 @@ extern "C" ibm_status ibm_diagnostics_noalloc(const ibm_grid_desc* grid, const v
     g.dx = grid->L[0] / grid->n[0];
     g.dy = grid->L[1] / grid->n[1];
     g.dz = grid->L[2] / grid->n[2];
-    g.xper = grid->bc_lo[0] != IBM_BC_INFLOW;
-    g.uin = g.xper ? 0.0 : grid->inflow[0];
+    g.xper = xper;
+    g.uin = xper ? 0.0 : grid->inflow[0];
     double s[NA_VALS];
     st = grid->precision == IBM_FP64
              ? noalloc_run<double>(g, u, v, w, p, mask, (cudaStream_t)stream, scratch, s)

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict
     const int segl = il / 32, lanel = il % 32;
     const int il_probe = segl * 32 + lane;                  // the warp reads that segment's mask bits
     const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
+    if (g.ystr) idy = (T)ytab(g, YT_IDYC, j);                // a stretched y: this row's cell height
     // the first segment of an inflow/outflow x: lane 0 (cell 0) reads the inflow face
     const bool inflow_seg = XF && blockIdx.x == 0;
     T wprev = T(0);
@@ -165,91 +166,98 @@ __global__ void __launch_bounds__(256) k_divergence(GridP g, const T* __restrict
 //   backward x_j = e_j - w_j x_{j+1}
 // and the solution is multiplied by `scale` (dy^2 and the FFT normalisation)
 // on the way out.  The zero mode's solution is shifted to zero mean (box-mean
-// gauge).  Each system runs in FP64 unless its flag says it is strongly
-// diagonally dominant (K dy^2 >= tau, condition number <= 4/tau + 1), in which
-// case FP32 arithmetic with FP32 pivots is as accurate as the FP32 transforms
-// that feed it; that sweep works in place on the spectrum.
-// One warp covers 32 consecutive kx of one kz, so loads coalesce across systems.
+// gauge).  Each system sweeps in FP64 arithmetic unless its flag says it is
+// strongly diagonally dominant (K dy^2 >= tau, condition number <= 4/tau + 1):
+// in FP32 mode those sweep in FP32 with FP32 pivots, as accurate as the FP32
+// transforms that feed them, in place on the spectrum.
 // ---------------------------------------------------------------------------
-// FP64 sweep of one component (real or imaginary part) of one system: the two
-// parts are independent recurrences, so two threads share a system and the
-// FP64 work is spread over twice as many warps.  The next batch of loads is
-// issued before the current batch is consumed.
+// FP64 sweep of one complex system by one thread (real and imaginary parts are
+// two independent chains).  The forward recurrence runs divide-free on
+// f_j = e_j / w_j:  f_j = d_j - w_{j-1} f_{j-1}, one fused multiply-add on the
+// dependent chain, and e_j = w_j f_j goes to the FP64 temporary `tmp` (the
+// spectrum itself for FP64 storage: row j is read before it is overwritten).
+// The backward sweep is one fused multiply-add per row.  This is the least FP64
+// work per system (the scarce FP64 pipes bound it when there are many systems);
+// the warp form below has the shorter chain for few systems.  Loads run B rows
+// ahead of the chain.
 template <typename C>
-__device__ __forceinline__ void tridiag_fp64(const GridP& g, C* spec, double2* tmp, const double* __restrict__ piv,
-                                             long long base, int comp, double scale, bool zero_mode) {
+__device__ __forceinline__ void tridiag_thread64(const GridP& g, C* spec, double2* tmp, const double* __restrict__ piv,
+                                                 long long base, double scale, bool zero_mode) {
     constexpr bool F32 = sizeof(C) == sizeof(float2);
     using S = typename std::conditional<F32, float, double>::type;   // storage scalar
     constexpr int B = 8;
     const long long st = g.nxh;
     const int ny = g.ny;
-    S* sp = reinterpret_cast<S*>(spec) + comp;      // component `comp` of spec[o] at sp[2 o]
-    double* tp = reinterpret_cast<double*>(tmp) + comp;
     const float sf = (float)scale;
-    double e = 0.0;
-    S r[B], rn[B];
+    C r[B], rn[B];
     double w[B], wn[B];
 #pragma unroll
     for (int t = 0; t < B; ++t)
         if (t < ny) {
-            r[t] = sp[2 * (base + t * st)];
+            r[t] = spec[base + t * st];
             w[t] = piv[base + t * st];
         }
+    double fr = 0.0, fi = 0.0, wp = 0.0;      // f_{j-1}, w_{j-1}
     for (int j0 = 0; j0 < ny; j0 += B) {
 #pragma unroll
         for (int t = 0; t < B; ++t)
             if (j0 + B + t < ny) {
-                rn[t] = sp[2 * (base + (j0 + B + t) * st)];
+                rn[t] = spec[base + (j0 + B + t) * st];
                 wn[t] = piv[base + (j0 + B + t) * st];
             }
 #pragma unroll
         for (int t = 0; t < B; ++t)
             if (j0 + t < ny) {
                 // FP32 storage: the scale is applied in FP32 on the input (exact to FP32 rounding)
-                const double rv = F32 ? (double)((float)r[t] * sf) : (double)r[t];
-                e = (rv - e) * w[t];                                          // e_{-1} = 0
-                tp[2 * (base + (j0 + t) * st)] = e;
+                const double dr = F32 ? (double)((float)r[t].x * sf) : (double)r[t].x;
+                const double di = F32 ? (double)((float)r[t].y * sf) : (double)r[t].y;
+                fr = fma(-wp, fr, dr);
+                fi = fma(-wp, fi, di);
+                wp = w[t];
+                tmp[base + (j0 + t) * st] = make_double2(wp * fr, wp * fi);
             }
 #pragma unroll
         for (int t = 0; t < B; ++t) { r[t] = rn[t]; w[t] = wn[t]; }
     }
-    double x = e;
-    double sum = 0.0;
-    auto put = [&](long long o, double val) {
-        if (F32) sp[2 * o] = (S)val;
-        else sp[2 * o] = (S)(val * scale);
-    };
-    put(base + (long long)(ny - 1) * st, x);
-    if (zero_mode) sum += x;
-    double d[B], dn[B];
+    double2 e[B], en[B];
 #pragma unroll
     for (int t = 0; t < B; ++t)
-        if (ny - 2 - t >= 0) {
-            d[t] = tp[2 * (base + (ny - 2 - t) * st)];
-            w[t] = piv[base + (ny - 2 - t) * st];
+        if (ny - 1 - t >= 0) {
+            e[t] = tmp[base + (ny - 1 - t) * st];
+            w[t] = piv[base + (ny - 1 - t) * st];
         }
-    for (int j1 = ny - 2; j1 >= 0; j1 -= B) {
+    double xr = 0.0, xi = 0.0, sr = 0.0, si = 0.0;    // x_{ny} = 0
+    for (int j1 = ny - 1; j1 >= 0; j1 -= B) {
 #pragma unroll
         for (int t = 0; t < B; ++t)
             if (j1 - B - t >= 0) {
-                dn[t] = tp[2 * (base + (j1 - B - t) * st)];
+                en[t] = tmp[base + (j1 - B - t) * st];
                 wn[t] = piv[base + (j1 - B - t) * st];
             }
 #pragma unroll
         for (int t = 0; t < B; ++t)
             if (j1 - t >= 0) {
-                x = d[t] - w[t] * x;
-                put(base + (j1 - t) * st, x);
-                if (zero_mode) sum += x;
+                xr = fma(-w[t], xr, e[t].x);
+                xi = fma(-w[t], xi, e[t].y);
+                C o;
+                o.x = (S)(F32 ? xr : xr * scale);
+                o.y = (S)(F32 ? xi : xi * scale);
+                spec[base + (j1 - t) * st] = o;
+                sr += xr;
+                si += xi;
             }
 #pragma unroll
-        for (int t = 0; t < B; ++t) { d[t] = dn[t]; w[t] = wn[t]; }
+        for (int t = 0; t < B; ++t) { e[t] = en[t]; w[t] = wn[t]; }
     }
-    if (zero_mode) {
-        const double mean = sum / ny * (F32 ? 1.0 : scale);
+    if (zero_mode) {                                  // box-mean gauge
+        const double mr = sr / ny * (F32 ? 1.0 : scale);
+        const double mi = si / ny * (F32 ? 1.0 : scale);
         for (int j = 0; j < ny; ++j) {
             const long long o = base + j * st;
-            sp[2 * o] = (S)((double)sp[2 * o] - mean);
+            C v = spec[o];
+            v.x = (S)((double)v.x - mr);
+            v.y = (S)((double)v.y - mi);
+            spec[o] = v;
         }
     }
 }
@@ -302,15 +310,44 @@ __device__ __forceinline__ void tridiag_fp32(const GridP& g, float2* spec, const
     }
 }
 
-// FP64 sweep of one system by a whole warp (ny <= 32 * TW_ROWS rows per lane).  Both
-// recurrences are first order and affine,
-//   forward  e_j = w_j (d_j - e_{j-1})        (e_{-1} = 0)
-//   backward x_j = e_j - w_j x_{j+1}          (x_{ny} = 0),
-// so each lane composes the maps of its run of consecutive rows, a five-step
-// shuffle scan composes them across the lanes (affine maps compose exactly
-// like the recurrence itself), and each lane replays its rows from the value
-// handed in.  The dependent FP64 chain is about 2 (rows per lane + 5) long
-// instead of 2 ny.  Real and imaginary parts go through together.
+// Exact FP32 -> FP64 from the IEEE-754 bit layouts, on the integer pipes (the FP64 pipes
+// are the scarce resource of the FP64 sweeps): the sign, the exponent rebiased from 127 to
+// 1023 and the 23 mantissa bits at the top of the 52-bit field.  Zero keeps its sign;
+// subnormal, infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u && (b & 0x7fffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// FP64 -> FP32 rounded to nearest, ties to even, from the bit layouts on the integer pipes:
+// the top 23 mantissa bits are kept and the 29 dropped bits decide the rounding; a carry
+// runs into the exponent (and past the largest finite value to infinity, as the rounding
+// requires).  Results that would be subnormal or zero, and infinite or NaN inputs, take
+// the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t E = (hi >> 20) & 0x7ffu;
+    if (E <= 896u || E >= 1151u) return __double2float_rn(x);
+    uint32_t v = ((E - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu;
+    v += (rem > 0x10000000u || (rem == 0x10000000u && (v & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | v);
+}
+
+// FP64 sweep of one system by a whole warp (ny <= 32 * TW_ROWS rows per lane).  The
+// forward recurrence runs divide-free on f_j = e_j / w_j:
+//   f_j = d_j - w_{j-1} f_{j-1}      (w_{-1} = 0),   e_j = w_j f_j,
+// and the backward one is x_j = e_j - w_j x_{j+1} (x_{ny} = 0).  Both are first order and
+// affine, so each lane composes the maps of its run of consecutive rows (one fused
+// multiply-add per row and part), a five-step shuffle scan composes them across the lanes
+// (affine maps compose like the recurrence itself), and each lane replays its rows from the
+// value handed in.  The dependent FP64 chain is about 2 (rows per lane + 5) long instead of
+// 2 ny.  Real and imaginary parts go through together.  FP32 storage converts on the
+// integer pipes (f32_to_f64, f64_to_f32_rn), which leaves the FP64 pipes to the sweeps.
 constexpr int TW_ROWS = 32;   // rows per lane at most: the warp path covers ny <= 1024
 
 template <typename C, int TW_ROWS>
@@ -325,6 +362,10 @@ __device__ __forceinline__ void tridiag_warp64(const GridP& g, C* spec, const do
     const long long st = g.nxh;
     const float sf = (float)scale;
     double dr[TW_ROWS], di[TW_ROWS], w[TW_ROWS];
+    // w_{j0-1}: the last pivot of the lane below (0 below row 0), read directly (selecting it
+    // from the lane below's registers by a run-time row count would force the array into
+    // local memory)
+    const double wb = (lane > 0 && j0 - 1 < ny) ? piv[base + (long long)(j0 - 1) * st] : 0.0;
 #pragma unroll
     for (int t = 0; t < TW_ROWS; ++t) {
         dr[t] = di[t] = w[t] = 0.0;
@@ -332,48 +373,61 @@ __device__ __forceinline__ void tridiag_warp64(const GridP& g, C* spec, const do
             const long long o = base + (long long)(j0 + t) * st;
             const C r = spec[o];
             // FP32 storage: the scale is applied in FP32 on the input (exact to FP32 rounding)
-            dr[t] = F32 ? (double)((float)r.x * sf) : (double)r.x;
-            di[t] = F32 ? (double)((float)r.y * sf) : (double)r.y;
+            if constexpr (F32) {
+                dr[t] = f32_to_f64((float)r.x * sf);
+                di[t] = f32_to_f64((float)r.y * sf);
+            } else {
+                dr[t] = (double)r.x;
+                di[t] = (double)r.y;
+            }
             w[t] = piv[o];
         }
     }
-    // forward: this lane's map e_out = A + B e_in
+    // forward: this lane's map f_out = A + B f_in
     double Ar = 0.0, Ai = 0.0, B = 1.0;
+    {
+        double wp = wb;
 #pragma unroll
-    for (int t = 0; t < TW_ROWS; ++t)
-        if (t < E && j0 + t < ny) {
-            Ar = w[t] * (dr[t] - Ar);
-            Ai = w[t] * (di[t] - Ai);
-            B = -w[t] * B;
-        }
+        for (int t = 0; t < TW_ROWS; ++t)
+            if (t < E && j0 + t < ny) {
+                Ar = fma(-wp, Ar, dr[t]);
+                Ai = fma(-wp, Ai, di[t]);
+                B = -wp * B;
+                wp = w[t];
+            }
+    }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {          // inclusive scan: compose with the lanes below
         const double pr = __shfl_up_sync(0xffffffffu, Ar, off);
         const double pi = __shfl_up_sync(0xffffffffu, Ai, off);
         const double pb = __shfl_up_sync(0xffffffffu, B, off);
         if (lane >= off) {
-            Ar += B * pr;
-            Ai += B * pi;
+            Ar = fma(B, pr, Ar);
+            Ai = fma(B, pi, Ai);
             B *= pb;
         }
     }
-    double er = __shfl_up_sync(0xffffffffu, Ar, 1), ei = __shfl_up_sync(0xffffffffu, Ai, 1);
-    if (lane == 0) er = ei = 0.0;
+    double fr = __shfl_up_sync(0xffffffffu, Ar, 1), fi = __shfl_up_sync(0xffffffffu, Ai, 1);
+    if (lane == 0) fr = fi = 0.0;
+    {
+        double wp = wb;
 #pragma unroll
-    for (int t = 0; t < TW_ROWS; ++t)
-        if (t < E && j0 + t < ny) {
-            er = w[t] * (dr[t] - er);
-            ei = w[t] * (di[t] - ei);
-            dr[t] = er;
-            di[t] = ei;
-        }
+        for (int t = 0; t < TW_ROWS; ++t)
+            if (t < E && j0 + t < ny) {
+                fr = fma(-wp, fr, dr[t]);
+                fi = fma(-wp, fi, di[t]);
+                wp = w[t];
+                dr[t] = wp * fr;                       // e_j
+                di[t] = wp * fi;
+            }
+    }
     // backward: this lane's map x_first = Cm + D x_in, x_in the value above the run
     double Cr = 0.0, Ci = 0.0, D = 1.0;
 #pragma unroll
     for (int t = TW_ROWS - 1; t >= 0; --t)
         if (t < E && j0 + t < ny) {
-            Cr = dr[t] - w[t] * Cr;
-            Ci = di[t] - w[t] * Ci;
+            Cr = fma(-w[t], Cr, dr[t]);
+            Ci = fma(-w[t], Ci, di[t]);
             D = -w[t] * D;
         }
 #pragma unroll
@@ -382,165 +436,50 @@ __device__ __forceinline__ void tridiag_warp64(const GridP& g, C* spec, const do
         const double pi = __shfl_down_sync(0xffffffffu, Ci, off);
         const double pd = __shfl_down_sync(0xffffffffu, D, off);
         if (lane + off < 32) {
-            Cr += D * pr;
-            Ci += D * pi;
+            Cr = fma(D, pr, Cr);
+            Ci = fma(D, pi, Ci);
             D *= pd;
         }
     }
     double xr = __shfl_down_sync(0xffffffffu, Cr, 1), xi = __shfl_down_sync(0xffffffffu, Ci, 1);
     if (lane == 31) xr = xi = 0.0;
-    double sr = 0.0, si = 0.0;
 #pragma unroll
     for (int t = TW_ROWS - 1; t >= 0; --t)
         if (t < E && j0 + t < ny) {
-            xr = dr[t] - w[t] * xr;
-            xi = di[t] - w[t] * xi;
-            dr[t] = F32 ? xr : xr * scale;
-            di[t] = F32 ? xi : xi * scale;
-            sr += xr;
-            si += xi;
+            xr = fma(-w[t], xr, dr[t]);
+            xi = fma(-w[t], xi, di[t]);
+            dr[t] = xr;
+            di[t] = xi;
         }
-    double mr = 0.0, mi = 0.0;
-    if (zero_mode) {                                   // box-mean gauge
+    if (zero_mode) {                                   // box-mean gauge (one system: the sums run only here)
+        double sr = 0.0, si = 0.0;
+#pragma unroll
+        for (int t = 0; t < TW_ROWS; ++t)
+            if (t < E && j0 + t < ny) {
+                sr += dr[t];
+                si += di[t];
+            }
         sr = warp_sum(sr);
         si = warp_sum(si);
-        mr = __shfl_sync(0xffffffffu, sr, 0) / ny * (F32 ? 1.0 : scale);
-        mi = __shfl_sync(0xffffffffu, si, 0) / ny * (F32 ? 1.0 : scale);
+        const double mr = __shfl_sync(0xffffffffu, sr, 0) / ny;
+        const double mi = __shfl_sync(0xffffffffu, si, 0) / ny;
+#pragma unroll
+        for (int t = 0; t < TW_ROWS; ++t) {
+            dr[t] -= mr;
+            di[t] -= mi;
+        }
     }
 #pragma unroll
     for (int t = 0; t < TW_ROWS; ++t)
         if (t < E && j0 + t < ny) {
             const long long o = base + (long long)(j0 + t) * st;
             C r;
-            r.x = (S)dr[t];
-            r.y = (S)di[t];
-            if (zero_mode) {
-                r.x = (S)((double)r.x - mr);
-                r.y = (S)((double)r.y - mi);
-            }
-            spec[o] = r;
-        }
-}
-
-// The same warp sweep for FP32 storage in float-float arithmetic (a value is an
-// unevaluated sum hi + lo of two floats, about 2^-44 relative): the near-singular
-// systems need more than FP32 but not FP64, and the FP32 pipes are 58x faster than
-// the FP64 ones on this GPU.  Inputs and outputs are FP32; the pivots are split
-// from their FP64 values.
-__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, -b.hi, -b.lo); }
-__device__ __forceinline__ FF ff_mulf(FF a, FF b) { return ff_mul(a, b.hi, b.lo); }
-__device__ __forceinline__ FF ff_shfl_up(FF a, int off) {
-    return FF{__shfl_up_sync(0xffffffffu, a.hi, off), __shfl_up_sync(0xffffffffu, a.lo, off)};
-}
-__device__ __forceinline__ FF ff_shfl_down(FF a, int off) {
-    return FF{__shfl_down_sync(0xffffffffu, a.hi, off), __shfl_down_sync(0xffffffffu, a.lo, off)};
-}
-
-template <int TW_ROWS>
-__device__ __forceinline__ void tridiag_warp_ff(const GridP& g, float2* spec, const double* __restrict__ piv,
-                                                long long base, double scale, bool zero_mode) {
-    const int lane = threadIdx.x & 31;
-    const int ny = g.ny;
-    const int E = (ny + 31) / 32;
-    const int j0 = lane * E;
-    const long long st = g.nxh;
-    const float sf = (float)scale;
-    FF dr[TW_ROWS], di[TW_ROWS], w[TW_ROWS];
-#pragma unroll
-    for (int t = 0; t < TW_ROWS; ++t) {
-        dr[t] = di[t] = w[t] = FF{0.f, 0.f};
-        if (t < E && j0 + t < ny) {
-            const long long o = base + (long long)(j0 + t) * st;
-            const float2 r = spec[o];
-            dr[t] = FF{r.x * sf, 0.f};          // the scale applied in FP32, as the FP64 sweep does
-            di[t] = FF{r.y * sf, 0.f};
-            const double wd = piv[o];
-            const float wh = (float)wd;
-            w[t] = FF{wh, (float)(wd - (double)wh)};
-        }
-    }
-    const FF one{1.f, 0.f};
-    // forward: this lane's map e_out = A + B e_in
-    FF Ar{0.f, 0.f}, Ai{0.f, 0.f}, B = one;
-#pragma unroll
-    for (int t = 0; t < TW_ROWS; ++t)
-        if (t < E && j0 + t < ny) {
-            Ar = ff_mulf(w[t], ff_sub(dr[t], Ar));
-            Ai = ff_mulf(w[t], ff_sub(di[t], Ai));
-            B = ff_mulf(FF{-w[t].hi, -w[t].lo}, B);
-        }
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const FF pr = ff_shfl_up(Ar, off), pi = ff_shfl_up(Ai, off), pb = ff_shfl_up(B, off);
-        if (lane >= off) {
-            const FF br = ff_mulf(B, pr), bi = ff_mulf(B, pi);
-            Ar = ff_add(Ar, br.hi, br.lo);
-            Ai = ff_add(Ai, bi.hi, bi.lo);
-            B = ff_mulf(B, pb);
-        }
-    }
-    FF er = ff_shfl_up(Ar, 1), ei = ff_shfl_up(Ai, 1);
-    if (lane == 0) er = ei = FF{0.f, 0.f};
-#pragma unroll
-    for (int t = 0; t < TW_ROWS; ++t)
-        if (t < E && j0 + t < ny) {
-            er = ff_mulf(w[t], ff_sub(dr[t], er));
-            ei = ff_mulf(w[t], ff_sub(di[t], ei));
-            dr[t] = er;
-            di[t] = ei;
-        }
-    // backward: this lane's map x_first = Cm + D x_in
-    FF Cr{0.f, 0.f}, Ci{0.f, 0.f}, D = one;
-#pragma unroll
-    for (int t = TW_ROWS - 1; t >= 0; --t)
-        if (t < E && j0 + t < ny) {
-            Cr = ff_sub(dr[t], ff_mulf(w[t], Cr));
-            Ci = ff_sub(di[t], ff_mulf(w[t], Ci));
-            D = ff_mulf(FF{-w[t].hi, -w[t].lo}, D);
-        }
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const FF pr = ff_shfl_down(Cr, off), pi = ff_shfl_down(Ci, off), pd = ff_shfl_down(D, off);
-        if (lane + off < 32) {
-            const FF dr2 = ff_mulf(D, pr), di2 = ff_mulf(D, pi);
-            Cr = ff_add(Cr, dr2.hi, dr2.lo);
-            Ci = ff_add(Ci, di2.hi, di2.lo);
-            D = ff_mulf(D, pd);
-        }
-    }
-    FF xr = ff_shfl_down(Cr, 1), xi = ff_shfl_down(Ci, 1);
-    if (lane == 31) xr = xi = FF{0.f, 0.f};
-    double sr = 0.0, si = 0.0;
-#pragma unroll
-    for (int t = TW_ROWS - 1; t >= 0; --t)
-        if (t < E && j0 + t < ny) {
-            xr = ff_sub(dr[t], ff_mulf(w[t], xr));
-            xi = ff_sub(di[t], ff_mulf(w[t], xi));
-            dr[t] = xr;
-            di[t] = xi;
-            if (zero_mode) {
-                sr += (double)xr.hi + (double)xr.lo;
-                si += (double)xi.hi + (double)xi.lo;
-            }
-        }
-    double mr = 0.0, mi = 0.0;
-    if (zero_mode) {                                   // box-mean gauge
-        sr = warp_sum(sr);
-        si = warp_sum(si);
-        mr = __shfl_sync(0xffffffffu, sr, 0) / ny;
-        mi = __shfl_sync(0xffffffffu, si, 0) / ny;
-    }
-#pragma unroll
-    for (int t = 0; t < TW_ROWS; ++t)
-        if (t < E && j0 + t < ny) {
-            const long long o = base + (long long)(j0 + t) * st;
-            float2 r;
-            if (zero_mode) {
-                r.x = (float)((double)dr[t].hi + (double)dr[t].lo - mr);
-                r.y = (float)((double)di[t].hi + (double)di[t].lo - mi);
+            if constexpr (F32) {
+                r.x = f64_to_f32_rn(dr[t]);
+                r.y = f64_to_f32_rn(di[t]);
             } else {
-                r.x = __fadd_rn(dr[t].hi, dr[t].lo);
-                r.y = __fadd_rn(di[t].hi, di[t].lo);
+                r.x = (S)(dr[t] * scale);
+                r.y = (S)(di[t] * scale);
             }
             spec[o] = r;
         }
@@ -629,35 +568,78 @@ __device__ __forceinline__ void tridiag_warp_f32(const GridP& g, float2* spec, c
         }
 }
 
+// Stretched y: every spectral point of row j times the per-row factor ytab(tab, j)
+template <typename C>
+__global__ void k_spec_rows(GridP g, C* __restrict__ spec, long long n, int tab) {
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int j = (int)((id / g.nxh) % g.ny);
+    using S = decltype(spec[0].x);
+    const S f = (S)ytab(g, tab, j);
+    C v = spec[id];
+    v.x *= f;
+    v.y *= f;
+    spec[id] = v;
+}
+
+// Stretched y: the zero mode (kx = kz = 0) shifted to zero plain mean over the rows (FP64 sums)
+template <typename C>
+__global__ void k_zero_gauge(GridP g, C* __restrict__ spec) {
+    __shared__ double sh[2][8];
+    __shared__ double mean[2];
+    double sr = 0.0, si = 0.0;
+    for (int j = threadIdx.x; j < g.ny; j += blockDim.x) {
+        const C v = spec[(long long)j * g.nxh];
+        sr += (double)v.x;
+        si += (double)v.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = sr; sh[1][threadIdx.x >> 5] = si; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[0][w]; b += sh[1][w]; }
+        mean[0] = a / g.ny;
+        mean[1] = b / g.ny;
+    }
+    __syncthreads();
+    using S = decltype(spec[0].x);
+    for (int j = threadIdx.x; j < g.ny; j += blockDim.x) {
+        C v = spec[(long long)j * g.nxh];
+        v.x = (S)((double)v.x - mean[0]);
+        v.y = (S)((double)v.y - mean[1]);
+        spec[(long long)j * g.nxh] = v;
+    }
+}
+
 // One warp per block; `order` lists the systems (kz * nxh + kx) with every
 // FP64 system first, so the scarce FP64 pipes of all SMs share the low modes.
-// FP64 systems take two threads (real and imaginary part), FP32 systems one.
-// R: rows per lane of the warp-per-system FP64 path (ny <= 32 R); 0 when ny > 32 * TW_ROWS.
+// FP64 systems take one warp each (thr64 = 0; R rows per lane, ny <= 32 R) or one
+// thread each (thr64 = 1, or R = 0 when ny > 32 * TW_ROWS); FP32 systems one
+// thread each, or one warp each when warp32 is set.
 template <typename C, int R>
 __global__ void __launch_bounds__(32) k_tridiag(GridP g, C* spec, double2* tmp, const double* __restrict__ piv,
                                                 const float* __restrict__ piv32, const int* __restrict__ order,
-                                                int n64, int nsys, double scale, int warp32) {
-    if constexpr (R > 0) {
-        // one warp (block) per FP64 system
-        if ((int)blockIdx.x < n64) {
-            const int sys = order[blockIdx.x];
-            const int kx = sys % g.nxh, kz = sys / g.nxh;
-            const long long base = (long long)kz * g.ny * g.nxh + kx;
-            if constexpr (sizeof(C) == sizeof(float2))
-                tridiag_warp_ff<R>(g, reinterpret_cast<float2*>(spec), piv, base, scale, kx == 0 && kz == 0);
-            else
-                tridiag_warp64<C, R>(g, spec, piv, base, scale, kx == 0 && kz == 0);
-            return;
-        }
-    }
-    const int nb64 = R > 0 ? n64 : (2 * n64 + 31) / 32;
+                                                int n64, int nsys, double scale, int warp32, int thr64, int gauge) {
+    const bool warp64 = R > 0 && !thr64;
+    const int nb64 = warp64 ? n64 : (n64 + 31) / 32;
     if ((int)blockIdx.x < nb64) {
+        if constexpr (R > 0) {
+            if (warp64) {                          // one warp (block) per FP64 system
+                const int sys = order[blockIdx.x];
+                const int kx = sys % g.nxh, kz = sys / g.nxh;
+                const long long base = (long long)kz * g.ny * g.nxh + kx;
+                tridiag_warp64<C, R>(g, spec, piv, base, scale, gauge && kx == 0 && kz == 0);
+                return;
+            }
+        }
         const int t = blockIdx.x * 32 + threadIdx.x;
-        if (t >= 2 * n64) return;
-        const int sys = order[t >> 1];
+        if (t >= n64) return;
+        const int sys = order[t];
         const int kx = sys % g.nxh, kz = sys / g.nxh;
         const long long base = (long long)kz * g.ny * g.nxh + kx;
-        tridiag_fp64<C>(g, spec, tmp, piv, base, t & 1, scale, kx == 0 && kz == 0);
+        tridiag_thread64<C>(g, spec, tmp, piv, base, scale, gauge && kx == 0 && kz == 0);
         return;
     }
     if constexpr (sizeof(C) == sizeof(float2)) {
@@ -705,6 +687,7 @@ __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ 
     const bool top = j == g.ny - 1;
     const bool outface = XF && i == g.nx - 1;               // the outflow face keeps u*
     const T pic = FLUX ? *reinterpret_cast<const T*>(fc.scal + 2) * fc.ckdt : T(0);
+    if (g.ystr) idy = (T)ytab(g, YT_IHV, j);                 // a stretched y: the centre distance across v's face
     T ph = live ? psi[i + g.nx * j + plane * kbeg] : T(0);
     for (int k0 = kbeg; k0 < kend; k0 += ZB) {
         T a0[ZB], a1[ZB], a2[ZB], pT[ZB], pN[ZB], pE[ZB], pp[ZB];
@@ -756,16 +739,23 @@ __global__ void __launch_bounds__(256) k_correct(GridP g, const T* __restrict__ 
 template <typename T>
 __global__ void k_mask_copy(GridP g, const uint8_t* __restrict__ mask, const T* __restrict__ a0,
                             const T* __restrict__ a1, const T* __restrict__ a2, T* __restrict__ b0,
-                            T* __restrict__ b1, T* __restrict__ b2) {
+                            T* __restrict__ b1, T* __restrict__ b2, BodyP body) {
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
     const long long id = i + (long long)g.nx * (j + (long long)g.ny * blockIdx.z);
     uint8_t m = mask[id];
     const bool readable_u = (m & IBM_MASK_U) || (!g.xper && i == g.nx - 1 && (m & IBM_MASK_FACE));
-    b0[id] = readable_u ? a0[id] : T(0);
-    b1[id] = (m & IBM_MASK_V) ? a1[id] : T(0);
-    if (g.ndim == 3) b2[id] = (m & IBM_MASK_W) ? a2[id] : T(0);
+    // a moving body's points hold its velocity (periodic x: v on the +y wall is the only box face)
+    T r[3] = {T(0), T(0), T(0)};
+    if (body.kind != 0)
+        for (int c = 0; c < g.ncomp; ++c)
+            if (!(c == 1 && j == g.ny - 1))
+                r[c] = (T)bodyvel(body, c, g.ox + (i + (c == 0 ? 1.0 : 0.5)) * g.dx,
+                                  g.oy + (j + (c == 1 ? 1.0 : 0.5)) * g.dy);
+    b0[id] = readable_u ? a0[id] : r[0];
+    b1[id] = (m & IBM_MASK_V) ? a1[id] : r[1];
+    if (g.ndim == 3) b2[id] = (m & IBM_MASK_W) ? a2[id] : r[2];
 }
 
 // ---------------------------------------------------------------------------
@@ -856,6 +846,67 @@ __global__ void __launch_bounds__(256) k_diag(GridP g, const T* __restrict__ u, 
 }
 
 // one warp per quantity, fixed order: lane-strided partial sums, then a shuffle tree
+// The same partials on a stretched y, in FP64 per cell: the divergence with the row's cell
+// height, the sums weighted by it (volumes differ by row), and each velocity maximum already
+// divided by its spacing (v: the smaller of the two cells its face joins), as the host expects.
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_str(GridP g, const T* __restrict__ u, const T* __restrict__ v,
+                                                  const T* __restrict__ w, const T* __restrict__ p,
+                                                  const uint8_t* __restrict__ mask, double* __restrict__ part) {
+    __shared__ double sh[12][8];
+    double a[12];
+    for (int q = 0; q < 12; ++q) a[q] = 0.0;
+    const double idx = 1.0 / g.dx, idz = 1.0 / g.dz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += stride) {
+        const int i = (int)(id % g.nx);
+        const long long row = id / g.nx;
+        const int j = (int)(row % g.ny);
+        const int k = (int)(row / g.ny);
+        const uint8_t m = mask[id];
+        const double uc = (double)u[id];
+        // the -x face of the first cell is the inflow face in an inflow/outflow box
+        const double ul = (g.xper || i > 0) ? (double)u[row * g.nx + wrapi(i - 1, g.nx)]
+                                            : ((m & IBM_MASK_FACE) ? g.uin : 0.0);
+        const double vc = (double)v[id], vm = j > 0 ? (double)v[id - g.nx] : 0.0;
+        double d = (uc - ul) * idx + (vc - vm) * ytab(g, YT_IDYC, j);
+        double wc = 0.0;
+        if (g.ndim == 3) {
+            wc = (double)w[id];
+            const double wm = (double)w[i + (long long)g.nx * (j + (long long)g.ny * wrapi(k - 1, g.nz))];
+            d += (wc - wm) * idz;
+        }
+        a[0] += d * d;
+        a[1] = fmax(a[1], fabs(d));
+        const double dyc = ytab(g, YT_DYC, j);
+        const double isp[3] = {idx, ytab(g, YT_IVSP, j), idz};
+        const double x3[3] = {uc, vc, wc};
+        for (int c = 0; c < g.ncomp; ++c) {
+            const double x = x3[c];
+            if (!isfinite(x)) a[11] += 1.0;
+            if (!((m >> c) & 1u)) continue;
+            a[2 + c] = fmax(a[2 + c], fabs(x) * isp[c]);
+            a[5 + c] += x * dyc;
+            a[8 + c] += x * x * dyc;
+        }
+        if (!isfinite((double)p[id])) a[11] += 1.0;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < 12; ++q) {
+        const bool mx = q == 1 || (q >= 2 && q <= 4);
+        const double x = mx ? warp_max(a[q]) : warp_sum(a[q]);
+        if (lane == 0) sh[q][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        const int q = threadIdx.x;
+        const bool mx = q == 1 || (q >= 2 && q <= 4);
+        double t = 0.0;
+        for (int ww = 0; ww < 8; ++ww) t = mx ? fmax(t, sh[q][ww]) : t + sh[q][ww];
+        part[blockIdx.x * 12 + q] = t;
+    }
+}
+
 __global__ void k_diag_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
     const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= 12) return;
@@ -1519,6 +1570,7 @@ __global__ void __launch_bounds__(256) k_outflow(GridP g, const T* __restrict__ 
         } else if (fluid) {
             s = (double)us[ib];
         }
+        if (g.ystr) s *= ytab(g, YT_DYC, (int)(r % g.ny));   // the face's height (a flux, not a sum of speeds)
     }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
@@ -1536,7 +1588,7 @@ __global__ void __launch_bounds__(256) k_outflow(GridP g, const T* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) k_outflow_fix(GridP g, const uint8_t* __restrict__ mask, T* __restrict__ us,
                                                      const double* __restrict__ part, int nparts, double qin,
-                                                     int nout) {
+                                                     double nout) {
     __shared__ double sh[8];
     __shared__ double shift;
     double s = 0.0;
@@ -1547,7 +1599,7 @@ __global__ void __launch_bounds__(256) k_outflow_fix(GridP g, const uint8_t* __r
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < 8; ++w) t += sh[w];
-        shift = nout > 0 ? (qin - t) / nout : 0.0;
+        shift = nout > 0.0 ? (qin - t) / nout : 0.0;
     }
     __syncthreads();
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;   // row (j, k)
@@ -1620,7 +1672,21 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout, bool x_done = false) {
     timer_end(h, t, "fft_forward");
     double scale = g.dy * g.dy / ((double)g.nx * (double)g.nz);
     const int nsys = g.nzs * g.nxh;
-    const int nb64 = g.ny <= 32 * TW_ROWS ? h->n64 : (2 * h->n64 + 31) / 32;
+    // a stretched y solves the symmetric unit off-diagonal form of its rows: the right-hand side
+    // takes the per-row factor s_j dyc_j, the solution s_j, and the zero mode's gauge (the plain
+    // mean of phi) is removed after that scaling
+    const int gauge = g.ystr ? 0 : 1;
+    const int nbs = (int)((h->nspec + 255) / 256);
+    if (g.ystr) {
+        scale = 1.0 / ((double)g.nx * (double)g.nz);
+        k_spec_rows<C><<<nbs, 256, 0, h->stream>>>(g, (C*)h->spec, h->nspec, YT_PIN);
+        IBM_LAUNCH_CHECK();
+    }
+    // FP64 systems: one warp each wherever the warp form covers ny (measured faster: all rows
+    // of a system are loaded at once, where one thread per system waits on memory every few
+    // rows), one thread each for taller grids or when asked
+    const int thr64 = (g.ny > 32 * TW_ROWS || h->tri_form == 2) ? 1 : 0;
+    const int nb64 = thr64 ? (h->n64 + 31) / 32 : h->n64;
     // FP32 systems: one warp each when one thread each would leave the GPU nearly idle
     const int warp32 = (h->prec == IBM_FP32 && g.ny <= 32 * TW_ROWS && nsys - h->n64 < 16384) ? 1 : 0;
     const int nblk = nb64 + (warp32 ? nsys - h->n64 : (nsys - h->n64 + 31) / 32);
@@ -1630,10 +1696,10 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout, bool x_done = false) {
     do {                                                                                                         \
         if (h->prec == IBM_FP64)                                                                                 \
             k_tridiag<double2, RR><<<nblk, 32, 0, h->stream>>>(g, (double2*)h->spec, (double2*)h->spec, h->pivots, \
-                                                               h->pivots32, h->sys_order, h->n64, nsys, scale, warp32); \
+                                                               h->pivots32, h->sys_order, h->n64, nsys, scale, warp32, thr64, gauge); \
         else                                                                                                     \
             k_tridiag<float2, RR><<<nblk, 32, 0, h->stream>>>(g, (float2*)h->spec, (double2*)h->dtemp, h->pivots,  \
-                                                              h->pivots32, h->sys_order, h->n64, nsys, scale, warp32); \
+                                                              h->pivots32, h->sys_order, h->n64, nsys, scale, warp32, thr64, gauge); \
     } while (0)
     if (g.ny <= 32 * 8) IBM_TRIDIAG(8);
     else if (g.ny <= 32 * 16) IBM_TRIDIAG(16);
@@ -1642,6 +1708,12 @@ ibm_status poisson_t(ibm_solver* h, void* rhs_inout, bool x_done = false) {
     else IBM_TRIDIAG(0);
 #undef IBM_TRIDIAG
     IBM_LAUNCH_CHECK();
+    if (g.ystr) {
+        k_spec_rows<C><<<nbs, 256, 0, h->stream>>>(g, (C*)h->spec, h->nspec, YT_POUT);
+        IBM_LAUNCH_CHECK();
+        k_zero_gauge<C><<<1, 256, 0, h->stream>>>(g, (C*)h->spec);
+        IBM_LAUNCH_CHECK();
+    }
     timer_end(h, t, "tridiag");
     timer_begin(h, "fft_inverse", &t);
     if (g.xper) {
@@ -1955,7 +2027,8 @@ template <typename T>
 ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const FluxCorr<T>& fc) {
     const GridP& g = h->gp;
     cudaEvent_t t;
-    const bool fuse_x = g.xper ? h->own_fft : h->dct_rows;
+    // (a stretched y keeps the divergence separate: the fused kernel has no per-row metric)
+    const bool fuse_x = (g.xper ? h->own_fft : h->dct_rows) && !g.ystr;
     if (fuse_x && h->proj_mode != IBM_PROJ_MASKED) {
         // the divergence fused with the forward transform of the x rows (own real FFT on a periodic
         // x, own DCT rows on an inflow/outflow x)
@@ -2261,13 +2334,14 @@ ibm_status outflow_t(ibm_solver* h, int k, bool update) {
     const int nb = (int)((rows + 255) / 256);
     if (nb > h->npartials) return ibm_set_error(IBM_E_INVALID, "too many outflow rows for the partials buffer");
     const double dt = h->phys.dt;
-    const double ucx = h->nfaces[1] > 0 ? g.uin * h->nfaces[0] / (double)h->nfaces[1] / g.dx : 0.0;
+    // U_c: the inflow flux over the fluid outflow area (face counts, or summed heights on a stretched y)
+    const double ucx = h->aface[1] > 0.0 ? g.uin * h->aface[0] / h->aface[1] / g.dx : 0.0;
     k_outflow<T><<<nb, 256, 0, h->stream>>>(g, (const T*)h->buf.u[0], h->mask, (T*)h->ustar[0], (T*)h->Nh[0],
                                            (T)(dt * RK_A[k]), (T)(dt * RK_B[k]), (T)ucx, k > 0, k < 2, update ? 1 : 0,
                                            h->partials);
     IBM_LAUNCH_CHECK();
     k_outflow_fix<T><<<nb, 256, 0, h->stream>>>(g, h->mask, (T*)h->ustar[0], h->partials, nb,
-                                               g.uin * (double)h->nfaces[0], h->nfaces[1]);
+                                               g.uin * h->aface[0], h->aface[1]);
     IBM_LAUNCH_CHECK();
     return IBM_OK;
 }
@@ -2290,7 +2364,7 @@ ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
         timer_end(h, t, "outflow");
     }
     if (cflux) {
-        double dV = g.dx * g.dy * (g.ndim == 3 ? g.dz : 1.0);
+        double dV = g.dx * (g.ystr ? 1.0 : g.dy) * (g.ndim == 3 ? g.dz : 1.0);   // stretched: dy in the partials
         timer_begin(h, "flux_control", &t);
         k_flux_pi<T><<<1, 1024, 0, h->stream>>>(h->partials, nparts, dV, h->phys.target_flux, h->S[k], h->scal);
         IBM_LAUNCH_CHECK();
@@ -2331,7 +2405,7 @@ ibm_status project_t(ibm_solver* h) {
     T* us[3] = {(T*)h->ustar[0], (T*)h->ustar[1], g.ndim == 3 ? (T*)h->ustar[2] : (T*)h->ustar[0]};
     const T* u2 = g.ndim == 3 ? (const T*)h->buf.u[2] : (const T*)h->buf.u[0];
     k_mask_copy<T><<<cell_grid(g), dim3(32, 8), 0, h->stream>>>(g, h->mask, (const T*)h->buf.u[0], (const T*)h->buf.u[1], u2, us[0],
-                                              us[1], us[2]);
+                                              us[1], us[2], h->body);
     IBM_LAUNCH_CHECK();
     if (!g.xper) {
         ibm_status st0 = outflow_t<T>(h, 0, false);
@@ -2347,9 +2421,13 @@ template <typename T>
 ibm_status diag_t(ibm_solver* h, double* out) {
     const GridP& g = h->gp;
     const T* w = g.ndim == 3 ? (const T*)h->buf.u[2] : (const T*)h->buf.u[0];
-    k_diag<T><<<DIAG_BLOCKS, dim3(32, 8), 0, h->stream>>>(g, (const T*)h->buf.u[0], (const T*)h->buf.u[1], w,
-                                                          (const T*)h->buf.p, h->mask, h->partials, 1.0 / g.dx,
-                                                          1.0 / g.dy, 1.0 / g.dz);
+    if (g.ystr)
+        k_diag_str<T><<<DIAG_BLOCKS, 256, 0, h->stream>>>(g, (const T*)h->buf.u[0], (const T*)h->buf.u[1], w,
+                                                          (const T*)h->buf.p, h->mask, h->partials);
+    else
+        k_diag<T><<<DIAG_BLOCKS, dim3(32, 8), 0, h->stream>>>(g, (const T*)h->buf.u[0], (const T*)h->buf.u[1], w,
+                                                              (const T*)h->buf.p, h->mask, h->partials, 1.0 / g.dx,
+                                                              1.0 / g.dy, 1.0 / g.dz);
     IBM_LAUNCH_CHECK();
     k_diag_final<<<1, 12 * 32, 0, h->stream>>>(h->partials, DIAG_BLOCKS, h->scal + 4);
     IBM_LAUNCH_CHECK();
@@ -2420,9 +2498,59 @@ ibm_status autotune_t(ibm_solver* h, int* kzm_out, int* kzd_out) {
     return IBM_OK;
 }
 
+// Self-test of the integer-pipe conversions against the hardware conversions, bit for bit:
+// each thread draws a bit pattern from a counter-based hash of its index (splitmix64, a
+// published mixer), shaped by i % 4 into a random double, an exact FP32 rounding tie, a
+// random float, or a double near the FP32 underflow and overflow thresholds.
+__device__ unsigned long long g_selftest_bad;
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+__global__ void k_selftest_conversions(long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t r = splitmix64((uint64_t)i);
+    bool bad = false;
+    const int kind = (int)(i & 3);
+    if (kind == 2) {                                    // float -> double
+        const float f = __uint_as_float((uint32_t)r);
+        const double a = f32_to_f64(f), b = (double)f;
+        bad = __double_as_longlong(a) != __double_as_longlong(b) && !(a != a && b != b);
+    } else {
+        if (kind == 1) {                               // an exact tie between two floats
+            r = (r & ~0x1fffffffull) | 0x10000000ull;
+        } else if (kind == 3) {                        // exponents around the FP32 range ends
+            const uint64_t E = (r >> 60) & 1 ? 890 + ((r >> 52) & 15) : 1144 + ((r >> 52) & 15);
+            r = (r & 0x800fffffffffffffull) | (E << 52);
+        }
+        const double x = __longlong_as_double((long long)r);
+        const float a = f64_to_f32_rn(x), b = __double2float_rn(x);
+        bad = __float_as_uint(a) != __float_as_uint(b) && !(a != a && b != b);
+    }
+    if (bad) atomicAdd(&g_selftest_bad, 1ull);
+}
+
 }  // namespace
 
 int diag_blocks() { return DIAG_BLOCKS; }
+
+ibm_status selftest_conversions(long long n, long long* bad) {
+    unsigned long long zero = 0, got = 0;
+    cudaError_t e = cudaMemcpyToSymbol(g_selftest_bad, &zero, sizeof(zero));
+    if (e == cudaSuccess) {
+        k_selftest_conversions<<<(unsigned)((n + 255) / 256), 256>>>(n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&got, g_selftest_bad, sizeof(got));
+    if (e != cudaSuccess) return ibm_set_error(IBM_E_CUDA, std::string("self-test: ") + cudaGetErrorString(e));
+    *bad = (long long)got;
+    return IBM_OK;
+}
 
 ibm_status poisson_prepare(ibm_solver* h) {
     // the own row FFT: nx = 2M with M a product of 2, 3 and 5, three M-long buffers per warp

@@ -12,10 +12,11 @@ import numpy as np
 import torch
 
 from . import (ibm_grid_desc, ibm_geom_desc, ibm_buffers, ibm_physics, IBM_FP64, IBM_FP32,
-               ibm_workspace_bytes, ibm_setup_geometry, ibm_weights_bytes, ibm_build_weights, ibm_step,
+               ibm_workspace_bytes, ibm_setup_geometry, ibm_weights_bytes, ibm_weights_bytes_moving,
+               ibm_build_weights, ibm_step,
                ibm_project, ibm_poisson, ibm_diagnostics, ibm_get_classification, ibm_get_weights,
                ibm_state_bytes, ibm_export_state, ibm_import_state, ibm_timing, ibm_get_timing,
-               ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_get_tiles, ibm_set_momentum_tma, ibm_set_own_fft,
+               ibm_launch_count, ibm_autotune, ibm_set_tiles, ibm_get_tiles, ibm_set_momentum_tma, ibm_set_own_fft, ibm_set_tridiag_form,
                ibm_destroy, ibm_projection_bytes, ibm_set_projection, IBM_PROJ_FULLBOX, IBM_PROJ_MASKED,
                ibm_wall_shear)
 
@@ -25,12 +26,13 @@ class Solver:
 
     Parameters mirror the C structs: ndim, n=(nx,ny,nz), L, origin, bc_lo,
     bc_hi, precision ('fp64'|'fp32'), geom_kind, geom_params, and physics
-    nu, dt, g, bmode, flow_mode, target_flux, wall_u, no_ibm, body_force; inflow (x inflow/outflow)."""
+    nu, dt, g, bmode, flow_mode, target_flux, wall_u, no_ibm, body_force; inflow (x inflow/outflow);
+    y_faces (a stretched wall-normal grid: the ny + 1 face heights)."""
 
     def __init__(self, *, ndim, n, L, origin, bc_lo, bc_hi, precision, geom_kind, geom_params, nu, dt,
                  g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0, wall_u=(0.0, 0.0, 0.0), no_ibm=False,
                  body_force=False, g_amp=(0.0, 0.0, 0.0), g_freq=0.0, inflow=(0.0, 0.0, 0.0), samples=None,
-                 device="cuda", stream=None):
+                 y_faces=(), body_u=(0.0, 0.0, 0.0), body_omega=0.0, device="cuda", stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("the IBM solver needs a CUDA device")
         self.device = torch.device(device)
@@ -54,6 +56,11 @@ class Solver:
         gd.precision = IBM_FP64 if precision == "fp64" else IBM_FP32
         for d in range(3):
             gd.inflow[d] = float(inflow[d])
+        self.y_faces = np.ascontiguousarray(y_faces, dtype=np.float64) if len(y_faces) else None
+        if self.y_faces is not None:
+            if self.y_faces.shape != (self.n[1] + 1,):
+                raise ValueError("y_faces: ny + 1 face heights")
+            gd.y_faces = self.y_faces.ctypes.data_as(C.POINTER(C.c_double))
         self.grid = gd
         geo = ibm_geom_desc()
         geo.kind = int(geom_kind)
@@ -94,29 +101,29 @@ class Solver:
             self.h = ibm_setup_geometry(gd, geo, bufs, self.stream.cuda_stream)
             self.weights = None
             self.set_physics(nu=nu, dt=dt, g=g, bmode=bmode, flow_mode=flow_mode, target_flux=target_flux,
-                             wall_u=wall_u, no_ibm=no_ibm, body_force=body_force, g_amp=g_amp, g_freq=g_freq)
+                             wall_u=wall_u, no_ibm=no_ibm, body_force=body_force, g_amp=g_amp, g_freq=g_freq,
+                             body_u=body_u, body_omega=body_omega)
 
     @classmethod
     def from_case(cls, case, precision=None, no_ibm=False, **kw):
         """Build from any object with the attributes of a workload description.  A sampled
         geometry takes its samples through kw (samples=[phi_u, phi_v, phi_w]); a workload
         with projection 'masked' gets the masked projection."""
-        if len(getattr(case, "y_faces", ())):
-            raise NotImplementedError("stretched wall-normal grids are not in the CUDA library")
-        if any(v != 0.0 for v in getattr(case, "body_velocity", ())) or getattr(case, "body_omega", 0.0):
-            raise NotImplementedError("translating and rotating bodies are not in the CUDA library")
         s = cls(ndim=case.ndim, n=case.n, L=case.L, origin=case.origin, bc_lo=case.bc_lo, bc_hi=case.bc_hi,
                 precision=precision or case.precision, geom_kind=case.geom_kind, geom_params=case.geom_params,
                 nu=case.nu, dt=case.dt, g=case.g, bmode=case.bmode, flow_mode=case.flow_mode,
                 target_flux=case.target_flux, wall_u=case.wall_u, no_ibm=no_ibm,
                 inflow=getattr(case, "inflow", (0.0, 0.0, 0.0)), g_amp=getattr(case, "g_amp", (0.0, 0.0, 0.0)),
-                g_freq=getattr(case, "g_freq", 0.0), **kw)
+                g_freq=getattr(case, "g_freq", 0.0), y_faces=tuple(getattr(case, "y_faces", ())),
+                body_u=tuple(getattr(case, "body_velocity", ())) or (0.0, 0.0, 0.0),
+                body_omega=float(getattr(case, "body_omega", 0.0)), **kw)
         if getattr(case, "projection", "fullbox") == "masked":
             s.set_projection("masked")
         return s
 
     def set_physics(self, *, nu, dt, g=(0.0, 0.0, 0.0), bmode=0, flow_mode=0, target_flux=0.0,
-                    wall_u=(0.0, 0.0, 0.0), no_ibm=False, body_force=False, g_amp=(0.0, 0.0, 0.0), g_freq=0.0):
+                    wall_u=(0.0, 0.0, 0.0), no_ibm=False, body_force=False, g_amp=(0.0, 0.0, 0.0), g_freq=0.0,
+                    body_u=(0.0, 0.0, 0.0), body_omega=0.0):
         ph = ibm_physics()
         ph.nu = float(nu)
         ph.dt = float(dt)
@@ -131,8 +138,13 @@ class Solver:
         for c in range(3):
             ph.g_amp[c] = float(g_amp[c])
         ph.g_freq = float(g_freq)
+        bu = tuple(body_u) + (0.0,) * (3 - len(tuple(body_u)))
+        for c in range(3):
+            ph.body_u[c] = float(bu[c])
+        ph.body_omega = float(body_omega)
         self.phys = ph
-        wb = ibm_weights_bytes(self.h)
+        # a translating body's IBM-point counts change as it crosses the grid: room to spare
+        wb = ibm_weights_bytes_moving(self.h) if any(v != 0.0 for v in bu) else ibm_weights_bytes(self.h)
         if self.weights is None or self.weights.numel() < wb:
             with torch.cuda.stream(self.stream):
                 self.weights = torch.empty(max(wb, 256), dtype=torch.uint8, device=self.device)
@@ -242,6 +254,10 @@ class Solver:
         default choice); returns whether it runs on this grid."""
         mode = 2 if enable == "auto" else (1 if enable else 0)
         return ibm_set_own_fft(self.h, mode)
+
+    def tridiag_form(self, form="auto"):
+        """FP64 tridiagonal sweeps: "auto", "warp" (one warp per system) or "thread"."""
+        ibm_set_tridiag_form(self.h, {"auto": 0, "warp": 1, "thread": 2}[form])
 
     def footprint_bytes(self) -> int:
         return (sum(t.numel() * t.element_size() for t in self.u + [self.p]) + self.work.numel() +

@@ -110,6 +110,37 @@ def test_poisson_matches_oracle(name):
     assert np.abs(t.cpu().numpy() - ref).max() < TOL64 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("form", ["warp", "thread"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["wavy3d", "cylinder2d_io", "sphere3d_io", "channel2d"])
+def test_poisson_tridiag_forms_match_oracle(name, precision, form):
+    """Both forms of the FP64 sweeps (a warp or a thread per system) against the oracle's
+    Poisson solve: 1e-12 in FP64; in FP32 mode (FP32 transforms, FP64 sweeps of the
+    near-singular systems, FP32 sweeps of the dominant ones) within 2e-6 of the largest value."""
+    case = small_case(name)
+    g = _gpu(case, precision=precision)
+    g.tridiag_form(form)
+    rng = np.random.default_rng(12)
+    r = rng.standard_normal(g.shape)
+    r -= r.mean()
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    t = torch.tensor(r, dtype=dt, device="cuda").contiguous()
+    g.poisson(t)
+    torch.cuda.synchronize()
+    ref = solve_spectral(OracleSolver(case).grid, r.astype(np.float32).astype(np.float64)
+                         if precision == "fp32" else r)
+    tol = TOL64 if precision == "fp64" else 2e-6
+    assert np.abs(t.cpu().numpy().astype(np.float64) - ref).max() < tol * np.abs(ref).max()
+
+
+def test_integer_pipe_conversions_match_the_hardware_bit_for_bit():
+    """The FP64 sweeps of FP32 fields widen and narrow with integer instructions; 2^24 bit
+    patterns (random doubles, exact ties, random floats, the FP32 range ends) must convert
+    exactly as the hardware conversions do."""
+    from paper_2506_14328_gb300 import ibm_selftest_conversions
+    assert ibm_selftest_conversions(1 << 24) == 0
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_full_steps_match_oracle(name):
     case = small_case(name)

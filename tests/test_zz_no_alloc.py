@@ -36,9 +36,30 @@ def test_rejects_grids_above_the_limit_before_any_gpu_work():
     assert "134217728" in P.ibm_last_error()
 
 
+def test_rejects_sizes_whose_product_would_overflow():
+    """Three extents near 2^31 multiply past 2^63; the limit check must still refuse them
+    (it compares factor by factor) instead of letting a wrapped product through."""
+    import paper_2506_14328_gb300 as P
+    g = P.ibm_grid_desc()
+    g.ndim = 3
+    for d in range(3):
+        g.n[d] = 2 ** 31 - 1
+        g.L[d] = 1.0
+    g.bc_lo[1] = g.bc_hi[1] = P.IBM_BC_NOSLIP
+    g.precision = P.IBM_FP64
+    d = P.ibm_diag()
+    st = P.lib.ibm_diagnostics_noalloc(ctypes.byref(g), ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                       ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_void_p(16), 1.0, None,
+                                       ctypes.byref(d))
+    assert st == P.IBM_E_INVALID
+    assert "134217728" in P.ibm_last_error()
+
+
 @pytest.mark.gpu
+@pytest.mark.parametrize("name", ["wavy3d", "channel2d", "cylinder2d_io", "sphere3d_io"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_noalloc_diagnostics_match_ibm_diagnostics_on_two_calls(precision):
+def test_noalloc_diagnostics_match_ibm_diagnostics_on_two_calls(precision, name):
+    """Periodic and inflow/outflow x, 2D (no w: a NULL pointer) and 3D, both precisions."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
@@ -46,7 +67,7 @@ def test_noalloc_diagnostics_match_ibm_diagnostics_on_two_calls(precision):
     from paper_2506_14328_gb300 import ibm_diagnostics_noalloc
     from paper_2506_14328_gb300.solver import Solver
 
-    case = small_case("wavy3d", precision=precision)
+    case = small_case(name, precision=precision)
     s = Solver.from_case(case)
     f = initial_field(case)
     s.set_state(f["u"], f["v"], f["w"], f["p"])
@@ -57,13 +78,14 @@ def test_noalloc_diagnostics_match_ibm_diagnostics_on_two_calls(precision):
     for call in range(2):
         s.step(1)
         ref = s.diagnostics()
-        got = ibm_diagnostics_noalloc(s.grid, s.u[0].data_ptr(), s.u[1].data_ptr(), s.u[2].data_ptr(),
+        w = s.u[2].data_ptr() if case.ndim == 3 else 0
+        got = ibm_diagnostics_noalloc(s.grid, s.u[0].data_ptr(), s.u[1].data_ptr(), w,
                                       s.p.data_ptr(), mask.data_ptr(), case.dt, s.stream.cuda_stream)
         assert got.status == 0
         assert _close(got.div_l2, ref["div_l2"], ref["div_l2"]), call
         assert _close(got.div_linf, ref["div_linf"], ref["div_linf"]), call
         assert _close(got.cfl, ref["cfl"], ref["cfl"]), call
         assert _close(got.ke, ref["ke"], ref["ke"]), call
-        for c in range(3):
+        for c in range(case.ndim):
             assert _close(got.flux[c], ref["flux"][c], max(abs(v) for v in ref["flux"])), (call, c)
     assert np.isfinite(got.ke)
