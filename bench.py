@@ -158,7 +158,9 @@ def serving_sample(device, n_requests: int = 16, seed: int = 0, load: float = 0.
     mix = serving_mix(seed=seed, n_requests=n_requests, rate_hz=rate)
     # each client sends its initial state with the request (prepared before arrival)
     reqs = [Request(q, t, c, s, init=initial_field(c)) for q, (t, c, s) in enumerate(mix)]
-    srv = Server(device=str(device), max_resident=32, steps_per_tick=25)
+    # default tiles (no autotuning inside the timed run: a deployed server has its tile choices
+    # cached per grid shape); small solves share the persistent momentum launches
+    srv = Server(device=str(device), max_resident=32, steps_per_tick=25, autotune=False)
     stats = srv.serve(reqs)
     srv.close()
     stats.update({"arrival_rate_hz": rate, "assumed_capacity_gcell_s": capacity / 1e9,

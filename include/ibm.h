@@ -370,6 +370,17 @@ ibm_status ibm_selftest_conversions(long long n, long long* mismatches);
 ibm_status ibm_batch_create(void* stream, ibm_batch** out);
 ibm_status ibm_batch_set(ibm_batch* b, ibm_solver* const* members, const int* steps, int n);
 ibm_status ibm_batch_run(ibm_batch* b);
+/* Members of at most max_cells cells (uniform y, no moving body) advance their momentum
+ * predictors -- the fused RHS, RK3 and implicit IBM division of Sec. 2.4 -- in ONE
+ * persistent launch per substage and precision: a fixed grid of blocks walks a work list of
+ * every such member's (column, z chunk) tiles, each with its own grid, fields, stage constants
+ * and coefficients (at most 40 members per precision).  The rest of each member's substage
+ * (flow-rate control, projection) stays on its own stream between those launches, so these
+ * members step in lockstep, substage by substage.  Their update is the register form of the
+ * predictor (compiled into another kernel: FP32 results may differ from the member's own
+ * launch in the last bits).  0 (the default) turns
+ * this off.  Takes effect at the next ibm_batch_set. */
+ibm_status ibm_batch_jobs(ibm_batch* b, long long max_cells);
 void ibm_batch_destroy(ibm_batch* b);
 
 /* Kernels this library has launched through this handle (a running count). */

@@ -31,7 +31,7 @@ EXPORTED = ("ibm_version", "ibm_last_error", "ibm_workspace_bytes", "ibm_setup_g
             "ibm_set_projection", "ibm_wall_shear", "ibm_diagnostics",
             "ibm_get_classification", "ibm_get_weights", "ibm_state_bytes", "ibm_export_state",
             "ibm_import_state", "ibm_timing", "ibm_get_timing", "ibm_launch_count", "ibm_diagnostics_noalloc",
-            "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_set_own_fft", "ibm_set_tridiag_form", "ibm_selftest_conversions", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run",
+            "ibm_autotune", "ibm_set_tiles", "ibm_get_tiles", "ibm_set_momentum_tma", "ibm_set_own_fft", "ibm_set_tridiag_form", "ibm_selftest_conversions", "ibm_batch_create", "ibm_batch_set", "ibm_batch_run", "ibm_batch_jobs",
             "ibm_batch_destroy", "ibm_destroy")
 
 
@@ -114,6 +114,7 @@ def _load() -> C.CDLL:
         "ibm_batch_create": ([C.c_void_p, P(C.c_void_p)], C.c_int),
         "ibm_batch_set": ([C.c_void_p, P(C.c_void_p), P(C.c_int), C.c_int], C.c_int),
         "ibm_batch_run": ([C.c_void_p], C.c_int),
+        "ibm_batch_jobs": ([C.c_void_p, C.c_longlong], C.c_int),
         "ibm_batch_destroy": ([C.c_void_p], None),
         "ibm_destroy": ([C.c_void_p], None),
     }
@@ -314,6 +315,10 @@ def ibm_batch_set(b: int, handles, steps):
 
 def ibm_batch_run(b: int):
     _check(lib.ibm_batch_run(C.c_void_p(b)), "ibm_batch_run")
+
+
+def ibm_batch_jobs(b: int, max_cells: int):
+    _check(lib.ibm_batch_jobs(C.c_void_p(b), int(max_cells)), "ibm_batch_jobs")
 
 
 def ibm_batch_destroy(b: int):

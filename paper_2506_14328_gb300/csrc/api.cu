@@ -965,6 +965,8 @@ struct ibm_batch {
     std::vector<ibm_solver*> members;
     std::vector<int> steps;
     std::vector<long long> launches;   // kernels of each member in one replay
+    long long job_cells = 0;           // members of at most this many cells: momentum by job kernel
+    cudaEvent_t jobev = nullptr;
     bool failed = false;
 };
 
@@ -1009,21 +1011,66 @@ ibm_status ibm_batch_set(ibm_batch* b, ibm_solver* const* members, const int* st
         b->joins.push_back(e);
     }
     if (n == 0) return IBM_OK;
+    if (b->job_cells > 0 && !b->jobev) {
+        if (cudaEventCreateWithFlags(&b->jobev, cudaEventDisableTiming) != cudaSuccess)
+            return ibm_set_error(IBM_E_CUDA, "cudaEventCreate failed");
+    }
+    // job members (small, uniform y, no moving body): their momentum predictors run in one
+    // persistent launch per substage and precision; the rest of each substage on their own streams
+    std::vector<int> solo, jobs[2];
+    for (int q = 0; q < n; ++q) {
+        ibm_solver* h = b->members[q];
+        const bool job = b->job_cells > 0 && h->N <= b->job_cells && !h->gp.ystr && h->body.kind == 0;
+        if (job) jobs[h->prec == IBM_FP64 ? 1 : 0].push_back(q);
+        else solo.push_back(q);
+    }
+    int maxsteps = 0;
+    for (int p = 0; p < 2; ++p) {
+        if ((int)jobs[p].size() > MOM_MAX_JOBS) return ibm_set_error(IBM_E_INVALID, "more job members than one launch takes");
+        // most steps first, so that the members still stepping are always a prefix
+        std::stable_sort(jobs[p].begin(), jobs[p].end(), [&](int a, int c) { return b->steps[a] > b->steps[c]; });
+        if (!jobs[p].empty()) maxsteps = std::max(maxsteps, b->steps[jobs[p][0]]);
+    }
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return ibm_set_error(IBM_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
     ibm_status st = IBM_OK;
     b->launches.assign(n, 0);
+    std::vector<long long> before(n);
+    for (int q = 0; q < n; ++q) before[q] = b->members[q]->launches;
     cudaEventRecord(b->fork, b->stream);
-    for (int q = 0; q < n && st == IBM_OK; ++q) {
+    for (int q : solo) {
+        if (st != IBM_OK) break;
         ibm_solver* h = b->members[q];
         cudaStreamWaitEvent(h->stream, b->fork, 0);
-        long long before = h->launches;
         for (int s = 0; s < b->steps[q] && st == IBM_OK; ++s)
             for (int k = 0; k < 3 && st == IBM_OK; ++k) st = run_substage(h, k, false);
-        b->launches[q] = h->launches - before;
-        h->launches = before;
         cudaEventRecord(b->joins[q], h->stream);
-        cudaStreamWaitEvent(b->stream, b->joins[q], 0);
+    }
+    for (int s = 0; s < maxsteps && st == IBM_OK; ++s)
+        for (int k = 0; k < 3 && st == IBM_OK; ++k) {
+            std::vector<ibm_solver*> act[2];
+            for (int p = 0; p < 2; ++p)
+                for (int q : jobs[p])
+                    if (b->steps[q] > s) act[p].push_back(b->members[q]);
+            for (int p = 0; p < 2 && st == IBM_OK; ++p)
+                st = momentum_jobs_launch(act[p].data(), (int)act[p].size(), k, b->stream);
+            cudaEventRecord(b->jobev, b->stream);
+            for (int p = 0; p < 2 && st == IBM_OK; ++p)
+                for (int q : jobs[p]) {
+                    if (b->steps[q] <= s || st != IBM_OK) continue;
+                    ibm_solver* h = b->members[q];
+                    cudaStreamWaitEvent(h->stream, b->jobev, 0);
+                    h->mom_external = true;
+                    st = run_substage(h, k, false);
+                    h->mom_external = false;
+                    cudaEventRecord(b->joins[q], h->stream);
+                    cudaStreamWaitEvent(b->stream, b->joins[q], 0);
+                }
+        }
+    for (int q : solo) cudaStreamWaitEvent(b->stream, b->joins[q], 0);
+    for (int q = 0; q < n; ++q) {
+        b->launches[q] = b->members[q]->launches - before[q];
+        b->members[q]->launches = before[q];
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(b->stream, &graph);
@@ -1053,9 +1100,16 @@ ibm_status ibm_batch_run(ibm_batch* b) {
     return IBM_OK;
 }
 
+ibm_status ibm_batch_jobs(ibm_batch* b, long long max_cells) {
+    if (!b || max_cells < 0) return ibm_set_error(IBM_E_INVALID, "bad batch or max_cells < 0");
+    b->job_cells = max_cells;
+    return IBM_OK;
+}
+
 void ibm_batch_destroy(ibm_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->jobev) cudaEventDestroy(b->jobev);
     for (auto e : b->joins) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     delete b;

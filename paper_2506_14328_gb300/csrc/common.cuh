@@ -371,6 +371,7 @@ struct ibm_solver {
     int* sys_order = nullptr;      // systems, FP64 ones first
     int n64 = 0;                   // number of FP64 systems
     int tri_form = 0;              // ibm_set_tridiag_form: 0 automatic, 1 warp, 2 thread per FP64 system
+    bool mom_external = false;     // a batch launches this solve's momentum predictor (job kernel)
     void* dtemp = nullptr;
     void* fft_work = nullptr;
     double* partials = nullptr;
@@ -466,6 +467,9 @@ ibm_status run_autotune(ibm_solver* h, int* kzm, int* kzd);
 // Launches the momentum predictor of RK stage k on the solver's stream;
 // *nparts receives the number of flux partials it wrote.
 ibm_status momentum_launch(ibm_solver* h, int k, int* nparts);
+// stage k's momentum predictors of n solves of one precision in one persistent launch on stream
+constexpr int MOM_MAX_JOBS = 40;
+ibm_status momentum_jobs_launch(ibm_solver* const* hs, int n, int k, cudaStream_t stream);
 int momentum_default_kzm(const GridP& g, int prec, bool tma);
 // Builds (or drops) the TMA kernel's tensor maps over the solver's buffers.
 void momentum_prepare(ibm_solver* h);

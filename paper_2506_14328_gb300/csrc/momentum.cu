@@ -461,16 +461,16 @@ __device__ __forceinline__ void mom_iter3(const GridP& g, const MomF<T>& F, cons
     s2 = t;
 }
 
+// One block's work of the register form: the 32 x 16 column (bx, by) over z chunk bz; the
+// flux partial goes to flux_part[pidx].  tiles: 3 plane slots (3D) or 1 (2D) of 3 * HP values.
 template <typename T, bool THREE>
-__global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
-    k_momentum(GridP g, MomF<T> F, StageP<T> sp, IbmStage<T> ib, double* __restrict__ flux_part) {
+__device__ __forceinline__ void mom_block(const GridP& g, const MomF<T>& F, const StageP<T>& sp,
+                                          const IbmStage<T>& ib, double* __restrict__ flux_part, int bx, int by,
+                                          int bz, long long pidx, T* tiles, double* shd) {
     constexpr int NC = THREE ? 3 : 2;
-    constexpr int NS = THREE ? 3 : 1;
     constexpr int SLOT = 3 * HP;                 // one plane tile (u, v, w)
-    __shared__ T tiles[NS * SLOT];
-    __shared__ double shd[MW];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * MX, j0 = blockIdx.y * MY;
+    const int i0 = bx * MX, j0 = by * MY;
     const int i = i0 + tx, jA = j0 + 2 * ty;
     const bool liveA = i < g.nx && jA < g.ny;
     const bool liveB = i < g.nx && jA + 1 < g.ny;
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
     const bool yedge = j0 == 0 || j0 + MY >= g.ny || (!g.xper && (i0 == 0 || i0 + MX >= g.nx));
     const int plane = g.nx * g.ny;
     const int rowA = i + g.nx * jA;               // in-plane index of A (B: + nx)
-    const int segrow = jA * g.nsegx + blockIdx.x;  // row segment of A at plane 0
+    const int segrow = jA * g.nsegx + bx;          // row segment of A at plane 0
     // the point masks of dead cells read 0, so they take part in no ballot
     const uint32_t live_bits = (liveA ? 0xffu : 0u) | (liveB ? 0xff00u : 0u);
     T fsum = T(0);
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
     for (int c = 0; c < 3; ++c) P0.qA[c] = P0.qB[c] = P1.qA[c] = P1.qB[c] = T(0);
 
     if constexpr (THREE) {
-        const int kbeg = blockIdx.z * g.kzm;
+        const int kbeg = bz * g.kzm;
         const int kend = min(kbeg + g.kzm, g.nz);
         int s0 = 0, s1 = SLOT, s2 = 2 * SLOT;
         // prologue: planes kbeg-1 (slot 2) and kbeg (slot 0) give the carried state
@@ -549,8 +549,65 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
         if (tx == 0 && ty == 0) {
             double s = 0.0;
             for (int w = 0; w < MW; ++w) s += shd[w];
-            flux_part[blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z)] = s;
+            flux_part[pidx] = s;
         }
+    }
+}
+
+template <typename T, bool THREE>
+__global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
+    k_momentum(GridP g, MomF<T> F, StageP<T> sp, IbmStage<T> ib, double* __restrict__ flux_part) {
+    constexpr int NS = THREE ? 3 : 1;
+    __shared__ T tiles[NS * 3 * HP];
+    __shared__ double shd[MW];
+    mom_block<T, THREE>(g, F, sp, ib, flux_part, blockIdx.x, blockIdx.y, blockIdx.z,
+                        blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z), tiles, shd);
+}
+
+// ---------------------------------------------------------------------------
+// Many solves' momentum predictors in one persistent launch (serving many small grids):
+// one block per SM slot walks a work list of (solve, column, z chunk) tiles of every job,
+// each job carrying its own grid, fields, stage constants and IBM coefficients.  The tile
+// work is the register form's (mom_block), so each solve's update is bit for bit what its
+// own k_momentum launch computes.  tile0[q]: the first tile of job q (prefix sums); the table
+// (at most MOM_MAX_JOBS jobs) goes by value with the launch.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct MomJob {
+    GridP g;
+    MomF<T> F;
+    StageP<T> sp;
+    IbmStage<T> ib;
+    double* part;
+    int nbx, nby, nbz;
+};
+
+template <typename T>
+struct MomJobs {
+    int njobs, ntiles;
+    int tile0[MOM_MAX_JOBS];
+    MomJob<T> job[MOM_MAX_JOBS];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 2 : 1)
+    k_momentum_jobs(const __grid_constant__ MomJobs<T> jobs) {
+    __shared__ T tiles[3 * 3 * HP];
+    __shared__ double shd[MW];
+    for (int t = blockIdx.x; t < jobs.ntiles; t += gridDim.x) {
+        int lo = 0, hi = jobs.njobs - 1;             // the job whose tile range holds t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs.tile0[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const MomJob<T>& J = jobs.job[lo];
+        const int l = t - jobs.tile0[lo];
+        const int bx = l % J.nbx, by = (l / J.nbx) % J.nby, bz = l / (J.nbx * J.nby);
+        const long long pidx = bx + (long long)J.nbx * (by + (long long)J.nby * bz);
+        __syncthreads();                             // the previous tile is done with the shared tiles
+        if (J.g.ndim == 3) mom_block<T, true>(J.g, J.F, J.sp, J.ib, J.part, bx, by, bz, pidx, tiles, shd);
+        else mom_block<T, false>(J.g, J.F, J.sp, J.ib, J.part, bx, by, bz, pidx, tiles, shd);
     }
 }
 
@@ -1197,10 +1254,26 @@ bool tma_smem_ready() {
     return state[dev] == 1;
 }
 
+// The fields, stage constants and IBM coefficients of stage k of one solve.
+template <typename T>
+void momentum_params(ibm_solver* h, int k, MomF<T>& F, StageP<T>& sp, IbmStage<T>& ib);
+template <typename T>
+ibm_status launch_momentum_kernels(ibm_solver* h, const MomF<T>& F, const StageP<T>& sp, const IbmStage<T>& ib,
+                                   dim3 grd, dim3 blk);
+
 template <typename T>
 ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib, dim3& grd) {
     const GridP& g = h->gp;
     MomF<T> F;
+    momentum_params<T>(h, k, F, sp, ib);
+    dim3 blk(MX, MW, 1);
+    grd = momentum_grid(g);
+    return launch_momentum_kernels<T>(h, F, sp, ib, grd, blk);
+}
+
+template <typename T>
+void momentum_params(ibm_solver* h, int k, MomF<T>& F, StageP<T>& sp, IbmStage<T>& ib) {
+    const GridP& g = h->gp;
     for (int c = 0; c < 3; ++c) {
         F.u[c] = (const T*)h->buf.u[c];
         F.us[c] = (T*)h->ustar[c];
@@ -1232,8 +1305,12 @@ ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib,
     sp.write_n = k < 2;
     sp.flux_sum = h->phys.flow_mode == IBM_FLOW_CONST_FLUX;
     ib = stage_coefs<T>(h, k);
-    dim3 blk(MX, MW, 1);
-    grd = momentum_grid(g);
+}
+
+template <typename T>
+ibm_status launch_momentum_kernels(ibm_solver* h, const MomF<T>& F, const StageP<T>& sp, const IbmStage<T>& ib,
+                                   dim3 grd, dim3 blk) {
+    const GridP& g = h->gp;
     if (g.ystr || h->body.kind != 0) {
         const BodyP& bd = h->body;
         if (g.ystr) {   // (a moving body needs a uniform y)
@@ -1258,7 +1335,49 @@ ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib,
     return IBM_OK;
 }
 
+// The momentum predictors of stage k of several solves of one precision in one persistent
+// launch (k_momentum_jobs); the job table goes by value with the launch.
+template <typename T>
+ibm_status launch_momentum_jobs(ibm_solver* const* hs, int n, int k, cudaStream_t stream) {
+    MomJobs<T> J;
+    J.njobs = n;
+    int tiles = 0;
+    for (int q = 0; q < n; ++q) {
+        ibm_solver* h = hs[q];
+        MomJob<T>& j = J.job[q];
+        j.g = h->gp;
+        IbmStage<T> ib;
+        momentum_params<T>(h, k, j.F, j.sp, ib);
+        j.ib = ib;
+        j.part = h->partials;
+        const dim3 d = momentum_grid(h->gp);
+        j.nbx = (int)d.x;
+        j.nby = (int)d.y;
+        j.nbz = (int)d.z;
+        J.tile0[q] = tiles;
+        tiles += (int)(d.x * d.y * d.z);
+    }
+    J.ntiles = tiles;
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_momentum_jobs<T>, MX * MW, 0) != cudaSuccess || per < 1)
+        return ibm_set_error(IBM_E_CUDA, "momentum jobs: device attributes");
+    const int blocks = std::max(1, std::min(tiles, sms * per));
+    k_momentum_jobs<T><<<blocks, dim3(MX, MW, 1), 0, stream>>>(J);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ibm_set_error(IBM_E_CUDA, std::string("momentum jobs: ") + cudaGetErrorString(e));
+    for (int q = 0; q < n; ++q) hs[q]->launches += 1;
+    return IBM_OK;
+}
+
 }  // namespace
+
+ibm_status momentum_jobs_launch(ibm_solver* const* hs, int n, int k, cudaStream_t stream) {
+    if (n <= 0) return IBM_OK;
+    if (n > MOM_MAX_JOBS) return ibm_set_error(IBM_E_INVALID, "too many momentum jobs in one launch");
+    return hs[0]->prec == IBM_FP64 ? launch_momentum_jobs<double>(hs, n, k, stream)
+                                   : launch_momentum_jobs<float>(hs, n, k, stream);
+}
 
 void momentum_release(ibm_solver* h) {
     delete static_cast<MomMaps*>(h->mom_maps);

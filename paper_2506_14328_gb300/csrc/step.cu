@@ -2354,7 +2354,13 @@ ibm_status substage_t(ibm_solver* h, int k, bool predictor_only) {
     cudaEvent_t t;
     int nparts = 0;
     timer_begin(h, "momentum", &t);
-    ibm_status st0 = momentum_launch(h, k, &nparts);
+    ibm_status st0 = IBM_OK;
+    if (h->mom_external) {       // a batch's persistent job kernel computed u* already
+        const dim3 d = momentum_grid(g);
+        nparts = (int)(d.x * d.y * d.z);
+    } else {
+        st0 = momentum_launch(h, k, &nparts);
+    }
     if (st0 != IBM_OK) return st0;
     timer_end(h, t, "momentum");
     if (!g.xper) {

@@ -2,9 +2,12 @@
 
 The serving contract: a solve's result is the same alone and in the mix.
 Every solve's kernels read and write only its own buffers, and every
-reduction has a fixed order for a fixed tiling, so the comparison is
-bitwise (the tiles are fixed here; the autotuner only changes the order of
-the flux-control partial sums, checked at the FP64 tolerance).
+reduction has a fixed order for a fixed tiling, so a batch of whole steps is
+bitwise equal to stepping alone.  The momentum job kernel of small members
+computes the register form of the predictor in another kernel, whose
+instruction selection may round FP32 differently: there the comparison is
+1e-12 of the largest value in FP64 and 2e-5 in FP32 (the FP32 mode's stated
+bound against FP64), as for the two forms of the predictor.
 """
 import numpy as np
 import pytest
@@ -31,6 +34,12 @@ def _same(a, b):
     return all(np.array_equal(x, y) for x, y in zip(ua, ub)) and np.array_equal(pa, pb)
 
 
+def _close(a, b, precision):
+    """Velocities within 1e-12 (FP64) or 2e-5 (FP32) of each component's largest value."""
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    return all(np.abs(x - y).max() <= tol * max(np.abs(y).max(), 1e-300) for x, y in zip(a[0], b[0]))
+
+
 def test_batch_graph_equals_separate_stepping():
     from paper_2506_14328_gb300 import ibm_batch_create, ibm_batch_set, ibm_batch_run, ibm_batch_destroy
     c1 = small_case("wavy3d", precision="fp32")
@@ -48,6 +57,38 @@ def test_batch_graph_equals_separate_stepping():
     assert _same(a1.state(), b1.state())
     assert _same(a2.state(), b2.state())
     assert a1.diagnostics()["step"] == 6 and a2.diagnostics()["step"] == 10
+    ibm_batch_destroy(batch)
+
+
+def test_batch_with_the_momentum_job_kernel_equals_separate_stepping():
+    """Small members advance their momentum predictors in one persistent launch per substage
+    (ibm_batch_jobs); each member's fields are bit for bit those of stepping it alone with the
+    register form of the predictor, to the tolerances above, for uneven step counts (members
+    drop out of the lockstep as their steps run out), both precisions, 2D and 3D, periodic and
+    inflow/outflow x."""
+    from paper_2506_14328_gb300 import (ibm_batch_create, ibm_batch_set, ibm_batch_run, ibm_batch_jobs,
+                                        ibm_batch_destroy)
+    cases = [small_case("wavy3d", precision="fp32"), small_case("channel2d", precision="fp64"),
+             small_case("sphere3d", precision="fp32"), small_case("cylinder2d_io", precision="fp32"),
+             small_case("sphere3d_io", precision="fp64")]
+    steps = [3, 5, 2, 4, 1]
+    a = [_solver(c) for c in cases]
+    b = [_solver(c) for c in cases]
+    for s in a + b:
+        s.use_tma(False)
+        s.sync()
+    st = torch.cuda.Stream()
+    batch = ibm_batch_create(st.cuda_stream)
+    ibm_batch_jobs(batch, 1 << 22)
+    ibm_batch_set(batch, [s.h for s in a], steps)
+    ibm_batch_run(batch)
+    ibm_batch_run(batch)
+    st.synchronize()
+    for s, n in zip(b, steps):
+        s.step(2 * n)
+    for x, y, n, c in zip(a, b, steps, cases):
+        assert _close(x.state(), y.state(), c.precision), c.name
+        assert x.diagnostics()["step"] == 2 * n
     ibm_batch_destroy(batch)
 
 
@@ -72,10 +113,10 @@ def test_server_result_is_the_same_alone_and_in_the_mix():
     assert stats["requests"] == len(reqs)
     assert stats["p50_s"] is not None and stats["p99_s"] >= stats["p50_s"]
     assert stats["recaptures"] >= 2
-    for r in reqs[:3]:
+    for r in reqs:
         s = _solver(r.case)
         s.step(r.steps)
-        assert _same(s.state(), r.result["state"]), r.case.name
+        assert _close(s.state(), r.result["state"], r.case.precision), r.case.name
         assert r.result["diag"]["status"] == 0
     srv.close()
 
