@@ -163,6 +163,14 @@ def serving_sample(device, n_requests: int = 16, seed: int = 0, load: float = 0.
     srv = Server(device=str(device), max_resident=32, steps_per_tick=25, autotune=False)
     stats = srv.serve(reqs)
     srv.close()
+    # capacity: the same requests all arriving at once (the server saturated)
+    sat = [Request(q, 0.0, c, s, init=r.init) for q, ((t, c, s), r) in enumerate(zip(mix, reqs))]
+    srv = Server(device=str(device), max_resident=32, steps_per_tick=25, autotune=False)
+    st2 = srv.serve(sat)
+    srv.close()
+    stats["saturated"] = {"gcell_updates_per_s": st2["gcell_updates_per_s"], "wall_s": st2["wall_s"],
+                          "p50_s": st2["p50_s"], "p99_s": st2["p99_s"],
+                          "what": "the same requests, all arriving at t = 0"}
     stats.update({"arrival_rate_hz": rate, "assumed_capacity_gcell_s": capacity / 1e9,
                   "mix": "C5 at its stated distributions: 2D n^2 n in [128,1024], 3D n^3 n in [64,192], "
                          "steps 500-5000, Re 10-2000, FP32 mode, Poisson arrivals", "seed": seed})

@@ -1231,10 +1231,93 @@ __global__ void __launch_bounds__(256) k_irfft_rows(FftPlan pl, long long rows, 
 // XF: an inflow/outflow x instead: the inflow face value is the left neighbour of x = 0,
 // the row goes into the DCT order, and the twiddled DCT coefficients are written over the
 // row of xout (as k_dct_rows) instead of a half spectrum.
+// The divergence of one x row by one warp for FP32 fields with nx a multiple of 128: each
+// lane takes 4 consecutive cells of a 128-cell chunk with 16-byte loads, u*(x-1) of its first
+// cell comes from the lane below (or the previous chunk), and the results go to the row
+// buffer as pairs (the real layout, padded or not, or the DCT order of an inflow/outflow x).
+// The constant-flow-rate increment of an IBM point finds its coefficient from the number of
+// IBM points before it in its 32-point segment (a prefix over the segment's 8 lanes).
+template <bool THREE, bool FLUX, bool XF, bool PAD>
+__device__ __forceinline__ void div_row_vec4(const GridP& g, const float* __restrict__ ur, const float* __restrict__ vr,
+                                             const float* __restrict__ vmr, const float* __restrict__ wr,
+                                             const float* __restrict__ wmr, const uint8_t* __restrict__ mr,
+                                             bool has_below, const FluxCorr<float>& fc, float pic, float idx,
+                                             float idy, float idz, int rowseg, float carry, float* __restrict__ d,
+                                             int N) {
+    const int lane = threadIdx.x & 31;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c0 = 0; c0 < g.nx; c0 += 128) {
+        const int x0 = c0 + 4 * lane;
+        const float4 u4 = *reinterpret_cast<const float4*>(ur + x0);
+        const float4 v4 = *reinterpret_cast<const float4*>(vr + x0);
+        const float4 m4 = has_below ? *reinterpret_cast<const float4*>(vmr + x0) : z4;
+        float4 w4 = z4, q4 = z4;
+        if (THREE) {
+            w4 = *reinterpret_cast<const float4*>(wr + x0);
+            q4 = *reinterpret_cast<const float4*>(wmr + x0);
+        }
+        float uc[4] = {u4.x, u4.y, u4.z, u4.w};
+        if (FLUX) {
+            const uint32_t mb = *reinterpret_cast<const uint32_t*>(mr + x0);
+            uint32_t ibm = 0;                                  // IBM-point bits of the 4 cells
+#pragma unroll
+            for (int e = 0; e < 4; ++e) ibm |= ((mb >> (8 * e + 4)) & 1u) << e;
+            if (__any_sync(0xffffffffu, ibm != 0u)) {
+                // IBM points before this lane's first cell within its 32-point segment (8 lanes)
+                const int cnt = __popc(ibm);
+                int pre = cnt;
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, pre, o, 8);
+                    if ((lane & 7) >= o) pre += t;
+                }
+                pre -= cnt;
+                const int seg = rowseg + (x0 >> 5);
+                const int base = fc.segoff[seg] + pre;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t me = (mb >> (8 * e)) & 0xffu;
+                    if (!(me & IBM_MASK_U)) continue;
+                    float beta = 1.f;
+                    if (me & IBM_MASK_IBM_U) beta = fc.coef[base + __popc(ibm & ((1u << e) - 1u))].b;
+                    uc[e] += pic * beta;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if ((mb >> (8 * e)) & IBM_MASK_U) uc[e] += pic;
+            }
+        }
+        float ul = __shfl_up_sync(0xffffffffu, uc[3], 1);
+        if (lane == 0) ul = carry;
+        carry = __shfl_sync(0xffffffffu, uc[3], 31);
+        const float vv[4] = {v4.x, v4.y, v4.z, v4.w}, vm[4] = {m4.x, m4.y, m4.z, m4.w};
+        const float ww[4] = {w4.x, w4.y, w4.z, w4.w}, wm[4] = {q4.x, q4.y, q4.z, q4.w};
+        float dv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float t = (uc[e] - (e == 0 ? ul : uc[e - 1])) * idx;
+            t += (vv[e] - vm[e]) * idy;
+            if (THREE) t += (ww[e] - wm[e]) * idz;
+            dv[e] = t;
+        }
+        if (XF) {
+            // DCT order: even x at x / 2, odd x at N - 1 - (x - 1) / 2 (each pair in one complex slot)
+            const int re = x0 >> 1, ro = N - 2 - (x0 >> 1);
+            *reinterpret_cast<float2*>(d + pzr<PAD>(re)) = make_float2(dv[0], dv[2]);
+            *reinterpret_cast<float2*>(d + pzr<PAD>(ro)) = make_float2(dv[3], dv[1]);
+        } else {
+            *reinterpret_cast<float2*>(d + pzr<PAD>(x0)) = make_float2(dv[0], dv[1]);
+            *reinterpret_cast<float2*>(d + pzr<PAD>(x0 + 2)) = make_float2(dv[2], dv[3]);
+        }
+    }
+}
+
 template <typename T, typename C, bool THREE, bool FLUX, bool XF>
 __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restrict__ u, const T* __restrict__ v,
                                                        const T* __restrict__ w, const uint8_t* __restrict__ mask,
-                                                       FluxCorr<T> fc, T idx, T idy, T idz, FftPlan pl,
+                                                       FluxCorr<T> fc, T idx, T idy, T idz,
+                                                       const __grid_constant__ FftPlan pl,
                                                        C* __restrict__ out, const C* __restrict__ tab,
                                                        T* __restrict__ xout, const T* __restrict__ tw) {
     extern __shared__ unsigned char fft_smem[];
@@ -1272,48 +1355,65 @@ __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restr
         }
         carry = __shfl_sync(0xffffffffu, uc, (g.nx - 1) & 31);
     }
-    constexpr int SB = 6;      // passes whose loads go out together (measured: 3, 4, 6, 12 -> 0.150, 0.146, 0.139, 0.187 ms)
-    for (int s0 = 0; s0 < nseg; s0 += SB) {
-        T uc[SB], vc[SB], vm[SB], wc[SB], wm[SB];
-        uint8_t m[SB];
-#pragma unroll
-        for (int t = 0; t < SB; ++t) {
-            const int x = (s0 + t) * 32 + lane;
-            uc[t] = vc[t] = vm[t] = wc[t] = wm[t] = T(0);
-            m[t] = 0;
-            if (s0 + t < nseg && x < g.nx) {
-                uc[t] = u[rowb + x];
-                vc[t] = v[rowb + x];
-                if (j > 0) vm[t] = v[rowb + x - g.nx];
-                if (THREE) {
-                    wc[t] = w[rowb + x];
-                    wm[t] = w[rowm + x];
-                }
-                if (FLUX) m[t] = mask[rowb + x];
-            }
+    // the row's own pointers: the loads below index them with 32-bit offsets
+    const T* __restrict__ ur = u + rowb;
+    const T* __restrict__ vr = v + rowb;
+    const T* __restrict__ vmr = v + rowb - (j > 0 ? g.nx : 0);
+    const T* __restrict__ wr = w + rowb;
+    const T* __restrict__ wmr = w + rowm;
+    const uint8_t* __restrict__ mr = mask + rowb;
+    if constexpr (sizeof(T) == 4) {
+        if ((g.nx & 127) == 0) {
+            div_row_vec4<THREE, FLUX, XF, PAD>(g, ur, vr, vmr, wr, wmr, mr, j > 0, fc, pic, idx, idy, idz, rowseg,
+                                               carry, reinterpret_cast<float*>(d), N);
+            goto transform;
         }
-#pragma unroll
-        for (int t = 0; t < SB; ++t) {
-            const int s = s0 + t;
-            if (s >= nseg) break;
-            const int x = s * 32 + lane;
-            const bool live = x < g.nx;
-            T ucc = uc[t];
-            if (FLUX) {
-                const unsigned b = __ballot_sync(0xffffffffu, (m[t] & IBM_MASK_IBM_U) != 0);
-                if (live) ucc += flux_increment(fc, pic, m[t], b, rowseg + s, lane);
+    }
+    {
+    constexpr int SB = 6;      // passes whose loads go out together (measured: 3, 4, 6, 12 -> 0.150, 0.146, 0.139, 0.187 ms)
+        for (int s0 = 0; s0 < nseg; s0 += SB) {
+            T uc[SB], vc[SB], vm[SB], wc[SB], wm[SB];
+            uint8_t m[SB];
+    #pragma unroll
+            for (int t = 0; t < SB; ++t) {
+                const int x = (s0 + t) * 32 + lane;
+                uc[t] = vc[t] = vm[t] = wc[t] = wm[t] = T(0);
+                m[t] = 0;
+                if (s0 + t < nseg && x < g.nx) {
+                    uc[t] = ur[x];
+                    vc[t] = vr[x];
+                    if (j > 0) vm[t] = vmr[x];
+                    if (THREE) {
+                        wc[t] = wr[x];
+                        wm[t] = wmr[x];
+                    }
+                    if (FLUX) m[t] = mr[x];
+                }
             }
-            T ul = __shfl_up_sync(0xffffffffu, ucc, 1);
-            if (lane == 0) ul = carry;
-            carry = __shfl_sync(0xffffffffu, ucc, 31);
-            if (live) {
-                T dv = (ucc - ul) * idx;
-                dv += (vc[t] - vm[t]) * idy;
-                if (THREE) dv += (wc[t] - wm[t]) * idz;
-                d[pzr<PAD>(XF ? ((x & 1) ? N - 1 - (x >> 1) : (x >> 1)) : x)] = dv;
+    #pragma unroll
+            for (int t = 0; t < SB; ++t) {
+                const int s = s0 + t;
+                if (s >= nseg) continue;          // (not break: the loop must unroll, keeping the arrays in registers)
+                const int x = s * 32 + lane;
+                const bool live = x < g.nx;
+                T ucc = uc[t];
+                if (FLUX) {
+                    const unsigned b = __ballot_sync(0xffffffffu, (m[t] & IBM_MASK_IBM_U) != 0);
+                    if (live) ucc += flux_increment(fc, pic, m[t], b, rowseg + s, lane);
+                }
+                T ul = __shfl_up_sync(0xffffffffu, ucc, 1);
+                if (lane == 0) ul = carry;
+                carry = __shfl_sync(0xffffffffu, ucc, 31);
+                if (live) {
+                    T dv = (ucc - ul) * idx;
+                    dv += (vc[t] - vm[t]) * idy;
+                    if (THREE) dv += (wc[t] - wm[t]) * idz;
+                    d[pzr<PAD>(XF ? ((x & 1) ? N - 1 - (x >> 1) : (x >> 1)) : x)] = dv;
+                }
             }
         }
     }
+transform:
     __syncwarp();
     const C* Z = warp_fft_any<-1, C, false, PAD>(pl, reinterpret_cast<const C*>(d), b0, b1, tab);
     if (!XF) {

@@ -614,6 +614,37 @@ def test_own_row_fft_matches_cufft_and_oracle(n, precision):
     g.close()
 
 
+@pytest.mark.parametrize("variant", ["wavy3d_flux", "sphere3d_forced", "cylinder2d_io", "tubes3d_io"])
+def test_fused_divergence_fp32_rows_of_128_cells(variant):
+    """FP32 fields with nx a multiple of 128 take the fused divergence's 16-byte row loads (four
+    cells per lane, the flow-rate increment's IBM coefficients found by a prefix over the
+    segment's lanes, pairs stored in the real or DCT order).  Over full steps against the FP64
+    oracle within 2e-5 of the largest value (the FP32 mode's stated bound), and within 1e-5 of
+    the unfused FP32 path (cuFFT rows, per-cell divergence)."""
+    from inputs import FLOW_FORCED
+    case = {
+        "wavy3d_flux": small_case("wavy3d", precision="fp32").with_(n=(128, 36, 20), name="wavy3d_128x36x20"),
+        "sphere3d_forced": small_case("sphere3d", precision="fp32").with_(n=(128, 30, 26), L=(4.2666, 1.0, 1.0)),
+        "cylinder2d_io": small_case("cylinder2d_io", precision="fp32").with_(n=(256, 50, 1)),
+        "tubes3d_io": small_case("tubes3d_io", precision="fp32").with_(n=(128, 48, 32)),
+    }[variant]
+    f = initial_field(case)
+    o = OracleSolver(case.with_(precision="fp64"))
+    o.set_state(f["u"], f["v"], f["w"], f["p"])
+    runs = []
+    for own in (True, False):
+        g = _gpu(case)
+        assert g.use_own_fft(own) == own
+        g.set_state(f["u"], f["v"], f["w"], f["p"])
+        g.step(case.steps)
+        runs.append(g.state()[0])
+        g.close()
+    o.step(case.steps)
+    for c in range(o.grid.ncomp):
+        assert _rel(o, runs[0][c], o.u[c], c) < 2e-5, c
+        assert _rel(o, runs[0][c], runs[1][c], c) < 1e-5, c
+
+
 @pytest.mark.parametrize("variant", ["wavy3d_flux", "cylinder2d_flux", "sphere3d_forced", "channel2d_forced",
                                      "cylinder2d_io", "sphere3d_io", "tubes3d_io"])
 def test_fused_divergence_and_row_transform_match_oracle(variant):
