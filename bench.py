@@ -426,6 +426,8 @@ def run_gpu(args):
         per_kernel = {}
         for name, (n, tot) in kt.items():
             per_kernel[name] = {"launches": n, "ms_total": tot, "share": tot / ms if ms > 0 else None}
+            if name == "ibm_division":   # timed inside the momentum interval
+                per_kernel[name]["within"] = "momentum"
         # roofline of the dominant kernel of this library
         mine = {k: v for k, v in kt.items() if not k.startswith("fft")}   # cuFFT is library code
         dom = max(mine, key=lambda k: mine[k][1]) if mine else "momentum"
@@ -445,6 +447,8 @@ def run_gpu(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic, "kernel": dom,
                 "alg_bytes_per_launch": alg, "avg_launch_ms": avg_s * 1e3,
+                "launches_timed": ("k_momentum_tma and the IBM division after it (k_ibm_division), one interval"
+                                   if dom == "momentum" else dom),
                 "peak_source": peaks["source"] + ", copy bandwidth; kernel timed inside a long step"}
         cpu = None
         if world == 1:

@@ -243,7 +243,7 @@ size_t carve(ibm_solver* h, const GridP& g, int prec, size_t fft_work, char* bas
     char* fftab = take(((size_t)g.nx + 2) * 2 * esz);                 // own row-FFT twiddles
     char* dtemp = prec == IBM_FP32 ? take(nspec * 2 * sizeof(double)) : nullptr;
     char* fftw = take(fft_work);
-    int npart = momentum_blocks(g);
+    int npart = momentum_blocks(g) + IBM_DIV_PARTS;
     if (npart < DIAG_PART) npart = DIAG_PART;
     if (npart < 120 * 4) npart = 120 * 4;
     char* partials = take((size_t)npart * sizeof(double));

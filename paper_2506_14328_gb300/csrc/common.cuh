@@ -93,7 +93,9 @@ __host__ __device__ __forceinline__ double bodyvel(const BodyP& b, int c, double
 // The IBM coefficients of one stage for one component: indexed by list
 // position; segoff gives the list position of the first IBM point of every
 // 32-point x segment (lists are sorted by linear index).
-template <typename T> struct Coef4 { T a, b, s, pad; };
+// 16-byte aligned: one vector load per coefficient set (the lists start on 256-byte boundaries
+// and every entry is 16 or 32 bytes)
+template <typename T> struct alignas(16) Coef4 { T a, b, s, pad; };
 
 template <typename T> struct IbmStage {
     const int* segoff[3];
@@ -128,6 +130,8 @@ inline constexpr double RK_T[3] = {0.0, 64.0 / 120.0, 80.0 / 120.0};
 // march g.kzm planes in z.  The autotuner picks kzm from KZM_CHOICES; the flux
 // partials are sized for the smallest choice.
 constexpr int MOM_TX = 32, MOM_WARPS = 8, MOM_TY = 16, MOM_KZ_MIN = 8;
+// blocks (and flux partials) of the IBM division after the TMA predictor, at most
+constexpr int IBM_DIV_PARTS = 256;
 constexpr int KZM_CHOICES[8] = {8, 12, 16, 24, 32, 48, 64, 86};
 constexpr int KZD_CHOICES[4] = {4, 8, 16, 32};
 inline dim3 momentum_grid(const GridP& g, int kzm) {

@@ -263,14 +263,24 @@ __device__ __forceinline__ void mom_ibm_fix(const IbmStage<T>& ib, const StageP<
     }
 }
 
-template <typename T, int NC>
+// DEFER: an IBM point keeps R (its update before the division) in u* and N without the wall
+// source; k_ibm_division finishes it, and the flow-rate sum leaves it out.
+template <typename T, int NC, bool DEFER = false>
 __device__ __forceinline__ void mom_write(const MomF<T>& F, const StageP<T>& sp, int ida, int idb, bool liveA,
                                           bool liveB, uint32_t mA, uint32_t mB, T (&oA)[3], T (&oB)[3], T (&NA)[3],
-                                          T (&NB)[3], T& fsum, bool outcol) {
+                                          T (&NB)[3], T& fsum, bool outcol, const T (&RA)[3], const T (&RB)[3]) {
+    if (DEFER) {
+        const T fa = ((mA >> 4) & 1u) ? T(0) : oA[0], fb = ((mB >> 4) & 1u) ? T(0) : oB[0];
+        fsum += ((mA & 1u) ? fa : T(0)) + ((mB & 1u) ? fb : T(0));
+    }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         if (c == 0 && outcol) continue;   // u on the outflow face: the outflow update writes it
         const bool ia = (mA >> c) & 1u, ibb = (mB >> c) & 1u;
+        if (DEFER) {
+            if ((mA >> (4 + c)) & 1u) oA[c] = RA[c];
+            if ((mB >> (4 + c)) & 1u) oB[c] = RB[c];
+        }
         oA[c] = ia ? oA[c] : T(0);
         oB[c] = ibb ? oB[c] : T(0);
         NA[c] = ia ? NA[c] : T(0);
@@ -282,12 +292,13 @@ __device__ __forceinline__ void mom_write(const MomF<T>& F, const StageP<T>& sp,
             if (liveB) F.Nn[c][idb] = NB[c];
         }
     }
-    fsum += oA[0] + oB[0];
+    if (!DEFER) fsum += oA[0] + oB[0];
 }
 
 // One plane k of the 3D update.  t0 / t1: the tiles of planes k and k+1, with
 // rows RS apart and components CS apart; a, b: the tile positions of A and B.
-template <typename T, int RS, int CS, bool OWN>
+// DEFER: the IBM division is left to k_ibm_division (see mom_write).
+template <typename T, int RS, int CS, bool OWN, bool DEFER = false>
 __device__ __forceinline__ void mom_plane3(const GridP& g, const MomF<T>& F, const StageP<T>& sp,
                                            const IbmStage<T>& ib, int a, int b, const T* __restrict__ t0,
                                            const T* __restrict__ t1, MomCarry<T>& C, const MomPre<T>& P,
@@ -375,11 +386,11 @@ __device__ __forceinline__ void mom_plane3(const GridP& g, const MomF<T>& F, con
         mom_update(sp, wB, NB[2], P.tB - pB, sp.cgz, P.qB[2], oB[2], RB[2]);
     }
     const uint32_t mA = m & 0xffu, mB = (m >> 8) & 0xffu;
-    if (__any_sync(0xffffffffu, (mA | mB) & (IBM_MASK_IBM_U | IBM_MASK_IBM_V | IBM_MASK_IBM_W))) {
+    if (!DEFER && __any_sync(0xffffffffu, (mA | mB) & (IBM_MASK_IBM_U | IBM_MASK_IBM_V | IBM_MASK_IBM_W))) {
         const T ua3[3] = {uA, vA, wA}, ub3[3] = {uB, vB, wB};
         mom_ibm_fix<T, 3>(ib, sp, mA, mB, segA, segA + g.nsegx, ua3, ub3, RA, RB, oA, oB, NA, NB);
     }
-    mom_write<T, 3>(F, sp, ida, idb, liveA, liveB, mA, mB, oA, oB, NA, NB, fsum, outcol);
+    mom_write<T, 3, DEFER>(F, sp, ida, idb, liveA, liveB, mA, mB, oA, oB, NA, NB, fsum, outcol, RA, RB);
 
     // carry this column into the next plane
     C.ubA = uA; C.ubB = uB; C.vbA = vA; C.vbB = vB; C.wbA = wA; C.wbB = wB;
@@ -434,7 +445,7 @@ __device__ __forceinline__ void mom_plane2(const GridP& g, const MomF<T>& F, con
         const T ua3[3] = {uA, vA, T(0)}, ub3[3] = {uB, vB, T(0)};
         mom_ibm_fix<T, 2>(ib, sp, mA, mB, segA, segA + g.nsegx, ua3, ub3, RA, RB, oA, oB, NA, NB);
     }
-    mom_write<T, 2>(F, sp, ida, idb, liveA, liveB, mA, mB, oA, oB, NA, NB, fsum, outcol);
+    mom_write<T, 2>(F, sp, ida, idb, liveA, liveB, mA, mB, oA, oB, NA, NB, fsum, outcol, RA, RB);
 }
 
 // One step of the 3D plane loop: store plane k+1 (register set R) into its
@@ -1163,7 +1174,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
             }
         }
         const int ida = rowA + k * plane;
-        mom_plane3<T, L::RX, L::CS, true>(g, F, sp, ib, ta, tb, reinterpret_cast<const T*>(s0),
+        mom_plane3<T, L::RX, L::CS, true, true>(g, F, sp, ib, ta, tb, reinterpret_cast<const T*>(s0),
                                           reinterpret_cast<const T*>(s1), C, P, ua, ub, mc, k, ida, ida + g.nx,
                                           liveA, liveB, segrow + k * g.ny * g.nsegx, fsum, outcol);
         mc = mn & live_bits;
@@ -1176,6 +1187,62 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
             double s = 0.0;
             for (int q = 0; q < MW; ++q) s += shd[q];
             flux_part[blockIdx.x + gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z)] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The implicit IBM division (Eq. rk3-rai) of the points that k_momentum_tma
+// leaves undivided: one thread per entry of each component's IBM list (block
+// row = component), in list order.  u* holds R there and N lacks the wall
+// source; mom_ibm finishes both exactly as the predictor's own division does.
+// The division needs a point's list position, which the predictor could find
+// only by two dependent global loads (segment offset, then coefficient) in the
+// warps that hold IBM points; the plane barrier then held every warp of the
+// block to the slowest.  Here the position is the thread index.  With a
+// constant flow rate the blocks of component u add their divided values into
+// flux partials after the predictor's own.
+// ---------------------------------------------------------------------------
+struct IbmDivLists {
+    const int* idx[3];
+    int count[3];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ibm_division(GridP g, MomF<T> F, StageP<T> sp, IbmStage<T> ib,
+                                                       IbmDivLists d, double* __restrict__ flux_part) {
+    __shared__ double shd[8];
+    const int c = blockIdx.y;
+    // the component's arrays by branches, not by a dynamic index into the parameter arrays
+    // (which would copy them to a local frame)
+    auto pick = [c](auto a, auto b, auto e) { return c == 0 ? a : (c == 1 ? b : e); };
+    const int n = pick(d.count[0], d.count[1], d.count[2]);
+    const int* __restrict__ idx = pick(d.idx[0], d.idx[1], d.idx[2]);
+    const Coef4<T>* __restrict__ coef = pick(ib.coef[0], ib.coef[1], ib.coef[2]);
+    const T* __restrict__ u = pick(F.u[0], F.u[1], F.u[2]);
+    T* __restrict__ us = pick(F.us[0], F.us[1], F.us[2]);
+    T* __restrict__ Nn = pick(F.Nn[0], F.Nn[1], F.Nn[2]);
+    T fs = T(0);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int i = idx[p];
+        if (c == 0 && !g.xper && i % g.nx == g.nx - 1) continue;   // the outflow update writes u there
+        const T uP = u[i];
+        const T R = us[i];
+        T N = sp.write_n ? Nn[i] : T(0);
+        T out;
+        mom_ibm(sp, coef[p], uP, R, out, N);
+        us[i] = out;
+        if (sp.write_n) Nn[i] = N;
+        fs += out;
+    }
+    if (sp.flux_sum && c == 0) {   // the same branch in every thread of the block
+        const T ws = warp_sum(fs);
+        if ((threadIdx.x & 31) == 0) shd[threadIdx.x >> 5] = (double)ws;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += shd[q];
+            flux_part[blockIdx.x] = s;
         }
     }
 }
@@ -1259,16 +1326,16 @@ template <typename T>
 void momentum_params(ibm_solver* h, int k, MomF<T>& F, StageP<T>& sp, IbmStage<T>& ib);
 template <typename T>
 ibm_status launch_momentum_kernels(ibm_solver* h, const MomF<T>& F, const StageP<T>& sp, const IbmStage<T>& ib,
-                                   dim3 grd, dim3 blk);
+                                   dim3 grd, dim3 blk, int* nextra = nullptr);
 
 template <typename T>
-ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib, dim3& grd) {
+ibm_status launch_momentum(ibm_solver* h, int k, StageP<T>& sp, IbmStage<T>& ib, dim3& grd, int* nextra) {
     const GridP& g = h->gp;
     MomF<T> F;
     momentum_params<T>(h, k, F, sp, ib);
     dim3 blk(MX, MW, 1);
     grd = momentum_grid(g);
-    return launch_momentum_kernels<T>(h, F, sp, ib, grd, blk);
+    return launch_momentum_kernels<T>(h, F, sp, ib, grd, blk, nextra);
 }
 
 template <typename T>
@@ -1307,9 +1374,11 @@ void momentum_params(ibm_solver* h, int k, MomF<T>& F, StageP<T>& sp, IbmStage<T
     ib = stage_coefs<T>(h, k);
 }
 
+// nextra: flux partials written after the predictor's own (the IBM division's)
 template <typename T>
 ibm_status launch_momentum_kernels(ibm_solver* h, const MomF<T>& F, const StageP<T>& sp, const IbmStage<T>& ib,
-                                   dim3 grd, dim3 blk) {
+                                   dim3 grd, dim3 blk, int* nextra) {
+    if (nextra) *nextra = 0;
     const GridP& g = h->gp;
     if (g.ystr || h->body.kind != 0) {
         const BodyP& bd = h->body;
@@ -1328,6 +1397,27 @@ ibm_status launch_momentum_kernels(ibm_solver* h, const MomF<T>& F, const StageP
         else
             k_momentum_tma<T, false><<<grd, blk, TmaLay<T>::SMEM, h->stream>>>(g, F, sp, ib, h->partials, h->scal,
                                                                                maps);
+        IBM_LAUNCH_CHECK();
+        IbmDivLists d;
+        int most = 0;
+        for (int c = 0; c < 3; ++c) {
+            d.idx[c] = h->idx[c];
+            d.count[c] = c < g.ncomp ? h->counts[c] : 0;
+            most = std::max(most, d.count[c]);
+        }
+        if (most > 0) {
+            const int gx = std::min(IBM_DIV_PARTS, (most + 255) / 256);
+            if ((long long)grd.x * grd.y * grd.z + gx > h->npartials)
+                return ibm_set_error(IBM_E_INVALID, "flux partials buffer too small for the IBM division");
+            cudaEvent_t t;
+            timer_begin(h, "ibm_division", &t);   // (inside the "momentum" interval)
+            k_ibm_division<T><<<dim3(gx, g.ncomp), 256, 0, h->stream>>>(
+                g, F, sp, ib, d, h->partials + (size_t)grd.x * grd.y * grd.z);
+            IBM_LAUNCH_CHECK();
+            timer_end(h, t, "ibm_division");
+            if (nextra && sp.flux_sum) *nextra = gx;
+        }
+        return IBM_OK;
     }
     else if (g.ndim == 3) k_momentum<T, true><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, h->partials);
     else k_momentum<T, false><<<grd, blk, 0, h->stream>>>(g, F, sp, ib, h->partials);
@@ -1403,9 +1493,10 @@ ibm_status momentum_launch(ibm_solver* h, int k, int* nparts) {
     IbmStage<float> ibf;
     IbmStage<double> ibd;
     dim3 grd;
-    ibm_status st = h->prec == IBM_FP64 ? launch_momentum<double>(h, k, spd, ibd, grd)
-                                        : launch_momentum<float>(h, k, spf, ibf, grd);
-    if (nparts) *nparts = (int)(grd.x * grd.y * grd.z);
+    int nextra = 0;
+    ibm_status st = h->prec == IBM_FP64 ? launch_momentum<double>(h, k, spd, ibd, grd, &nextra)
+                                        : launch_momentum<float>(h, k, spf, ibf, grd, &nextra);
+    if (nparts) *nparts = (int)(grd.x * grd.y * grd.z) + nextra;
     return st;
 }
 

@@ -1049,19 +1049,15 @@ struct FftPlan {
 // Shared-memory place of complex value i of a row buffer: one pad slot after every 16,
 // so that the stride-R and stride-NS stores of the early stages spread over the banks
 // (unpadded, the first radix-8 stage's stores hit the same two banks 16 times).
-// PAD = false keeps the plain layout (the flow-rate divergence kernel, whose integer
-// pipe is the busy one: the pads' index arithmetic cost it more than they saved).
-template <bool PAD = true>
-__device__ __forceinline__ int pz(int i) { return PAD ? i + (i >> 4) : i; }
+__device__ __forceinline__ int pz(int i) { return i + (i >> 4); }
 // ... and of real value r of a row buffer viewed as reals
-template <bool PAD = true>
-__device__ __forceinline__ int pzr(int r) { return 2 * pz<PAD>(r >> 1) + (r & 1); }
+__device__ __forceinline__ int pzr(int r) { return 2 * pz(r >> 1) + (r & 1); }
 // complex slots of one row buffer (values 0 .. M + 2 with their pads)
 __host__ __device__ inline int fft_ps(int M) { return M + (M >> 4) + 4; }
 
 // The warp's FFT of length M from src (shared or global) to a shared buffer; returns the
 // buffer holding the result.  tw[t] = exp(-2 pi i t / M).
-template <int SIGN, bool GS, bool PAD, typename C>
+template <int SIGN, bool GS, typename C>
 __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ src, C* b0, C* b1,
                                        const C* __restrict__ tw) {
     const int lane = threadIdx.x & 31;
@@ -1079,7 +1075,7 @@ __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ 
 #pragma unroll
             for (int q = 0; q < 5; ++q)
                 if (q < R) {
-                    C a = (GS && s == 0) ? x[j + q * MR] : x[pz<PAD>(j + q * MR)];
+                    C a = (GS && s == 0) ? x[j + q * MR] : x[pz(j + q * MR)];
                     if (q > 0 && k > 0) {
                         C w = tw[q * k * step];
                         if (SIGN > 0) w = cconj(w);
@@ -1091,7 +1087,7 @@ __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ 
             const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
             for (int q = 0; q < 5; ++q)
-                if (q < R) y[pz<PAD>(base + q * Ns)] = v[q];
+                if (q < R) y[pz(base + q * Ns)] = v[q];
         }
         __syncwarp();
         x = y;
@@ -1103,7 +1099,7 @@ __device__ __forceinline__ C* warp_fft(const FftPlan& pl, const C* __restrict__ 
 
 // The same FFT with the length known at compile time: the stage loop unrolled, the
 // index arithmetic by constants, radix 8 where it divides (then 4, 2, 3, 5).
-template <int SIGN, int M, int R, int NS, bool GS, bool PAD, typename C>
+template <int SIGN, int M, int R, int NS, bool GS, typename C>
 __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict__ y, const C* __restrict__ tw) {
     constexpr int MR = M / R;
     constexpr int STEP = M / (NS * R);
@@ -1114,7 +1110,7 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict
         C v[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            C a = GS ? x[j + q * MR] : x[pz<PAD>(j + q * MR)];
+            C a = GS ? x[j + q * MR] : x[pz(j + q * MR)];
             if (q > 0 && NS > 1) {
                 C w = tw[q * k * STEP];
                 if (SIGN > 0) w = cconj(w);
@@ -1129,46 +1125,46 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ x, C* __restrict
         else dft_small<SIGN>(vv, R);
         const int base = (j / NS) * NS * R + k;
 #pragma unroll
-        for (int q = 0; q < R; ++q) y[pz<PAD>(base + q * NS)] = vv[q];
+        for (int q = 0; q < R; ++q) y[pz(base + q * NS)] = vv[q];
     }
 }
 
-template <int SIGN, int M, int NS, int REM, bool GS, bool PAD>
+template <int SIGN, int M, int NS, int REM, bool GS>
 struct FftRun {
     static constexpr int R = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : (REM % 3 == 0 ? 3 : 5)));
     template <typename C>
     static __device__ __forceinline__ const C* run(const C* x, C* b0, C* b1, const C* tw) {
-        fft_stage<SIGN, M, R, NS, GS, PAD>(x, b0, tw);
+        fft_stage<SIGN, M, R, NS, GS>(x, b0, tw);
         __syncwarp();
-        return FftRun<SIGN, M, NS * R, REM / R, false, PAD>::run(b0, b1, b0, tw);
+        return FftRun<SIGN, M, NS * R, REM / R, false>::run(b0, b1, b0, tw);
     }
 };
-template <int SIGN, int M, int NS, bool GS, bool PAD>
-struct FftRun<SIGN, M, NS, 1, GS, PAD> {
+template <int SIGN, int M, int NS, bool GS>
+struct FftRun<SIGN, M, NS, 1, GS> {
     template <typename C>
     static __device__ __forceinline__ const C* run(const C* x, C*, C*, const C*) { return x; }
 };
 
 // lengths with a compiled form (the workloads' rows: 384, 512 and 1536 reals)
 // GS: src is the row in global memory (unpadded); else a padded shared row buffer.
-template <int SIGN, typename C, bool GS = false, bool PAD = true>
+template <int SIGN, typename C, bool GS = false>
 __device__ __forceinline__ const C* warp_fft_any(const FftPlan& pl, const C* src, C* b0, C* b1, const C* tw) {
     switch (pl.M) {
-        case 192: return FftRun<SIGN, 192, 1, 192, GS, PAD>::run(src, b0, b1, tw);
-        case 256: return FftRun<SIGN, 256, 1, 256, GS, PAD>::run(src, b0, b1, tw);
-        case 768: return FftRun<SIGN, 768, 1, 768, GS, PAD>::run(src, b0, b1, tw);
-        default: return warp_fft<SIGN, GS, PAD, C>(pl, src, b0, b1, tw);
+        case 192: return FftRun<SIGN, 192, 1, 192, GS>::run(src, b0, b1, tw);
+        case 256: return FftRun<SIGN, 256, 1, 256, GS>::run(src, b0, b1, tw);
+        case 768: return FftRun<SIGN, 768, 1, 768, GS>::run(src, b0, b1, tw);
+        default: return warp_fft<SIGN, GS, C>(pl, src, b0, b1, tw);
     }
 }
 
 // The split of the two interleaved real transforms: X_k, k = 0..M, from Z = FFT(z).
-template <typename C, bool PAD = true>
+template <typename C>
 __device__ __forceinline__ void rfft_post(int M, const C* Z, C* __restrict__ o, const C* __restrict__ twN) {
     using T = typename CT<C>::T;
     const int lane = threadIdx.x & 31;
     for (int k = lane; k <= M; k += 32) {
-        const C zk = Z[pz<PAD>(k == M ? 0 : k)];
-        const C zc = cconj(Z[pz<PAD>(k == 0 ? 0 : M - k)]);
+        const C zk = Z[pz(k == M ? 0 : k)];
+        const C zc = cconj(Z[pz(k == 0 ? 0 : M - k)]);
         const C e = C{(zk.x + zc.x) * (T)0.5, (zk.y + zc.y) * (T)0.5};        // (Z_k + conj Z_{M-k}) / 2
         const C d = C{(zk.x - zc.x) * (T)0.5, (zk.y - zc.y) * (T)0.5};
         const C od = C{d.y, -d.x};                                              // d / i
@@ -1234,10 +1230,10 @@ __global__ void __launch_bounds__(256) k_irfft_rows(FftPlan pl, long long rows, 
 // The divergence of one x row by one warp for FP32 fields with nx a multiple of 128: each
 // lane takes 4 consecutive cells of a 128-cell chunk with 16-byte loads, u*(x-1) of its first
 // cell comes from the lane below (or the previous chunk), and the results go to the row
-// buffer as pairs (the real layout, padded or not, or the DCT order of an inflow/outflow x).
+// buffer as pairs (the padded real layout, or the DCT order of an inflow/outflow x).
 // The constant-flow-rate increment of an IBM point finds its coefficient from the number of
 // IBM points before it in its 32-point segment (a prefix over the segment's 8 lanes).
-template <bool THREE, bool FLUX, bool XF, bool PAD>
+template <bool THREE, bool FLUX, bool XF>
 __device__ __forceinline__ void div_row_vec4(const GridP& g, const float* __restrict__ ur, const float* __restrict__ vr,
                                              const float* __restrict__ vmr, const float* __restrict__ wr,
                                              const float* __restrict__ wmr, const uint8_t* __restrict__ mr,
@@ -1304,24 +1300,22 @@ __device__ __forceinline__ void div_row_vec4(const GridP& g, const float* __rest
         if (XF) {
             // DCT order: even x at x / 2, odd x at N - 1 - (x - 1) / 2 (each pair in one complex slot)
             const int re = x0 >> 1, ro = N - 2 - (x0 >> 1);
-            *reinterpret_cast<float2*>(d + pzr<PAD>(re)) = make_float2(dv[0], dv[2]);
-            *reinterpret_cast<float2*>(d + pzr<PAD>(ro)) = make_float2(dv[3], dv[1]);
+            *reinterpret_cast<float2*>(d + pzr(re)) = make_float2(dv[0], dv[2]);
+            *reinterpret_cast<float2*>(d + pzr(ro)) = make_float2(dv[3], dv[1]);
         } else {
-            *reinterpret_cast<float2*>(d + pzr<PAD>(x0)) = make_float2(dv[0], dv[1]);
-            *reinterpret_cast<float2*>(d + pzr<PAD>(x0 + 2)) = make_float2(dv[2], dv[3]);
+            *reinterpret_cast<float2*>(d + pzr(x0)) = make_float2(dv[0], dv[1]);
+            *reinterpret_cast<float2*>(d + pzr(x0 + 2)) = make_float2(dv[2], dv[3]);
         }
     }
 }
 
 template <typename T, typename C, bool THREE, bool FLUX, bool XF>
-__global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restrict__ u, const T* __restrict__ v,
-                                                       const T* __restrict__ w, const uint8_t* __restrict__ mask,
-                                                       FluxCorr<T> fc, T idx, T idy, T idz,
-                                                       const __grid_constant__ FftPlan pl,
-                                                       C* __restrict__ out, const C* __restrict__ tab,
-                                                       T* __restrict__ xout, const T* __restrict__ tw) {
+__device__ __forceinline__ void div_rfft_rows(const GridP& g, const T* __restrict__ u, const T* __restrict__ v,
+                                              const T* __restrict__ w, const uint8_t* __restrict__ mask,
+                                              const FluxCorr<T>& fc, T idx, T idy, T idz, const FftPlan& pl,
+                                              C* __restrict__ out, const C* __restrict__ tab,
+                                              T* __restrict__ xout, const T* __restrict__ tw) {
     extern __shared__ unsigned char fft_smem[];
-    constexpr bool PAD = !FLUX;
     const int M = pl.M;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const long long rows = (long long)g.ny * g.nz;
@@ -1364,7 +1358,7 @@ __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restr
     const uint8_t* __restrict__ mr = mask + rowb;
     if constexpr (sizeof(T) == 4) {
         if ((g.nx & 127) == 0) {
-            div_row_vec4<THREE, FLUX, XF, PAD>(g, ur, vr, vmr, wr, wmr, mr, j > 0, fc, pic, idx, idy, idz, rowseg,
+            div_row_vec4<THREE, FLUX, XF>(g, ur, vr, vmr, wr, wmr, mr, j > 0, fc, pic, idx, idy, idz, rowseg,
                                                carry, reinterpret_cast<float*>(d), N);
             goto transform;
         }
@@ -1408,38 +1402,62 @@ __global__ void __launch_bounds__(256) k_div_rfft_rows(GridP g, const T* __restr
                     T dv = (ucc - ul) * idx;
                     dv += (vc[t] - vm[t]) * idy;
                     if (THREE) dv += (wc[t] - wm[t]) * idz;
-                    d[pzr<PAD>(XF ? ((x & 1) ? N - 1 - (x >> 1) : (x >> 1)) : x)] = dv;
+                    d[pzr(XF ? ((x & 1) ? N - 1 - (x >> 1) : (x >> 1)) : x)] = dv;
                 }
             }
         }
     }
 transform:
     __syncwarp();
-    const C* Z = warp_fft_any<-1, C, false, PAD>(pl, reinterpret_cast<const C*>(d), b0, b1, tab);
+    const C* Z = warp_fft_any<-1, C, false>(pl, reinterpret_cast<const C*>(d), b0, b1, tab);
     if (!XF) {
-        rfft_post<C, PAD>(M, Z, out + row * (M + 1), tab + M);
+        rfft_post<C>(M, Z, out + row * (M + 1), tab + M);
         return;
     }
     // DCT twiddle as in k_dct_rows
     C* V = (Z == b0) ? b1 : b0;
     const C* twN = tab + M;
     for (int kk = lane; kk < M; kk += 32) {
-        const C zk = Z[pz<PAD>(kk)];
-        const C zc = cconj(Z[pz<PAD>(kk == 0 ? 0 : M - kk)]);
+        const C zk = Z[pz(kk)];
+        const C zc = cconj(Z[pz(kk == 0 ? 0 : M - kk)]);
         const C e = C{(zk.x + zc.x) * (T)0.5, (zk.y + zc.y) * (T)0.5};
         const C dd = C{(zk.x - zc.x) * (T)0.5, (zk.y - zc.y) * (T)0.5};
-        V[pz<PAD>(kk)] = cadd(e, cmul(twN[kk], C{dd.y, -dd.x}));
+        V[pz(kk)] = cadd(e, cmul(twN[kk], C{dd.y, -dd.x}));
     }
     const C z0 = Z[0];
     __syncwarp();
     T* xr = xout + row * N;
     for (int kk = lane; kk < N; kk += 32) {
         C vk;
-        if (kk < M) vk = V[pz<PAD>(kk)];
+        if (kk < M) vk = V[pz(kk)];
         else if (kk == M) vk = C{z0.x - z0.y, (T)0};
-        else { vk = V[pz<PAD>(N - kk)]; vk.y = -vk.y; }
+        else { vk = V[pz(N - kk)]; vk.y = -vk.y; }
         xr[kk] = tw[2 * kk] * vk.x + tw[2 * kk + 1] * vk.y;
     }
+}
+
+#define IBM_DIV_RFFT_PARAMS                                                                                      \
+    GridP g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,                          \
+        const uint8_t* __restrict__ mask, FluxCorr<T> fc, T idx, T idy, T idz, const __grid_constant__ FftPlan pl, \
+        C* __restrict__ out, const C* __restrict__ tab, T* __restrict__ xout, const T* __restrict__ tw
+template <typename T, typename C, bool THREE, bool FLUX, bool XF>
+__global__ void __launch_bounds__(256) k_div_rfft_rows(IBM_DIV_RFFT_PARAMS) {
+    div_rfft_rows<T, C, THREE, FLUX, XF>(g, u, v, w, mask, fc, idx, idy, idz, pl, out, tab, xout, tw);
+}
+// The FP32 constant-flow-rate instance held to 64 registers, four blocks of eight warps per SM: it is
+// latency-bound, and the extra warps outweigh a few spilled bytes (0.126 -> 0.108 ms on 384x256x256).
+template <typename T, typename C, bool THREE, bool FLUX, bool XF>
+__global__ void __launch_bounds__(256, 4) k_div_rfft_rows_flux(IBM_DIV_RFFT_PARAMS) {
+    div_rfft_rows<T, C, THREE, FLUX, XF>(g, u, v, w, mask, fc, idx, idy, idz, pl, out, tab, xout, tw);
+}
+#undef IBM_DIV_RFFT_PARAMS
+
+template <typename T, typename C, bool THREE, bool FLUX, bool XF, typename... A>
+void launch_div_rfft_rows(int nb, int nt, size_t smem, cudaStream_t st, A... a) {
+    if constexpr (FLUX && sizeof(T) == 4)
+        k_div_rfft_rows_flux<T, C, THREE, FLUX, XF><<<nb, nt, smem, st>>>(a...);
+    else
+        k_div_rfft_rows<T, C, THREE, FLUX, XF><<<nb, nt, smem, st>>>(a...);
 }
 
 // The type-II DCT of whole x rows in one pass (inflow/outflow x): the row is read, placed in
@@ -2148,9 +2166,9 @@ ibm_status divergence_and_solve(ibm_solver* h, T* const us[3], bool flux, const 
         const C* tab = (const C*)h->fftab;
         T* xo = (T*)h->rhs;
         const T* twd = (const T*)h->twid;
-#define IBM_DIVFFT(THREE_, FLUX_, XF_)                                                                            \
-    k_div_rfft_rows<T, C, THREE_, FLUX_, XF_><<<nb, 32 * rpb, smem, h->stream>>>(g, us[0], us[1], w, h->mask, fc, ix, iy, \
-                                                                                  iz, pl, out, tab, xo, twd)
+#define IBM_DIVFFT(THREE_, FLUX_, XF_)                                                                          \
+    launch_div_rfft_rows<T, C, THREE_, FLUX_, XF_>(nb, 32 * rpb, smem, h->stream, g, us[0], us[1], w, h->mask, fc, \
+                                                     ix, iy, iz, pl, out, tab, xo, twd)
         if (!g.xper) {   // inflow/outflow x (no constant flow rate)
             if (g.ndim == 3) IBM_DIVFFT(true, false, true);
             else IBM_DIVFFT(false, false, true);
