@@ -7,7 +7,7 @@ inputs.configs.airway_c4).  A "step" is one full RK3 time step: three
 substages, each a momentum predictor with the implicit IBM division followed
 by the projection.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c4|c3|c3s|c3_fp64|c1|c2|c2_fp64|c2_periodic] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c4|c4s|c3|c3s|c3_fp64|c1|c2|c2_fp64|c2_periodic] [--impl reference]
 
 One JSON line on stdout (rank 0).  `value` is cells x steps / time over all
 ranks (replicas: every rank advances its own copy of the workload, no
@@ -104,6 +104,8 @@ def workload(name: str):
         return cylinder_c2(re=100.0, precision="fp32")
     if name == "c4":         # tube-union airway, inflow / convective outflow, weights built on the device
         return airway_c4(precision="fp32")
+    if name == "c4s":        # profiling size: the airway layout on 512x384x64 (dz = 4 dx), 12.6M cells
+        return airway_c4(precision="fp32", n=(512, 384, 64))
     raise SystemExit(f"unknown workload {name}")
 
 

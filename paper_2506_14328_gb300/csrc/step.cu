@@ -1427,12 +1427,15 @@ transform:
     const C z0 = Z[0];
     __syncwarp();
     T* xr = xout + row * N;
+    const C* tw2 = reinterpret_cast<const C*>(tw);        // (cos, sin) pairs, one load each
+#pragma unroll 4
     for (int kk = lane; kk < N; kk += 32) {
+        const C t = tw2[kk];
         C vk;
         if (kk < M) vk = V[pz(kk)];
         else if (kk == M) vk = C{z0.x - z0.y, (T)0};
         else { vk = V[pz(N - kk)]; vk.y = -vk.y; }
-        xr[kk] = tw[2 * kk] * vk.x + tw[2 * kk + 1] * vk.y;
+        xr[kk] = t.x * vk.x + t.y * vk.y;
     }
 }
 
@@ -1493,12 +1496,15 @@ __global__ void __launch_bounds__(256) k_dct_rows(FftPlan pl, long long rows, T*
     }
     const C z0 = Z[0];                                    // V_M = Re Z_0 - Im Z_0 (real)
     __syncwarp();
+    const C* tw2 = reinterpret_cast<const C*>(tw);        // (cos, sin) pairs, one load each
+#pragma unroll 4
     for (int k = lane; k < N; k += 32) {
+        const C t = tw2[k];
         C vk;
         if (k < M) vk = V[pz(k)];
         else if (k == M) vk = C{z0.x - z0.y, (T)0};
         else { vk = V[pz(N - k)]; vk.y = -vk.y; }
-        xr[k] = tw[2 * k] * vk.x + tw[2 * k + 1] * vk.y;
+        xr[k] = t.x * vk.x + t.y * vk.y;
     }
 }
 
@@ -1516,10 +1522,13 @@ __global__ void __launch_bounds__(256) k_idct_rows(FftPlan pl, long long rows, T
     C* b2 = b1 + fft_ps(M);                               // V_0..V_M
     if (row >= rows) return;
     T* xr = x + row * N;
+    const C* tw2 = reinterpret_cast<const C*>(tw);        // (cos, sin) pairs, one load each
+#pragma unroll 4
     for (int k = lane; k <= M; k += 32) {
         const T a = xr[k];
         const T b = k == 0 ? T(0) : xr[N - k];
-        const T c = tw[2 * k], sn = tw[2 * k + 1];
+        const C t = tw2[k];
+        const T c = t.x, sn = t.y;
         b2[pz(k)] = C{c * a + sn * b, sn * a - c * b};
     }
     __syncwarp();
