@@ -490,6 +490,15 @@ ibm_status ibm_setup_geometry(const ibm_grid_desc* grid, const ibm_geom_desc* ge
         }
         h->gp.yt = h->ytab;
     }
+    if (h->prec == IBM_FP32) {   // the tridiagonal solve's FP64 systems run on a second stream
+        cudaError_t e = cudaStreamCreateWithFlags(&h->tri_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->tri_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->tri_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            ibm_destroy(h);
+            return ibm_set_error(IBM_E_CUDA, std::string("tridiagonal stream: ") + cudaGetErrorString(e));
+        }
+    }
     momentum_prepare(h);
     h->gp.kzm = momentum_default_kzm(h->gp, h->prec, momentum_uses_tma(h));
     bool plan_ok = true;
@@ -1125,6 +1134,9 @@ void ibm_destroy(ibm_solver* h) {
     for (cudaStream_t s : h->copy_streams)
         if (s) cudaStreamDestroy(s);
     if (h->copy_fork) cudaEventDestroy(h->copy_fork);
+    if (h->tri_stream) cudaStreamDestroy(h->tri_stream);
+    if (h->tri_fork) cudaEventDestroy(h->tri_fork);
+    if (h->tri_join) cudaEventDestroy(h->tri_join);
     if (h->plans) {
         cufftDestroy(h->plan_f);
         cufftDestroy(h->plan_i);

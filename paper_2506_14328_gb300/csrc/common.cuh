@@ -351,6 +351,8 @@ struct ibm_solver {
     // state import / export: the field copies go out on their own streams (several copy
     // engines), ordered after the solver's stream by an event; created on first use
     cudaStream_t copy_streams[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t tri_stream = nullptr;             // the FP64 tridiagonal systems beside the FP32 ones
+    cudaEvent_t tri_fork = nullptr, tri_join = nullptr;
     cudaEvent_t copy_fork = nullptr;
     GridP gp;
     GeomP geo;
