@@ -264,7 +264,8 @@ __device__ __forceinline__ void mom_ibm_fix(const IbmStage<T>& ib, const StageP<
 }
 
 // DEFER: an IBM point keeps R (its update before the division) in u* and N without the wall
-// source; k_ibm_division finishes it, and the flow-rate sum leaves it out.
+// source; k_ibm_division finishes u* (and, for the explicit IBM, N), and the flow-rate sum
+// leaves the point out.
 template <typename T, int NC, bool DEFER = false>
 __device__ __forceinline__ void mom_write(const MomF<T>& F, const StageP<T>& sp, int ida, int idb, bool liveA,
                                           bool liveB, uint32_t mA, uint32_t mB, T (&oA)[3], T (&oB)[3], T (&NA)[3],
@@ -1195,7 +1196,7 @@ __global__ void __launch_bounds__(MX * MW, sizeof(T) == 4 ? 3 : 1)
 // The implicit IBM division (Eq. rk3-rai) of the points that k_momentum_tma
 // leaves undivided: one thread per entry of each component's IBM list (block
 // row = component), in list order.  u* holds R there and N lacks the wall
-// source; mom_ibm finishes both exactly as the predictor's own division does.
+// source; mom_ibm finishes u* with the predictor's own division arithmetic.
 // The division needs a point's list position, which the predictor could find
 // only by two dependent global loads (segment offset, then coefficient) in the
 // warps that hold IBM points; the plane barrier then held every warp of the
@@ -1208,7 +1209,10 @@ struct IbmDivLists {
     int count[3];
 };
 
-template <typename T>
+// NUPD: the explicit IBM (pad = lambda) adds s - pad u to N here.  Otherwise N stays without the
+// wall source s (the same at every stage), and the next stage, whose R then lacks dt b s, adds it
+// back here: the division touches u and u* only (two scattered sectors a point instead of three).
+template <typename T, bool NUPD>
 __global__ void __launch_bounds__(256) k_ibm_division(GridP g, MomF<T> F, StageP<T> sp, IbmStage<T> ib,
                                                        IbmDivLists d, double* __restrict__ flux_part) {
     __shared__ double shd[8];
@@ -1227,12 +1231,14 @@ __global__ void __launch_bounds__(256) k_ibm_division(GridP g, MomF<T> F, StageP
         const int i = idx[p];
         if (c == 0 && !g.xper && i % g.nx == g.nx - 1) continue;   // the outflow update writes u there
         const T uP = u[i];
-        const T R = us[i];
-        T N = sp.write_n ? Nn[i] : T(0);
+        const Coef4<T> q = coef[p];
+        T R = us[i];
+        if (!NUPD && sp.read_prev) R += sp.dtb * q.s;
+        T N = (NUPD && sp.write_n) ? Nn[i] : T(0);
         T out;
-        mom_ibm(sp, coef[p], uP, R, out, N);
+        mom_ibm(sp, q, uP, R, out, N);
         us[i] = out;
-        if (sp.write_n) Nn[i] = N;
+        if (NUPD && sp.write_n) Nn[i] = N;
         fs += out;
     }
     if (sp.flux_sum && c == 0) {   // the same branch in every thread of the block
@@ -1411,8 +1417,12 @@ ibm_status launch_momentum_kernels(ibm_solver* h, const MomF<T>& F, const StageP
                 return ibm_set_error(IBM_E_INVALID, "flux partials buffer too small for the IBM division");
             cudaEvent_t t;
             timer_begin(h, "ibm_division", &t);   // (inside the "momentum" interval)
-            k_ibm_division<T><<<dim3(gx, g.ncomp), 256, 0, h->stream>>>(
-                g, F, sp, ib, d, h->partials + (size_t)grd.x * grd.y * grd.z);
+            if (h->phys.bmode == IBM_B_EXPLICIT)
+                k_ibm_division<T, true><<<dim3(gx, g.ncomp), 256, 0, h->stream>>>(
+                    g, F, sp, ib, d, h->partials + (size_t)grd.x * grd.y * grd.z);
+            else
+                k_ibm_division<T, false><<<dim3(gx, g.ncomp), 256, 0, h->stream>>>(
+                    g, F, sp, ib, d, h->partials + (size_t)grd.x * grd.y * grd.z);
             IBM_LAUNCH_CHECK();
             timer_end(h, t, "ibm_division");
             if (nextra && sp.flux_sum) *nextra = gx;
