@@ -31,6 +31,10 @@
  *     allocates or frees device memory except inside cuFFT plans (twiddle
  *     tables); cuFFT's work area comes from the caller's workspace.
  *   - Streams: all device work is enqueued on the stream given at setup.
+ *     An IBM_FP32 handle also owns one internal stream (created at setup,
+ *     destroyed by ibm_destroy): the tridiagonal solve forks its FP64 systems
+ *     onto it and joins back with events recorded on the setup stream, so the
+ *     work stays ordered on that stream and a captured step holds both.
  *     Calls are asynchronous except where stated ("blocking").
  *   - Errors: every call returns an ibm_status; nothing throws across the
  *     ABI.  ibm_last_error() gives a thread-local message.  After a CUDA

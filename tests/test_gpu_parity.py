@@ -154,6 +154,26 @@ def test_full_steps_match_oracle(name):
         assert _rel_p(o, pg, o.p) < 1e-11, s
 
 
+@pytest.mark.parametrize("inflow", [False, True])
+def test_tma_form_without_ibm_points_matches_oracle(inflow):
+    """A box with no body in the TMA form of the predictor (48 x 30 x 26, nx a multiple of 16): no
+    IBM points, so no IBM division follows the predictor; periodic and inflow/outflow x, full steps
+    against the oracle to 1e-12."""
+    from inputs import GEOM_NONE
+    case = small_case("sphere3d_io" if inflow else "sphere3d").with_(geom_kind=GEOM_NONE, geom_params=())
+    g, o = _pair(case)
+    assert g.tiles()[2]                       # the TMA form
+    assert all(len(x) == 0 for x in g.classification()[1])
+    for s in range(case.steps):
+        g.step(1)
+        o.step(1)
+        ug, pg = g.state()
+        for c in range(3):
+            assert _rel(o, ug[c], o.u[c], c) < TOL64, (s, c)
+        assert _rel_p(o, pg, o.p) < 1e-11, s
+    g.close()
+
+
 def test_project_matches_oracle():
     case = small_case("sphere3d")
     g, o = _pair(case)
