@@ -68,7 +68,8 @@ def tube_union(seed: int, L=(1.0, 0.75, 0.5), ntubes=(6, 12), radius=(0.05, 0.2)
     Tube 0 is the trunk: it enters through the x = 0 face and leaves through the
     x = L_x face along a Catmull-Rom spline through 5 seeded control points.  Every
     other tube branches off a seeded interior point of an earlier tube, no wider
-    than its parent there, and ends inside the box after 3 seeded steps of
+    than its parent there (or than the smallest radius, where the parent is
+    narrower), and ends inside the box after 3 seeded steps of
     0.15-0.3 box units.  Each radius is r0 (1 + 0.1 sin(k s + ph)) along the tube,
     s in [0, 1] the sample position and k, ph seeded (the wall bumps).  Every point
     keeps its tube clear of the y and z faces by `margin`, and branches keep clear of
